@@ -1,0 +1,151 @@
+"""Seeded synthetic inputs for the advection-diffusion-reaction workloads.
+
+This module only samples coefficient fields and initial data on the grid; it holds
+none of the method's arithmetic (no stencil, no matrix function, no time stepping).
+It is the one module that both the CUDA path's callers and the FP64 oracle's
+callers use, so that both sides see bit-identical inputs.
+
+Grid convention (Section 5.2 of the paper: second-order centred finite differences on
+a tensor grid): the unit box (0,1)^d holds n_mu interior nodes per direction,
+x_i = i*h_mu with h_mu = 1/(n_mu+1), i = 1..n_mu, and homogeneous Dirichlet values
+on the boundary. Arrays are C-ordered with x1 varying fastest: a 3-D state has
+numpy shape (n3, n2, n1); the nodal coefficient a(x) includes the boundary ring and
+has shape (n3+2, n2+2, n1+2).
+
+Workload recipes (stated once, used by tests and bench.py):
+  * a(x) = 1 + c * prod_mu sin(2*pi*k*x_mu)       (c = 0.5, k = 1 unless batched)
+  * b constant, reaction r(u) = u^2 (1 - u)        (coefficients r0..r3 = 0, 0, 1, -1)
+  * 2-D u0 = 16 x(1-x) y(1-y) + 1e-3 N(0,1)
+  * 3-D u0 = (27/4)^3 x1 x2 x3 (1-x1)^2 (1-x2)^2 (1-x3)^2 + 1e-3 N(0,1)
+    (the smooth datum of the paper's three-dimensional experiment, Section 5.2)
+  * noise from numpy.random.default_rng(seed) on interior nodes only.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import numpy as np
+
+REACTION_U2_1MU = (0.0, 0.0, 1.0, -1.0)  # r(u) = u^2 - u^3
+
+
+@dataclass
+class Workload:
+    """One ADR instance: grid, coefficients, initial state and time grid."""
+    name: str
+    dims: tuple            # interior points per direction, x1 first: (n1, n2[, n3])
+    a_nodes: np.ndarray    # nodal diffusion coefficient incl. boundary ring, C-order
+    b: tuple               # constant advection velocity (b1, b2, b3); unused entries 0
+    r_poly: tuple          # reaction r(u) = r0 + r1 u + r2 u^2 + r3 u^3
+    u0: np.ndarray         # initial state on interior nodes, C-order, x1 fastest
+    tau: float             # time step
+    m: int                 # number of steps
+    scheme: str            # "lawson_euler" | "etd2rk" | "lawson4"
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def dim(self) -> int:
+        return len(self.dims)
+
+    @property
+    def dof(self) -> int:
+        return int(np.prod(self.dims))
+
+
+def axis_nodes(n: int, with_boundary: bool) -> np.ndarray:
+    """Node coordinates along one direction of the unit interval."""
+    h = 1.0 / (n + 1)
+    if with_boundary:
+        return np.arange(0, n + 2, dtype=np.float64) * h
+    return np.arange(1, n + 1, dtype=np.float64) * h
+
+
+def mesh(dims, with_boundary):
+    axes = [axis_nodes(n, with_boundary) for n in dims]      # x1, x2, ...
+    # numpy index order is (x_d, ..., x_1) so that x1 is the fastest index
+    grids = np.meshgrid(*axes[::-1], indexing="ij")
+    return grids[::-1]                                        # return x1, x2, ...
+
+
+def sine_product_coefficient(dims, c=0.5, k=1) -> np.ndarray:
+    """a(x) = 1 + c prod_mu sin(2 pi k x_mu) sampled on all nodes incl. the boundary."""
+    xs = mesh(dims, True)
+    prod = np.ones_like(xs[0])
+    for x in xs:
+        prod = prod * np.sin(2.0 * np.pi * k * x)
+    return 1.0 + c * prod
+
+
+def smooth_initial_state(dims, noise=1e-3, seed=0, rng=None) -> np.ndarray:
+    """Smooth datum vanishing on the boundary plus seeded Gaussian noise."""
+    xs = mesh(dims, False)
+    if len(dims) == 2:
+        x, y = xs
+        u = 16.0 * x * (1.0 - x) * y * (1.0 - y)
+    else:
+        u = np.full_like(xs[0], (27.0 / 4.0) ** 3)
+        for x in xs:
+            u = u * x * (1.0 - x) ** 2
+    if noise:
+        rng = np.random.default_rng(seed) if rng is None else rng
+        u = u + noise * rng.standard_normal(u.shape)
+    return np.ascontiguousarray(u)
+
+
+def single_grid(name, dims, b, scheme, T, m, c=0.5, k=1, noise=1e-3, seed=0) -> Workload:
+    dims = tuple(int(n) for n in dims)
+    bb = tuple(float(v) for v in b) + (0.0,) * (3 - len(b))
+    return Workload(name=name, dims=dims, a_nodes=sine_product_coefficient(dims, c, k),
+                    b=bb, r_poly=REACTION_U2_1MU,
+                    u0=smooth_initial_state(dims, noise=noise, seed=seed),
+                    tau=T / m, m=int(m), scheme=scheme)
+
+
+# --- the five workload recipes ------------------------------------------------------
+
+def config1(scheme="etd2rk", n=32):
+    """2-D 32x32, b=(10,10), 20 steps to T=0.1, FP64."""
+    return single_grid(f"2d_{n}_{scheme}", (n, n), (10.0, 10.0), scheme, 0.1, 20)
+
+
+def config2(n=128, m=50, scheme="etd2rk"):
+    """3-D 128^3, b=(10,10,10), ETD2RK, 50 steps to T=0.1, FP64."""
+    return single_grid(f"3d_{n}_{scheme}", (n, n, n), (10.0, 10.0, 10.0), scheme, 0.1 * m / 50, m)
+
+
+def config3(n=256, m=40, scheme="lawson4"):
+    """3-D 256^3, Lawson4, 40 steps to T=0.1 (tau = 2.5e-3), mixed precision."""
+    return single_grid(f"3d_{n}_{scheme}", (n, n, n), (10.0, 10.0, 10.0), scheme, 0.1 * m / 40, m)
+
+
+def config5(n=384, m=200, scheme="lawson4"):
+    """3-D 384^3, b=(50,50,50), 200 steps to T=1.0."""
+    return single_grid(f"3d_{n}_{scheme}_b50", (n, n, n), (50.0, 50.0, 50.0), scheme, 1.0 * m / 200, m)
+
+
+BATCH_SIZES = (48, 64, 96, 128, 192, 256)
+
+
+def config4_draws(count=512, seed=2303):
+    """Per-instance draws of the batched 2-D workload, in a fixed order:
+    n_i from BATCH_SIZES, c_i ~ U[0.1, 0.9], k_i in {1,2,3}, b_i ~ U[0,20]^2."""
+    rng = np.random.default_rng(seed)
+    n = rng.choice(np.array(BATCH_SIZES), size=count)
+    c = rng.uniform(0.1, 0.9, size=count)
+    k = rng.integers(1, 4, size=count)
+    b = rng.uniform(0.0, 20.0, size=(count, 2))
+    return [dict(n=int(n[i]), c=float(c[i]), k=int(k[i]), b=(float(b[i, 0]), float(b[i, 1])))
+            for i in range(count)]
+
+
+def config4(count=512, m=30, T=0.1, seed=2303):
+    """Batched 2-D: independent instances of uneven size, ETD2RK, FP32 state."""
+    out = []
+    for i, d in enumerate(config4_draws(count, seed)):
+        dims = (d["n"], d["n"])
+        out.append(Workload(
+            name=f"batch{i}_{d['n']}", dims=dims,
+            a_nodes=sine_product_coefficient(dims, d["c"], d["k"]),
+            b=(d["b"][0], d["b"][1], 0.0), r_poly=REACTION_U2_1MU,
+            u0=smooth_initial_state(dims, noise=1e-3, rng=np.random.default_rng((seed, i))),
+            tau=T / m, m=m, scheme="etd2rk", extra=d))
+    return out
