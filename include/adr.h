@@ -1,0 +1,145 @@
+/*
+ * adr.h -- C ABI of libadr: exponential Runge--Kutta and Lawson time stepping for
+ * semilinear advection-diffusion-reaction equations with an extracted constant-
+ * coefficient operator, on one GB300 GPU.
+ *
+ * The problem (Eq. (adr), Section 3 of Caliari, Cassini, Einkemmer, Ostermann,
+ * "Accelerating exponential integrators to efficiently solve semilinear
+ * advection-diffusion-reaction equations"):
+ *
+ *     u_t = div(a(x) grad u) + b . grad u + r(u)   on (0,1)^d, d in {2,3},
+ *
+ * homogeneous Dirichlet boundary, second-order centred finite differences on n_mu
+ * interior nodes per direction (x_i = i h_mu, h_mu = 1/(n_mu+1)), rewritten as
+ * u' = A u + g(u) with (Eqs. (linop), (nonlin), (amaxbeta))
+ *
+ *     A = lambda a_max sum_mu d_mumu + beta . grad,     a_max = max a,
+ *     beta_mu = |Omega|^-1 int (b_mu + d_mu a) dx,      g = F(u) - A u.
+ *
+ * The discrete A is the Kronecker sum A_3 (+) A_2 (+) A_1 of tridiagonal 1-D
+ * factors (Section 5.2); e^{c tau A} is applied by mu-mode products with the dense
+ * factors e^{c tau A_mu} (Section 1), phi_k(tau A) by mu-mode products with the
+ * eigenvector matrices V_mu^-1, a pointwise phi_k(tau(l1+l2+l3)) scaling, and V_mu.
+ *
+ * Conventions for every entry point
+ *   - Arrays are C-ordered with x1 varying fastest: a 3-D state is n3*n2*n1
+ *     elements, element (i1,i2,i3) at i1 + n1*(i2 + n2*i3); interior nodes only.
+ *   - State arrays live on the device of the context, are owned by the caller, and
+ *     hold double (ADR_FP64) or float (all other precisions).
+ *   - Calls are ordered on the stream given to adr_create and return after
+ *     enqueueing, except where stated. The library owns its factors and workspace
+ *     and frees them in adr_destroy.
+ *   - Errors: every call returns an adr_status; arguments are validated on the host
+ *     before any launch; the message of the last failure is kept per context
+ *     (adr_last_error). Nothing throws across the ABI.
+ */
+#ifndef ADR_H
+#define ADR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct adr_ctx adr_ctx; /* opaque, library-owned */
+
+typedef enum {
+    ADR_OK = 0,
+    ADR_ERR_ARG = 1,              /* invalid argument (sizes, pointers, enums)          */
+    ADR_ERR_ALLOC = 2,            /* device or host allocation failed                   */
+    ADR_ERR_CUDA = 3,             /* a CUDA runtime call failed                         */
+    ADR_ERR_ILL_CONDITIONED = 4,  /* prod_mu kappa(V_mu) * eps exceeds kappa_tol        */
+    ADR_ERR_COMPLEX_SPECTRUM = 5, /* s*p <= 0 (cell Peclet >= 1): no real eigenbasis     */
+    ADR_ERR_TIMEOUT = 6,          /* a bounded device wait gave up                      */
+    ADR_ERR_STATE = 7,            /* call out of order (e.g. step before set_coeffs)    */
+    ADR_ERR_UNSUPPORTED = 8       /* valid request this build does not implement        */
+} adr_status;
+
+typedef enum {
+    ADR_FP64 = 0,          /* FP64 state, stencil and contractions (FP64 FMA)            */
+    ADR_FP32 = 1,          /* FP32 state, stencil and contractions (FP32 FMA)            */
+    ADR_MIXED_TF32X3 = 2,  /* reserved: not implemented (returns ADR_ERR_UNSUPPORTED)    */
+    ADR_MIXED_BF16X3 = 3   /* FP32 state and stencil; mu-mode contractions on the tensor
+                              cores from three BF16 slices per operand (six products) with
+                              exact FP32 accumulation; factors and phi near 0 in FP64    */
+} adr_precision;
+
+typedef enum {
+    ADR_LAWSON_EULER = 0,  /* u+ = e^{tau A}(u + tau g(u))                 (Appendix)     */
+    ADR_ETD2RK = 1,        /* exponential RK2 with phi_2, c2 = 1           (Appendix)     */
+    ADR_LAWSON4 = 2        /* Lawson's construction on classical RK4 (Section 1)          */
+} adr_scheme;
+
+typedef struct {
+    int dim;               /* 2 or 3                                                     */
+    int n[3];              /* interior points per direction, x1 first; n[2] unused if 2-D */
+    double lambda;         /* lambda of Eq. (linop); <= 0 selects 1                     */
+    double abar_override;  /* > 0: use this value as lambda*a_max instead of the nodal max */
+    double tau;            /* time step (> 0)                                            */
+    int scheme;            /* adr_scheme                                                 */
+    int precision;         /* adr_precision                                              */
+    double kappa_tol;      /* eigen route guard: fail with ADR_ERR_ILL_CONDITIONED when
+                              prod_mu kappa(V_mu) * unit roundoff > kappa_tol; <= 0 selects
+                              1e-2. Only schemes that need phi_k (ADR_ETD2RK) check it.  */
+} adr_params;
+
+/* Create a context for one grid. cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream) on the current device. Validates params, allocates the device workspace.
+ * The factors are built by adr_set_coeffs. On failure *out is NULL. */
+adr_status adr_create(const adr_params* p, void* cuda_stream, adr_ctx** out);
+
+/* Set the coefficients of Eq. (adr) (instance must be 0).
+ *   a_nodes: host, (n3+2)*(n2+2)*(n1+2) doubles (2-D: (n2+2)*(n1+2)), the diffusion
+ *            coefficient at every node including the boundary ring, x1 fastest.
+ *   b:       host, 3 doubles, constant velocity (b3 ignored in 2-D).
+ *   r_poly:  host, 4 doubles, reaction r(u) = r0 + r1 u + r2 u^2 + r3 u^3.
+ * Computes a_max, beta (Eq. (amaxbeta)) and, on the host in FP64, the factors
+ * e^{c tau A_mu} (Pade-13 scaling and squaring) and the closed-form eigenpairs of
+ * A_mu; uploads them. Synchronous with respect to the host data (it may be freed on
+ * return). Returns ADR_ERR_COMPLEX_SPECTRUM / ADR_ERR_ILL_CONDITIONED for ADR_ETD2RK
+ * when the eigen route is unavailable or fails the kappa guard. */
+adr_status adr_set_coeffs(adr_ctx* ctx, int instance, const double* a_nodes,
+                          const double b[3], const double r_poly[4]);
+
+/* One time step of the context's scheme, in place on the device state u_dev.
+ * t is the time of the step's start (the reaction is autonomous; t is recorded only). */
+adr_status adr_step(adr_ctx* ctx, void* u_dev, double t);
+
+/* m steps from t0 with step tau (T must equal t0 + m*tau up to 1e-9 relative, or be
+ * <= 0 to skip the check). The step is captured once into a CUDA graph per state
+ * pointer and replayed m times on the context stream. Asynchronous. */
+adr_status adr_integrate(adr_ctx* ctx, void* u_dev, double t0, double T, int m);
+
+/* End-to-end variant of adr_integrate on a HOST state: copies u_host (pinned or
+ * pageable, dtype of the precision) to a library-owned device buffer, integrates m
+ * steps, copies the result back into u_host and synchronises the stream. */
+adr_status adr_integrate_host(adr_ctx* ctx, void* u_host, double t0, double T, int m);
+
+/* Building blocks of a step, exposed for verification. Inputs and outputs are
+ * device arrays of the state's dtype and size; none may alias another.
+ *   adr_eval_rhs:  F_out = F(u) (may be NULL), g_out = F(u) - A u (may be NULL).
+ *   adr_apply_exp: y = e^{c tau A} v for c in {0.5, 1}.
+ *   adr_apply_phi: y = phi_k(tau A) v for k in {0, 1, 2} through the eigenbasis. */
+adr_status adr_eval_rhs(adr_ctx* ctx, const void* u_dev, void* F_out, void* g_out);
+adr_status adr_apply_exp(adr_ctx* ctx, double c, const void* v_dev, void* y_dev);
+adr_status adr_apply_phi(adr_ctx* ctx, int k, const void* v_dev, void* y_dev);
+
+/* Host-side facts of the current operator: kappa(V_mu) per direction (0 when the
+ * spectrum is complex), lambda*a_max, and beta. Any pointer may be NULL. */
+adr_status adr_get_info(const adr_ctx* ctx, double kappa[3], double* abar, double beta[3]);
+
+/* Number of kernels one adr_step launches (for launch accounting). */
+int adr_kernels_per_step(const adr_ctx* ctx);
+
+/* Message of the last failed call on ctx (or of the last failed adr_create when ctx
+ * is NULL). Valid until the next call on the same context. */
+const char* adr_last_error(const adr_ctx* ctx);
+
+/* Free the context and all library-owned device memory (synchronises its stream). */
+void adr_destroy(adr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADR_H */

@@ -1,0 +1,234 @@
+"""Thin ctypes binding of libadr (include/adr.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls. Device arrays are torch
+tensors (their data pointers are passed), host coefficient arrays are numpy arrays,
+streams are torch.cuda.Stream objects (their cudaStream_t is passed). All compute
+runs in libadr's CUDA kernels; there is no fallback: loading fails loudly when the
+library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libadr.so")
+
+ADR_OK = 0
+STATUS = {0: "ADR_OK", 1: "ADR_ERR_ARG", 2: "ADR_ERR_ALLOC", 3: "ADR_ERR_CUDA",
+          4: "ADR_ERR_ILL_CONDITIONED", 5: "ADR_ERR_COMPLEX_SPECTRUM", 6: "ADR_ERR_TIMEOUT",
+          7: "ADR_ERR_STATE", 8: "ADR_ERR_UNSUPPORTED"}
+PRECISION = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x3": 3}
+SCHEME = {"lawson_euler": 0, "etd2rk": 1, "lawson4": 2}
+
+
+class AdrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class adr_params(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("lambda_", C.c_double),
+                ("abar_override", C.c_double), ("tau", C.c_double), ("scheme", C.c_int),
+                ("precision", C.c_int), ("kappa_tol", C.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libadr.so (built by build_lib.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libadr.so not found at {path}: run paper_2303_15861_gb300.build_lib.build() "
+                           "(the CUDA library is required; there is no CPU fallback)")
+    lib = C.CDLL(path)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+    sig = {
+        "adr_create": (ip, [C.POINTER(adr_params), vp, C.POINTER(vp)]),
+        "adr_set_coeffs": (ip, [vp, ip, dp, dp, dp]),
+        "adr_step": (ip, [vp, vp, C.c_double]),
+        "adr_integrate": (ip, [vp, vp, C.c_double, C.c_double, ip]),
+        "adr_integrate_host": (ip, [vp, vp, C.c_double, C.c_double, ip]),
+        "adr_eval_rhs": (ip, [vp, vp, vp, vp]),
+        "adr_apply_exp": (ip, [vp, C.c_double, vp, vp]),
+        "adr_apply_phi": (ip, [vp, ip, vp, vp]),
+        "adr_get_info": (ip, [vp, dp, dp, dp]),
+        "adr_kernels_per_step": (ip, [vp]),
+        "adr_last_error": (C.c_char_p, [vp]),
+        "adr_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status, ctx=None):
+    if status != ADR_OK:
+        msg = _lib.adr_last_error(ctx).decode()
+        raise AdrError(status, msg)
+
+
+def _ptr(t):
+    """Data pointer of a device tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device arrays must be contiguous CUDA tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def _dbl(a, count=None):
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if count is not None and arr.size != count:
+        raise ValueError(f"expected {count} values, got {arr.size}")
+    return arr, arr.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(int(stream.cuda_stream))
+
+
+# ------------------------------------------------------------------- C entry points
+def adr_create(dims, tau, scheme="lawson4", precision="fp64", lam=1.0, abar_override=0.0,
+               kappa_tol=0.0, stream=None):
+    lib = load_library()
+    p = adr_params()
+    p.dim = len(dims)
+    for i, n in enumerate(dims):
+        p.n[i] = int(n)
+    p.lambda_ = float(lam)
+    p.abar_override = float(abar_override)
+    p.tau = float(tau)
+    p.scheme = SCHEME[scheme] if isinstance(scheme, str) else int(scheme)
+    p.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    p.kappa_tol = float(kappa_tol)
+    ctx = C.c_void_p()
+    _check(lib.adr_create(C.byref(p), _stream_handle(stream), C.byref(ctx)))
+    return ctx
+
+
+def adr_set_coeffs(ctx, instance, a_nodes, b, r_poly):
+    a, ap = _dbl(a_nodes)
+    bb, bp = _dbl(list(b) + [0.0] * (3 - len(b)), 3)
+    rr, rp = _dbl(r_poly, 4)
+    _check(_lib.adr_set_coeffs(ctx, int(instance), ap, bp, rp), ctx)
+
+
+def adr_step(ctx, u, t=0.0):
+    _check(_lib.adr_step(ctx, _ptr(u), float(t)), ctx)
+
+
+def adr_integrate(ctx, u, t0, T, m):
+    _check(_lib.adr_integrate(ctx, _ptr(u), float(t0), float(T), int(m)), ctx)
+
+
+def adr_integrate_host(ctx, u_host, t0, T, m):
+    """u_host: contiguous CPU torch tensor or numpy array of the state dtype (in/out)."""
+    if hasattr(u_host, "data_ptr"):
+        if u_host.is_cuda or not u_host.is_contiguous():
+            raise ValueError("u_host must be a contiguous CPU tensor")
+        ptr = C.c_void_p(u_host.data_ptr())
+    else:
+        if not u_host.flags["C_CONTIGUOUS"]:
+            raise ValueError("u_host must be C-contiguous")
+        ptr = C.c_void_p(u_host.ctypes.data)
+    _check(_lib.adr_integrate_host(ctx, ptr, float(t0), float(T), int(m)), ctx)
+
+
+def adr_eval_rhs(ctx, u, F_out=None, g_out=None):
+    _check(_lib.adr_eval_rhs(ctx, _ptr(u), _ptr(F_out), _ptr(g_out)), ctx)
+
+
+def adr_apply_exp(ctx, c, v, y):
+    _check(_lib.adr_apply_exp(ctx, float(c), _ptr(v), _ptr(y)), ctx)
+
+
+def adr_apply_phi(ctx, k, v, y):
+    _check(_lib.adr_apply_phi(ctx, int(k), _ptr(v), _ptr(y)), ctx)
+
+
+def adr_get_info(ctx):
+    kappa = (C.c_double * 3)()
+    abar = C.c_double()
+    beta = (C.c_double * 3)()
+    _check(_lib.adr_get_info(ctx, kappa, C.byref(abar), beta), ctx)
+    return {"kappa": list(kappa), "abar": abar.value, "beta": list(beta)}
+
+
+def adr_kernels_per_step(ctx):
+    return int(_lib.adr_kernels_per_step(ctx))
+
+
+def adr_last_error(ctx=None):
+    return _lib.adr_last_error(ctx).decode()
+
+
+def adr_destroy(ctx):
+    if ctx is not None and ctx.value:
+        _lib.adr_destroy(ctx)
+
+
+# ------------------------------------------------------------------- convenience wrapper
+class Context:
+    """Owns one adr_ctx; methods forward to the C entry points above."""
+
+    def __init__(self, dims, tau, scheme="lawson4", precision="fp64", stream=None, **kw):
+        self.dims = tuple(int(n) for n in dims)
+        self.precision = precision
+        self.ctx = adr_create(self.dims, tau, scheme, precision, stream=stream, **kw)
+
+    def set_coeffs(self, a_nodes, b, r_poly):
+        adr_set_coeffs(self.ctx, 0, a_nodes, b, r_poly)
+        return self
+
+    def step(self, u, t=0.0):
+        adr_step(self.ctx, u, t)
+
+    def integrate(self, u, t0, T, m):
+        adr_integrate(self.ctx, u, t0, T, m)
+
+    def integrate_host(self, u_host, t0, T, m):
+        adr_integrate_host(self.ctx, u_host, t0, T, m)
+
+    def eval_rhs(self, u, F_out=None, g_out=None):
+        adr_eval_rhs(self.ctx, u, F_out, g_out)
+
+    def apply_exp(self, c, v, y):
+        adr_apply_exp(self.ctx, c, v, y)
+
+    def apply_phi(self, k, v, y):
+        adr_apply_phi(self.ctx, k, v, y)
+
+    def info(self):
+        return adr_get_info(self.ctx)
+
+    def kernels_per_step(self):
+        return adr_kernels_per_step(self.ctx)
+
+    def close(self):
+        adr_destroy(self.ctx)
+        self.ctx = None
+
+    def __del__(self):
+        try:
+            if self.ctx is not None:
+                self.close()
+        except Exception:
+            pass
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.float64 if self.precision == "fp64" else torch.float32

@@ -1,0 +1,564 @@
+// C ABI of libadr (declared in include/adr.h): context, host setup, step schedules of
+// the integrators and CUDA-graph replay.
+//
+// Schedules (per time step; B*, T* are library workspace arrays of N elements):
+//   Lawson--Euler (Appendix):   W = u + tau g(u)                          [K1]
+//                               u = e^{tau A} W                          [K2 x d]
+//   ETD2RK = exponential RK2 with phi_2, c2 = 1 (Appendix), written with U:
+//                               F = F(u), G0 = g(u)                       [K1]
+//                               U = u + tau phi_1(tau A) F                [K2 x 2d, K3, K4]
+//                               D = g(U) - G0                             [K1]
+//                               u = U + tau phi_2(tau A) D                [K2 x 2d, K3, K4]
+//   Lawson4 (Lawson's construction on classical RK4, E = e^{tau A / 2}):
+//                               W = u + tau/2 g(u)                        [K1]
+//                               X = E W (= U2),  Eu = E u                 [K2 x 2d]
+//                               W = Eu + tau/2 g(X)        (= U3)
+//                               ACC = 2/3 Eu + 1/3 X + tau/3 g(X)         [K1]
+//                               X = Eu + tau g(W),  ACC += tau/3 g(W)     [K1]
+//                               W = E X (= U4),  X = E ACC                [K2 x 2d]
+//                               u = X + tau/6 g(W)                        [K1]
+//     using E(u + tau/6 k1) = 2/3 Eu + 1/3 U2, so a step costs four E actions.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/adr.h"
+#include "adr_internal.h"
+
+using adr::ContractArgs;
+using adr::StencilArgs;
+
+namespace {
+
+using Op = std::function<cudaError_t(cudaStream_t)>;
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct adr_ctx {
+    adr_params p{};
+    cudaStream_t stream = nullptr;
+    int dim = 0;
+    int n[3] = {1, 1, 1};
+    size_t N = 0;
+    size_t nodes = 0;
+    bool fp64 = true;
+    size_t esize = 8;
+
+    bool coeffs_set = false;
+    double b[3] = {0, 0, 0}, r[4] = {0, 0, 0, 0};
+    double abar = 0, beta[3] = {0, 0, 0};
+    double kappa[3] = {0, 0, 0};
+    bool eig_real = false;
+    adr::Factor1D f[3];
+
+    // device memory (library-owned)
+    void* d_a = nullptr;                   // nodal (a - abar)
+    void* d_E[2][3] = {{nullptr}};         // e^{c tau A_mu}, c = 0.5 (0) and 1 (1)
+    void* d_V[3] = {nullptr};
+    void* d_Vi[3] = {nullptr};
+    double* d_lam[3] = {nullptr};
+    void* ws[6] = {nullptr};
+    void* d_host_state = nullptr;
+
+    // graph cache for adr_integrate
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    void* graph_u = nullptr;
+
+    std::string err;
+};
+
+namespace {
+
+adr_status fail(adr_ctx* c, adr_status s, const std::string& msg) {
+    if (c) c->err = msg; else g_create_error = msg;
+    return s;
+}
+
+adr_status cuda_fail(adr_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, ADR_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void free_dev(void*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+void drop_graph(adr_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    c->graph_u = nullptr;
+}
+
+// Upload an FP64 host array in the working precision.
+cudaError_t upload(adr_ctx* c, void** dst, const std::vector<double>& src) {
+    const size_t bytes = src.size() * c->esize;
+    cudaError_t e = cudaSuccess;
+    if (!*dst) e = cudaMalloc(dst, bytes);
+    if (e != cudaSuccess) return e;
+    if (c->fp64) return cudaMemcpy(*dst, src.data(), bytes, cudaMemcpyHostToDevice);
+    std::vector<float> tmp(src.begin(), src.end());
+    return cudaMemcpy(*dst, tmp.data(), bytes, cudaMemcpyHostToDevice);
+}
+
+// ------------------------------------------------------------------ schedule builders
+template <typename T>
+ContractArgs<T> mode_args(const adr_ctx* c, int mu, const T* M, const T* X, T* Y) {
+    // state viewed as [P][n][Q]; see contract_simt.cu
+    const int n = c->n[mu - 1];
+    long long Q = 1, P = 1;
+    for (int nu = 1; nu < mu; ++nu) Q *= c->n[nu - 1];
+    for (int nu = mu + 1; nu <= c->dim; ++nu) P *= c->n[nu - 1];
+    ContractArgs<T> a;
+    if (mu == 1) {
+        a.A = X; a.sam = n; a.sak = 1; a.sab = 0;
+        a.B = M; a.sbk = 1; a.sbn = n; a.sbb = 0;    // B[k][j] = M[j][k]
+        a.C = Y; a.scm = n; a.scn = 1; a.scb = 0;
+        a.M = int(P); a.N = n; a.K = n; a.batch = 1;
+    } else {
+        a.A = M; a.sam = n; a.sak = 1; a.sab = 0;
+        a.B = X; a.sbk = Q; a.sbn = 1; a.sbb = (long long)n * Q;
+        a.C = Y; a.scm = Q; a.scn = 1; a.scb = (long long)n * Q;
+        a.M = n; a.N = int(Q); a.K = n; a.batch = int(P);
+    }
+    a.n1 = c->n[0];
+    a.n2 = c->n[1];
+    return a;
+}
+
+template <typename T>
+void push_contract(std::vector<Op>& ops, const ContractArgs<T>& a) {
+    ops.push_back([a](cudaStream_t s) { return adr::launch_contract(a, s); });
+}
+
+// y = e^{c tau A} x, optionally finished by y = base + alpha * (e^{c tau A} x).
+template <typename T>
+void push_exp(const adr_ctx* c, std::vector<Op>& ops, int ci, const T* x, T* y,
+              const T* base = nullptr, double alpha = 0.0) {
+    T* t0 = static_cast<T*>(c->ws[4]);
+    T* t1 = static_cast<T*>(c->ws[5]);
+    const T* in = x;
+    for (int mu = 1; mu <= c->dim; ++mu) {
+        T* out = (mu == c->dim) ? y : ((mu % 2) ? t0 : t1);
+        auto a = mode_args<T>(c, mu, static_cast<const T*>(c->d_E[ci][mu - 1]), in, out);
+        if (mu == c->dim && base) { a.epi = adr::EPI_AXPY; a.base = base; a.alpha = alpha; }
+        push_contract(ops, a);
+        in = out;
+    }
+}
+
+// y = phi_k(tau A) x through the eigenbasis (k = 0 gives e^{tau A}), optionally
+// finished by y = base + alpha * (phi_k(tau A) x).
+template <typename T>
+void push_phi(const adr_ctx* c, std::vector<Op>& ops, int k, const T* x, T* y,
+              const T* base = nullptr, double alpha = 0.0) {
+    T* tmp[2] = {static_cast<T*>(c->ws[4]), static_cast<T*>(c->ws[5])};
+    int flip = 0;
+    const T* in = x;
+    for (int mu = 1; mu <= c->dim; ++mu) {       // forward: V_mu^-1
+        T* out = tmp[flip]; flip ^= 1;
+        auto a = mode_args<T>(c, mu, static_cast<const T*>(c->d_Vi[mu - 1]), in, out);
+        if (mu == c->dim) {
+            a.epi = adr::EPI_PHI;
+            a.phik = k;
+            a.ctau = c->p.tau;
+            for (int m = 0; m < 3; ++m) a.lam[m] = (m < c->dim) ? c->d_lam[m] : nullptr;
+        }
+        push_contract(ops, a);
+        in = out;
+    }
+    for (int mu = c->dim; mu >= 1; --mu) {       // back: V_mu
+        T* out = (mu == 1) ? y : tmp[flip];
+        if (mu != 1) flip ^= 1;
+        auto a = mode_args<T>(c, mu, static_cast<const T*>(c->d_V[mu - 1]), in, out);
+        if (mu == 1 && base) { a.epi = adr::EPI_AXPY; a.base = base; a.alpha = alpha; }
+        push_contract(ops, a);
+        in = out;
+    }
+}
+
+template <typename T>
+StencilArgs<T> stencil_base(const adr_ctx* c, const T* u) {
+    StencilArgs<T> s;
+    s.u = u;
+    s.a = static_cast<const T*>(c->d_a);
+    s.dim = c->dim;
+    s.n1 = c->n[0];
+    s.n2 = c->n[1];
+    s.n3 = c->dim == 3 ? c->n[2] : 1;
+    for (int m = 0; m < c->dim; ++m) {
+        const double h = 1.0 / (c->n[m] + 1);
+        s.inv_h2[m] = 1.0 / (h * h);
+        s.inv_2h[m] = 1.0 / (2.0 * h);
+        s.bmb[m] = c->b[m] - c->beta[m];
+        s.beta[m] = c->beta[m];
+    }
+    s.abar = c->abar;
+    for (int i = 0; i < 4; ++i) s.r[i] = c->r[i];
+    return s;
+}
+
+template <typename T>
+void push_stencil(std::vector<Op>& ops, const StencilArgs<T>& s) {
+    ops.push_back([s](cudaStream_t st) { return adr::launch_stencil(s, st); });
+}
+
+template <typename T>
+std::vector<Op> build_step(const adr_ctx* c, T* u) {
+    std::vector<Op> ops;
+    const double tau = c->p.tau;
+    T* B0 = static_cast<T*>(c->ws[0]);
+    T* B1 = static_cast<T*>(c->ws[1]);
+    T* B2 = static_cast<T*>(c->ws[2]);
+    T* B3 = static_cast<T*>(c->ws[3]);
+    switch (c->p.scheme) {
+    case ADR_LAWSON_EULER: {
+        auto s = stencil_base<T>(c, u);
+        s.nout = 1; s.out[0] = B0; s.cu[0] = 1.0; s.cg[0] = tau;       // W = u + tau g(u)
+        push_stencil(ops, s);
+        push_exp<T>(c, ops, 1, B0, u);                                  // u = e^{tau A} W
+        break;
+    }
+    case ADR_ETD2RK: {
+        auto s1 = stencil_base<T>(c, u);
+        s1.nout = 2; s1.out[0] = B0; s1.cF[0] = 1.0;                    // F(u)
+        s1.out[1] = B1; s1.cg[1] = 1.0;                                 // G0 = g(u)
+        push_stencil(ops, s1);
+        push_phi<T>(c, ops, 1, B0, B2, u, tau);                          // U = u + tau phi1 F
+        auto s2 = stencil_base<T>(c, B2);
+        s2.nx = 1; s2.X[0] = B1;
+        s2.nout = 1; s2.out[0] = B0; s2.cg[0] = 1.0; s2.cx[0][0] = -1.0; // D = g(U) - G0
+        push_stencil(ops, s2);
+        push_phi<T>(c, ops, 2, B0, u, B2, tau);                          // u = U + tau phi2 D
+        break;
+    }
+    case ADR_LAWSON4: {
+        T* W = B0; T* X = B1; T* Eu = B2; T* ACC = B3;
+        auto s1 = stencil_base<T>(c, u);
+        s1.nout = 1; s1.out[0] = W; s1.cu[0] = 1.0; s1.cg[0] = 0.5 * tau;       // u + tau/2 k1
+        push_stencil(ops, s1);
+        push_exp<T>(c, ops, 0, W, X);                                             // U2
+        push_exp<T>(c, ops, 0, u, Eu);                                            // Eu
+        auto s2 = stencil_base<T>(c, X);
+        s2.nx = 1; s2.X[0] = Eu;
+        s2.nout = 2;
+        s2.out[0] = W; s2.cx[0][0] = 1.0; s2.cg[0] = 0.5 * tau;                  // U3 = Eu + tau/2 k2
+        s2.out[1] = ACC; s2.cx[1][0] = 2.0 / 3.0; s2.cu[1] = 1.0 / 3.0; s2.cg[1] = tau / 3.0;
+        push_stencil(ops, s2);
+        auto s3 = stencil_base<T>(c, W);
+        s3.nx = 2; s3.X[0] = Eu; s3.X[1] = ACC;
+        s3.nout = 2;
+        s3.out[0] = X; s3.cx[0][0] = 1.0; s3.cg[0] = tau;                         // Eu + tau k3
+        s3.out[1] = ACC; s3.cx[1][1] = 1.0; s3.cg[1] = tau / 3.0;                 // ACC += tau/3 k3
+        push_stencil(ops, s3);
+        push_exp<T>(c, ops, 0, X, W);                                             // U4
+        push_exp<T>(c, ops, 0, ACC, X);                                           // E ACC
+        auto s4 = stencil_base<T>(c, W);
+        s4.nx = 1; s4.X[0] = X;
+        s4.nout = 1; s4.out[0] = u; s4.cx[0][0] = 1.0; s4.cg[0] = tau / 6.0;     // u+ = E ACC + tau/6 k4
+        push_stencil(ops, s4);
+        break;
+    }
+    default:
+        break;
+    }
+    return ops;
+}
+
+std::vector<Op> step_ops(const adr_ctx* c, void* u) {
+    return c->fp64 ? build_step<double>(c, static_cast<double*>(u)) : build_step<float>(c, static_cast<float*>(u));
+}
+
+adr_status run_ops(adr_ctx* c, const std::vector<Op>& ops, const char* where) {
+    for (const auto& op : ops) {
+        cudaError_t e = op(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, where);
+    }
+    return ADR_OK;
+}
+
+bool needs_phi(int scheme) { return scheme == ADR_ETD2RK; }
+
+adr_status check_ready(adr_ctx* c) {
+    if (!c) return ADR_ERR_ARG;
+    if (!c->coeffs_set) return fail(c, ADR_ERR_STATE, "adr_set_coeffs has not been called");
+    return ADR_OK;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+adr_status adr_create(const adr_params* p, void* cuda_stream, adr_ctx** out) {
+    if (!out) return fail(nullptr, ADR_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail(nullptr, ADR_ERR_ARG, "params is NULL");
+    if (p->dim != 2 && p->dim != 3) return fail(nullptr, ADR_ERR_ARG, "dim must be 2 or 3");
+    for (int m = 0; m < p->dim; ++m)
+        if (p->n[m] < 2 || p->n[m] > 4096) return fail(nullptr, ADR_ERR_ARG, "n must be in [2, 4096]");
+    if (!(p->tau > 0.0) || !std::isfinite(p->tau)) return fail(nullptr, ADR_ERR_ARG, "tau must be positive");
+    if (p->scheme < ADR_LAWSON_EULER || p->scheme > ADR_LAWSON4) return fail(nullptr, ADR_ERR_ARG, "unknown scheme");
+    if (p->precision == ADR_MIXED_TF32X3)
+        return fail(nullptr, ADR_ERR_UNSUPPORTED, "ADR_MIXED_TF32X3 is not implemented");
+    if (p->precision != ADR_FP64 && p->precision != ADR_FP32 && p->precision != ADR_MIXED_BF16X3)
+        return fail(nullptr, ADR_ERR_ARG, "unknown precision");
+    if (p->precision == ADR_MIXED_BF16X3)
+        return fail(nullptr, ADR_ERR_UNSUPPORTED, "ADR_MIXED_BF16X3 needs the tensor-core kernel");
+    size_t N = 1, nodes = 1;
+    for (int m = 0; m < p->dim; ++m) { N *= size_t(p->n[m]); nodes *= size_t(p->n[m] + 2); }
+    if (N > (size_t(1) << 31) - 1) return fail(nullptr, ADR_ERR_ARG, "grid too large");
+
+    std::unique_ptr<adr_ctx> c(new adr_ctx);
+    c->p = *p;
+    if (c->p.lambda <= 0.0) c->p.lambda = 1.0;
+    if (c->p.kappa_tol <= 0.0) c->p.kappa_tol = 1e-2;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->dim = p->dim;
+    for (int m = 0; m < 3; ++m) c->n[m] = (m < p->dim) ? p->n[m] : 1;
+    c->N = N;
+    c->nodes = nodes;
+    c->fp64 = (p->precision == ADR_FP64);
+    c->esize = c->fp64 ? 8 : 4;
+    for (auto& w : c->ws) {
+        cudaError_t e = cudaMalloc(&w, N * c->esize);
+        if (e != cudaSuccess) {
+            adr_destroy(c.release());
+            return fail(nullptr, ADR_ERR_ALLOC, std::string("workspace: ") + cudaGetErrorString(e));
+        }
+    }
+    *out = c.release();
+    return ADR_OK;
+}
+
+adr_status adr_set_coeffs(adr_ctx* c, int instance, const double* a_nodes, const double b[3], const double r_poly[4]) {
+    if (!c) return ADR_ERR_ARG;
+    if (instance != 0) return fail(c, ADR_ERR_ARG, "instance must be 0 for a single-grid context");
+    if (!a_nodes || !b || !r_poly) return fail(c, ADR_ERR_ARG, "NULL coefficient pointer");
+    for (size_t i = 0; i < c->nodes; ++i)
+        if (!std::isfinite(a_nodes[i])) return fail(c, ADR_ERR_ARG, "a_nodes has a non-finite value");
+    drop_graph(c);
+    c->coeffs_set = false;
+    for (int m = 0; m < 3; ++m) c->b[m] = (m < c->dim) ? b[m] : 0.0;
+    for (int i = 0; i < 4; ++i) c->r[i] = r_poly[i];
+    // Eq. (amaxbeta)
+    c->abar = c->p.abar_override > 0 ? c->p.abar_override : c->p.lambda * adr::nodal_max(a_nodes, c->nodes);
+    if (!(c->abar > 0)) return fail(c, ADR_ERR_ARG, "lambda * a_max must be positive");
+    for (int m = 0; m < c->dim; ++m) c->beta[m] = c->b[m] + adr::mean_face_jump(a_nodes, c->dim, c->n, m + 1);
+
+    std::vector<double> amb(a_nodes, a_nodes + c->nodes);
+    for (auto& v : amb) v -= c->abar;
+    cudaError_t e = upload(c, &c->d_a, amb);
+    if (e != cudaSuccess) return cuda_fail(c, e, "upload a");
+
+    c->eig_real = true;
+    struct CachedE { int n; double beta, c; std::vector<double> E; };
+    std::vector<CachedE> cache;
+    cache.reserve(6);
+    for (int m = 0; m < c->dim; ++m) {
+        c->f[m] = adr::make_factor(c->n[m], c->abar, c->beta[m]);
+        const auto A = adr::factor_dense(c->f[m]);
+        for (int ci = 0; ci < 2; ++ci) {
+            const double cc = ci == 0 ? 0.5 : 1.0;
+            // directions with the same (n, beta) share one host computation of e^{c tau A_mu}
+            const std::vector<double>* E = nullptr;
+            for (const auto& hit : cache)
+                if (hit.n == c->n[m] && hit.beta == c->beta[m] && hit.c == cc) E = &hit.E;
+            if (!E) {
+                std::vector<double> sA(A);
+                for (auto& v : sA) v *= cc * c->p.tau;
+                try {
+                    cache.push_back({c->n[m], c->beta[m], cc, adr::expm_pade13(sA, c->n[m])});
+                } catch (const std::exception& ex) {
+                    return fail(c, ADR_ERR_ARG, std::string("expm: ") + ex.what());
+                }
+                E = &cache.back().E;
+            }
+            e = upload(c, &c->d_E[ci][m], *E);
+            if (e != cudaSuccess) return cuda_fail(c, e, "upload E");
+        }
+        const adr::Eigen1D eg = adr::eigen_closed_form(c->f[m]);
+        c->kappa[m] = eg.real ? eg.kappa : 0.0;
+        if (!eg.real) { c->eig_real = false; continue; }
+        e = upload(c, &c->d_V[m], eg.V);
+        if (e == cudaSuccess) e = upload(c, &c->d_Vi[m], eg.Vinv);
+        if (e == cudaSuccess && !c->d_lam[m]) e = cudaMalloc(reinterpret_cast<void**>(&c->d_lam[m]), c->n[m] * sizeof(double));
+        if (e == cudaSuccess) e = cudaMemcpy(c->d_lam[m], eg.lam.data(), c->n[m] * sizeof(double), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(c, e, "upload eigenpairs");
+    }
+    if (needs_phi(c->p.scheme)) {
+        if (!c->eig_real)
+            return fail(c, ADR_ERR_COMPLEX_SPECTRUM, "cell Peclet number >= 1: A_mu has no real eigenbasis");
+        double kp = 1.0;
+        for (int m = 0; m < c->dim; ++m) kp *= c->kappa[m];
+        const double unit = c->fp64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+        if (kp * unit > c->p.kappa_tol) {
+            char buf[160];
+            std::snprintf(buf, sizeof buf, "eigen route ill-conditioned: prod kappa * u = %.3e > kappa_tol %.3e",
+                          kp * unit, c->p.kappa_tol);
+            return fail(c, ADR_ERR_ILL_CONDITIONED, buf);
+        }
+    }
+    c->coeffs_set = true;
+    return ADR_OK;
+}
+
+adr_status adr_step(adr_ctx* c, void* u, double t) {
+    (void)t;
+    adr_status st = check_ready(c);
+    if (st != ADR_OK) return st;
+    if (!u) return fail(c, ADR_ERR_ARG, "u is NULL");
+    return run_ops(c, step_ops(c, u), "adr_step");
+}
+
+adr_status adr_integrate(adr_ctx* c, void* u, double t0, double T, int m) {
+    adr_status st = check_ready(c);
+    if (st != ADR_OK) return st;
+    if (!u) return fail(c, ADR_ERR_ARG, "u is NULL");
+    if (m < 0) return fail(c, ADR_ERR_ARG, "m must be >= 0");
+    if (T > 0 && std::fabs(t0 + m * c->p.tau - T) > 1e-9 * std::max(1.0, std::fabs(T)))
+        return fail(c, ADR_ERR_ARG, "T != t0 + m * tau");
+    if (m == 0) return ADR_OK;
+    if (c->stream == nullptr) {   // the legacy stream cannot be captured: replay directly
+        const auto ops = step_ops(c, u);
+        for (int i = 0; i < m; ++i) {
+            st = run_ops(c, ops, "adr_integrate");
+            if (st != ADR_OK) return st;
+        }
+        return ADR_OK;
+    }
+    if (c->graph_u != u) {
+        drop_graph(c);
+        const auto ops = step_ops(c, u);
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
+        cudaError_t le = cudaSuccess;
+        for (const auto& op : ops) {
+            le = op(c->stream);
+            if (le != cudaSuccess) break;
+        }
+        e = cudaStreamEndCapture(c->stream, &c->graph);
+        if (le != cudaSuccess) { drop_graph(c); return cuda_fail(c, le, "capture launch"); }
+        if (e != cudaSuccess) { drop_graph(c); return cuda_fail(c, e, "end capture"); }
+        e = cudaGraphInstantiate(&c->gexec, c->graph, 0);
+        if (e != cudaSuccess) { drop_graph(c); return cuda_fail(c, e, "instantiate graph"); }
+        c->graph_u = u;
+    }
+    for (int i = 0; i < m; ++i) {
+        cudaError_t e = cudaGraphLaunch(c->gexec, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    }
+    return ADR_OK;
+}
+
+adr_status adr_integrate_host(adr_ctx* c, void* u_host, double t0, double T, int m) {
+    adr_status st = check_ready(c);
+    if (st != ADR_OK) return st;
+    if (!u_host) return fail(c, ADR_ERR_ARG, "u_host is NULL");
+    const size_t bytes = c->N * c->esize;
+    cudaError_t e = cudaSuccess;
+    if (!c->d_host_state) {
+        e = cudaMalloc(&c->d_host_state, bytes);
+        if (e != cudaSuccess) return fail(c, ADR_ERR_ALLOC, std::string("state buffer: ") + cudaGetErrorString(e));
+    }
+    e = cudaMemcpyAsync(c->d_host_state, u_host, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "H2D");
+    st = adr_integrate(c, c->d_host_state, t0, T, m);
+    if (st != ADR_OK) return st;
+    e = cudaMemcpyAsync(u_host, c->d_host_state, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "D2H");
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+    return ADR_OK;
+}
+
+adr_status adr_eval_rhs(adr_ctx* c, const void* u, void* F_out, void* g_out) {
+    adr_status st = check_ready(c);
+    if (st != ADR_OK) return st;
+    if (!u || (!F_out && !g_out)) return fail(c, ADR_ERR_ARG, "NULL array");
+    if (u == F_out || u == g_out) return fail(c, ADR_ERR_ARG, "output aliases input");
+    std::vector<Op> ops;
+    auto fill = [&](auto* uu, auto* F, auto* g) {
+        auto s = stencil_base(c, uu);
+        if (F) { s.out[s.nout] = F; s.cF[s.nout] = 1.0; ++s.nout; }
+        if (g) { s.out[s.nout] = g; s.cg[s.nout] = 1.0; ++s.nout; }
+        push_stencil(ops, s);
+    };
+    if (c->fp64) fill(static_cast<const double*>(u), static_cast<double*>(F_out), static_cast<double*>(g_out));
+    else         fill(static_cast<const float*>(u), static_cast<float*>(F_out), static_cast<float*>(g_out));
+    return run_ops(c, ops, "adr_eval_rhs");
+}
+
+adr_status adr_apply_exp(adr_ctx* c, double cc, const void* v, void* y) {
+    adr_status st = check_ready(c);
+    if (st != ADR_OK) return st;
+    if (!v || !y || v == y) return fail(c, ADR_ERR_ARG, "NULL or aliased array");
+    int ci = -1;
+    if (cc == 0.5) ci = 0;
+    if (cc == 1.0) ci = 1;
+    if (ci < 0) return fail(c, ADR_ERR_ARG, "c must be 0.5 or 1");
+    std::vector<Op> ops;
+    if (c->fp64) push_exp<double>(c, ops, ci, static_cast<const double*>(v), static_cast<double*>(y));
+    else         push_exp<float>(c, ops, ci, static_cast<const float*>(v), static_cast<float*>(y));
+    return run_ops(c, ops, "adr_apply_exp");
+}
+
+adr_status adr_apply_phi(adr_ctx* c, int k, const void* v, void* y) {
+    adr_status st = check_ready(c);
+    if (st != ADR_OK) return st;
+    if (!v || !y || v == y) return fail(c, ADR_ERR_ARG, "NULL or aliased array");
+    if (k < 0 || k > 2) return fail(c, ADR_ERR_ARG, "k must be 0, 1 or 2");
+    if (!c->eig_real) return fail(c, ADR_ERR_COMPLEX_SPECTRUM, "A_mu has no real eigenbasis");
+    std::vector<Op> ops;
+    if (c->fp64) push_phi<double>(c, ops, k, static_cast<const double*>(v), static_cast<double*>(y));
+    else         push_phi<float>(c, ops, k, static_cast<const float*>(v), static_cast<float*>(y));
+    return run_ops(c, ops, "adr_apply_phi");
+}
+
+adr_status adr_get_info(const adr_ctx* c, double kappa[3], double* abar, double beta[3]) {
+    if (!c) return ADR_ERR_ARG;
+    if (kappa) for (int m = 0; m < 3; ++m) kappa[m] = c->kappa[m];
+    if (abar) *abar = c->abar;
+    if (beta) for (int m = 0; m < 3; ++m) beta[m] = c->beta[m];
+    return ADR_OK;
+}
+
+int adr_kernels_per_step(const adr_ctx* c) {
+    if (!c) return -1;
+    const int d = c->dim;
+    switch (c->p.scheme) {
+    case ADR_LAWSON_EULER: return 1 + d;
+    case ADR_ETD2RK: return 2 + 4 * d;
+    case ADR_LAWSON4: return 4 + 4 * d;
+    default: return -1;
+    }
+}
+
+const char* adr_last_error(const adr_ctx* c) {
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+void adr_destroy(adr_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    drop_graph(c);
+    free_dev(c->d_a);
+    for (auto& row : c->d_E) for (auto& p : row) free_dev(p);
+    for (auto& p : c->d_V) free_dev(p);
+    for (auto& p : c->d_Vi) free_dev(p);
+    for (auto& p : c->d_lam) { void* q = p; free_dev(q); p = nullptr; }
+    for (auto& p : c->ws) free_dev(p);
+    free_dev(c->d_host_state);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,96 @@
+// Internal declarations shared by the translation units of libadr.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace adr {
+
+// ------------------------------------------------------------------ host setup (FP64)
+// 1-D factor A_mu of the Kronecker sum: tridiagonal Toeplitz discretisation of
+// a_max d_mumu + beta_mu d_mu on n interior nodes (Section 5.2).
+struct Factor1D {
+    int n = 0;
+    double h = 0, sub = 0, diag = 0, sup = 0;  // coefficients of u_{i-1}, u_i, u_{i+1}
+};
+
+Factor1D make_factor(int n, double abar, double beta);
+std::vector<double> factor_dense(const Factor1D& f);                   // row-major n*n
+std::vector<double> expm_pade13(const std::vector<double>& A, int n);  // e^A, row-major
+
+// Closed-form eigenpairs of the tridiagonal Toeplitz factor (real when sub*sup > 0):
+// lambda_j = diag + 2 sqrt(sub*sup) cos(j pi/(n+1)),
+// V[i][j] = rho^{i-c} sin(i j pi/(n+1)), rho = sqrt(sub/sup), c = (n+1)/2,
+// Vinv[j][i] = 2/(n+1) sin(i j pi/(n+1)) rho^{c-i}  (1-based i, j).
+struct Eigen1D {
+    bool real = false;
+    double kappa = 0;                 // 2-norm condition number of V (= of the diagonal scaling)
+    std::vector<double> lam, V, Vinv;  // n, n*n, n*n (row-major)
+};
+Eigen1D eigen_closed_form(const Factor1D& f);
+
+// a_max and beta of Eq. (amaxbeta) from the nodal a (incl. boundary ring).
+double nodal_max(const double* a, size_t count);
+double mean_face_jump(const double* a, int dim, const int* n, int mu);  // mu = 1..dim
+
+// ------------------------------------------------------------------ kernel arguments
+constexpr int kMaxExtra = 3;
+constexpr int kMaxOut = 2;
+
+// K1: variable-coefficient stencil with a fused stage-combination epilogue.
+//   g   = div_h((a - abar) grad_h u) + (b - beta) . grad_h u + r(u)
+//   F   = g + A_h u,  A_h u = abar lap_h u + beta . grad_h u
+//   out_j = cu[j] u + sum_i cx[j][i] X_i + cg[j] g + cF[j] F
+template <typename T>
+struct StencilArgs {
+    const T* u = nullptr;
+    const T* a = nullptr;            // nodal (a - abar), (n1+2)(n2+2)(n3+2)
+    int dim = 3, n1 = 1, n2 = 1, n3 = 1;
+    double inv_h2[3] = {0, 0, 0}, inv_2h[3] = {0, 0, 0};
+    double bmb[3] = {0, 0, 0};       // b - beta
+    double beta[3] = {0, 0, 0};
+    double abar = 0;
+    double r[4] = {0, 0, 0, 0};
+    const T* X[kMaxExtra] = {nullptr, nullptr, nullptr};
+    int nx = 0;
+    T* out[kMaxOut] = {nullptr, nullptr};
+    int nout = 0;
+    double cu[kMaxOut] = {0, 0};
+    double cx[kMaxOut][kMaxExtra] = {{0, 0, 0}, {0, 0, 0}};
+    double cg[kMaxOut] = {0, 0};
+    double cF[kMaxOut] = {0, 0};
+    unsigned* amax[kMaxOut] = {nullptr, nullptr};  // optional max|out_j| (float bits)
+};
+
+// K2 (SIMT): strided batched contraction C[b] = A[b] * B[b] with a fused epilogue.
+// Element (m,k) of A[b] is A[b*sab + m*sam + k*sak]; likewise B (k,n), C (m,n).
+// The linear offset of a C element is its index in the state array, which the phi
+// epilogue decodes into (i1, i2, i3).
+enum Epilogue { EPI_STORE = 0, EPI_PHI = 1, EPI_AXPY = 2 };
+
+template <typename T>
+struct ContractArgs {
+    const T* A = nullptr;
+    const T* B = nullptr;
+    T* C = nullptr;
+    long long sam = 0, sak = 0, sbk = 0, sbn = 0, scm = 0, scn = 0;
+    long long sab = 0, sbb = 0, scb = 0;
+    int M = 0, N = 0, K = 0, batch = 1;
+    int epi = EPI_STORE;
+    const T* base = nullptr;  // EPI_AXPY: C = base + alpha * acc
+    double alpha = 0;
+    int phik = 1;             // EPI_PHI: C = phi_k(ctau * (l1[i1]+l2[i2]+l3[i3])) * acc
+    double ctau = 0;
+    const double* lam[3] = {nullptr, nullptr, nullptr};
+    int n1 = 1, n2 = 1;
+};
+
+cudaError_t launch_stencil(const StencilArgs<double>& a, cudaStream_t s);
+cudaError_t launch_stencil(const StencilArgs<float>& a, cudaStream_t s);
+cudaError_t launch_contract(const ContractArgs<double>& a, cudaStream_t s);
+cudaError_t launch_contract(const ContractArgs<float>& a, cudaStream_t s);
+cudaError_t launch_convert_f64_to_f32(const double* in, float* out, size_t n, cudaStream_t s);
+
+}  // namespace adr

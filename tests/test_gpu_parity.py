@@ -1,0 +1,212 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: FP64 paths 1e-12 relative l2 (the FP64 requirement of the workloads);
+FP32 paths are bounded by FP32 rounding of the stencil and the contractions.
+Sizes span several CTA tiles and ragged tails; guard bands around every caller-owned
+array check that nothing is written out of bounds.
+"""
+import numpy as np
+import pytest
+
+from oracle import adr_oracle as O
+from paper_2303_15861_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2303_15861_gb300 import adr, build_lib  # noqa: E402
+
+build_lib.build()
+adr.load_library()
+
+GUARD = 1024
+
+
+def guarded(shape, dtype, fill=None):
+    """A device array with NaN guard bands on both sides; returns (full, view)."""
+    n = int(np.prod(shape))
+    full = torch.full((n + 2 * GUARD,), float("nan"), dtype=dtype, device="cuda")
+    view = full[GUARD:GUARD + n].view(shape)
+    if fill is not None:
+        view.copy_(torch.as_tensor(np.asarray(fill), dtype=dtype))
+    return full, view
+
+
+def check_guards(full):
+    g = torch.cat([full[:GUARD], full[-GUARD:]])
+    assert torch.isnan(g).all(), "write outside the caller's array"
+
+
+def make_case(dims, b=None, c=0.5, k=1, noise=1e-3, seed=0):
+    b = b if b is not None else (10.0,) * len(dims)
+    a = W.sine_product_coefficient(dims, c=c, k=k)
+    u0 = W.smooth_initial_state(dims, noise=noise, seed=seed)
+    return a, tuple(b) + (0.0,) * (3 - len(b)), W.REACTION_U2_1MU, u0
+
+
+def context(dims, tau, scheme, prec, a, b, r):
+    ctx = adr.Context(dims, tau, scheme, prec)
+    ctx.set_coeffs(a, b, r)
+    return ctx
+
+
+DTYPES = {"fp64": torch.float64, "fp32": torch.float32}
+STENCIL_DIMS = [(32, 32), (37, 29), (33, 33, 33), (45, 19, 23)]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+@pytest.mark.parametrize("dims", STENCIL_DIMS)
+def test_stencil_F_and_g(dims, prec, tol):
+    b = (10.0, -7.0, 4.0)[: len(dims)]
+    a, bb, r, u0 = make_case(dims, b=b, k=2)
+    prob = O.ADRProblem(dims, a, bb, r)
+    ctx = context(dims, 1e-3, "lawson4", prec, a, bb, r)
+    dt = DTYPES[prec]
+    fu, u = guarded(u0.shape, dt, u0)
+    fF, F = guarded(u0.shape, dt)
+    fg, g = guarded(u0.shape, dt)
+    ctx.eval_rhs(u, F, g)
+    torch.cuda.synchronize()
+    for full in (fu, fF, fg):
+        check_guards(full)
+    uin = u.double().cpu().numpy()          # the FP32 path sees the rounded state
+    refF, refg = prob.F(uin), prob.g(uin)
+    assert O.rel_l2(F.cpu().numpy(), refF) < tol
+    assert O.rel_l2(g.cpu().numpy(), refg) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 1e-6)])
+@pytest.mark.parametrize("dims", [(32, 32), (70, 45), (33, 33, 33), (45, 19, 23), (130, 65, 67)])
+@pytest.mark.parametrize("c", [0.5, 1.0])
+def test_exp_action(dims, c, prec, tol):
+    a, b, r, _ = make_case(dims)
+    v0 = np.random.default_rng(4).standard_normal(tuple(dims[::-1]))
+    tau = 2.5e-3
+    prob = O.ADRProblem(dims, a, b, r)
+    ctx = context(dims, tau, "lawson4", prec, a, b, r)
+    dt = DTYPES[prec]
+    fv, v = guarded(v0.shape, dt, v0)
+    fy, y = guarded(v0.shape, dt)
+    ctx.apply_exp(c, v, y)
+    torch.cuda.synchronize()
+    check_guards(fv)
+    check_guards(fy)
+    ref = O.MatrixFunctions(prob, tau).exp_action(c, v.double().cpu().numpy())
+    assert O.rel_l2(y.cpu().numpy(), ref) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("dims", [(32, 32), (37, 29), (24, 24, 24), (31, 17, 22)])
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_phi_action(dims, k, prec, tol):
+    a, b, r, _ = make_case(dims)
+    v0 = np.random.default_rng(6).standard_normal(tuple(dims[::-1]))
+    tau = 2e-3
+    prob = O.ADRProblem(dims, a, b, r)
+    ctx = context(dims, tau, "etd2rk", prec, a, b, r)
+    dt = DTYPES[prec]
+    fv, v = guarded(v0.shape, dt, v0)
+    fy, y = guarded(v0.shape, dt)
+    ctx.apply_phi(k, v, y)
+    torch.cuda.synchronize()
+    check_guards(fy)
+    vin = v.double().cpu().numpy()
+    mf = O.MatrixFunctions(prob, tau)
+    ref = mf.exp_action(1.0, vin) if k == 0 else mf.phi_action(k, 1.0, vin)
+    assert O.rel_l2(y.cpu().numpy(), ref) < tol
+
+
+INTEGRATE = [
+    # (dims, b, scheme, T, m)
+    ((32, 32), (10.0, 10.0), "lawson_euler", 0.1, 20),
+    ((32, 32), (10.0, 10.0), "etd2rk", 0.1, 20),
+    ((32, 32), (10.0, 10.0), "lawson4", 0.1, 20),
+    ((41, 27), (6.0, -9.0), "etd2rk", 0.05, 10),
+    ((20, 20, 20), (10.0, 10.0, 10.0), "etd2rk", 0.04, 8),
+    ((24, 24, 24), (10.0, 10.0, 10.0), "lawson4", 0.04, 8),
+    ((19, 26, 33), (3.0, -5.0, 8.0), "lawson_euler", 0.04, 8),
+    ((19, 26, 33), (3.0, -5.0, 8.0), "lawson4", 0.04, 8),
+]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("dims,b,scheme,T,m", INTEGRATE)
+def test_integrate_matches_oracle(dims, b, scheme, T, m, prec, tol):
+    a, bb, r, u0 = make_case(dims, b=b)
+    tau = T / m
+    ctx = context(dims, tau, scheme, prec, a, bb, r)
+    dt = DTYPES[prec]
+    fu, u = guarded(u0.shape, dt, u0)
+    ctx.integrate(u, 0.0, T, m)
+    torch.cuda.synchronize()
+    check_guards(fu)
+    ref = O.solve(dims, a, bb, r, u0, tau, m, scheme)
+    assert O.rel_l2(u.cpu().numpy(), ref) < tol
+
+
+@pytest.mark.parametrize("scheme", ["lawson_euler", "etd2rk", "lawson4"])
+def test_graph_replay_equals_direct_steps_bitwise(scheme):
+    """adr_integrate (captured graph) and m calls of adr_step give identical bits,
+    and two runs are bitwise deterministic."""
+    dims = (29, 23, 21)
+    a, b, r, u0 = make_case(dims)
+    tau = 2e-3
+    ctx = context(dims, tau, scheme, "fp64", a, b, r)
+    u1 = torch.tensor(u0, device="cuda")
+    u2 = torch.tensor(u0, device="cuda")
+    u3 = torch.tensor(u0, device="cuda")
+    ctx.integrate(u1, 0.0, 5 * tau, 5)
+    for i in range(5):
+        ctx.step(u2, i * tau)
+    ctx.integrate(u3, 0.0, 5 * tau, 5)
+    torch.cuda.synchronize()
+    assert torch.equal(u1, u2) and torch.equal(u1, u3)
+
+
+def test_integrate_host_matches_device():
+    dims = (32, 32)
+    a, b, r, u0 = make_case(dims)
+    ctx = context(dims, 5e-3, "etd2rk", "fp64", a, b, r)
+    ud = torch.tensor(u0, device="cuda")
+    uh = torch.tensor(u0).pin_memory()
+    ctx.integrate(ud, 0.0, 0.1, 20)
+    ctx.integrate_host(uh, 0.0, 0.1, 20)
+    torch.cuda.synchronize()
+    assert torch.equal(ud.cpu(), uh)
+
+
+def test_config2_full_size_fp64():
+    """3-D 128^3 FP64 ETD2RK, 50 steps to T = 0.1 (the full workload), against the oracle."""
+    w = W.config2()
+    ctx = context(w.dims, w.tau, w.scheme, "fp64", w.a_nodes, w.b, w.r_poly)
+    u = torch.tensor(w.u0, device="cuda")
+    ctx.integrate(u, 0.0, w.tau * w.m, w.m)
+    torch.cuda.synchronize()
+    ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, w.m, w.scheme)
+    err = O.rel_l2(u.cpu().numpy(), ref)
+    print(f"config2 128^3 etd2rk fp64 rel l2 {err:.3e}")
+    assert err < 1e-12
+
+
+def test_state_errors():
+    dims = (16, 16)
+    ctx = adr.Context(dims, 1e-3, "etd2rk", "fp64")
+    u = torch.zeros(dims, dtype=torch.float64, device="cuda")
+    with pytest.raises(adr.AdrError) as e:
+        ctx.step(u)
+    assert e.value.status == 7
+    a, b, r, _ = make_case(dims)
+    # cell Peclet number |b| h / (2 abar) >= 1: no real eigenbasis for the phi route
+    with pytest.raises(adr.AdrError) as e:
+        ctx.set_coeffs(a, (400.0, 0.0), r)
+    assert e.value.status == 5
+    # the same coefficients are fine for an exp-only (Lawson) scheme
+    adr.Context(dims, 1e-3, "lawson4", "fp64").set_coeffs(a, (400.0, 0.0), r)
+    # kappa guard
+    ctx2 = adr.Context((64, 64), 1e-3, "etd2rk", "fp32", kappa_tol=1e-9)
+    with pytest.raises(adr.AdrError) as e:
+        ctx2.set_coeffs(*make_case((64, 64))[:3])
+    assert e.value.status == 4
