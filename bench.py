@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""Benchmark of the ADR exponential-integrator hot path on GB300.
+
+Workload: 3-D unit cube, 256^3 interior nodes, Dirichlet, u_t = div(a grad u) + b.grad u
++ u^2(1-u) with a = 1 + 0.5 sin(2 pi x) sin(2 pi y) sin(2 pi z), b = (10,10,10); Lawson4
+with 40 steps to T = 0.1; FP32 state and stencil, mu-mode contractions on the tensor
+cores (three BF16 slices per operand). One benchmark step = one integration of the 40
+time steps; the metric is DOF*steps/s (interior nodes times time steps per second).
+
+Prints one JSON line (rank 0). --impl reference times the FP64 numpy oracle on the host
+cores on a bounded sample (one time step of the same workload per benchmark step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+_CORES = len(os.sched_getaffinity(0))
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, str(_CORES))
+
+import numpy as np  # noqa: E402
+
+METRIC = "DOF*steps/s at 3D 256^3, mixed-precision vs FP64 GPU at rel err <=1e-6"
+UNIT = "DOF*steps/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30, help="timed integrations of m time steps")
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32", "fp64"])
+    p.add_argument("--n", type=int, default=256)
+    p.add_argument("--m", type=int, default=40)
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison run")
+    p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return p.parse_args()
+
+
+def workload(args):
+    from paper_2303_15861_gb300 import workloads as W
+    return W.config3(n=args.n, m=args.m)
+
+
+# ----------------------------------------------------------------------------- oracle
+def oracle_step_timer(w):
+    """Time one Lawson4 time step of the FP64 oracle on the host cores."""
+    from oracle import adr_oracle as O
+    prob = O.ADRProblem(w.dims, w.a_nodes, w.b, w.r_poly)
+    ops = O.GridOps(prob, w.tau)
+    ops.mf.E_factors(0.5)                       # factors are setup, not the step
+    u = w.u0.copy()
+
+    def one():
+        nonlocal u
+        t0 = time.perf_counter()
+        u = O.step_lawson4(ops, u)
+        return time.perf_counter() - t0
+    return one
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = workload(args)
+    one = oracle_step_timer(w)
+    for _ in range(args.warmup):
+        one()
+    ts = [one() for _ in range(args.steps)]
+    total = sum(ts)
+    value = w.dof * len(ts) / total
+    sample = f"{len(ts)} Lawson4 time steps of the {w.dims[0]}^3 workload (of {w.m} per integration)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(ts),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"3d_{w.dims[0]}^3_lawson4_T0.1_m{w.m}", "grid": list(w.dims),
+                   "scheme": "lawson4", "precision": "fp64-numpy-oracle", "step": "one time step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": _CORES, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.5)
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                sm.append(float(f[2]))
+                smax = float(f[3])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[6:10]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- ours
+def ours(args):
+    import torch
+    from paper_2303_15861_gb300 import adr, build_lib
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    build_lib.build()
+    adr.load_library()
+
+    w = workload(args)
+    N = w.dof
+    stream = torch.cuda.Stream()
+    dt = torch.float64 if args.precision == "fp64" else torch.float32
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        ctx = adr.Context(w.dims, w.tau, "lawson4", args.precision, stream=stream)
+        t0 = time.perf_counter()
+        ctx.set_coeffs(w.a_nodes, w.b, w.r_poly)
+        setup_s = time.perf_counter() - t0
+        u = torch.tensor(w.u0, dtype=dt, device="cuda")
+        for _ in range(args.warmup):
+            ctx.integrate(u, 0.0, 0.0, w.m)
+        ctx.synchronize()
+
+        # ---------------- timed region: K integrations of m steps, device-resident state
+        sampler = ClockSampler(local)
+        barrier()
+        sampler.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ctx.integrate(u, 0.0, 0.0, w.m)
+        ev1.record(stream)
+        ev1.synchronize()
+        barrier()
+        sampler.stop()
+        ms = ev0.elapsed_time(ev1)
+        ctx.synchronize()                       # raises on a device-side timeout
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        value = world * N * w.m * args.steps / (ms_max * 1e-3)
+
+        # ---------------- per-kernel durations (CUDA events around each op of one step)
+        kinds = {}
+        for _ in range(3):
+            for kind, kms in ctx.profile_step(u):
+                kinds.setdefault(kind, []).append(kms)
+        tc_ms = statistics.mean(kinds.get(4, kinds.get(3, [float("nan")])))
+        stencil_ms = statistics.mean(kinds.get(2, [float("nan")]))
+        step_kernel_ms = {k: sum(v) / 3.0 for k, v in kinds.items()}
+
+        # ---------------- end to end through the C ABI with host buffers
+        u_host = torch.tensor(w.u0, dtype=dt).pin_memory()
+        ctx.integrate_host(u_host, 0.0, 0.0, w.m)          # warm (allocates its device state)
+        barrier()
+        e2e_steps = max(2, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ctx.integrate_host(u_host, 0.0, 0.0, w.m)
+        e2e_s = time.perf_counter() - t0
+        barrier()
+        e2e_value = world * N * w.m * e2e_steps / e2e_s
+
+        # ---------------- accuracy and the FP64 GPU form on the same grid
+        acc = {}
+        if not args.no_fp64 and rank == 0:
+            from oracle import adr_oracle as O
+            um = torch.tensor(w.u0, dtype=dt, device="cuda")
+            ctx.integrate(um, 0.0, w.m * w.tau, w.m)
+            ctx.synchronize()
+            c64 = adr.Context(w.dims, w.tau, "lawson4", "fp64", stream=stream)
+            c64.set_coeffs(w.a_nodes, w.b, w.r_poly)
+            ud = torch.tensor(w.u0, dtype=torch.float64, device="cuda")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c64.integrate(ud, 0.0, w.m * w.tau, w.m)
+            e1.record(stream)
+            e1.synchronize()
+            f64_ms = e0.elapsed_time(e1)
+            acc = {"rel_l2_vs_fp64_gpu": O.rel_l2(um.cpu().numpy(), ud.cpu().numpy()),
+                   "rel_inf_vs_fp64_gpu": O.rel_inf(um.cpu().numpy(), ud.cpu().numpy()),
+                   "fp64_gpu": {"value": N * w.m / (f64_ms * 1e-3), "unit": UNIT,
+                                "ms_per_integration": f64_ms}}
+            c64.close()
+        launches = ctx.kernels_per_step() * w.m * args.steps
+        ctx.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # ---------------- roofline of the dominant kernel (the mu-mode contraction)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+        hbm_peak, bf16_peak, peak_src = peaks["hbm_gbs"], peaks["bf16_tflops_sustained"], "measured"
+    except (OSError, KeyError, ValueError):
+        hbm_peak, bf16_peak, peak_src = 6800.0, 1700.0, "fallback"
+    n = w.dims[0]
+    bytes_per_launch = 8.0 * N                       # read X, write Y (FP32)
+    hbm_gbs = bytes_per_launch / (tc_ms * 1e-3) / 1e9
+    if args.precision == "bf16x3":
+        flops = 6 * 2.0 * n * N                      # six BF16 products per multiply-add
+        tflops = flops / (tc_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                "frac": tflops / bf16_peak, "traffic": None,
+                "kernel": "tc_contract_kernel (mu-mode contraction, tcgen05 kind::f16)",
+                "launch_ms": tc_ms, "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / hbm_peak,
+                "peak_source": f"{peak_src} bf16 sustained"}
+    else:
+        roof = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": hbm_gbs / hbm_peak, "traffic": None, "kernel": "contract_kernel (SIMT)",
+                "launch_ms": tc_ms, "peak_source": f"{peak_src} hbm"}
+    roof["stencil_launch_ms"] = stencil_ms
+    roof["stencil_hbm_gbs_3arrays"] = 12.0 * N / (stencil_ms * 1e-3) / 1e9
+
+    cpu = None
+    if not args.no_cpu:
+        one = oracle_step_timer(w)
+        dt_cpu = one()
+        cpu = {"value": N / dt_cpu, "unit": UNIT, "cores": _CORES, "kind": "oracle",
+               "sample": f"1 Lawson4 time step of the {n}^3 workload ({dt_cpu:.1f} s)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16x3": "bf16x3+f32", "fp32": "f32", "fp64": "f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"3d_{n}^3_lawson4_T0.1_m{w.m}", "grid": list(w.dims), "scheme": "lawson4",
+                   "precision": args.precision, "tau": w.tau, "time_steps_per_bench_step": w.m,
+                   "parallelism": f"replicas{world}",
+                   "l2": "working set per time step > 1 GB (inputs larger than L2)"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * (8 if dt == torch.float64 else 4),
+                "d2h_bytes_per_step": N * (8 if dt == torch.float64 else 4)},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": sampler.summary(),
+        "setup_s": setup_s,
+        "kernel_ms_per_time_step": {str(k): v for k, v in step_kernel_ms.items()},
+    }
+    line.update(acc)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

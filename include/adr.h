@@ -125,9 +125,21 @@ adr_status adr_eval_rhs(adr_ctx* ctx, const void* u_dev, void* F_out, void* g_ou
 adr_status adr_apply_exp(adr_ctx* ctx, double c, const void* v_dev, void* y_dev);
 adr_status adr_apply_phi(adr_ctx* ctx, int k, const void* v_dev, void* y_dev);
 
+/* Wait for the context's stream and report device-side failures: returns
+ * ADR_ERR_TIMEOUT (and clears the flag) when a bounded wait inside a tensor-core
+ * kernel gave up since the last call. */
+adr_status adr_synchronize(adr_ctx* ctx);
+
 /* Host-side facts of the current operator: kappa(V_mu) per direction (0 when the
  * spectrum is complex), lambda*a_max, and beta. Any pointer may be NULL. */
 adr_status adr_get_info(const adr_ctx* ctx, double kappa[3], double* abar, double beta[3]);
+
+/* One adr_step with a CUDA event recorded on the context stream around every enqueued
+ * operation (no graph). Writes, for the i-th operation, its duration in ms[i] and its kind
+ * in kind[i] (0 memset, 1 max-abs reduction, 2 stencil, 3 SIMT contraction,
+ * 4 tensor-core contraction) and the count in *n_ops. Synchronous. ADR_ERR_ARG if the step
+ * has more than max_ops operations. */
+adr_status adr_profile_step(adr_ctx* ctx, void* u_dev, int max_ops, float* ms, int* kind, int* n_ops);
 
 /* Number of kernels one adr_step launches (for launch accounting). */
 int adr_kernels_per_step(const adr_ctx* ctx);

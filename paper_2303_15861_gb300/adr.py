@@ -58,6 +58,8 @@ def load_library(path: str = LIB_PATH):
         "adr_eval_rhs": (ip, [vp, vp, vp, vp]),
         "adr_apply_exp": (ip, [vp, C.c_double, vp, vp]),
         "adr_apply_phi": (ip, [vp, ip, vp, vp]),
+        "adr_synchronize": (ip, [vp]),
+        "adr_profile_step": (ip, [vp, vp, ip, C.POINTER(C.c_float), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "adr_get_info": (ip, [vp, dp, dp, dp]),
         "adr_kernels_per_step": (ip, [vp]),
         "adr_last_error": (C.c_char_p, [vp]),
@@ -159,6 +161,21 @@ def adr_apply_phi(ctx, k, v, y):
     _check(_lib.adr_apply_phi(ctx, int(k), _ptr(v), _ptr(y)), ctx)
 
 
+def adr_synchronize(ctx):
+    """Wait for the context stream; raises AdrError(ADR_ERR_TIMEOUT) if a bounded device
+    wait gave up."""
+    _check(_lib.adr_synchronize(ctx), ctx)
+
+
+def adr_profile_step(ctx, u, max_ops=256):
+    """One step with per-operation CUDA-event timing; returns [(kind, ms), ...]."""
+    ms = (C.c_float * max_ops)()
+    kind = (C.c_int * max_ops)()
+    n = C.c_int()
+    _check(_lib.adr_profile_step(ctx, _ptr(u), int(max_ops), ms, kind, C.byref(n)), ctx)
+    return [(int(kind[i]), float(ms[i])) for i in range(n.value)]
+
+
 def adr_get_info(ctx):
     kappa = (C.c_double * 3)()
     abar = C.c_double()
@@ -213,6 +230,12 @@ class Context:
 
     def info(self):
         return adr_get_info(self.ctx)
+
+    def synchronize(self):
+        adr_synchronize(self.ctx)
+
+    def profile_step(self, u):
+        return adr_profile_step(self.ctx, u)
 
     def kernels_per_step(self):
         return adr_kernels_per_step(self.ctx)

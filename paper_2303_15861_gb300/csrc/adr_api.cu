@@ -34,7 +34,13 @@ using adr::StencilArgs;
 
 namespace {
 
-using Op = std::function<cudaError_t(cudaStream_t)>;
+// One enqueued operation of a schedule and the kind of kernel it launches.
+enum OpKind { OP_MEMSET = 0, OP_AMAX = 1, OP_STENCIL = 2, OP_CONTRACT_SIMT = 3, OP_CONTRACT_TC = 4 };
+struct Op {
+    std::function<cudaError_t(cudaStream_t)> fn;
+    int kind;
+    cudaError_t operator()(cudaStream_t s) const { return fn(s); }
+};
 
 thread_local std::string g_create_error;
 
@@ -65,6 +71,14 @@ struct adr_ctx {
     double* d_lam[3] = {nullptr};
     void* ws[6] = {nullptr};
     void* d_host_state = nullptr;
+
+    // mixed precision (tensor cores): sliced factor images, per-row scales, c tau lambda
+    bool tc = false;
+    uint8_t* d_img[4][3] = {{nullptr}};    // 0: E(0.5), 1: E(1), 2: V, 3: V^-1
+    float* d_fsc[4][3] = {{nullptr}};
+    float* d_zt[3] = {nullptr};            // tau * lambda_mu[j] (FP32)
+    unsigned* d_slots = nullptr;           // max-abs slots of the arrays a step produces
+    int* d_err = nullptr;                  // device error word (bounded waits)
 
     // graph cache for adr_integrate
     cudaGraph_t graph = nullptr;
@@ -109,7 +123,57 @@ cudaError_t upload(adr_ctx* c, void** dst, const std::vector<double>& src) {
     return cudaMemcpy(*dst, tmp.data(), bytes, cudaMemcpyHostToDevice);
 }
 
+// Slice an FP64 factor for the tensor-core kernel and upload image + row scales.
+cudaError_t upload_tc(adr_ctx* c, int kind, int m, const std::vector<double>& M) {
+    const adr::TcFactor f = adr::make_tc_factor(M, c->n[m]);
+    cudaError_t e = cudaSuccess;
+    if (!c->d_img[kind][m]) e = cudaMalloc(reinterpret_cast<void**>(&c->d_img[kind][m]), f.img.size());
+    if (e == cudaSuccess && !c->d_fsc[kind][m])
+        e = cudaMalloc(reinterpret_cast<void**>(&c->d_fsc[kind][m]), f.fscale.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_img[kind][m], f.img.data(), f.img.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_fsc[kind][m], f.fscale.data(), f.fscale.size() * sizeof(float), cudaMemcpyHostToDevice);
+    return e;
+}
+
 // ------------------------------------------------------------------ schedule builders
+constexpr int kSlots = 64;
+
+// The ops of one call, plus the max-abs bookkeeping of the mixed path: every array a
+// step produces gets a fresh slot (zeroed at the start of the step) that its producer
+// fills and its tensor-core consumer reads to choose the slicing scale.
+struct Sched {
+    const adr_ctx* c;
+    std::vector<Op> ops;
+    int next = 0;
+    std::vector<std::pair<const void*, int>> slot_of;
+
+    explicit Sched(const adr_ctx* ctx) : c(ctx) {
+        if (c->tc) {
+            unsigned* sl = c->d_slots;
+            ops.push_back({[sl](cudaStream_t s) { return cudaMemsetAsync(sl, 0, kSlots * sizeof(unsigned), s); }, OP_MEMSET});
+        }
+    }
+    unsigned* produce(const void* buf) {
+        if (!c->tc) return nullptr;
+        const int id = next++;
+        for (auto& e : slot_of)
+            if (e.first == buf) { e.second = id; return c->d_slots + id; }
+        slot_of.push_back({buf, id});
+        return c->d_slots + id;
+    }
+    const unsigned* consume(const void* buf) {
+        for (auto& e : slot_of)
+            if (e.first == buf) return c->d_slots + e.second;
+        // not produced in this schedule (a caller's array): measure it first
+        unsigned* sl = produce(buf);
+        const float* x = static_cast<const float*>(buf);
+        const size_t N = c->N;
+        ops.push_back({[x, N, sl](cudaStream_t s) { return adr::launch_amax(x, N, sl, s); }, OP_AMAX});
+        return sl;
+    }
+};
+
 template <typename T>
 ContractArgs<T> mode_args(const adr_ctx* c, int mu, const T* M, const T* X, T* Y) {
     // state viewed as [P][n][Q]; see contract_simt.cu
@@ -134,23 +198,68 @@ ContractArgs<T> mode_args(const adr_ctx* c, int mu, const T* M, const T* X, T* Y
     return a;
 }
 
+enum FactorKind { FK_EXP_HALF = 0, FK_EXP_ONE = 1, FK_V = 2, FK_VINV = 3 };
+
+// One mu-mode pass y = x x_mu M_kind with epilogue (epi, base, alpha, phik).
 template <typename T>
-void push_contract(std::vector<Op>& ops, const ContractArgs<T>& a) {
-    ops.push_back([a](cudaStream_t s) { return adr::launch_contract(a, s); });
+void push_mode(Sched& S, int mu, int kind, const T* x, T* y, int epi = adr::EPI_STORE,
+               const T* base = nullptr, double alpha = 0.0, int phik = 0) {
+    const adr_ctx* c = S.c;
+    if (!c->tc) {
+        const void* M = kind == FK_EXP_HALF ? c->d_E[0][mu - 1] : kind == FK_EXP_ONE ? c->d_E[1][mu - 1]
+                      : kind == FK_V ? c->d_V[mu - 1] : c->d_Vi[mu - 1];
+        auto a = mode_args<T>(c, mu, static_cast<const T*>(M), x, y);
+        a.epi = epi; a.base = base; a.alpha = alpha; a.phik = phik; a.ctau = c->p.tau;
+        for (int m = 0; m < 3; ++m) a.lam[m] = (m < c->dim) ? c->d_lam[m] : nullptr;
+        S.ops.push_back({[a](cudaStream_t s) { return adr::launch_contract(a, s); }, OP_CONTRACT_SIMT});
+        return;
+    }
+    adr::TcArgs a;
+    const int n = c->n[mu - 1];
+    long long Q = 1, P = 1;
+    for (int nu = 1; nu < mu; ++nu) Q *= c->n[nu - 1];
+    for (int nu = mu + 1; nu <= c->dim; ++nu) P *= c->n[nu - 1];
+    a.X = reinterpret_cast<const float*>(x);
+    a.Y = reinterpret_cast<float*>(y);
+    a.fimg = c->d_img[kind][mu - 1];
+    a.fscale = c->d_fsc[kind][mu - 1];
+    a.n = n;
+    a.Q = Q;
+    a.state_is_a = (mu >= 2);
+    a.vec4 = (mu == 1) && (n % 4 == 0) && (reinterpret_cast<uintptr_t>(x) % 16 == 0);
+    a.npos = (mu >= 2) ? P * Q : P;
+    a.nK = (n + 63) / 64;
+    a.nOut = (n + 127) / 128;
+    a.ntiles = ((a.npos + 127) / 128) * a.nOut;
+    if (epi == adr::EPI_PHI) {
+        // the phi scaling is fused into a mode >= 2 pass: decode (q, p) into the other directions
+        a.zmu = c->d_zt[mu - 1];
+        a.zq_a = c->d_zt[0];
+        a.na = c->n[0];
+        a.zq_b = (mu == 3) ? c->d_zt[1] : nullptr;
+        a.zp = (mu == 2 && c->dim == 3) ? c->d_zt[2] : nullptr;
+    }
+    a.epi = epi;
+    a.base = reinterpret_cast<const float*>(base);
+    a.alpha = float(alpha);
+    a.phik = phik;
+    a.amax_in = S.consume(x);
+    a.amax_out = S.produce(y);
+    a.err = c->d_err;
+    S.ops.push_back({[a](cudaStream_t s) { return adr::launch_contract_tc(a, s); }, OP_CONTRACT_TC});
 }
 
 // y = e^{c tau A} x, optionally finished by y = base + alpha * (e^{c tau A} x).
 template <typename T>
-void push_exp(const adr_ctx* c, std::vector<Op>& ops, int ci, const T* x, T* y,
-              const T* base = nullptr, double alpha = 0.0) {
+void push_exp(Sched& S, int ci, const T* x, T* y, const T* base = nullptr, double alpha = 0.0) {
+    const adr_ctx* c = S.c;
     T* t0 = static_cast<T*>(c->ws[4]);
     T* t1 = static_cast<T*>(c->ws[5]);
     const T* in = x;
     for (int mu = 1; mu <= c->dim; ++mu) {
         T* out = (mu == c->dim) ? y : ((mu % 2) ? t0 : t1);
-        auto a = mode_args<T>(c, mu, static_cast<const T*>(c->d_E[ci][mu - 1]), in, out);
-        if (mu == c->dim && base) { a.epi = adr::EPI_AXPY; a.base = base; a.alpha = alpha; }
-        push_contract(ops, a);
+        const bool last = (mu == c->dim) && base;
+        push_mode<T>(S, mu, ci, in, out, last ? adr::EPI_AXPY : adr::EPI_STORE, last ? base : nullptr, alpha);
         in = out;
     }
 }
@@ -158,29 +267,22 @@ void push_exp(const adr_ctx* c, std::vector<Op>& ops, int ci, const T* x, T* y,
 // y = phi_k(tau A) x through the eigenbasis (k = 0 gives e^{tau A}), optionally
 // finished by y = base + alpha * (phi_k(tau A) x).
 template <typename T>
-void push_phi(const adr_ctx* c, std::vector<Op>& ops, int k, const T* x, T* y,
-              const T* base = nullptr, double alpha = 0.0) {
+void push_phi(Sched& S, int k, const T* x, T* y, const T* base = nullptr, double alpha = 0.0) {
+    const adr_ctx* c = S.c;
     T* tmp[2] = {static_cast<T*>(c->ws[4]), static_cast<T*>(c->ws[5])};
     int flip = 0;
     const T* in = x;
-    for (int mu = 1; mu <= c->dim; ++mu) {       // forward: V_mu^-1
+    for (int mu = 1; mu <= c->dim; ++mu) {       // forward: V_mu^-1, phi_k on the last
         T* out = tmp[flip]; flip ^= 1;
-        auto a = mode_args<T>(c, mu, static_cast<const T*>(c->d_Vi[mu - 1]), in, out);
-        if (mu == c->dim) {
-            a.epi = adr::EPI_PHI;
-            a.phik = k;
-            a.ctau = c->p.tau;
-            for (int m = 0; m < 3; ++m) a.lam[m] = (m < c->dim) ? c->d_lam[m] : nullptr;
-        }
-        push_contract(ops, a);
+        if (mu == c->dim) push_mode<T>(S, mu, FK_VINV, in, out, adr::EPI_PHI, nullptr, 0.0, k);
+        else              push_mode<T>(S, mu, FK_VINV, in, out);
         in = out;
     }
     for (int mu = c->dim; mu >= 1; --mu) {       // back: V_mu
         T* out = (mu == 1) ? y : tmp[flip];
         if (mu != 1) flip ^= 1;
-        auto a = mode_args<T>(c, mu, static_cast<const T*>(c->d_V[mu - 1]), in, out);
-        if (mu == 1 && base) { a.epi = adr::EPI_AXPY; a.base = base; a.alpha = alpha; }
-        push_contract(ops, a);
+        const bool last = (mu == 1) && base;
+        push_mode<T>(S, mu, FK_V, in, out, last ? adr::EPI_AXPY : adr::EPI_STORE, last ? base : nullptr, alpha);
         in = out;
     }
 }
@@ -206,14 +308,19 @@ StencilArgs<T> stencil_base(const adr_ctx* c, const T* u) {
     return s;
 }
 
+// Push a stencil op; on the mixed path its outputs (and, if asked, its input) get slots.
 template <typename T>
-void push_stencil(std::vector<Op>& ops, const StencilArgs<T>& s) {
-    ops.push_back([s](cudaStream_t st) { return adr::launch_stencil(s, st); });
+void push_stencil(Sched& S, StencilArgs<T> s, bool record_input = false) {
+    if (S.c->tc) {
+        if (record_input) s.amax_u = S.produce(s.u);
+        for (int j = 0; j < s.nout; ++j) s.amax[j] = S.produce(s.out[j]);
+    }
+    S.ops.push_back({[s](cudaStream_t st) { return adr::launch_stencil(s, st); }, OP_STENCIL});
 }
 
 template <typename T>
 std::vector<Op> build_step(const adr_ctx* c, T* u) {
-    std::vector<Op> ops;
+    Sched S(c);
     const double tau = c->p.tau;
     T* B0 = static_cast<T*>(c->ws[0]);
     T* B1 = static_cast<T*>(c->ws[1]);
@@ -223,54 +330,54 @@ std::vector<Op> build_step(const adr_ctx* c, T* u) {
     case ADR_LAWSON_EULER: {
         auto s = stencil_base<T>(c, u);
         s.nout = 1; s.out[0] = B0; s.cu[0] = 1.0; s.cg[0] = tau;       // W = u + tau g(u)
-        push_stencil(ops, s);
-        push_exp<T>(c, ops, 1, B0, u);                                  // u = e^{tau A} W
+        push_stencil(S, s);
+        push_exp<T>(S, FK_EXP_ONE, B0, u);                               // u = e^{tau A} W
         break;
     }
     case ADR_ETD2RK: {
         auto s1 = stencil_base<T>(c, u);
         s1.nout = 2; s1.out[0] = B0; s1.cF[0] = 1.0;                    // F(u)
         s1.out[1] = B1; s1.cg[1] = 1.0;                                 // G0 = g(u)
-        push_stencil(ops, s1);
-        push_phi<T>(c, ops, 1, B0, B2, u, tau);                          // U = u + tau phi1 F
+        push_stencil(S, s1);
+        push_phi<T>(S, 1, B0, B2, u, tau);                               // U = u + tau phi1 F
         auto s2 = stencil_base<T>(c, B2);
         s2.nx = 1; s2.X[0] = B1;
         s2.nout = 1; s2.out[0] = B0; s2.cg[0] = 1.0; s2.cx[0][0] = -1.0; // D = g(U) - G0
-        push_stencil(ops, s2);
-        push_phi<T>(c, ops, 2, B0, u, B2, tau);                          // u = U + tau phi2 D
+        push_stencil(S, s2);
+        push_phi<T>(S, 2, B0, u, B2, tau);                               // u = U + tau phi2 D
         break;
     }
     case ADR_LAWSON4: {
         T* W = B0; T* X = B1; T* Eu = B2; T* ACC = B3;
         auto s1 = stencil_base<T>(c, u);
         s1.nout = 1; s1.out[0] = W; s1.cu[0] = 1.0; s1.cg[0] = 0.5 * tau;       // u + tau/2 k1
-        push_stencil(ops, s1);
-        push_exp<T>(c, ops, 0, W, X);                                             // U2
-        push_exp<T>(c, ops, 0, u, Eu);                                            // Eu
+        push_stencil(S, s1, /*record_input=*/true);
+        push_exp<T>(S, FK_EXP_HALF, W, X);                                        // U2
+        push_exp<T>(S, FK_EXP_HALF, u, Eu);                                       // Eu
         auto s2 = stencil_base<T>(c, X);
         s2.nx = 1; s2.X[0] = Eu;
         s2.nout = 2;
         s2.out[0] = W; s2.cx[0][0] = 1.0; s2.cg[0] = 0.5 * tau;                  // U3 = Eu + tau/2 k2
         s2.out[1] = ACC; s2.cx[1][0] = 2.0 / 3.0; s2.cu[1] = 1.0 / 3.0; s2.cg[1] = tau / 3.0;
-        push_stencil(ops, s2);
+        push_stencil(S, s2);
         auto s3 = stencil_base<T>(c, W);
         s3.nx = 2; s3.X[0] = Eu; s3.X[1] = ACC;
         s3.nout = 2;
         s3.out[0] = X; s3.cx[0][0] = 1.0; s3.cg[0] = tau;                         // Eu + tau k3
         s3.out[1] = ACC; s3.cx[1][1] = 1.0; s3.cg[1] = tau / 3.0;                 // ACC += tau/3 k3
-        push_stencil(ops, s3);
-        push_exp<T>(c, ops, 0, X, W);                                             // U4
-        push_exp<T>(c, ops, 0, ACC, X);                                           // E ACC
+        push_stencil(S, s3);
+        push_exp<T>(S, FK_EXP_HALF, X, W);                                        // U4
+        push_exp<T>(S, FK_EXP_HALF, ACC, X);                                      // E ACC
         auto s4 = stencil_base<T>(c, W);
         s4.nx = 1; s4.X[0] = X;
         s4.nout = 1; s4.out[0] = u; s4.cx[0][0] = 1.0; s4.cg[0] = tau / 6.0;     // u+ = E ACC + tau/6 k4
-        push_stencil(ops, s4);
+        push_stencil(S, s4);
         break;
     }
     default:
         break;
     }
-    return ops;
+    return std::move(S.ops);
 }
 
 std::vector<Op> step_ops(const adr_ctx* c, void* u) {
@@ -312,7 +419,9 @@ adr_status adr_create(const adr_params* p, void* cuda_stream, adr_ctx** out) {
     if (p->precision != ADR_FP64 && p->precision != ADR_FP32 && p->precision != ADR_MIXED_BF16X3)
         return fail(nullptr, ADR_ERR_ARG, "unknown precision");
     if (p->precision == ADR_MIXED_BF16X3)
-        return fail(nullptr, ADR_ERR_UNSUPPORTED, "ADR_MIXED_BF16X3 needs the tensor-core kernel");
+        for (int m = 0; m < p->dim; ++m)
+            if (p->n[m] > 512)
+                return fail(nullptr, ADR_ERR_ARG, "ADR_MIXED_BF16X3 supports n <= 512 per direction");
     size_t N = 1, nodes = 1;
     for (int m = 0; m < p->dim; ++m) { N *= size_t(p->n[m]); nodes *= size_t(p->n[m] + 2); }
     if (N > (size_t(1) << 31) - 1) return fail(nullptr, ADR_ERR_ARG, "grid too large");
@@ -328,6 +437,16 @@ adr_status adr_create(const adr_params* p, void* cuda_stream, adr_ctx** out) {
     c->nodes = nodes;
     c->fp64 = (p->precision == ADR_FP64);
     c->esize = c->fp64 ? 8 : 4;
+    c->tc = (p->precision == ADR_MIXED_BF16X3);
+    {
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&c->d_err), sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+        if (e == cudaSuccess && c->tc) e = cudaMalloc(reinterpret_cast<void**>(&c->d_slots), kSlots * sizeof(unsigned));
+        if (e != cudaSuccess) {
+            adr_destroy(c.release());
+            return fail(nullptr, ADR_ERR_ALLOC, std::string("context: ") + cudaGetErrorString(e));
+        }
+    }
     for (auto& w : c->ws) {
         cudaError_t e = cudaMalloc(&w, N * c->esize);
         if (e != cudaSuccess) {
@@ -384,6 +503,10 @@ adr_status adr_set_coeffs(adr_ctx* c, int instance, const double* a_nodes, const
             }
             e = upload(c, &c->d_E[ci][m], *E);
             if (e != cudaSuccess) return cuda_fail(c, e, "upload E");
+            if (c->tc) {
+                e = upload_tc(c, ci, m, *E);
+                if (e != cudaSuccess) return cuda_fail(c, e, "upload sliced E");
+            }
         }
         const adr::Eigen1D eg = adr::eigen_closed_form(c->f[m]);
         c->kappa[m] = eg.real ? eg.kappa : 0.0;
@@ -392,6 +515,14 @@ adr_status adr_set_coeffs(adr_ctx* c, int instance, const double* a_nodes, const
         if (e == cudaSuccess) e = upload(c, &c->d_Vi[m], eg.Vinv);
         if (e == cudaSuccess && !c->d_lam[m]) e = cudaMalloc(reinterpret_cast<void**>(&c->d_lam[m]), c->n[m] * sizeof(double));
         if (e == cudaSuccess) e = cudaMemcpy(c->d_lam[m], eg.lam.data(), c->n[m] * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && c->tc) e = upload_tc(c, FK_V, m, eg.V);
+        if (e == cudaSuccess && c->tc) e = upload_tc(c, FK_VINV, m, eg.Vinv);
+        if (e == cudaSuccess && c->tc) {
+            std::vector<float> zt(c->n[m]);
+            for (int j = 0; j < c->n[m]; ++j) zt[j] = static_cast<float>(c->p.tau * eg.lam[j]);
+            if (!c->d_zt[m]) e = cudaMalloc(reinterpret_cast<void**>(&c->d_zt[m]), zt.size() * sizeof(float));
+            if (e == cudaSuccess) e = cudaMemcpy(c->d_zt[m], zt.data(), zt.size() * sizeof(float), cudaMemcpyHostToDevice);
+        }
         if (e != cudaSuccess) return cuda_fail(c, e, "upload eigenpairs");
     }
     if (needs_phi(c->p.scheme)) {
@@ -475,9 +606,7 @@ adr_status adr_integrate_host(adr_ctx* c, void* u_host, double t0, double T, int
     if (st != ADR_OK) return st;
     e = cudaMemcpyAsync(u_host, c->d_host_state, bytes, cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "D2H");
-    e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
-    return ADR_OK;
+    return adr_synchronize(c);
 }
 
 adr_status adr_eval_rhs(adr_ctx* c, const void* u, void* F_out, void* g_out) {
@@ -485,16 +614,16 @@ adr_status adr_eval_rhs(adr_ctx* c, const void* u, void* F_out, void* g_out) {
     if (st != ADR_OK) return st;
     if (!u || (!F_out && !g_out)) return fail(c, ADR_ERR_ARG, "NULL array");
     if (u == F_out || u == g_out) return fail(c, ADR_ERR_ARG, "output aliases input");
-    std::vector<Op> ops;
+    Sched S(c);
     auto fill = [&](auto* uu, auto* F, auto* g) {
         auto s = stencil_base(c, uu);
         if (F) { s.out[s.nout] = F; s.cF[s.nout] = 1.0; ++s.nout; }
         if (g) { s.out[s.nout] = g; s.cg[s.nout] = 1.0; ++s.nout; }
-        push_stencil(ops, s);
+        push_stencil(S, s);
     };
     if (c->fp64) fill(static_cast<const double*>(u), static_cast<double*>(F_out), static_cast<double*>(g_out));
     else         fill(static_cast<const float*>(u), static_cast<float*>(F_out), static_cast<float*>(g_out));
-    return run_ops(c, ops, "adr_eval_rhs");
+    return run_ops(c, S.ops, "adr_eval_rhs");
 }
 
 adr_status adr_apply_exp(adr_ctx* c, double cc, const void* v, void* y) {
@@ -505,10 +634,10 @@ adr_status adr_apply_exp(adr_ctx* c, double cc, const void* v, void* y) {
     if (cc == 0.5) ci = 0;
     if (cc == 1.0) ci = 1;
     if (ci < 0) return fail(c, ADR_ERR_ARG, "c must be 0.5 or 1");
-    std::vector<Op> ops;
-    if (c->fp64) push_exp<double>(c, ops, ci, static_cast<const double*>(v), static_cast<double*>(y));
-    else         push_exp<float>(c, ops, ci, static_cast<const float*>(v), static_cast<float*>(y));
-    return run_ops(c, ops, "adr_apply_exp");
+    Sched S(c);
+    if (c->fp64) push_exp<double>(S, ci, static_cast<const double*>(v), static_cast<double*>(y));
+    else         push_exp<float>(S, ci, static_cast<const float*>(v), static_cast<float*>(y));
+    return run_ops(c, S.ops, "adr_apply_exp");
 }
 
 adr_status adr_apply_phi(adr_ctx* c, int k, const void* v, void* y) {
@@ -517,10 +646,50 @@ adr_status adr_apply_phi(adr_ctx* c, int k, const void* v, void* y) {
     if (!v || !y || v == y) return fail(c, ADR_ERR_ARG, "NULL or aliased array");
     if (k < 0 || k > 2) return fail(c, ADR_ERR_ARG, "k must be 0, 1 or 2");
     if (!c->eig_real) return fail(c, ADR_ERR_COMPLEX_SPECTRUM, "A_mu has no real eigenbasis");
-    std::vector<Op> ops;
-    if (c->fp64) push_phi<double>(c, ops, k, static_cast<const double*>(v), static_cast<double*>(y));
-    else         push_phi<float>(c, ops, k, static_cast<const float*>(v), static_cast<float*>(y));
-    return run_ops(c, ops, "adr_apply_phi");
+    Sched S(c);
+    if (c->fp64) push_phi<double>(S, k, static_cast<const double*>(v), static_cast<double*>(y));
+    else         push_phi<float>(S, k, static_cast<const float*>(v), static_cast<float*>(y));
+    return run_ops(c, S.ops, "adr_apply_phi");
+}
+
+adr_status adr_profile_step(adr_ctx* c, void* u, int max_ops, float* ms, int* kind, int* n_ops) {
+    adr_status st = check_ready(c);
+    if (st != ADR_OK) return st;
+    if (!u || !ms || !kind || !n_ops || max_ops <= 0) return fail(c, ADR_ERR_ARG, "NULL argument");
+    const auto ops = step_ops(c, u);
+    if (int(ops.size()) > max_ops) return fail(c, ADR_ERR_ARG, "max_ops too small");
+    std::vector<cudaEvent_t> ev(ops.size() + 1);
+    for (auto& e : ev) cudaEventCreate(&e);
+    cudaError_t e = cudaEventRecord(ev[0], c->stream);
+    for (size_t i = 0; i < ops.size() && e == cudaSuccess; ++i) {
+        e = ops[i](c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[i + 1], c->stream);
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev.back());
+    for (size_t i = 0; i < ops.size() && e == cudaSuccess; ++i) {
+        e = cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+        kind[i] = ops[i].kind;
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    if (e != cudaSuccess) return cuda_fail(c, e, "adr_profile_step");
+    *n_ops = int(ops.size());
+    return ADR_OK;
+}
+
+adr_status adr_synchronize(adr_ctx* c) {
+    if (!c) return ADR_ERR_ARG;
+    cudaError_t e = c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+    int err = 0;
+    e = cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read error word");
+    if (err != 0) {
+        cudaMemset(c->d_err, 0, sizeof(int));
+        char buf[96];
+        std::snprintf(buf, sizeof buf, "a bounded device wait timed out (code 0x%x)", err);
+        return fail(c, ADR_ERR_TIMEOUT, buf);
+    }
+    return ADR_OK;
 }
 
 adr_status adr_get_info(const adr_ctx* c, double kappa[3], double* abar, double beta[3]) {
@@ -558,6 +727,11 @@ void adr_destroy(adr_ctx* c) {
     for (auto& p : c->d_lam) { void* q = p; free_dev(q); p = nullptr; }
     for (auto& p : c->ws) free_dev(p);
     free_dev(c->d_host_state);
+    for (auto& row : c->d_img) for (auto& p : row) { void* q = p; free_dev(q); p = nullptr; }
+    for (auto& row : c->d_fsc) for (auto& p : row) { void* q = p; free_dev(q); p = nullptr; }
+    for (auto& p : c->d_zt) { void* q = p; free_dev(q); p = nullptr; }
+    { void* q = c->d_slots; free_dev(q); c->d_slots = nullptr; }
+    { void* q = c->d_err; free_dev(q); c->d_err = nullptr; }
     delete c;
 }
 

@@ -62,6 +62,7 @@ struct StencilArgs {
     double cg[kMaxOut] = {0, 0};
     double cF[kMaxOut] = {0, 0};
     unsigned* amax[kMaxOut] = {nullptr, nullptr};  // optional max|out_j| (float bits)
+    unsigned* amax_u = nullptr;                      // optional max|u| over the interior
 };
 
 // K2 (SIMT): strided batched contraction C[b] = A[b] * B[b] with a fused epilogue.
@@ -86,6 +87,48 @@ struct ContractArgs {
     const double* lam[3] = {nullptr, nullptr, nullptr};
     int n1 = 1, n2 = 1;
 };
+
+// K2 (tensor cores, mixed precision): see contract_tc.cu for the exact-slice split.
+// The factor M (n x n) is passed as a pre-sliced, pre-swizzled image: for output tile
+// o (128 rows) and K chunk c (64 columns), four 16 KB tiles F0, F1, 2^-8 F1, 2^-8 F2.
+struct TcArgs {
+    const float* X = nullptr;
+    float* Y = nullptr;
+    const uint8_t* fimg = nullptr;   // factor image (tc_factor_image_bytes(n) bytes)
+    const float* fscale = nullptr;   // per output row i: 2^(e_i - 7)
+    int n = 0;                       // extent of the contracted direction
+    long long Q = 1;                 // product of the faster extents (1 for mode 1)
+    long long npos = 0;              // positions P*Q (mode >= 2) or fibres P (mode 1)
+    int nK = 0, nOut = 0;            // K chunks of 64, output tiles of 128
+    long long ntiles = 0;
+    bool state_is_a = true;          // modes >= 2: true; mode 1: false
+    bool vec4 = false;               // mode 1: X rows 16-byte aligned (n % 4 == 0)
+    int epi = EPI_STORE;
+    const float* base = nullptr;
+    float alpha = 0.f;
+    int phik = 1;
+    // EPI_PHI (modes >= 2): z = zmu[i] + zq_a[q % na] + zq_b[q / na] + zp[p], with
+    // tau*lambda tables (FP32) of the contracted direction and of the others
+    const float* zmu = nullptr;
+    const float* zq_a = nullptr;
+    const float* zq_b = nullptr;
+    const float* zp = nullptr;
+    int na = 1;
+    const unsigned* amax_in = nullptr;                  // max|X| (float bits)
+    unsigned* amax_out = nullptr;                       // max|Y| accumulator (float bits)
+    int* err = nullptr;                                 // bounded-wait timeout flags
+};
+
+// Host: slice an FP64 factor into the tensor-core image (see contract_tc.cu).
+struct TcFactor {
+    std::vector<uint8_t> img;
+    std::vector<float> fscale;
+};
+TcFactor make_tc_factor(const std::vector<double>& M, int n);
+int tc_factor_image_bytes(int n);
+
+cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s);
+cudaError_t launch_amax(const float* x, size_t n, unsigned* slot, cudaStream_t s);
 
 cudaError_t launch_stencil(const StencilArgs<double>& a, cudaStream_t s);
 cudaError_t launch_stencil(const StencilArgs<float>& a, cudaStream_t s);

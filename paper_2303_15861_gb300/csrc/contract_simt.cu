@@ -10,37 +10,10 @@
 #include <cuda_runtime.h>
 
 #include "adr_internal.h"
+#include "phi_device.cuh"
 
 namespace adr {
 namespace {
-
-// phi_k(z) for k = 0, 1, 2 (Section 1; Theorem 2.4). Near zero (|z| < 1) the Taylor
-// series sum_j z^j/(j+k)! is summed in FP64, which avoids the cancellation of the
-// closed forms; elsewhere the closed forms with expm1.
-__device__ __forceinline__ double phi_series(int k, double z) {
-    double fact = 1.0;
-    for (int j = 2; j <= k; ++j) fact *= j;
-    double term = 1.0 / fact, sum = 0.0;
-    for (int j = 0; j < 22; ++j) {
-        sum += term;
-        term *= z / double(j + k + 1);
-    }
-    return sum;
-}
-
-__device__ __forceinline__ double phi_eval(int k, double z) {
-    if (k == 0) return exp(z);
-    if (fabs(z) < 1.0) return phi_series(k, z);
-    const double e = expm1(z);
-    return k == 1 ? e / z : (e - z) / (z * z);
-}
-
-__device__ __forceinline__ float phi_eval(int k, float z) {
-    if (k == 0) return expf(z);
-    if (fabsf(z) < 1.0f) return float(phi_series(k, double(z)));   // FP64 near zero
-    const float e = expm1f(z);
-    return k == 1 ? e / z : (e - z) / (z * z);
-}
 
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))

@@ -1,0 +1,512 @@
+// K2 (tensor cores): mu-mode contraction Y = X x_mu M of the mixed-precision path on the
+// 5th-generation tensor cores (tcgen05.mma kind::f16, BF16 operands, FP32 accumulators
+// in TMEM), with the pointwise phi_k scaling (K3) and the stage axpy (K4) fused into the
+// epilogue. The mu-mode product is the one of Section 1 / Section 5.2:
+// e^{A_d (+) ... (+) A_1} v = vec(V x_1 e^{A_1} x_2 ... x_d e^{A_d}).
+//
+// Exact-slice split. The FP32 state x gets one power-of-two scale 2^es from the max-abs
+// that its producing kernel recorded; each row i of the FP64 factor (output index) gets
+// its own scale 2^e_i. With integer slices |s_j|, |f_j| <= 128 (exact in BF16):
+//     x = 2^(es-7) (s0 + 2^-8 s1 + 2^-16 s2),   f = 2^(e_i-7) (f0 + 2^-8 f1 + 2^-16 f2),
+//     sum_k x f = 2^(es+e_i-14) (D0 + 2^-8 D1),
+//     D0 = S0.F0,  D1 = S0.F1 + S1.F0 + S0.F2' + S2'.F0 + S1.F1'    (six MMAs per K step)
+// with F1' = 2^-8 F1, F2' = 2^-8 F2, S2' = 2^-8 S2 (exact scalings). Every term of D0 is
+// an integer of magnitude < 2^14 and |D0| < 2^24 for K <= 512, so D0 is exact in the FP32
+// accumulator whatever rounding the tensor core applies: the dominant, same-signed part
+// of a heat-kernel product carries no accumulation bias. D1 is weighted 2^-8 and its
+// terms have random signs. Representation errors are 2^-24 of the scales (as FP32).
+//
+// CTA organisation (persistent, one CTA per SM, 416 threads):
+//   warps 0-7  producers: load the FP32 state chunk (coalesced; the next chunk's loads are
+//              in flight while the current one is sliced), slice it into S0, S1, S2' and
+//              store the 128B-swizzled K-major tiles; thread 0 also bulk-copies the
+//              pre-sliced, pre-swizzled factor tiles (F0, F1, F1', F2') of the chunk.
+//   warps 8-11 epilogue: tcgen05.ld the two accumulators, combine, fused op, store,
+//              record max|y| for the next pass.
+//   warp 12    one thread issues the tcgen05.mma chain and commits to mbarriers.
+// Two pipeline stages of 112 KB (K chunk of 64) and two TMEM accumulator sets
+// (2 x (128 + 128) columns) let loads, MMAs and the epilogue of consecutive tiles overlap.
+//
+// Operand roles. Modes mu >= 2 (positions contiguous in memory): A = state (128
+// positions), B = factor (128 outputs), D[pos][i]; the epilogue store is coalesced along
+// positions. Mode 1 (fibres contiguous along K): A = factor (128 outputs), B = state
+// (128 fibres), D[i][fibre]; the store is coalesced along outputs.
+//
+// Every mbarrier wait is bounded (about 2 s of clock64 cycles); on timeout the kernel
+// records an error code, stops its roles, drains its MMAs and frees TMEM.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "adr_internal.h"
+#include "phi_device.cuh"
+
+namespace adr {
+namespace {
+
+constexpr int kRows = 128;                       // UMMA M, TMEM lanes
+constexpr int kCols = 128;                       // UMMA N, columns per accumulator
+constexpr int kChunk = 64;                       // K per stage: one 128-byte bf16 row
+constexpr int kTileBytes = kRows * kChunk * 2;   // one slice tile: 16 KB
+constexpr int kStateBytes = 3 * kTileBytes;      // S0, S1, S2'
+constexpr int kFactorBytes = 4 * kTileBytes;     // F0, F1, F1', F2'
+constexpr int kStageBytes = kStateBytes + kFactorBytes;
+constexpr int kStages = 2;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024;   // + alignment slack
+constexpr int kProducerWarps = 8;
+constexpr int kMmaWarp = kProducerWarps + 4;
+constexpr int kThreads = (kMmaWarp + 1) * 32;   // 416
+constexpr uint32_t kTmemCols = 512;
+constexpr long long kWaitCycles = 4000000000LL;           // bounded waits (~2 s)
+
+// MMA instruction descriptor: kind::f16, D = F32, A = B = BF16, both K-major,
+// N = 128 (bits 17-22: N>>3), M = 128 (bits 24-28: M>>4).
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kCols >> 3) << 17) |
+                            (uint32_t(kRows >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    return uint64_t((saddr & 0x3FFFFu) >> 4) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) |
+           (uint64_t(1) << 46) | (uint64_t(2) << 61);
+}
+
+// byte offset of the 16-byte chunk j (8 bf16 along K) of row r in a 128B-swizzled tile
+__device__ __forceinline__ uint32_t swz(int r, int j) {
+    return uint32_t((r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on phase `parity`; false on timeout (error recorded) or when the CTA aborts.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code, volatile int* abort_flag) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            if (err) atomicOr(err, code);
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+// Load 16 columns of D0 and of D1 for this warp's 32 lanes, then wait for both.
+__device__ __forceinline__ void tmem_ld_pair(uint32_t ta, uint32_t tb, float (&a)[16], float (&b)[16]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%33];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(ta), "r"(tb)
+        : "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        a[j] = __uint_as_float(r[j]);
+        b[j] = __uint_as_float(r[16 + j]);
+    }
+}
+
+// Split y = x * 2^(7-es) (|y| < 128) into integer slices s0, s1 and s2' = 2^-8 s2.
+// Every step is exact in FP32; the slices have at most 8 significant bits, so their
+// BF16 patterns are the upper halves of the FP32 patterns.
+__device__ __forceinline__ void split3(float y, uint32_t& b0, uint32_t& b1, uint32_t& b2) {
+    const float s0 = rintf(y);
+    const float y1 = (y - s0) * 256.f;
+    const float s1 = rintf(y1);
+    const float s2 = rintf((y1 - s1) * 256.f) * 0.00390625f;
+    b0 = __float_as_uint(s0) >> 16;
+    b1 = __float_as_uint(s1) >> 16;
+    b2 = __float_as_uint(s2) >> 16;
+}
+
+// Slice v[o .. o+7] (8 consecutive K values) and store them as chunk j of row r of the
+// three tiles.
+__device__ __forceinline__ void slice_store8(const float (&v)[32], int o, float sc, uint32_t tile0, int r, int j) {
+    uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        uint32_t a0, a1, a2, c0, c1, c2;
+        split3(v[o + 2 * e] * sc, a0, a1, a2);
+        split3(v[o + 2 * e + 1] * sc, c0, c1, c2);
+        w0[e] = a0 | (c0 << 16);
+        w1[e] = a1 | (c1 << 16);
+        w2[e] = a2 | (c2 << 16);
+    }
+    const uint32_t off = swz(r, j);
+    st_shared_v4(tile0 + off, make_uint4(w0[0], w0[1], w0[2], w0[3]));
+    st_shared_v4(tile0 + kTileBytes + off, make_uint4(w1[0], w1[1], w1[2], w1[3]));
+    st_shared_v4(tile0 + 2 * kTileBytes + off, make_uint4(w2[0], w2[1], w2[2], w2[3]));
+}
+
+// Producer helpers (force-inlined so the 32 values of a thread stay in registers).
+// Item `it` of a CTA is K chunk (it % nK) of its (it / nK)-th tile.
+template <bool STATE_IS_A>
+__device__ __forceinline__ void produce_load(const TcArgs& p, long long it, long long items, int t, float (&v)[32]) {
+    if (it >= items) return;
+    const long long tile = blockIdx.x + (it / p.nK) * gridDim.x;
+    const long long pt = tile / p.nOut;
+    const int k0 = int(it % p.nK) * kChunk;
+    const int n = p.n;
+    if (STATE_IS_A) {
+        // thread t: position row t % 128, K half t / 128; 32 strided, warp-coalesced loads
+        const int row = t & (kRows - 1), half = t >> 7;
+        const long long pos = pt * kRows + row;
+        const bool valid = pos < p.npos;
+        const long long Q = p.Q;
+        const long long pp = valid ? pos / Q : 0, qq = valid ? pos % Q : 0;
+        const int kb = k0 + 32 * half;
+        const float* xr = p.X + (pp * n + kb) * Q + qq;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = (valid && kb + i < n) ? __ldg(xr + (long long)i * Q) : 0.f;
+    } else {
+        // thread t: 16-byte chunk j = t % 8 of fibre rows t / 8 + 32 rr
+        const int j = t & 7, r0 = t >> 3;
+        const int kb = k0 + 8 * j;
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+            const long long f = pt * kRows + r0 + 32 * rr;
+            const bool valid = f < p.npos;
+            const float* xr = p.X + (valid ? f : 0) * n + kb;
+            if (valid && p.vec4 && kb + 8 <= n) {
+                const float4 a = __ldg(reinterpret_cast<const float4*>(xr));
+                const float4 b = __ldg(reinterpret_cast<const float4*>(xr) + 1);
+                v[8 * rr + 0] = a.x; v[8 * rr + 1] = a.y; v[8 * rr + 2] = a.z; v[8 * rr + 3] = a.w;
+                v[8 * rr + 4] = b.x; v[8 * rr + 5] = b.y; v[8 * rr + 6] = b.z; v[8 * rr + 7] = b.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[8 * rr + e] = (valid && kb + e < n) ? __ldg(xr + e) : 0.f;
+            }
+        }
+    }
+}
+
+template <bool STATE_IS_A>
+__device__ __forceinline__ void produce_store(const float (&v)[32], int t, float sc, uint32_t sA) {
+    if (STATE_IS_A) {
+        const int row = t & (kRows - 1), half = t >> 7;
+#pragma unroll
+        for (int j4 = 0; j4 < 4; ++j4) slice_store8(v, 8 * j4, sc, sA, row, 4 * half + j4);
+    } else {
+        const int j = t & 7, r0 = t >> 3;
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) slice_store8(v, 8 * rr, sc, sA, r0 + 32 * rr, j);
+    }
+}
+
+// One pipeline item: wait for the stage, start the factor copy, prefetch the next item,
+// slice the current one, publish.
+template <bool STATE_IS_A>
+__device__ __forceinline__ bool produce_step(const TcArgs& p, long long it, long long items, int t, float sc,
+                                             uint32_t sbase, uint32_t bar0, volatile int* abort_flag,
+                                             const float (&cur)[32], float (&nxt)[32]) {
+    const int s = int(it & 1);
+    const uint32_t ph = uint32_t(it >> 1) & 1u;
+    const uint32_t full = bar0 + 8u * s, empty = bar0 + 16u + 8u * s;
+    if (!mbar_wait(empty, ph ^ 1u, p.err, 1, abort_flag)) return false;
+    const uint32_t sA = sbase + s * kStageBytes;
+    const uint32_t sF = sA + kStateBytes;
+    if (t == 0) {
+        const long long tile = blockIdx.x + (it / p.nK) * gridDim.x;
+        const int ot = int(tile % p.nOut);
+        const int c = int(it % p.nK);
+        mbar_arrive_expect_tx(full, kFactorBytes);
+        const uint8_t* src = p.fimg + (size_t(ot) * p.nK + c) * kFactorBytes;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) bulk_g2s(sF + q * kTileBytes, src + q * kTileBytes, kTileBytes, full);
+    }
+    produce_load<STATE_IS_A>(p, it + 1, items, t, nxt);
+    produce_store<STATE_IS_A>(cur, t, sc, sA);
+    fence_proxy_async();
+    mbar_arrive(full);
+    return true;
+}
+
+template <bool STATE_IS_A>
+__global__ void __launch_bounds__(kThreads, 1) tc_contract_kernel(TcArgs p) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bars[9];
+    __shared__ uint32_t tmem_base_s;
+    __shared__ volatile int abort_s;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    const uint32_t bar0 = smem_u32(&bars[0]);
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 16u + 8u * s; };
+    auto accf_bar = [&](int a) { return bar0 + 32u + 8u * a; };
+    auto acce_bar = [&](int a) { return bar0 + 48u + 8u * a; };
+    const uint32_t drain_bar = bar0 + 64u;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(full_bar(s), kProducerWarps * 32 + 1);   // producers + 1 expect_tx arrival
+            mbar_init(empty_bar(s), 1);    // tcgen05.commit
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(accf_bar(a), 1);     // tcgen05.commit
+            mbar_init(acce_bar(a), 128);   // epilogue threads
+        }
+        mbar_init(drain_bar, 1);
+        abort_s = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_s;
+
+    // scale of the state from the max-abs recorded by its producer (amax < 2^es)
+    const float amax = __uint_as_float(*p.amax_in);
+    int es = 0;
+    if (amax > 0.f) frexpf(amax, &es);
+    const float sc = ldexpf(1.f, 7 - es);
+    const float sback = ldexpf(1.f, es - 7);
+
+    const int n = p.n;
+    const long long Q = p.Q;
+
+    if (warp < kProducerWarps) {
+        // ------------------------------------------------------------ producers
+        // 256 threads; each owns 32 state values of a chunk. The loads of the next chunk
+        // are issued before the current one is sliced, so global latency overlaps the ALU work.
+        const int t = threadIdx.x;
+        const long long my_tiles = (p.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
+        const long long items = my_tiles * p.nK;
+        float va[32], vb[32];
+        produce_load<STATE_IS_A>(p, 0, items, t, va);
+        for (long long it = 0; it < items; it += 2) {
+            if (!produce_step<STATE_IS_A>(p, it, items, t, sc, sbase, bar0, &abort_s, va, vb)) break;
+            if (it + 1 >= items) break;
+            if (!produce_step<STATE_IS_A>(p, it + 1, items, t, sc, sbase, bar0, &abort_s, vb, va)) break;
+        }
+    } else if (warp < kProducerWarps + 4) {
+        // ------------------------------------------------------------ epilogue
+        const int ew = warp - kProducerWarps;   // warps 8-11: TMEM lane quarters 0-3                 // TMEM lane quarter of this warp
+        const int row = ew * 32 + lane;
+        long long tl = 0;
+        for (long long tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, ++tl) {
+            const int a = int(tl & 1);
+            const uint32_t ph = uint32_t(tl >> 1) & 1u;
+            const bool waited = mbar_wait(accf_bar(a), ph, p.err, 2, &abort_s);
+            if (!__all_sync(0xffffffffu, waited)) break;   // warp-uniform: TMEM loads are .sync.aligned
+            tc_fence_after();
+            const long long pt = tile / p.nOut;
+            const int ot = int(tile % p.nOut);
+            float vmax = 0.f;
+            // row meaning
+            long long pos = 0, pp = 0, qq = 0;
+            bool rvalid;
+            float zrow = 0.f, rscale = 0.f;
+            int irow = 0;
+            if (STATE_IS_A) {
+                pos = pt * kRows + row;
+                rvalid = pos < p.npos;
+                if (rvalid) { pp = pos / Q; qq = pos % Q; }
+                if (p.epi == EPI_PHI && rvalid) {
+                    // position part of z = tau (l1 + l2 + l3): the directions other than mu
+                    zrow = __ldg(p.zq_a + qq % p.na);
+                    if (p.zq_b) zrow += __ldg(p.zq_b + qq / p.na);
+                    if (p.zp) zrow += __ldg(p.zp + pp);
+                }
+            } else {
+                irow = ot * kCols + row;
+                rvalid = irow < n;
+                if (rvalid) rscale = sback * __ldg(p.fscale + irow);
+            }
+            const uint32_t tbase = tmem + (uint32_t(ew * 32) << 16) + uint32_t(a) * 256u;
+#pragma unroll 1
+            for (int j0 = 0; j0 < kCols; j0 += 16) {
+                float d0[16], d1[16];
+                __syncwarp();
+                tmem_ld_pair(tbase + j0, tbase + 128u + j0, d0, d1);
+                if (!rvalid) continue;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = j0 + j;
+                    long long off;
+                    float scale;
+                    int iout;
+                    if (STATE_IS_A) {
+                        iout = ot * kCols + col;
+                        if (iout >= n) continue;
+                        off = (pp * n + iout) * Q + qq;
+                        scale = sback * __ldg(p.fscale + iout);
+                    } else {
+                        const long long f = pt * kRows + col;
+                        if (f >= p.npos) continue;
+                        iout = irow;
+                        off = f * n + irow;
+                        scale = rscale;
+                    }
+                    float v = fmaf(d1[j], 0.00390625f, d0[j]) * scale;
+                    if (p.epi == EPI_PHI) {
+                        v *= phi_eval(p.phik, zrow + __ldg(p.zmu + iout));
+                    } else if (p.epi == EPI_AXPY) {
+                        v = fmaf(p.alpha, v, __ldg(p.base + off));
+                    }
+                    p.Y[off] = v;
+                    vmax = fmaxf(vmax, fabsf(v));
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(acce_bar(a));
+            for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+            if (lane == 0 && p.amax_out && vmax > 0.f) atomicMax(p.amax_out, __float_as_uint(vmax));
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------------------ MMA issuer
+        long long g = 0, tl = 0;
+        for (long long tile = blockIdx.x; tile < p.ntiles && !abort_s; tile += gridDim.x, ++tl) {
+            const int a = int(tl & 1);
+            const uint32_t aph = uint32_t(tl >> 1) & 1u;
+            if (!mbar_wait(acce_bar(a), aph ^ 1u, p.err, 4, &abort_s)) break;
+            tc_fence_after();
+            const uint32_t d0 = tmem + uint32_t(a) * 256u;
+            const uint32_t d1 = d0 + 128u;
+            bool ok = true;
+            for (int c = 0; c < p.nK; ++c, ++g) {
+                const int s = int(g & 1);
+                const uint32_t ph = uint32_t(g >> 1) & 1u;
+                if (!mbar_wait(full_bar(s), ph, p.err, 8, &abort_s)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t sS = sbase + s * kStageBytes;
+                const uint32_t sF = sS + kStateBytes;
+                const uint64_t S0 = sdesc(sS), S1 = sdesc(sS + kTileBytes), S2 = sdesc(sS + 2 * kTileBytes);
+                const uint64_t F0 = sdesc(sF), F1 = sdesc(sF + kTileBytes), F1s = sdesc(sF + 2 * kTileBytes),
+                               F2s = sdesc(sF + 3 * kTileBytes);
+#pragma unroll
+                for (int kk = 0; kk < kChunk / 16; ++kk) {
+                    const uint64_t adv = uint64_t(kk * 32) >> 4;   // 16 bf16 = 32 bytes along K
+                    const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+                    if (STATE_IS_A) {
+                        tc_mma(d0, S0 + adv, F0 + adv, acc);
+                        tc_mma(d1, S0 + adv, F1 + adv, acc);
+                        tc_mma(d1, S1 + adv, F0 + adv, 1u);
+                        tc_mma(d1, S0 + adv, F2s + adv, 1u);
+                        tc_mma(d1, S2 + adv, F0 + adv, 1u);
+                        tc_mma(d1, S1 + adv, F1s + adv, 1u);
+                    } else {
+                        tc_mma(d0, F0 + adv, S0 + adv, acc);
+                        tc_mma(d1, F1 + adv, S0 + adv, acc);
+                        tc_mma(d1, F0 + adv, S1 + adv, 1u);
+                        tc_mma(d1, F2s + adv, S0 + adv, 1u);
+                        tc_mma(d1, F0 + adv, S2 + adv, 1u);
+                        tc_mma(d1, F1s + adv, S1 + adv, 1u);
+                    }
+                }
+                tc_commit(empty_bar(s));
+            }
+            if (!ok) break;
+            tc_commit(accf_bar(a));
+        }
+        // wait for every MMA this thread issued before TMEM is released
+        tc_commit(drain_bar);
+        {
+            const long long t0 = clock64();
+            while (!mbar_try_wait(drain_bar, 0) && clock64() - t0 < kWaitCycles) {}
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+int g_num_sms = 0;
+
+}  // namespace
+
+cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(tc_contract_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(tc_contract_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        attr_set = true;
+    }
+    if (a.n > 512 || a.n < 1) return cudaErrorInvalidValue;
+    const long long grid = a.ntiles < g_num_sms ? a.ntiles : g_num_sms;
+    if (grid <= 0) return cudaSuccess;
+    if (a.state_is_a)
+        tc_contract_kernel<true><<<unsigned(grid), kThreads, kSmemBytes, s>>>(a);
+    else
+        tc_contract_kernel<false><<<unsigned(grid), kThreads, kSmemBytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+int tc_factor_image_bytes(int n) {
+    const int nK = (n + kChunk - 1) / kChunk, nOut = (n + kCols - 1) / kCols;
+    return nOut * nK * kFactorBytes;
+}
+
+}  // namespace adr

@@ -2,6 +2,7 @@
 // their exponentials and their closed-form eigenpairs (Sections 3 and 5.2).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <stdexcept>
 
 #include "adr_internal.h"
@@ -162,6 +163,69 @@ Eigen1D eigen_closed_form(const Factor1D& f) {
     }
     e.kappa = std::exp(std::fabs(lrho) * (n - 1));
     return e;
+}
+
+namespace {
+uint16_t bf16_bits_exact(double v) {
+    // v has at most 8 significant bits (an integer slice, possibly times 2^-8), so the
+    // upper half of its FP32 pattern is its exact BF16 pattern.
+    const float f = static_cast<float>(v);
+    uint32_t u;
+    std::memcpy(&u, &f, sizeof u);
+    return static_cast<uint16_t>(u >> 16);
+}
+}  // namespace
+
+TcFactor make_tc_factor(const std::vector<double>& M, int n) {
+    // Each row i of M (an output index) is written as 2^(e_i-7) (f0 + 2^-8 f1 + 2^-16 f2)
+    // with integer slices |f_j| <= 128 and max_k |M[i][k]| < 2^e_i; the image stores, per
+    // (output tile of 128 rows, K chunk of 64), the four 16 KB tiles F0, F1, 2^-8 F1, 2^-8 F2
+    // in the 128-byte-swizzled K-major layout the tensor cores read (8-row groups of
+    // 1024 B; 16-byte chunk j of row r at position j ^ (r mod 8)).
+    const int chunk = 64, rows = 128, tile = rows * chunk * 2;
+    const int nK = (n + chunk - 1) / chunk, nOut = (n + rows - 1) / rows;
+    TcFactor out;
+    out.img.assign(size_t(nOut) * nK * 4 * tile, 0);
+    out.fscale.assign(size_t(nOut) * rows, 0.0f);
+    std::vector<double> slices(size_t(n) * n * 4, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double rmax = 0.0;
+        for (int k = 0; k < n; ++k) rmax = std::max(rmax, std::fabs(M[size_t(i) * n + k]));
+        int e = 0;
+        if (rmax > 0.0) std::frexp(rmax, &e);   // rmax < 2^e
+        out.fscale[i] = static_cast<float>(std::ldexp(1.0, e - 7));
+        for (int k = 0; k < n; ++k) {
+            const double y = std::ldexp(M[size_t(i) * n + k], 7 - e);
+            const double f0 = std::nearbyint(y);
+            const double y1 = (y - f0) * 256.0;
+            const double f1 = std::nearbyint(y1);
+            const double f2 = std::nearbyint((y1 - f1) * 256.0);
+            double* sl = &slices[(size_t(i) * n + k) * 4];
+            sl[0] = f0;
+            sl[1] = f1;
+            sl[2] = f1 / 256.0;
+            sl[3] = f2 / 256.0;
+        }
+    }
+    for (int ot = 0; ot < nOut; ++ot)
+        for (int c = 0; c < nK; ++c)
+            for (int q = 0; q < 4; ++q) {
+                uint8_t* t = &out.img[((size_t(ot) * nK + c) * 4 + q) * tile];
+                for (int r = 0; r < rows; ++r) {
+                    const int i = ot * rows + r;
+                    if (i >= n) continue;
+                    for (int j = 0; j < 8; ++j)
+                        for (int e2 = 0; e2 < 8; ++e2) {
+                            const int k = c * chunk + 8 * j + e2;
+                            if (k >= n) continue;
+                            const uint16_t b = bf16_bits_exact(slices[(size_t(i) * n + k) * 4 + q]);
+                            const size_t off = size_t((r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4) + 2 * e2);
+                            t[off] = uint8_t(b & 0xFF);
+                            t[off + 1] = uint8_t(b >> 8);
+                        }
+                }
+            }
+    return out;
 }
 
 double nodal_max(const double* a, size_t count) {

@@ -9,9 +9,7 @@
 // Dirichlet ghosts u = 0. F = g + A u.
 //
 // Layout: u is n3*n2*n1 (x1 fastest), the nodal (a - abar) is (n3+2)(n2+2)(n1+2).
-// Each CTA owns a 32 x 8 column of (x1, x2) and marches along x3, keeping the three
-// u planes it needs in registers / shared memory so that u and a are read from HBM
-// once (plus a one-node halo).
+// A CTA covers 32 x 8 nodes of (x1, x2) and ZCHUNK planes of x3.
 #include <cuda_runtime.h>
 
 #include "adr_internal.h"
@@ -21,7 +19,7 @@ namespace {
 
 constexpr int TX = 32;   // x1 extent of a CTA tile (one warp wide: coalesced rows)
 constexpr int TY = 8;    // x2 extent
-constexpr int ZCHUNK = 16;  // x3 planes per CTA
+constexpr int ZCHUNK = 4;   // x3 planes per thread
 
 template <typename T>
 struct Coefs {
@@ -38,123 +36,104 @@ __device__ __forceinline__ void block_amax(float v, unsigned* slot) {
     if ((threadIdx.x & 31) == 0 && v > 0.f) atomicMax(slot, __float_as_uint(v));
 }
 
-// One pass over the grid. DIM = 2 uses n3 = 1 and no x3 terms.
-template <typename T, int DIM>
+// One pass over the grid. Each thread owns the nodes (i1, i2, z0 .. z0+ZC-1): it issues
+// every load of its column up front (centre column with its x3 halo, the four x1/x2
+// neighbours per plane, the extra stage inputs), all independent and warp-coalesced along
+// x1, so no barrier is needed and many requests are in flight; x1/x2 neighbours are served
+// by L1, x3 neighbours by registers. DIM = 2 has one plane and no x3 terms.
+template <typename T, int DIM, int ZC>
 __global__ void __launch_bounds__(TX * TY) stencil_kernel(StencilArgs<T> p, Coefs<T> c, bool needF) {
-    __shared__ T su[TY + 2][TX + 2];   // u plane with x1/x2 halo
-    __shared__ T sa[TY + 2][TX + 2];   // (a - abar) plane with halo
-
     const int n1 = p.n1, n2 = p.n2, n3 = p.n3;
     const int A1 = n1 + 2, A2 = n2 + 2;
     const long long plane_u = (long long)n1 * n2;
     const long long plane_a = (long long)A1 * A2;
-
-    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    const int i1 = blockIdx.x * TX + tx;
-    const int i2 = blockIdx.y * TY + ty;
-    const int z0 = (DIM == 3) ? blockIdx.z * ZCHUNK : 0;
-    const int z1 = (DIM == 3) ? min(z0 + ZCHUNK, n3) : 1;
+    const int i1 = blockIdx.x * TX + int(threadIdx.x % TX);
+    const int i2 = blockIdx.y * TY + int(threadIdx.x / TX);
+    const int z0 = (DIM == 3) ? int(blockIdx.z) * ZC : 0;
     const bool inside = (i1 < n1) && (i2 < n2);
-    // a is needed one node past the interior (boundary ring) for the last face
-    const bool inside_a = (i1 <= n1) && (i2 <= n2);
 
-    // Register window along x3 (DIM == 3): u and a at z-1, z, z+1 for this thread's column.
-    T u_m = T(0), u_c = T(0), u_p = T(0), a_m = T(0), a_c = T(0), a_p = T(0);
-    auto load_u = [&](int z) -> T {
-        return (inside && z >= 0 && z < n3) ? p.u[(long long)z * plane_u + (long long)i2 * n1 + i1] : T(0);
-    };
-    auto load_a = [&](int z) -> T {  // z in interior numbering, z = -1 and n3 are boundary nodes
-        if (!inside_a) return T(0);
-        const long long za = (DIM == 3) ? (long long)(z + 1) : 0;
-        return p.a[za * plane_a + (long long)(i2 + 1) * A1 + (i1 + 1)];
-    };
-    if (DIM == 3) {
-        u_m = load_u(z0 - 1); u_c = load_u(z0);
-        a_m = load_a(z0 - 1); a_c = load_a(z0);
-    } else {
-        u_c = load_u(0); a_c = load_a(0);
-    }
-
-    for (int z = z0; z < z1; ++z) {
-        if (DIM == 3) { u_p = load_u(z + 1); a_p = load_a(z + 1); }
-        // stage the current plane with its x1/x2 halo in shared memory
-        __syncthreads();
-        su[ty + 1][tx + 1] = u_c;
-        sa[ty + 1][tx + 1] = a_c;
-        const long long zu = (long long)z * plane_u;
-        const long long za = (DIM == 3) ? (long long)(z + 1) * plane_a : 0;
-        // halo: x1 edges (2 columns of TY) and x2 edges (2 rows of TX)
-        if (threadIdx.x < 2 * TY) {
-            const int side = threadIdx.x / TY, r = threadIdx.x % TY;
-            const int hx = side ? blockIdx.x * TX + TX : blockIdx.x * TX - 1;
-            const int hy = blockIdx.y * TY + r;
-            T uv = T(0), av = T(0);
-            if (hy < n2 && hx >= -1 && hx <= n1) {
-                if (hx >= 0 && hx < n1) uv = p.u[zu + (long long)hy * n1 + hx];
-                av = p.a[za + (long long)(hy + 1) * A1 + (hx + 1)];
-            }
-            su[r + 1][side ? TX + 1 : 0] = uv;
-            sa[r + 1][side ? TX + 1 : 0] = av;
-        } else if (threadIdx.x < 2 * TY + 2 * TX) {
-            const int t = threadIdx.x - 2 * TY;
-            const int side = t / TX, col = t % TX;
-            const int hx = blockIdx.x * TX + col;
-            const int hy = side ? blockIdx.y * TY + TY : blockIdx.y * TY - 1;
-            T uv = T(0), av = T(0);
-            if (hx < n1 && hy >= -1 && hy <= n2) {
-                if (hy >= 0 && hy < n2) uv = p.u[zu + (long long)hy * n1 + hx];
-                av = p.a[za + (long long)(hy + 1) * A1 + (hx + 1)];
-            }
-            su[side ? TY + 1 : 0][col + 1] = uv;
-            sa[side ? TY + 1 : 0][col + 1] = av;
+    T uc[ZC + 2], ac[ZC + 2];
+    T uw[ZC], ue[ZC], us[ZC], un[ZC], aw[ZC], ae[ZC], as_[ZC], an[ZC];
+    T xv[ZC][kMaxExtra];
+    const long long row_u = (long long)i2 * n1 + i1;
+    const long long row_a = (long long)(i2 + 1) * A1 + (i1 + 1);
+#pragma unroll
+    for (int q = 0; q < ZC + 2; ++q) { uc[q] = T(0); ac[q] = T(0); }
+    if (inside) {
+#pragma unroll
+        for (int q = 0; q < ZC + 2; ++q) {
+            const int z = z0 - 1 + q;                  // interior plane index, -1 and n3 are boundary
+            if (DIM == 2 && q != 1) continue;
+            if (DIM == 3 && z > n3) continue;
+            const long long za = (DIM == 3) ? (long long)(z + 1) * plane_a : 0;
+            ac[q] = __ldg(p.a + za + row_a);
+            if (DIM == 2 || (z >= 0 && z < n3)) uc[q] = __ldg(p.u + (DIM == 3 ? (long long)z * plane_u : 0) + row_u);
         }
-        __syncthreads();
-
-        float outabs[kMaxOut] = {0.f, 0.f};
-        if (inside) {
-            const T uw = su[ty + 1][tx], ue = su[ty + 1][tx + 2];
-            const T us = su[ty][tx + 1], un = su[ty + 2][tx + 1];
-            const T aw = sa[ty + 1][tx], ae = sa[ty + 1][tx + 2];
-            const T as_ = sa[ty][tx + 1], an = sa[ty + 2][tx + 1];
-            const T half = T(0.5);
-            // diffusion remainder (a - abar) in flux form and advection remainder
-            T g = (half * (a_c + ae) * (ue - u_c) - half * (a_c + aw) * (u_c - uw)) * c.ih2[0]
-                + (half * (a_c + an) * (un - u_c) - half * (a_c + as_) * (u_c - us)) * c.ih2[1]
-                + c.bmb[0] * (ue - uw) * c.i2h[0] + c.bmb[1] * (un - us) * c.i2h[1];
-            if (DIM == 3) {
-                g += (half * (a_c + a_p) * (u_p - u_c) - half * (a_c + a_m) * (u_c - u_m)) * c.ih2[2]
-                   + c.bmb[2] * (u_p - u_m) * c.i2h[2];
-            }
-            g += c.r0 + u_c * (c.r1 + u_c * (c.r2 + u_c * c.r3));
-            T F = T(0);
-            if (needF) {
-                const T two = T(2);
-                F = g + c.abar * ((ue - two * u_c + uw) * c.ih2[0] + (un - two * u_c + us) * c.ih2[1])
-                      + c.beta[0] * (ue - uw) * c.i2h[0] + c.beta[1] * (un - us) * c.i2h[1];
-                if (DIM == 3)
-                    F += c.abar * (u_p - two * u_c + u_m) * c.ih2[2] + c.beta[2] * (u_p - u_m) * c.i2h[2];
-            }
-            const long long idx = zu + (long long)i2 * n1 + i1;
-            T xv[kMaxExtra];
 #pragma unroll
-            for (int e = 0; e < kMaxExtra; ++e) xv[e] = (e < p.nx) ? p.X[e][idx] : T(0);
+        for (int q = 0; q < ZC; ++q) {
+            const int z = z0 + q;
+            uw[q] = ue[q] = us[q] = un[q] = T(0);
+            aw[q] = ae[q] = as_[q] = an[q] = T(0);
+            if (DIM == 3 && z >= n3) continue;
+            const long long zu = (DIM == 3) ? (long long)z * plane_u : 0;
+            const long long za = (DIM == 3) ? (long long)(z + 1) * plane_a : 0;
+            const T* uz = p.u + zu + row_u;
+            const T* az = p.a + za + row_a;
+            if (i1 > 0) uw[q] = __ldg(uz - 1);
+            if (i1 + 1 < n1) ue[q] = __ldg(uz + 1);
+            if (i2 > 0) us[q] = __ldg(uz - n1);
+            if (i2 + 1 < n2) un[q] = __ldg(uz + n1);
+            aw[q] = __ldg(az - 1);                      // the boundary ring makes these valid
+            ae[q] = __ldg(az + 1);
+            as_[q] = __ldg(az - A1);
+            an[q] = __ldg(az + A1);
 #pragma unroll
-            for (int j = 0; j < kMaxOut; ++j) {
-                if (j < p.nout) {
-                    T v = c.cu[j] * u_c + c.cg[j] * g + c.cF[j] * F;
+            for (int e = 0; e < kMaxExtra; ++e) xv[q][e] = (e < p.nx) ? __ldg(p.X[e] + zu + row_u) : T(0);
+        }
+    }
+    float outabs[kMaxOut] = {0.f, 0.f};
+    float uabs = 0.f;
+    const T half = T(0.5), two = T(2);
 #pragma unroll
-                    for (int e = 0; e < kMaxExtra; ++e) v += c.cx[j][e] * xv[e];
-                    p.out[j][idx] = v;
-                    outabs[j] = (float)absval(v);
-                }
+    for (int q = 0; q < ZC; ++q) {
+        const int z = z0 + q;
+        if (!inside || (DIM == 3 && z >= n3)) continue;
+        const T u0 = uc[q + 1], a0 = ac[q + 1];
+        // diffusion remainder (a - abar) in flux form and advection remainder
+        T g = (half * (a0 + ae[q]) * (ue[q] - u0) - half * (a0 + aw[q]) * (u0 - uw[q])) * c.ih2[0]
+            + (half * (a0 + an[q]) * (un[q] - u0) - half * (a0 + as_[q]) * (u0 - us[q])) * c.ih2[1]
+            + c.bmb[0] * (ue[q] - uw[q]) * c.i2h[0] + c.bmb[1] * (un[q] - us[q]) * c.i2h[1];
+        if (DIM == 3) {
+            const T up = uc[q + 2], um = uc[q], ap = ac[q + 2], am = ac[q];
+            g += (half * (a0 + ap) * (up - u0) - half * (a0 + am) * (u0 - um)) * c.ih2[2]
+               + c.bmb[2] * (up - um) * c.i2h[2];
+        }
+        g += c.r0 + u0 * (c.r1 + u0 * (c.r2 + u0 * c.r3));
+        T F = T(0);
+        if (needF) {
+            F = g + c.abar * ((ue[q] - two * u0 + uw[q]) * c.ih2[0] + (un[q] - two * u0 + us[q]) * c.ih2[1])
+                  + c.beta[0] * (ue[q] - uw[q]) * c.i2h[0] + c.beta[1] * (un[q] - us[q]) * c.i2h[1];
+            if (DIM == 3)
+                F += c.abar * (uc[q + 2] - two * u0 + uc[q]) * c.ih2[2] + c.beta[2] * (uc[q + 2] - uc[q]) * c.i2h[2];
+        }
+        const long long idx = (DIM == 3 ? (long long)z * plane_u : 0) + row_u;
+        uabs = fmaxf(uabs, (float)absval(u0));
+#pragma unroll
+        for (int j = 0; j < kMaxOut; ++j) {
+            if (j < p.nout) {
+                T v = c.cu[j] * u0 + c.cg[j] * g + c.cF[j] * F;
+#pragma unroll
+                for (int e = 0; e < kMaxExtra; ++e) v += c.cx[j][e] * xv[q][e];
+                p.out[j][idx] = v;
+                outabs[j] = fmaxf(outabs[j], (float)absval(v));
             }
         }
-        // converged warp reduction (amax slots are uniform across the grid)
-#pragma unroll
-        for (int j = 0; j < kMaxOut; ++j)
-            if (j < p.nout && p.amax[j]) block_amax(outabs[j], p.amax[j]);
-        if (DIM == 3) { u_m = u_c; u_c = u_p; a_m = a_c; a_c = a_p; }
     }
+    // converged warp reductions (amax slots are uniform across the grid)
+    if (p.amax_u) block_amax(uabs, p.amax_u);
+#pragma unroll
+    for (int j = 0; j < kMaxOut; ++j)
+        if (j < p.nout && p.amax[j]) block_amax(outabs[j], p.amax[j]);
 }
 
 template <typename T>
@@ -176,9 +155,16 @@ cudaError_t launch_impl(const StencilArgs<T>& p, cudaStream_t s) {
     }
     dim3 block(TX * TY);
     dim3 grid((p.n1 + TX - 1) / TX, (p.n2 + TY - 1) / TY, p.dim == 3 ? (p.n3 + ZCHUNK - 1) / ZCHUNK : 1);
-    if (p.dim == 3) stencil_kernel<T, 3><<<grid, block, 0, s>>>(p, c, needF);
-    else            stencil_kernel<T, 2><<<grid, block, 0, s>>>(p, c, needF);
+    if (p.dim == 3) stencil_kernel<T, 3, ZCHUNK><<<grid, block, 0, s>>>(p, c, needF);
+    else            stencil_kernel<T, 2, 1><<<grid, block, 0, s>>>(p, c, needF);
     return cudaGetLastError();
+}
+
+__global__ void amax_kernel(const float* x, size_t n, unsigned* slot) {
+    float m = 0.f;
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+        m = fmaxf(m, fabsf(x[i]));
+    block_amax(m, slot);
 }
 
 __global__ void convert_kernel(const double* in, float* out, size_t n) {
@@ -190,6 +176,12 @@ __global__ void convert_kernel(const double* in, float* out, size_t n) {
 
 cudaError_t launch_stencil(const StencilArgs<double>& a, cudaStream_t s) { return launch_impl(a, s); }
 cudaError_t launch_stencil(const StencilArgs<float>& a, cudaStream_t s) { return launch_impl(a, s); }
+
+cudaError_t launch_amax(const float* x, size_t n, unsigned* slot, cudaStream_t s) {
+    const int blocks = int(std::min<size_t>((n + 255) / 256, 152 * 8));
+    amax_kernel<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(x, n, slot);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_convert_f64_to_f32(const double* in, float* out, size_t n, cudaStream_t s) {
     const int blocks = int(std::min<size_t>((n + 255) / 256, 152 * 16));

@@ -1,0 +1,173 @@
+"""Parity of the mixed-precision path (FP32 state and stencil, mu-mode contractions on the
+tensor cores from three BF16 slices per operand) with the FP64 oracle.
+
+Tolerance: 1e-6 relative l2 for the 256^3 Lawson4 workload (the mixed-precision
+requirement); per-kernel checks use the same bound. The phi route through the eigenbasis
+loses up to prod_mu kappa(V_mu) times the slicing error, so its bound scales with kappa.
+"""
+import numpy as np
+import pytest
+
+from oracle import adr_oracle as O
+from paper_2303_15861_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2303_15861_gb300 import adr, build_lib  # noqa: E402
+
+build_lib.build()
+adr.load_library()
+
+GUARD = 4096
+
+
+def guarded(shape, fill=None):
+    n = int(np.prod(shape))
+    full = torch.full((n + 2 * GUARD,), float("nan"), dtype=torch.float32, device="cuda")
+    view = full[GUARD:GUARD + n].view(shape)
+    if fill is not None:
+        view.copy_(torch.as_tensor(np.asarray(fill), dtype=torch.float32))
+    return full, view
+
+
+def check_guards(full):
+    g = torch.cat([full[:GUARD], full[-GUARD:]])
+    assert torch.isnan(g).all(), "write outside the caller's array"
+
+
+def make(dims, b=None, k=1):
+    b = b if b is not None else (10.0,) * len(dims)
+    a = W.sine_product_coefficient(dims, k=k)
+    return a, tuple(b) + (0.0,) * (3 - len(b)), W.REACTION_U2_1MU
+
+
+def ctx_for(dims, tau, scheme, a, b, r, prec="bf16x3"):
+    c = adr.Context(dims, tau, scheme, prec)
+    c.set_coeffs(a, b, r)
+    return c
+
+
+@pytest.mark.parametrize("dims", [(128, 128), (48, 48), (130, 65), (64, 64, 64), (45, 19, 23), (130, 65, 67),
+                                  (256, 256, 256)])
+@pytest.mark.parametrize("c", [0.5, 1.0])
+def test_exp_action(dims, c):
+    a, b, r = make(dims)
+    tau = 2.5e-3
+    rng = np.random.default_rng(11)
+    v0 = W.smooth_initial_state(dims, noise=0.0) + 0.1 * rng.standard_normal(tuple(dims[::-1]))
+    ctx = ctx_for(dims, tau, "lawson4", a, b, r)
+    fv, v = guarded(v0.shape, v0)
+    fy, y = guarded(v0.shape)
+    ctx.apply_exp(c, v, y)
+    ctx.synchronize()
+    check_guards(fv)
+    check_guards(fy)
+    vin = v.double().cpu().numpy()
+    prob = O.ADRProblem(dims, a, b, r)
+    ref = O.MatrixFunctions(prob, tau).exp_action(c, vin)
+    err = O.rel_l2(y.cpu().numpy(), ref)
+    assert err < 1e-6, err
+
+
+@pytest.mark.parametrize("dims", [(128, 128), (64, 64, 64), (31, 17, 22)])
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_phi_action(dims, k):
+    a, b, r = make(dims)
+    tau = 2e-3
+    v0 = np.random.default_rng(6).standard_normal(tuple(dims[::-1]))
+    ctx = ctx_for(dims, tau, "etd2rk", a, b, r)
+    kappa = np.prod([x for x in ctx.info()["kappa"][: len(dims)]])
+    fv, v = guarded(v0.shape, v0)
+    fy, y = guarded(v0.shape)
+    ctx.apply_phi(k, v, y)
+    torch.cuda.synchronize()
+    check_guards(fy)
+    vin = v.double().cpu().numpy()
+    mf = O.MatrixFunctions(O.ADRProblem(dims, a, b, r), tau)
+    ref = mf.exp_action(1.0, vin) if k == 0 else mf.phi_action(k, 1.0, vin)
+    err = O.rel_l2(y.cpu().numpy(), ref)
+    assert err < 2e-7 * max(1.0, kappa), (err, kappa)
+
+
+def test_no_accumulation_bias():
+    """Two hundred E actions of a positive state: the tensor-core result must track the
+    FP64 oracle without a systematic drift (exact accumulation of the high slices)."""
+    dims = (128, 128)
+    a, b, r = make(dims)
+    tau = 2.5e-3
+    u0 = W.smooth_initial_state(dims, noise=0.0)
+    ctx = ctx_for(dims, tau, "lawson4", a, b, r)
+    x = torch.tensor(u0, dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    mf = O.MatrixFunctions(O.ADRProblem(dims, a, b, r), tau)
+    ref = u0.copy()
+    for _ in range(100):
+        ctx.apply_exp(0.5, x, y)
+        ctx.apply_exp(0.5, y, x)
+        ref = mf.exp_action(0.5, mf.exp_action(0.5, ref))
+    torch.cuda.synchronize()
+    got = x.double().cpu().numpy()
+    err = O.rel_l2(got, ref)
+    drift = abs(got.sum() / ref.sum() - 1.0)
+    assert err < 1e-6 and drift < 1e-6, (err, drift)
+
+
+INTEGRATE = [
+    ((64, 64, 64), (10.0, 10.0, 10.0), "lawson4", 0.05, 20, 1e-6),
+    ((45, 19, 23), (3.0, -5.0, 8.0), "lawson4", 0.04, 8, 1e-6),
+    ((64, 64, 64), (10.0, 10.0, 10.0), "lawson_euler", 0.05, 20, 1e-6),
+    ((128, 128), (10.0, 10.0), "lawson4", 0.1, 40, 1e-6),
+    ((64, 64), (10.0, 10.0), "etd2rk", 0.1, 30, 1e-5),
+    ((32, 32, 32), (10.0, 10.0, 10.0), "etd2rk", 0.04, 8, 1e-5),
+]
+
+
+@pytest.mark.parametrize("dims,b,scheme,T,m,tol", INTEGRATE)
+def test_integrate_matches_oracle(dims, b, scheme, T, m, tol):
+    a, bb, r = make(dims, b=b)
+    u0 = W.smooth_initial_state(dims)
+    tau = T / m
+    ctx = ctx_for(dims, tau, scheme, a, bb, r)
+    fu, u = guarded(u0.shape, u0)
+    ctx.integrate(u, 0.0, T, m)
+    ctx.synchronize()
+    check_guards(fu)
+    ref = O.solve(dims, a, bb, r, u0, tau, m, scheme)
+    err = O.rel_l2(u.cpu().numpy(), ref)
+    assert err < tol, err
+
+
+def test_config3_full_size_two_steps_vs_oracle():
+    """256^3 Lawson4 in the launch configuration the benchmark times: two steps against the
+    FP64 oracle (the full 40 are compared against the FP64 GPU path below)."""
+    w = W.config3()
+    ctx = ctx_for(w.dims, w.tau, w.scheme, w.a_nodes, w.b, w.r_poly)
+    u = torch.tensor(w.u0, dtype=torch.float32, device="cuda")
+    ctx.integrate(u, 0.0, 2 * w.tau, 2)
+    ctx.synchronize()
+    ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, 2, w.scheme)
+    err = O.rel_l2(u.cpu().numpy(), ref)
+    print(f"256^3 lawson4 bf16x3, 2 steps: rel l2 vs oracle {err:.3e}")
+    assert err < 1e-6
+
+
+def test_config3_full_run_vs_fp64_gpu():
+    """All 40 steps of the 256^3 Lawson4 workload: mixed precision against the FP64 GPU
+    path (itself matched to the oracle at 1e-12), relative l2 <= 1e-6."""
+    w = W.config3()
+    mixed = ctx_for(w.dims, w.tau, w.scheme, w.a_nodes, w.b, w.r_poly)
+    u = torch.tensor(w.u0, dtype=torch.float32, device="cuda")
+    mixed.integrate(u, 0.0, w.m * w.tau, w.m)
+    mixed.synchronize()
+    mixed.close()
+    f64 = ctx_for(w.dims, w.tau, w.scheme, w.a_nodes, w.b, w.r_poly, prec="fp64")
+    ud = torch.tensor(w.u0, dtype=torch.float64, device="cuda")
+    f64.integrate(ud, 0.0, w.m * w.tau, w.m)
+    torch.cuda.synchronize()
+    err = O.rel_l2(u.cpu().numpy(), ud.cpu().numpy())
+    print(f"256^3 lawson4 40 steps: bf16x3 vs fp64 GPU rel l2 {err:.3e}")
+    assert err < 1e-6
