@@ -53,6 +53,7 @@ struct adr_ctx {
     int n[3] = {1, 1, 1};
     size_t N = 0;
     size_t nodes = 0;
+    int apitch = 0;                        // padded row pitch of the device copy of a
     bool fp64 = true;
     size_t esize = 8;
 
@@ -292,6 +293,7 @@ StencilArgs<T> stencil_base(const adr_ctx* c, const T* u) {
     StencilArgs<T> s;
     s.u = u;
     s.a = static_cast<const T*>(c->d_a);
+    s.apitch = c->apitch;
     s.dim = c->dim;
     s.n1 = c->n[0];
     s.n2 = c->n[1];
@@ -473,8 +475,16 @@ adr_status adr_set_coeffs(adr_ctx* c, int instance, const double* a_nodes, const
     if (!(c->abar > 0)) return fail(c, ADR_ERR_ARG, "lambda * a_max must be positive");
     for (int m = 0; m < c->dim; ++m) c->beta[m] = c->b[m] + adr::mean_face_jump(a_nodes, c->dim, c->n, m + 1);
 
-    std::vector<double> amb(a_nodes, a_nodes + c->nodes);
-    for (auto& v : amb) v -= c->abar;
+    // device copy of (a - abar) with padded rows: interior x1 nodes start 16-byte aligned
+    const int N1 = c->n[0] + 2, N2 = c->n[1] + 2, N3 = c->dim == 3 ? c->n[2] + 2 : 1;
+    c->apitch = ((c->n[0] + 5) + 3) / 4 * 4;
+    std::vector<double> amb(size_t(c->apitch) * N2 * N3, 0.0);
+    for (int j3 = 0; j3 < N3; ++j3)
+        for (int j2 = 0; j2 < N2; ++j2)
+            for (int j1 = 0; j1 < N1; ++j1)
+                amb[(size_t(j3) * N2 + j2) * c->apitch + j1 + 3] =
+                    a_nodes[(size_t(j3) * N2 + j2) * N1 + j1] - c->abar;
+    if (c->d_a) { void* q = c->d_a; free_dev(q); c->d_a = nullptr; }
     cudaError_t e = upload(c, &c->d_a, amb);
     if (e != cudaSuccess) return cuda_fail(c, e, "upload a");
 

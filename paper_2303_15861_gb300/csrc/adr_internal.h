@@ -46,7 +46,10 @@ constexpr int kMaxOut = 2;
 template <typename T>
 struct StencilArgs {
     const T* u = nullptr;
-    const T* a = nullptr;            // nodal (a - abar), (n1+2)(n2+2)(n3+2)
+    const T* a = nullptr;            // nodal (a - abar) with the boundary ring, padded rows:
+                                     // node (j1, j2, j3) in 0..n+1 at
+                                     // (j3 * (n2 + 2) + j2) * apitch + j1 + 3
+    int apitch = 0;                  // row pitch of a: multiple of 4, >= n1 + 5
     int dim = 3, n1 = 1, n2 = 1, n3 = 1;
     double inv_h2[3] = {0, 0, 0}, inv_2h[3] = {0, 0, 0};
     double bmb[3] = {0, 0, 0};       // b - beta

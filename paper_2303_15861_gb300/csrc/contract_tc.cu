@@ -99,9 +99,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait on phase `parity`; false on timeout (error recorded) or when the CTA aborts.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code, volatile int* abort_flag) {
+// backoff_ns > 0 sleeps between polls so waiting warps leave issue slots to working ones.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code, volatile int* abort_flag,
+                          unsigned backoff_ns = 0) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
+        if (backoff_ns) __nanosleep(backoff_ns);
         if (*abort_flag) return false;
         if (clock64() - t0 > kWaitCycles) {
             if (err) atomicOr(err, code);
@@ -170,9 +173,9 @@ __device__ __forceinline__ void split3(float y, uint32_t& b0, uint32_t& b1, uint
     const float y1 = (y - s0) * 256.f;
     const float s1 = rintf(y1);
     const float s2 = rintf((y1 - s1) * 256.f) * 0.00390625f;
-    b0 = __float_as_uint(s0) >> 16;
-    b1 = __float_as_uint(s1) >> 16;
-    b2 = __float_as_uint(s2) >> 16;
+    b0 = __float_as_uint(s0);
+    b1 = __float_as_uint(s1);
+    b2 = __float_as_uint(s2);
 }
 
 // Slice v[o .. o+7] (8 consecutive K values) and store them as chunk j of row r of the
@@ -184,9 +187,9 @@ __device__ __forceinline__ void slice_store8(const float (&v)[32], int o, float 
         uint32_t a0, a1, a2, c0, c1, c2;
         split3(v[o + 2 * e] * sc, a0, a1, a2);
         split3(v[o + 2 * e + 1] * sc, c0, c1, c2);
-        w0[e] = a0 | (c0 << 16);
-        w1[e] = a1 | (c1 << 16);
-        w2[e] = a2 | (c2 << 16);
+        w0[e] = __byte_perm(a0, c0, 0x7632);   // upper halves: exact BF16 patterns
+        w1[e] = __byte_perm(a1, c1, 0x7632);
+        w2[e] = __byte_perm(a2, c2, 0x7632);
     }
     const uint32_t off = swz(r, j);
     st_shared_v4(tile0 + off, make_uint4(w0[0], w0[1], w0[2], w0[3]));
@@ -258,7 +261,7 @@ __device__ __forceinline__ bool produce_step(const TcArgs& p, long long it, long
     const int s = int(it & 1);
     const uint32_t ph = uint32_t(it >> 1) & 1u;
     const uint32_t full = bar0 + 8u * s, empty = bar0 + 16u + 8u * s;
-    if (!mbar_wait(empty, ph ^ 1u, p.err, 1, abort_flag)) return false;
+    if (!mbar_wait(empty, ph ^ 1u, p.err, 1, abort_flag, 64)) return false;
     const uint32_t sA = sbase + s * kStageBytes;
     const uint32_t sF = sA + kStateBytes;
     if (t == 0) {
@@ -277,7 +280,7 @@ __device__ __forceinline__ bool produce_step(const TcArgs& p, long long it, long
     return true;
 }
 
-template <bool STATE_IS_A>
+template <bool STATE_IS_A, int EPI>
 __global__ void __launch_bounds__(kThreads, 1) tc_contract_kernel(TcArgs p) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bars[9];
@@ -349,64 +352,59 @@ __global__ void __launch_bounds__(kThreads, 1) tc_contract_kernel(TcArgs p) {
         for (long long tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, ++tl) {
             const int a = int(tl & 1);
             const uint32_t ph = uint32_t(tl >> 1) & 1u;
-            const bool waited = mbar_wait(accf_bar(a), ph, p.err, 2, &abort_s);
+            const bool waited = mbar_wait(accf_bar(a), ph, p.err, 2, &abort_s, 64);
             if (!__all_sync(0xffffffffu, waited)) break;   // warp-uniform: TMEM loads are .sync.aligned
             tc_fence_after();
             const long long pt = tile / p.nOut;
             const int ot = int(tile % p.nOut);
             float vmax = 0.f;
-            // row meaning
-            long long pos = 0, pp = 0, qq = 0;
+            // per-row setup: rows are positions (STATE_IS_A) or outputs; columns the other
             bool rvalid;
+            long long off0, cstep;      // offset of (row, column 0) and per-column stride
             float zrow = 0.f, rscale = 0.f;
-            int irow = 0;
+            int ncol;                    // valid columns of this tile
             if (STATE_IS_A) {
-                pos = pt * kRows + row;
+                const long long pos = pt * kRows + row;
                 rvalid = pos < p.npos;
-                if (rvalid) { pp = pos / Q; qq = pos % Q; }
-                if (p.epi == EPI_PHI && rvalid) {
+                const long long pp = rvalid ? pos / Q : 0, qq = rvalid ? pos % Q : 0;
+                off0 = (pp * n + ot * kCols) * Q + qq;
+                cstep = Q;
+                ncol = min(kCols, n - ot * kCols);
+                if (EPI == EPI_PHI && rvalid) {
                     // position part of z = tau (l1 + l2 + l3): the directions other than mu
                     zrow = __ldg(p.zq_a + qq % p.na);
                     if (p.zq_b) zrow += __ldg(p.zq_b + qq / p.na);
                     if (p.zp) zrow += __ldg(p.zp + pp);
                 }
             } else {
-                irow = ot * kCols + row;
+                const int irow = ot * kCols + row;
                 rvalid = irow < n;
                 if (rvalid) rscale = sback * __ldg(p.fscale + irow);
+                off0 = pt * kRows * (long long)n + irow;
+                cstep = n;
+                ncol = int(min((long long)kCols, p.npos - pt * kRows));
             }
+            const float* fsc = p.fscale + ot * kCols;      // column scales (STATE_IS_A)
+            const float* zc = p.zmu + ot * kCols;          // column part of z (EPI_PHI)
+            float* yrow = p.Y + off0;
+            const float* brow = (EPI == EPI_AXPY) ? p.base + off0 : nullptr;
             const uint32_t tbase = tmem + (uint32_t(ew * 32) << 16) + uint32_t(a) * 256u;
 #pragma unroll 1
             for (int j0 = 0; j0 < kCols; j0 += 16) {
                 float d0[16], d1[16];
                 __syncwarp();
                 tmem_ld_pair(tbase + j0, tbase + 128u + j0, d0, d1);
-                if (!rvalid) continue;
+                if (!rvalid || j0 >= ncol) continue;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int col = j0 + j;
-                    long long off;
-                    float scale;
-                    int iout;
-                    if (STATE_IS_A) {
-                        iout = ot * kCols + col;
-                        if (iout >= n) continue;
-                        off = (pp * n + iout) * Q + qq;
-                        scale = sback * __ldg(p.fscale + iout);
-                    } else {
-                        const long long f = pt * kRows + col;
-                        if (f >= p.npos) continue;
-                        iout = irow;
-                        off = f * n + irow;
-                        scale = rscale;
-                    }
+                    if (col >= ncol) break;
+                    const float scale = STATE_IS_A ? sback * __ldg(fsc + col) : rscale;
                     float v = fmaf(d1[j], 0.00390625f, d0[j]) * scale;
-                    if (p.epi == EPI_PHI) {
-                        v *= phi_eval(p.phik, zrow + __ldg(p.zmu + iout));
-                    } else if (p.epi == EPI_AXPY) {
-                        v = fmaf(p.alpha, v, __ldg(p.base + off));
-                    }
-                    p.Y[off] = v;
+                    const long long o = (long long)col * cstep;
+                    if (EPI == EPI_PHI) v *= phi_eval(p.phik, zrow + __ldg(zc + col));
+                    if (EPI == EPI_AXPY) v = fmaf(p.alpha, v, __ldg(brow + o));
+                    yrow[o] = v;
                     vmax = fmaxf(vmax, fabsf(v));
                 }
             }
@@ -482,26 +480,37 @@ int g_num_sms = 0;
 
 }  // namespace
 
-cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
+template <bool SA, int EPI>
+cudaError_t launch_variant(const TcArgs& a, unsigned grid, cudaStream_t s) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(tc_contract_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(tc_contract_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        cudaError_t e = cudaFuncSetAttribute(tc_contract_kernel<SA, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kSmemBytes);
         if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    tc_contract_kernel<SA, EPI><<<grid, kThreads, kSmemBytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
+    if (g_num_sms == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-        attr_set = true;
     }
     if (a.n > 512 || a.n < 1) return cudaErrorInvalidValue;
     const long long grid = a.ntiles < g_num_sms ? a.ntiles : g_num_sms;
     if (grid <= 0) return cudaSuccess;
-    if (a.state_is_a)
-        tc_contract_kernel<true><<<unsigned(grid), kThreads, kSmemBytes, s>>>(a);
-    else
-        tc_contract_kernel<false><<<unsigned(grid), kThreads, kSmemBytes, s>>>(a);
-    return cudaGetLastError();
+    const unsigned g = unsigned(grid);
+    if (a.state_is_a) {
+        if (a.epi == EPI_PHI) return launch_variant<true, EPI_PHI>(a, g, s);
+        if (a.epi == EPI_AXPY) return launch_variant<true, EPI_AXPY>(a, g, s);
+        return launch_variant<true, EPI_STORE>(a, g, s);
+    }
+    if (a.epi == EPI_PHI) return cudaErrorInvalidValue;   // phi is fused into a mode >= 2 pass only
+    if (a.epi == EPI_AXPY) return launch_variant<false, EPI_AXPY>(a, g, s);
+    return launch_variant<false, EPI_STORE>(a, g, s);
 }
 
 int tc_factor_image_bytes(int n) {
