@@ -70,13 +70,13 @@ struct adr_ctx {
     void* d_V[3] = {nullptr};
     void* d_Vi[3] = {nullptr};
     double* d_lam[3] = {nullptr};
-    void* ws[6] = {nullptr};
+    void* ws[9] = {nullptr};               // state-sized workspace; ws[6..8]: low parts (mixed)
     void* d_host_state = nullptr;
 
     // mixed precision (tensor cores): sliced factor images, per-row scales, c tau lambda
     bool tc = false;
-    uint8_t* d_img[4][3] = {{nullptr}};    // 0: E(0.5), 1: E(1), 2: V, 3: V^-1
-    float* d_fsc[4][3] = {{nullptr}};
+    uint8_t* d_img[5][3] = {{nullptr}};    // 0: E(0.5), 1: E(1), 2: V, 3: V^-1, 4: E(0.5) precise
+    float* d_fsc[5][3] = {{nullptr}};
     float* d_zt[3] = {nullptr};            // tau * lambda_mu[j] (FP32)
     unsigned* d_slots = nullptr;           // max-abs slots of the arrays a step produces
     int* d_err = nullptr;                  // device error word (bounded waits)
@@ -124,9 +124,11 @@ cudaError_t upload(adr_ctx* c, void** dst, const std::vector<double>& src) {
     return cudaMemcpy(*dst, tmp.data(), bytes, cudaMemcpyHostToDevice);
 }
 
-// Slice an FP64 factor for the tensor-core kernel and upload image + row scales.
+// Slice an FP64 factor for the tensor-core kernel and upload image + row scales. Mode 1
+// uses the factor as the A operand (128-row tiles), modes >= 2 as the B operand.
 cudaError_t upload_tc(adr_ctx* c, int kind, int m, const std::vector<double>& M) {
-    const adr::TcFactor f = adr::make_tc_factor(M, c->n[m]);
+    const bool precise = (kind == 4);
+    const adr::TcFactor f = adr::make_tc_factor(M, c->n[m], adr::tc_out_rows(m >= 1, precise), precise);
     cudaError_t e = cudaSuccess;
     if (!c->d_img[kind][m]) e = cudaMalloc(reinterpret_cast<void**>(&c->d_img[kind][m]), f.img.size());
     if (e == cudaSuccess && !c->d_fsc[kind][m])
@@ -199,12 +201,13 @@ ContractArgs<T> mode_args(const adr_ctx* c, int mu, const T* M, const T* X, T* Y
     return a;
 }
 
-enum FactorKind { FK_EXP_HALF = 0, FK_EXP_ONE = 1, FK_V = 2, FK_VINV = 3 };
+enum FactorKind { FK_EXP_HALF = 0, FK_EXP_ONE = 1, FK_V = 2, FK_VINV = 3, FK_EXP_HALF_PRECISE = 4 };
 
 // One mu-mode pass y = x x_mu M_kind with epilogue (epi, base, alpha, phik).
 template <typename T>
 void push_mode(Sched& S, int mu, int kind, const T* x, T* y, int epi = adr::EPI_STORE,
-               const T* base = nullptr, double alpha = 0.0, int phik = 0) {
+               const T* base = nullptr, double alpha = 0.0, int phik = 0, T* ylo = nullptr,
+               const T* xlo = nullptr) {
     const adr_ctx* c = S.c;
     if (!c->tc) {
         const void* M = kind == FK_EXP_HALF ? c->d_E[0][mu - 1] : kind == FK_EXP_ONE ? c->d_E[1][mu - 1]
@@ -221,7 +224,9 @@ void push_mode(Sched& S, int mu, int kind, const T* x, T* y, int epi = adr::EPI_
     for (int nu = 1; nu < mu; ++nu) Q *= c->n[nu - 1];
     for (int nu = mu + 1; nu <= c->dim; ++nu) P *= c->n[nu - 1];
     a.X = reinterpret_cast<const float*>(x);
+    a.Xlo = reinterpret_cast<const float*>(xlo);
     a.Y = reinterpret_cast<float*>(y);
+    a.precise = (kind == FK_EXP_HALF_PRECISE);
     a.fimg = c->d_img[kind][mu - 1];
     a.fscale = c->d_fsc[kind][mu - 1];
     a.n = n;
@@ -230,8 +235,9 @@ void push_mode(Sched& S, int mu, int kind, const T* x, T* y, int epi = adr::EPI_
     a.vec4 = (mu == 1) && (n % 4 == 0) && (reinterpret_cast<uintptr_t>(x) % 16 == 0);
     a.npos = (mu >= 2) ? P * Q : P;
     a.nK = (n + 63) / 64;
-    a.nOut = (n + 127) / 128;
-    a.ntiles = ((a.npos + 127) / 128) * a.nOut;
+    const int orows = adr::tc_out_rows(a.state_is_a, a.precise), prows = adr::tc_pos_rows(a.state_is_a, a.precise);
+    a.nOut = (n + orows - 1) / orows;
+    a.ntiles = ((a.npos + prows - 1) / prows) * a.nOut;
     if (epi == adr::EPI_PHI) {
         // the phi scaling is fused into a mode >= 2 pass: decode (q, p) into the other directions
         a.zmu = c->d_zt[mu - 1];
@@ -241,6 +247,7 @@ void push_mode(Sched& S, int mu, int kind, const T* x, T* y, int epi = adr::EPI_
         a.zp = (mu == 2 && c->dim == 3) ? c->d_zt[2] : nullptr;
     }
     a.epi = epi;
+    a.Ylo = reinterpret_cast<float*>(ylo);
     a.base = reinterpret_cast<const float*>(base);
     a.alpha = float(alpha);
     a.phik = phik;
@@ -262,6 +269,25 @@ void push_exp(Sched& S, int ci, const T* x, T* y, const T* base = nullptr, doubl
         const bool last = (mu == c->dim) && base;
         push_mode<T>(S, mu, ci, in, out, last ? adr::EPI_AXPY : adr::EPI_STORE, last ? base : nullptr, alpha);
         in = out;
+    }
+}
+
+// Mixed path: y + ylo = e^{tau A / 2} x with every pass in the precise configuration and
+// double-float intermediates (low parts in ws[6], ws[7]).
+template <typename T>
+void push_exp_precise(Sched& S, const T* x, T* y, T* ylo) {
+    const adr_ctx* c = S.c;
+    T* hi[2] = {static_cast<T*>(c->ws[4]), static_cast<T*>(c->ws[5])};
+    T* lo[2] = {static_cast<T*>(c->ws[6]), static_cast<T*>(c->ws[7])};
+    const T* in = x;
+    const T* inlo = nullptr;
+    for (int mu = 1; mu <= c->dim; ++mu) {
+        const bool last = mu == c->dim;
+        T* out = last ? y : hi[(mu - 1) % 2];
+        T* outlo = last ? ylo : lo[(mu - 1) % 2];
+        push_mode<T>(S, mu, FK_EXP_HALF_PRECISE, in, out, adr::EPI_STORE2, nullptr, 0.0, 0, outlo, inlo);
+        in = out;
+        inlo = outlo;
     }
 }
 
@@ -368,9 +394,15 @@ std::vector<Op> build_step(const adr_ctx* c, T* u) {
         s3.out[0] = X; s3.cx[0][0] = 1.0; s3.cg[0] = tau;                         // Eu + tau k3
         s3.out[1] = ACC; s3.cx[1][1] = 1.0; s3.cg[1] = tau / 3.0;                 // ACC += tau/3 k3
         push_stencil(S, s3);
-        push_exp<T>(S, FK_EXP_HALF, X, W);                                        // U4
+        // U4 feeds the one stencil whose output no later exponential smooths (u+ = ... +
+        // tau/6 g(U4)); on the mixed path it is kept as a double-float pair W + Wlo so that
+        // FP32 rounding of U4 is not amplified by the 1/h^2 of the stencil.
+        T* Wlo = c->tc ? static_cast<T*>(c->ws[8]) : nullptr;
+        if (c->tc) push_exp_precise<T>(S, X, W, Wlo);                            // U4 (double-float)
+        else       push_exp<T>(S, FK_EXP_HALF, X, W);                            // U4
         push_exp<T>(S, FK_EXP_HALF, ACC, X);                                      // E ACC
         auto s4 = stencil_base<T>(c, W);
+        s4.u_lo = Wlo;
         s4.nx = 1; s4.X[0] = X;
         s4.nout = 1; s4.out[0] = u; s4.cx[0][0] = 1.0; s4.cg[0] = tau / 6.0;     // u+ = E ACC + tau/6 k4
         push_stencil(S, s4);
@@ -449,8 +481,9 @@ adr_status adr_create(const adr_params* p, void* cuda_stream, adr_ctx** out) {
             return fail(nullptr, ADR_ERR_ALLOC, std::string("context: ") + cudaGetErrorString(e));
         }
     }
-    for (auto& w : c->ws) {
-        cudaError_t e = cudaMalloc(&w, N * c->esize);
+    for (int i = 0; i < 9; ++i) {
+        if (i >= 6 && !c->tc) continue;   // low parts exist on the mixed path only
+        cudaError_t e = cudaMalloc(&c->ws[i], N * c->esize);
         if (e != cudaSuccess) {
             adr_destroy(c.release());
             return fail(nullptr, ADR_ERR_ALLOC, std::string("workspace: ") + cudaGetErrorString(e));
@@ -515,6 +548,7 @@ adr_status adr_set_coeffs(adr_ctx* c, int instance, const double* a_nodes, const
             if (e != cudaSuccess) return cuda_fail(c, e, "upload E");
             if (c->tc) {
                 e = upload_tc(c, ci, m, *E);
+                if (e == cudaSuccess && ci == 0) e = upload_tc(c, 4, m, *E);   // precise E(0.5)
                 if (e != cudaSuccess) return cuda_fail(c, e, "upload sliced E");
             }
         }
@@ -737,7 +771,7 @@ void adr_destroy(adr_ctx* c) {
     for (auto& p : c->d_lam) { void* q = p; free_dev(q); p = nullptr; }
     for (auto& p : c->ws) free_dev(p);
     free_dev(c->d_host_state);
-    for (auto& row : c->d_img) for (auto& p : row) { void* q = p; free_dev(q); p = nullptr; }
+    for (auto& row : c->d_img) for (auto& p : row) { void* q = p; free_dev(q); p = nullptr; }  // 5 kinds
     for (auto& row : c->d_fsc) for (auto& p : row) { void* q = p; free_dev(q); p = nullptr; }
     for (auto& p : c->d_zt) { void* q = p; free_dev(q); p = nullptr; }
     { void* q = c->d_slots; free_dev(q); c->d_slots = nullptr; }

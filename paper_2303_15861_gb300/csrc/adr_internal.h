@@ -46,6 +46,7 @@ constexpr int kMaxOut = 2;
 template <typename T>
 struct StencilArgs {
     const T* u = nullptr;
+    const T* u_lo = nullptr;         // optional low part: the state is u + u_lo (FP32 only)
     const T* a = nullptr;            // nodal (a - abar) with the boundary ring, padded rows:
                                      // node (j1, j2, j3) in 0..n+1 at
                                      // (j3 * (n2 + 2) + j2) * apitch + j1 + 3
@@ -72,7 +73,7 @@ struct StencilArgs {
 // Element (m,k) of A[b] is A[b*sab + m*sam + k*sak]; likewise B (k,n), C (m,n).
 // The linear offset of a C element is its index in the state array, which the phi
 // epilogue decodes into (i1, i2, i3).
-enum Epilogue { EPI_STORE = 0, EPI_PHI = 1, EPI_AXPY = 2 };
+enum Epilogue { EPI_STORE = 0, EPI_PHI = 1, EPI_AXPY = 2, EPI_STORE2 = 3 /* hi + lo pair */ };
 
 template <typename T>
 struct ContractArgs {
@@ -96,7 +97,9 @@ struct ContractArgs {
 // o (128 rows) and K chunk c (64 columns), four 16 KB tiles F0, F1, 2^-8 F1, 2^-8 F2.
 struct TcArgs {
     const float* X = nullptr;
+    const float* Xlo = nullptr;      // precise: optional low part of a double-float input
     float* Y = nullptr;
+    float* Ylo = nullptr;            // EPI_STORE2: low part of the double-float result
     const uint8_t* fimg = nullptr;   // factor image (tc_factor_image_bytes(n) bytes)
     const float* fscale = nullptr;   // per output row i: 2^(e_i - 7)
     int n = 0;                       // extent of the contracted direction
@@ -105,6 +108,7 @@ struct TcArgs {
     int nK = 0, nOut = 0;            // K chunks of 64, output tiles of 128
     long long ntiles = 0;
     bool state_is_a = true;          // modes >= 2: true; mode 1: false
+    bool precise = false;            // four slices per operand, ten MMAs, double-float result
     bool vec4 = false;               // mode 1: X rows 16-byte aligned (n % 4 == 0)
     int epi = EPI_STORE;
     const float* base = nullptr;
@@ -122,13 +126,15 @@ struct TcArgs {
     int* err = nullptr;                                 // bounded-wait timeout flags
 };
 
-// Host: slice an FP64 factor into the tensor-core image (see contract_tc.cu).
+// Host: slice an FP64 factor into the tensor-core image (see contract_tc.cu), with output
+// tiles of `rows` rows; standard slices F0, F1, 2^-8 F1, 2^-8 F2 or precise F0..F3.
 struct TcFactor {
     std::vector<uint8_t> img;
     std::vector<float> fscale;
 };
-TcFactor make_tc_factor(const std::vector<double>& M, int n);
-int tc_factor_image_bytes(int n);
+TcFactor make_tc_factor(const std::vector<double>& M, int n, int rows, bool precise);
+int tc_out_rows(bool state_is_a, bool precise);   // rows of an output tile of a kernel variant
+int tc_pos_rows(bool state_is_a, bool precise);   // rows of a position / fibre tile
 
 cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s);
 cudaError_t launch_amax(const float* x, size_t n, unsigned* slot, cudaStream_t s);

@@ -16,6 +16,13 @@
 // of a heat-kernel product carries no accumulation bias. D1 is weighted 2^-8 and its
 // terms have random signs. Representation errors are 2^-24 of the scales (as FP32).
 //
+// Precise configuration (the exponential whose result feeds the one stencil that no later
+// exponential smooths): four slices per operand, x = 2^(es-7) sum_j 2^(-8j) s_j (j < 4),
+// the input itself a double-float pair hi + lo, and ten MMAs per K step
+//     D0 = S0.F0, D1 = S0.F1 + S1.F0, D2 = S0.F2 + S1.F1 + S2.F0 (all three exact),
+//     D3 = S0.F3 + S1.F2 + S2.F1 + S3.F0,
+// combined in double-float arithmetic into a hi + lo result (about 2^-31 of the scales).
+//
 // CTA organisation (persistent, one CTA per SM, 416 threads):
 //   warps 0-7  producers: load the FP32 state chunk (coalesced; the next chunk's loads are
 //              in flight while the current one is sliced), slice it into S0, S1, S2' and
@@ -24,8 +31,9 @@
 //   warps 8-11 epilogue: tcgen05.ld the two accumulators, combine, fused op, store,
 //              record max|y| for the next pass.
 //   warp 12    one thread issues the tcgen05.mma chain and commits to mbarriers.
-// Two pipeline stages of 112 KB (K chunk of 64) and two TMEM accumulator sets
-// (2 x (128 + 128) columns) let loads, MMAs and the epilogue of consecutive tiles overlap.
+// Two pipeline stages (K chunk of 64; 112 KB standard, 96 KB precise) and two TMEM
+// accumulator sets of 256 columns (2 x 128 standard, 4 x 64 precise) let loads, MMAs and
+// the epilogue of consecutive tiles overlap.
 //
 // Operand roles. Modes mu >= 2 (positions contiguous in memory): A = state (128
 // positions), B = factor (128 outputs), D[pos][i]; the epilogue store is coalesced along
@@ -44,25 +52,37 @@
 namespace adr {
 namespace {
 
-constexpr int kRows = 128;                       // UMMA M, TMEM lanes
-constexpr int kCols = 128;                       // UMMA N, columns per accumulator
+constexpr int kM = 128;                          // UMMA M, TMEM lanes, rows of the A tile
 constexpr int kChunk = 64;                       // K per stage: one 128-byte bf16 row
-constexpr int kTileBytes = kRows * kChunk * 2;   // one slice tile: 16 KB
-constexpr int kStateBytes = 3 * kTileBytes;      // S0, S1, S2'
-constexpr int kFactorBytes = 4 * kTileBytes;     // F0, F1, F1', F2'
-constexpr int kStageBytes = kStateBytes + kFactorBytes;
-constexpr int kStages = 2;
-constexpr int kSmemBytes = kStages * kStageBytes + 1024;   // + alignment slack
 constexpr int kProducerWarps = 8;
 constexpr int kMmaWarp = kProducerWarps + 4;
 constexpr int kThreads = (kMmaWarp + 1) * 32;   // 416
 constexpr uint32_t kTmemCols = 512;
-constexpr long long kWaitCycles = 4000000000LL;           // bounded waits (~2 s)
+constexpr long long kWaitCycles = 4000000000LL; // bounded waits (~2 s)
 
-// MMA instruction descriptor: kind::f16, D = F32, A = B = BF16, both K-major,
-// N = 128 (bits 17-22: N>>3), M = 128 (bits 24-28: M>>4).
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kCols >> 3) << 17) |
-                            (uint32_t(kRows >> 4) << 24);
+// Compile-time shape of one kernel variant. SA: the state is the A operand (modes >= 2);
+// PR: precise configuration.
+template <bool SA, bool PR>
+struct Cfg {
+    static constexpr int N = PR ? 64 : 128;            // UMMA N: columns of each accumulator
+    static constexpr int SS = PR ? 4 : 3;              // state slices
+    static constexpr int FS = 4;                       // factor slices
+    static constexpr int NACC = PR ? 4 : 2;            // accumulators per TMEM set (NACC * N = 256)
+    static constexpr int SROWS = SA ? kM : N;          // rows of a state tile (positions or fibres)
+    static constexpr int FROWS = SA ? N : kM;          // rows of a factor tile (outputs)
+    static constexpr int STILE = SROWS * kChunk * 2;   // bytes of one state slice tile
+    static constexpr int FTILE = FROWS * kChunk * 2;   // bytes of one factor slice tile
+    static constexpr int SBYTES = SS * STILE;
+    static constexpr int FBYTES = FS * FTILE;          // one factor block (output tile, K chunk)
+    static constexpr int STAGE = SBYTES + FBYTES;
+    static constexpr int SMEM = 2 * STAGE + 1024;      // two stages + alignment slack
+    static constexpr int NV = SROWS * kChunk / (kProducerWarps * 32);   // state values per thread
+    // instruction descriptor: kind::f16, D = F32, A = B = BF16, K-major, N >> 3, M >> 4
+    static constexpr uint32_t IDESC =
+        (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(kM >> 4) << 24);
+    static_assert(NACC * N == 256, "one accumulator set is 256 TMEM columns");
+    static_assert(2 * STAGE + 1024 <= 227 * 1024, "shared memory budget");
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -135,16 +155,17 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
-// Load 16 columns of D0 and of D1 for this warp's 32 lanes, then wait for both.
-__device__ __forceinline__ void tmem_ld_pair(uint32_t ta, uint32_t tb, float (&a)[16], float (&b)[16]) {
+// Load 16 columns of two accumulators for this warp's 32 lanes, then wait.
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float (&a)[16], float (&b)[16]) {
     uint32_t r[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -165,123 +186,211 @@ __device__ __forceinline__ void tmem_ld_pair(uint32_t ta, uint32_t tb, float (&a
     }
 }
 
-// Split y = x * 2^(7-es) (|y| < 128) into integer slices s0, s1 and s2' = 2^-8 s2.
-// Every step is exact in FP32; the slices have at most 8 significant bits, so their
-// BF16 patterns are the upper halves of the FP32 patterns.
-__device__ __forceinline__ void split3(float y, uint32_t& b0, uint32_t& b1, uint32_t& b2) {
-    const float s0 = rintf(y);
-    const float y1 = (y - s0) * 256.f;
-    const float s1 = rintf(y1);
-    const float s2 = rintf((y1 - s1) * 256.f) * 0.00390625f;
-    b0 = __float_as_uint(s0);
-    b1 = __float_as_uint(s1);
-    b2 = __float_as_uint(s2);
+// Load 8 columns of four accumulators (columns 64 apart) for this warp's 32 lanes, then wait.
+__device__ __forceinline__ void tmem_ld8x4(uint32_t t0, float (&d)[4][8]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%32];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%33];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%34];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%35];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(t0), "r"(t0 + 64u), "r"(t0 + 128u), "r"(t0 + 192u)
+        : "memory");
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) d[k][j] = __uint_as_float(r[8 * k + j]);
 }
 
-// Slice v[o .. o+7] (8 consecutive K values) and store them as chunk j of row r of the
-// three tiles.
-__device__ __forceinline__ void slice_store8(const float (&v)[32], int o, float sc, uint32_t tile0, int r, int j) {
-    uint32_t w0[4], w1[4], w2[4];
+// Integer slices of y (|y| < 128; exact FP32 steps; at most 8 significant bits each, so the
+// upper half of each FP32 pattern is its exact BF16 pattern).
+//   standard: s0, s1, 2^-8 s2;  precise: s0, s1, s2, s3 of y + ylo (double-float input).
+template <bool PR>
+__device__ __forceinline__ void split(float y, float ylo, uint32_t (&b)[4]) {
+    const float s0 = rintf(y);
+    const float r0 = PR ? (y - s0) + ylo : (y - s0);   // the sum with ylo rounds below 2^-32
+    const float y1 = r0 * 256.f;
+    const float s1 = rintf(y1);
+    const float y2 = (y1 - s1) * 256.f;
+    const float s2 = rintf(y2);
+    b[0] = __float_as_uint(s0);
+    b[1] = __float_as_uint(s1);
+    if (PR) {
+        b[2] = __float_as_uint(s2);
+        b[3] = __float_as_uint(rintf((y2 - s2) * 256.f));
+    } else {
+        b[2] = __float_as_uint(s2 * 0.00390625f);
+        b[3] = 0u;
+    }
+}
+
+// Slice 8 consecutive K values v[o..o+7] (+ low parts) into chunk j of row r of each of the
+// SS state tiles (tile stride `stile` bytes).
+template <bool PR, int NV>
+__device__ __forceinline__ void slice_store8(const float (&v)[NV], const float (&vl)[NV], int o, float sc,
+                                             uint32_t tile0, uint32_t stile, int r, int j) {
+    constexpr int SS = PR ? 4 : 3;
+    uint32_t w[4][4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-        uint32_t a0, a1, a2, c0, c1, c2;
-        split3(v[o + 2 * e] * sc, a0, a1, a2);
-        split3(v[o + 2 * e + 1] * sc, c0, c1, c2);
-        w0[e] = __byte_perm(a0, c0, 0x7632);   // upper halves: exact BF16 patterns
-        w1[e] = __byte_perm(a1, c1, 0x7632);
-        w2[e] = __byte_perm(a2, c2, 0x7632);
+        uint32_t a[4], c[4];
+        split<PR>(v[o + 2 * e] * sc, vl[o + 2 * e] * sc, a);
+        split<PR>(v[o + 2 * e + 1] * sc, vl[o + 2 * e + 1] * sc, c);
+#pragma unroll
+        for (int q = 0; q < SS; ++q) w[q][e] = __byte_perm(a[q], c[q], 0x7632);
     }
     const uint32_t off = swz(r, j);
-    st_shared_v4(tile0 + off, make_uint4(w0[0], w0[1], w0[2], w0[3]));
-    st_shared_v4(tile0 + kTileBytes + off, make_uint4(w1[0], w1[1], w1[2], w1[3]));
-    st_shared_v4(tile0 + 2 * kTileBytes + off, make_uint4(w2[0], w2[1], w2[2], w2[3]));
+#pragma unroll
+    for (int q = 0; q < SS; ++q) st_shared_v4(tile0 + q * stile + off, make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]));
 }
 
-// Producer helpers (force-inlined so the 32 values of a thread stay in registers).
-// Item `it` of a CTA is K chunk (it % nK) of its (it / nK)-th tile.
-template <bool STATE_IS_A>
-__device__ __forceinline__ void produce_load(const TcArgs& p, long long it, long long items, int t, float (&v)[32]) {
+// Producer item `it` of a CTA: K chunk (it % nK) of its (it / nK)-th tile. Loads the NV state
+// values (and low parts) of thread t.
+template <bool SA, bool PR>
+__device__ __forceinline__ void produce_load(const TcArgs& p, long long it, long long items, int t,
+                                             float (&v)[Cfg<SA, PR>::NV], float (&vl)[Cfg<SA, PR>::NV]) {
+    using C = Cfg<SA, PR>;
+    constexpr int NV = C::NV;
     if (it >= items) return;
     const long long tile = blockIdx.x + (it / p.nK) * gridDim.x;
     const long long pt = tile / p.nOut;
     const int k0 = int(it % p.nK) * kChunk;
     const int n = p.n;
-    if (STATE_IS_A) {
-        // thread t: position row t % 128, K half t / 128; 32 strided, warp-coalesced loads
-        const int row = t & (kRows - 1), half = t >> 7;
-        const long long pos = pt * kRows + row;
+    const bool lo = PR && p.Xlo != nullptr;
+    if (SA) {
+        // thread t: position row t % 128, K part t / 128 (NV = 32 values); warp-coalesced
+        const int row = t & (kM - 1), part = t >> 7;
+        const long long pos = pt * kM + row;
         const bool valid = pos < p.npos;
         const long long Q = p.Q;
         const long long pp = valid ? pos / Q : 0, qq = valid ? pos % Q : 0;
-        const int kb = k0 + 32 * half;
-        const float* xr = p.X + (pp * n + kb) * Q + qq;
+        const int kb = k0 + NV * part;
+        const long long base = (pp * n + kb) * Q + qq;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = (valid && kb + i < n) ? __ldg(xr + (long long)i * Q) : 0.f;
+        for (int i = 0; i < NV; ++i) {
+            const bool ok = valid && kb + i < n;
+            v[i] = ok ? __ldg(p.X + base + (long long)i * Q) : 0.f;
+            vl[i] = (lo && ok) ? __ldg(p.Xlo + base + (long long)i * Q) : 0.f;
+        }
     } else {
-        // thread t: 16-byte chunk j = t % 8 of fibre rows t / 8 + 32 rr
+        // thread t: 16-byte chunk j = t % 8 of fibre rows t / 8 + 32 rr (NV / 8 rows)
         const int j = t & 7, r0 = t >> 3;
         const int kb = k0 + 8 * j;
 #pragma unroll
-        for (int rr = 0; rr < 4; ++rr) {
-            const long long f = pt * kRows + r0 + 32 * rr;
+        for (int rr = 0; rr < NV / 8; ++rr) {
+            const long long f = pt * C::SROWS + r0 + 32 * rr;
             const bool valid = f < p.npos;
-            const float* xr = p.X + (valid ? f : 0) * n + kb;
+            const long long base = (valid ? f : 0) * n + kb;
             if (valid && p.vec4 && kb + 8 <= n) {
-                const float4 a = __ldg(reinterpret_cast<const float4*>(xr));
-                const float4 b = __ldg(reinterpret_cast<const float4*>(xr) + 1);
+                const float4 a = __ldg(reinterpret_cast<const float4*>(p.X + base));
+                const float4 b = __ldg(reinterpret_cast<const float4*>(p.X + base) + 1);
                 v[8 * rr + 0] = a.x; v[8 * rr + 1] = a.y; v[8 * rr + 2] = a.z; v[8 * rr + 3] = a.w;
                 v[8 * rr + 4] = b.x; v[8 * rr + 5] = b.y; v[8 * rr + 6] = b.z; v[8 * rr + 7] = b.w;
             } else {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[8 * rr + e] = (valid && kb + e < n) ? __ldg(xr + e) : 0.f;
+                for (int e = 0; e < 8; ++e) v[8 * rr + e] = (valid && kb + e < n) ? __ldg(p.X + base + e) : 0.f;
             }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) vl[8 * rr + e] = (lo && valid && kb + e < n) ? __ldg(p.Xlo + base + e) : 0.f;
         }
     }
 }
 
-template <bool STATE_IS_A>
-__device__ __forceinline__ void produce_store(const float (&v)[32], int t, float sc, uint32_t sA) {
-    if (STATE_IS_A) {
-        const int row = t & (kRows - 1), half = t >> 7;
+template <bool SA, bool PR>
+__device__ __forceinline__ void produce_store(const float (&v)[Cfg<SA, PR>::NV], const float (&vl)[Cfg<SA, PR>::NV],
+                                              int t, float sc, uint32_t sA) {
+    using C = Cfg<SA, PR>;
+    if (SA) {
+        const int row = t & (kM - 1), part = t >> 7;
 #pragma unroll
-        for (int j4 = 0; j4 < 4; ++j4) slice_store8(v, 8 * j4, sc, sA, row, 4 * half + j4);
+        for (int j4 = 0; j4 < C::NV / 8; ++j4)
+            slice_store8<PR, C::NV>(v, vl, 8 * j4, sc, sA, C::STILE, row, (C::NV / 8) * part + j4);
     } else {
         const int j = t & 7, r0 = t >> 3;
 #pragma unroll
-        for (int rr = 0; rr < 4; ++rr) slice_store8(v, 8 * rr, sc, sA, r0 + 32 * rr, j);
+        for (int rr = 0; rr < C::NV / 8; ++rr) slice_store8<PR, C::NV>(v, vl, 8 * rr, sc, sA, C::STILE, r0 + 32 * rr, j);
     }
 }
 
 // One pipeline item: wait for the stage, start the factor copy, prefetch the next item,
 // slice the current one, publish.
-template <bool STATE_IS_A>
+template <bool SA, bool PR>
 __device__ __forceinline__ bool produce_step(const TcArgs& p, long long it, long long items, int t, float sc,
                                              uint32_t sbase, uint32_t bar0, volatile int* abort_flag,
-                                             const float (&cur)[32], float (&nxt)[32]) {
+                                             const float (&cur)[Cfg<SA, PR>::NV], const float (&curl)[Cfg<SA, PR>::NV],
+                                             float (&nxt)[Cfg<SA, PR>::NV], float (&nxtl)[Cfg<SA, PR>::NV]) {
+    using C = Cfg<SA, PR>;
     const int s = int(it & 1);
     const uint32_t ph = uint32_t(it >> 1) & 1u;
     const uint32_t full = bar0 + 8u * s, empty = bar0 + 16u + 8u * s;
     if (!mbar_wait(empty, ph ^ 1u, p.err, 1, abort_flag, 64)) return false;
-    const uint32_t sA = sbase + s * kStageBytes;
-    const uint32_t sF = sA + kStateBytes;
+    const uint32_t sA = sbase + s * C::STAGE;
+    const uint32_t sF = sA + C::SBYTES;
     if (t == 0) {
         const long long tile = blockIdx.x + (it / p.nK) * gridDim.x;
         const int ot = int(tile % p.nOut);
         const int c = int(it % p.nK);
-        mbar_arrive_expect_tx(full, kFactorBytes);
-        const uint8_t* src = p.fimg + (size_t(ot) * p.nK + c) * kFactorBytes;
+        mbar_arrive_expect_tx(full, C::FBYTES);
+        const uint8_t* src = p.fimg + (size_t(ot) * p.nK + c) * C::FBYTES;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) bulk_g2s(sF + q * kTileBytes, src + q * kTileBytes, kTileBytes, full);
+        for (int q = 0; q < C::FS; ++q) bulk_g2s(sF + q * C::FTILE, src + q * C::FTILE, C::FTILE, full);
     }
-    produce_load<STATE_IS_A>(p, it + 1, items, t, nxt);
-    produce_store<STATE_IS_A>(cur, t, sc, sA);
+    produce_load<SA, PR>(p, it + 1, items, t, nxt, nxtl);
+    produce_store<SA, PR>(cur, curl, t, sc, sA);
     fence_proxy_async();
     mbar_arrive(full);
     return true;
 }
 
-template <bool STATE_IS_A, int EPI>
+// Issue the MMAs of one 16-wide K step. Standard: D0 += S0.F0; D1 += S0.F1 + S1.F0 +
+// S0.(2^-8 F2) + (2^-8 S2).F0 + S1.(2^-8 F1) (factor tiles F0, F1, 2^-8 F1, 2^-8 F2; state
+// tiles S0, S1, 2^-8 S2). Precise: D0..D3 as in the file header (tiles F0..F3, S0..S3).
+template <bool SA, bool PR>
+__device__ __forceinline__ void mma_kstep(uint32_t d, const uint64_t (&S)[4], const uint64_t (&F)[4], uint64_t adv,
+                                          uint32_t first) {
+    using C = Cfg<SA, PR>;
+    auto mma = [&](int acc, int si, int fi, uint32_t accumulate) {
+        const uint32_t dd = d + uint32_t(acc * C::N);
+        if (SA) tc_mma(dd, S[si] + adv, F[fi] + adv, C::IDESC, accumulate);
+        else    tc_mma(dd, F[fi] + adv, S[si] + adv, C::IDESC, accumulate);
+    };
+    const uint32_t acc = first ? 0u : 1u;
+    if (!PR) {
+        mma(0, 0, 0, acc);
+        mma(1, 0, 1, acc);
+        mma(1, 1, 0, 1u);
+        mma(1, 0, 3, 1u);
+        mma(1, 2, 0, 1u);
+        mma(1, 1, 2, 1u);
+    } else {
+        mma(0, 0, 0, acc);
+        mma(1, 0, 1, acc);
+        mma(1, 1, 0, 1u);
+        mma(2, 0, 2, acc);
+        mma(2, 1, 1, 1u);
+        mma(2, 2, 0, 1u);
+        mma(3, 0, 3, acc);
+        mma(3, 1, 2, 1u);
+        mma(3, 2, 1, 1u);
+        mma(3, 3, 0, 1u);
+    }
+}
+
+// TwoSum: s + e = a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+template <bool SA, bool PR, int EPI>
 __global__ void __launch_bounds__(kThreads, 1) tc_contract_kernel(TcArgs p) {
+    using C = Cfg<SA, PR>;
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bars[9];
     __shared__ uint32_t tmem_base_s;
@@ -297,9 +406,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_contract_kernel(TcArgs p) {
     const uint32_t drain_bar = bar0 + 64u;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < 2; ++s) {
             mbar_init(full_bar(s), kProducerWarps * 32 + 1);   // producers + 1 expect_tx arrival
-            mbar_init(empty_bar(s), 1);    // tcgen05.commit
+            mbar_init(empty_bar(s), 1);                         // tcgen05.commit
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(accf_bar(a), 1);     // tcgen05.commit
@@ -332,21 +441,44 @@ __global__ void __launch_bounds__(kThreads, 1) tc_contract_kernel(TcArgs p) {
 
     if (warp < kProducerWarps) {
         // ------------------------------------------------------------ producers
-        // 256 threads; each owns 32 state values of a chunk. The loads of the next chunk
-        // are issued before the current one is sliced, so global latency overlaps the ALU work.
+        // The loads of the next chunk are issued before the current one is sliced, so
+        // global latency overlaps the ALU work.
         const int t = threadIdx.x;
         const long long my_tiles = (p.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
         const long long items = my_tiles * p.nK;
-        float va[32], vb[32];
-        produce_load<STATE_IS_A>(p, 0, items, t, va);
-        for (long long it = 0; it < items; it += 2) {
-            if (!produce_step<STATE_IS_A>(p, it, items, t, sc, sbase, bar0, &abort_s, va, vb)) break;
-            if (it + 1 >= items) break;
-            if (!produce_step<STATE_IS_A>(p, it + 1, items, t, sc, sbase, bar0, &abort_s, vb, va)) break;
+        if (!PR) {
+            float va[C::NV], vb[C::NV], la[C::NV], lb[C::NV];   // la, lb stay zero (no low parts)
+            produce_load<SA, PR>(p, 0, items, t, va, la);
+            for (long long it = 0; it < items; it += 2) {
+                if (!produce_step<SA, PR>(p, it, items, t, sc, sbase, bar0, &abort_s, va, la, vb, lb)) break;
+                if (it + 1 >= items) break;
+                if (!produce_step<SA, PR>(p, it + 1, items, t, sc, sbase, bar0, &abort_s, vb, lb, va, la)) break;
+            }
+        } else {
+            // precise: hi and lo values of one item at a time (registers do not allow a prefetch)
+            float v[C::NV], vl[C::NV];
+            for (long long it = 0; it < items; ++it) {
+                const int s = int(it & 1);
+                const uint32_t ph = uint32_t(it >> 1) & 1u;
+                if (!mbar_wait(empty_bar(s), ph ^ 1u, p.err, 1, &abort_s, 64)) break;
+                const uint32_t sA = sbase + s * C::STAGE;
+                const uint32_t sF = sA + C::SBYTES;
+                if (t == 0) {
+                    const long long tile = blockIdx.x + (it / p.nK) * gridDim.x;
+                    mbar_arrive_expect_tx(full_bar(s), C::FBYTES);
+                    const uint8_t* src = p.fimg + (size_t(tile % p.nOut) * p.nK + it % p.nK) * C::FBYTES;
+#pragma unroll
+                    for (int q = 0; q < C::FS; ++q) bulk_g2s(sF + q * C::FTILE, src + q * C::FTILE, C::FTILE, full_bar(s));
+                }
+                produce_load<SA, PR>(p, it, items, t, v, vl);
+                produce_store<SA, PR>(v, vl, t, sc, sA);
+                fence_proxy_async();
+                mbar_arrive(full_bar(s));
+            }
         }
     } else if (warp < kProducerWarps + 4) {
         // ------------------------------------------------------------ epilogue
-        const int ew = warp - kProducerWarps;   // warps 8-11: TMEM lane quarters 0-3                 // TMEM lane quarter of this warp
+        const int ew = warp - kProducerWarps;   // TMEM lane quarter of this warp
         const int row = ew * 32 + lane;
         long long tl = 0;
         for (long long tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, ++tl) {
@@ -358,18 +490,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_contract_kernel(TcArgs p) {
             const long long pt = tile / p.nOut;
             const int ot = int(tile % p.nOut);
             float vmax = 0.f;
-            // per-row setup: rows are positions (STATE_IS_A) or outputs; columns the other
+            // per-row setup: rows are positions (SA) or outputs; columns the other
             bool rvalid;
             long long off0, cstep;      // offset of (row, column 0) and per-column stride
             float zrow = 0.f, rscale = 0.f;
             int ncol;                    // valid columns of this tile
-            if (STATE_IS_A) {
-                const long long pos = pt * kRows + row;
+            if (SA) {
+                const long long pos = pt * kM + row;
                 rvalid = pos < p.npos;
                 const long long pp = rvalid ? pos / Q : 0, qq = rvalid ? pos % Q : 0;
-                off0 = (pp * n + ot * kCols) * Q + qq;
+                off0 = (pp * n + ot * C::N) * Q + qq;
                 cstep = Q;
-                ncol = min(kCols, n - ot * kCols);
+                ncol = min(C::N, n - ot * C::N);
                 if (EPI == EPI_PHI && rvalid) {
                     // position part of z = tau (l1 + l2 + l3): the directions other than mu
                     zrow = __ldg(p.zq_a + qq % p.na);
@@ -377,35 +509,74 @@ __global__ void __launch_bounds__(kThreads, 1) tc_contract_kernel(TcArgs p) {
                     if (p.zp) zrow += __ldg(p.zp + pp);
                 }
             } else {
-                const int irow = ot * kCols + row;
+                const int irow = ot * kM + row;
                 rvalid = irow < n;
                 if (rvalid) rscale = sback * __ldg(p.fscale + irow);
-                off0 = pt * kRows * (long long)n + irow;
+                off0 = pt * C::N * (long long)n + irow;
                 cstep = n;
-                ncol = int(min((long long)kCols, p.npos - pt * kRows));
+                ncol = int(min((long long)C::N, p.npos - pt * C::N));
             }
-            const float* fsc = p.fscale + ot * kCols;      // column scales (STATE_IS_A)
-            const float* zc = p.zmu + ot * kCols;          // column part of z (EPI_PHI)
+            const float* fsc = p.fscale + ot * C::N;      // column scales (SA)
+            const float* zc = p.zmu + ot * C::N;          // column part of z (EPI_PHI)
             float* yrow = p.Y + off0;
+            float* ylo = (EPI == EPI_STORE2) ? p.Ylo + off0 : nullptr;
             const float* brow = (EPI == EPI_AXPY) ? p.base + off0 : nullptr;
             const uint32_t tbase = tmem + (uint32_t(ew * 32) << 16) + uint32_t(a) * 256u;
+            auto emit = [&](int col, float hi, float lo) {
+                // hi + lo: the combined accumulators of (row, col) before scaling
+                const float scale = SA ? sback * __ldg(fsc + col) : rscale;
+                const long long o = (long long)col * cstep;
+                if (EPI == EPI_STORE2) {
+                    yrow[o] = hi * scale;
+                    ylo[o] = lo * scale;
+                    vmax = fmaxf(vmax, fabsf(hi * scale));
+                    return;
+                }
+                float v = (hi + lo) * scale;
+                if (EPI == EPI_PHI) v *= phi_eval(p.phik, zrow + __ldg(zc + col));
+                if (EPI == EPI_AXPY) v = fmaf(p.alpha, v, __ldg(brow + o));
+                yrow[o] = v;
+                vmax = fmaxf(vmax, fabsf(v));
+            };
+            if (!PR) {
 #pragma unroll 1
-            for (int j0 = 0; j0 < kCols; j0 += 16) {
-                float d0[16], d1[16];
-                __syncwarp();
-                tmem_ld_pair(tbase + j0, tbase + 128u + j0, d0, d1);
-                if (!rvalid || j0 >= ncol) continue;
+                for (int j0 = 0; j0 < C::N; j0 += 16) {
+                    float d0[16], d1[16];
+                    __syncwarp();
+                    tmem_ld16x2(tbase + j0, tbase + uint32_t(C::N) + j0, d0, d1);
+                    if (!rvalid || j0 >= ncol) continue;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = j0 + j;
-                    if (col >= ncol) break;
-                    const float scale = STATE_IS_A ? sback * __ldg(fsc + col) : rscale;
-                    float v = fmaf(d1[j], 0.00390625f, d0[j]) * scale;
-                    const long long o = (long long)col * cstep;
-                    if (EPI == EPI_PHI) v *= phi_eval(p.phik, zrow + __ldg(zc + col));
-                    if (EPI == EPI_AXPY) v = fmaf(p.alpha, v, __ldg(brow + o));
-                    yrow[o] = v;
-                    vmax = fmaxf(vmax, fabsf(v));
+                    for (int j = 0; j < 16; ++j) {
+                        if (j0 + j >= ncol) break;
+                        // D0 is an exact integer, 2^-8 D1 an exact scaling
+                        const float t1 = d1[j] * 0.00390625f;
+                        if (EPI == EPI_STORE2) {
+                            float hi, lo;
+                            two_sum(d0[j], t1, hi, lo);
+                            emit(j0 + j, hi, lo);
+                        } else {
+                            emit(j0 + j, d0[j] + t1, 0.f);
+                        }
+                    }
+                }
+            } else {
+#pragma unroll 1
+                for (int j0 = 0; j0 < C::N; j0 += 8) {
+                    float d[4][8];
+                    __syncwarp();
+                    tmem_ld8x4(tbase + j0, d);
+                    if (!rvalid || j0 >= ncol) continue;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (j0 + j >= ncol) break;
+                        // D0 + 2^-8 D1 + 2^-16 D2 + 2^-24 D3 in double-float arithmetic
+                        float hi, lo;
+                        two_sum(d[0][j], d[1][j] * 0.00390625f, hi, lo);
+                        lo += fmaf(d[3][j], 5.9604644775390625e-08f, d[2][j] * 1.52587890625e-05f);
+                        const float s = hi + lo;
+                        lo = lo - (s - hi);
+                        emit(j0 + j, s, lo);
+                    }
                 }
             }
             tc_fence_before();
@@ -421,39 +592,24 @@ __global__ void __launch_bounds__(kThreads, 1) tc_contract_kernel(TcArgs p) {
             const uint32_t aph = uint32_t(tl >> 1) & 1u;
             if (!mbar_wait(acce_bar(a), aph ^ 1u, p.err, 4, &abort_s)) break;
             tc_fence_after();
-            const uint32_t d0 = tmem + uint32_t(a) * 256u;
-            const uint32_t d1 = d0 + 128u;
+            const uint32_t d = tmem + uint32_t(a) * 256u;
             bool ok = true;
             for (int c = 0; c < p.nK; ++c, ++g) {
                 const int s = int(g & 1);
                 const uint32_t ph = uint32_t(g >> 1) & 1u;
                 if (!mbar_wait(full_bar(s), ph, p.err, 8, &abort_s)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t sS = sbase + s * kStageBytes;
-                const uint32_t sF = sS + kStateBytes;
-                const uint64_t S0 = sdesc(sS), S1 = sdesc(sS + kTileBytes), S2 = sdesc(sS + 2 * kTileBytes);
-                const uint64_t F0 = sdesc(sF), F1 = sdesc(sF + kTileBytes), F1s = sdesc(sF + 2 * kTileBytes),
-                               F2s = sdesc(sF + 3 * kTileBytes);
+                const uint32_t sS = sbase + s * C::STAGE;
+                const uint32_t sF = sS + C::SBYTES;
+                uint64_t S[4], F[4];
 #pragma unroll
-                for (int kk = 0; kk < kChunk / 16; ++kk) {
-                    const uint64_t adv = uint64_t(kk * 32) >> 4;   // 16 bf16 = 32 bytes along K
-                    const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
-                    if (STATE_IS_A) {
-                        tc_mma(d0, S0 + adv, F0 + adv, acc);
-                        tc_mma(d1, S0 + adv, F1 + adv, acc);
-                        tc_mma(d1, S1 + adv, F0 + adv, 1u);
-                        tc_mma(d1, S0 + adv, F2s + adv, 1u);
-                        tc_mma(d1, S2 + adv, F0 + adv, 1u);
-                        tc_mma(d1, S1 + adv, F1s + adv, 1u);
-                    } else {
-                        tc_mma(d0, F0 + adv, S0 + adv, acc);
-                        tc_mma(d1, F1 + adv, S0 + adv, acc);
-                        tc_mma(d1, F0 + adv, S1 + adv, 1u);
-                        tc_mma(d1, F2s + adv, S0 + adv, 1u);
-                        tc_mma(d1, F0 + adv, S2 + adv, 1u);
-                        tc_mma(d1, F1s + adv, S1 + adv, 1u);
-                    }
+                for (int q = 0; q < 4; ++q) {
+                    S[q] = sdesc(sS + (q < C::SS ? q : 0) * C::STILE);
+                    F[q] = sdesc(sF + q * C::FTILE);
                 }
+#pragma unroll
+                for (int kk = 0; kk < kChunk / 16; ++kk)
+                    mma_kstep<SA, PR>(d, S, F, uint64_t(kk * 32) >> 4, (c == 0 && kk == 0) ? 1u : 0u);
                 tc_commit(empty_bar(s));
             }
             if (!ok) break;
@@ -478,20 +634,24 @@ __global__ void __launch_bounds__(kThreads, 1) tc_contract_kernel(TcArgs p) {
 
 int g_num_sms = 0;
 
-}  // namespace
-
-template <bool SA, int EPI>
+template <bool SA, bool PR, int EPI>
 cudaError_t launch_variant(const TcArgs& a, unsigned grid, cudaStream_t s) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(tc_contract_kernel<SA, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kSmemBytes);
+        cudaError_t e = cudaFuncSetAttribute(tc_contract_kernel<SA, PR, EPI>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<SA, PR>::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    tc_contract_kernel<SA, EPI><<<grid, kThreads, kSmemBytes, s>>>(a);
+    tc_contract_kernel<SA, PR, EPI><<<grid, kThreads, Cfg<SA, PR>::SMEM, s>>>(a);
     return cudaGetLastError();
 }
+
+}  // namespace
+
+// Rows of an output tile and of a position tile for a variant (the host tiles with these).
+int tc_out_rows(bool state_is_a, bool precise) { return state_is_a ? (precise ? 64 : 128) : 128; }
+int tc_pos_rows(bool state_is_a, bool precise) { return state_is_a ? 128 : (precise ? 64 : 128); }
 
 cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
     if (g_num_sms == 0) {
@@ -503,19 +663,22 @@ cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
     const long long grid = a.ntiles < g_num_sms ? a.ntiles : g_num_sms;
     if (grid <= 0) return cudaSuccess;
     const unsigned g = unsigned(grid);
-    if (a.state_is_a) {
-        if (a.epi == EPI_PHI) return launch_variant<true, EPI_PHI>(a, g, s);
-        if (a.epi == EPI_AXPY) return launch_variant<true, EPI_AXPY>(a, g, s);
-        return launch_variant<true, EPI_STORE>(a, g, s);
+    if (a.precise) {
+        if (a.epi != EPI_STORE2 && a.epi != EPI_STORE) return cudaErrorInvalidValue;
+        if (a.state_is_a) return a.epi == EPI_STORE2 ? launch_variant<true, true, EPI_STORE2>(a, g, s)
+                                                     : launch_variant<true, true, EPI_STORE>(a, g, s);
+        return a.epi == EPI_STORE2 ? launch_variant<false, true, EPI_STORE2>(a, g, s)
+                                   : launch_variant<false, true, EPI_STORE>(a, g, s);
     }
-    if (a.epi == EPI_PHI) return cudaErrorInvalidValue;   // phi is fused into a mode >= 2 pass only
-    if (a.epi == EPI_AXPY) return launch_variant<false, EPI_AXPY>(a, g, s);
-    return launch_variant<false, EPI_STORE>(a, g, s);
-}
-
-int tc_factor_image_bytes(int n) {
-    const int nK = (n + kChunk - 1) / kChunk, nOut = (n + kCols - 1) / kCols;
-    return nOut * nK * kFactorBytes;
+    if (a.state_is_a) {
+        if (a.epi == EPI_PHI) return launch_variant<true, false, EPI_PHI>(a, g, s);
+        if (a.epi == EPI_AXPY) return launch_variant<true, false, EPI_AXPY>(a, g, s);
+        if (a.epi == EPI_STORE2) return launch_variant<true, false, EPI_STORE2>(a, g, s);
+        return launch_variant<true, false, EPI_STORE>(a, g, s);
+    }
+    if (a.epi == EPI_PHI || a.epi == EPI_STORE2) return cudaErrorInvalidValue;   // fused into modes >= 2 only
+    if (a.epi == EPI_AXPY) return launch_variant<false, false, EPI_AXPY>(a, g, s);
+    return launch_variant<false, false, EPI_STORE>(a, g, s);
 }
 
 }  // namespace adr

@@ -176,13 +176,14 @@ uint16_t bf16_bits_exact(double v) {
 }
 }  // namespace
 
-TcFactor make_tc_factor(const std::vector<double>& M, int n) {
-    // Each row i of M (an output index) is written as 2^(e_i-7) (f0 + 2^-8 f1 + 2^-16 f2)
-    // with integer slices |f_j| <= 128 and max_k |M[i][k]| < 2^e_i; the image stores, per
-    // (output tile of 128 rows, K chunk of 64), the four 16 KB tiles F0, F1, 2^-8 F1, 2^-8 F2
-    // in the 128-byte-swizzled K-major layout the tensor cores read (8-row groups of
-    // 1024 B; 16-byte chunk j of row r at position j ^ (r mod 8)).
-    const int chunk = 64, rows = 128, tile = rows * chunk * 2;
+TcFactor make_tc_factor(const std::vector<double>& M, int n, int rows, bool precise) {
+    // Each row i of M (an output index) is written as 2^(e_i-7) sum_j 2^(-8j) f_j with
+    // integer slices |f_j| <= 128 and max_k |M[i][k]| < 2^e_i. The image stores, per
+    // (output tile of `rows` rows, K chunk of 64), four slice tiles in the 128-byte-swizzled
+    // K-major layout the tensor cores read (8-row groups of 1024 B; 16-byte chunk j of row r
+    // at position j ^ (r mod 8)): F0, F1, 2^-8 F1, 2^-8 F2 (standard) or F0, F1, F2, F3
+    // (precise).
+    const int chunk = 64, tile = rows * chunk * 2;
     const int nK = (n + chunk - 1) / chunk, nOut = (n + rows - 1) / rows;
     TcFactor out;
     out.img.assign(size_t(nOut) * nK * 4 * tile, 0);
@@ -199,12 +200,15 @@ TcFactor make_tc_factor(const std::vector<double>& M, int n) {
             const double f0 = std::nearbyint(y);
             const double y1 = (y - f0) * 256.0;
             const double f1 = std::nearbyint(y1);
-            const double f2 = std::nearbyint((y1 - f1) * 256.0);
+            const double y2 = (y1 - f1) * 256.0;
+            const double f2 = std::nearbyint(y2);
+            const double f3 = std::nearbyint((y2 - f2) * 256.0);
             double* sl = &slices[(size_t(i) * n + k) * 4];
-            sl[0] = f0;
-            sl[1] = f1;
-            sl[2] = f1 / 256.0;
-            sl[3] = f2 / 256.0;
+            if (precise) {
+                sl[0] = f0; sl[1] = f1; sl[2] = f2; sl[3] = f3;
+            } else {
+                sl[0] = f0; sl[1] = f1; sl[2] = f1 / 256.0; sl[3] = f2 / 256.0;
+            }
         }
     }
     for (int ot = 0; ot < nOut; ++ot)

@@ -39,12 +39,32 @@ __device__ __forceinline__ void block_amax(float v, unsigned* slot) {
     if ((threadIdx.x & 31) == 0 && v > 0.f) atomicMax(slot, __float_as_uint(v));
 }
 
+
+// The stencil at one node from its one-sided differences dE = u_E - u_C, dW = u_C - u_W
+// (and N/S, P/M for x2, x3), the centre value and the face-coefficient sums
+// sE = (a - abar)_C + (a - abar)_E etc. Returns g; F = g + A u when needF.
+template <typename T, int DIM>
+__device__ __forceinline__ T stencil_core(const Coefs<T>& c, T uC, T dE, T dW, T dN, T dS, T dP, T dM, T sE, T sW,
+                                          T sN, T sS, T sP, T sM, bool needF, T& F) {
+    const T h = T(0.5);
+    T g = (h * sE * dE - h * sW * dW) * c.ih2[0] + (h * sN * dN - h * sS * dS) * c.ih2[1]
+        + c.bmb[0] * (dE + dW) * c.i2h[0] + c.bmb[1] * (dN + dS) * c.i2h[1];
+    if (DIM == 3) g += (h * sP * dP - h * sM * dM) * c.ih2[2] + c.bmb[2] * (dP + dM) * c.i2h[2];
+    g += c.r0 + uC * (c.r1 + uC * (c.r2 + uC * c.r3));
+    if (needF) {
+        F = g + c.abar * ((dE - dW) * c.ih2[0] + (dN - dS) * c.ih2[1]) + c.beta[0] * (dE + dW) * c.i2h[0]
+              + c.beta[1] * (dN + dS) * c.i2h[1];
+        if (DIM == 3) F += c.abar * (dP - dM) * c.ih2[2] + c.beta[2] * (dP + dM) * c.i2h[2];
+    }
+    return g;
+}
+
 // One pass over the grid. Each thread owns the nodes (i1, i2, z0 .. z0+ZC-1): it issues
 // every load of its column up front (centre column with its x3 halo, the four x1/x2
 // neighbours per plane, the extra stage inputs), all independent and warp-coalesced along
 // x1, so no barrier is needed and many requests are in flight; x1/x2 neighbours are served
 // by L1, x3 neighbours by registers. DIM = 2 has one plane and no x3 terms.
-template <typename T, int DIM, int ZC>
+template <typename T, int DIM, int ZC, bool HASLO>
 __global__ void __launch_bounds__(TX * TY) stencil_kernel(StencilArgs<T> p, Coefs<T> c, bool needF) {
     const int n1 = p.n1, n2 = p.n2, n3 = p.n3;
     const int A1 = p.apitch, A2 = n2 + 2;
@@ -54,77 +74,80 @@ __global__ void __launch_bounds__(TX * TY) stencil_kernel(StencilArgs<T> p, Coef
     const int i2 = blockIdx.y * TY + int(threadIdx.x / TX);
     const int z0 = (DIM == 3) ? int(blockIdx.z) * ZC : 0;
     const bool inside = (i1 < n1) && (i2 < n2);
-
-    T uc[ZC + 2], ac[ZC + 2];
-    T uw[ZC], ue[ZC], us[ZC], un[ZC], aw[ZC], ae[ZC], as_[ZC], an[ZC];
-    T xv[ZC][kMaxExtra];
     const long long row_u = (long long)i2 * n1 + i1;
     const long long row_a = (long long)(i2 + 1) * A1 + (i1 + 4);   // interior i1 at offset 4
+
+    // loads: u (and its low part) at the node and its 6 neighbours, a at the node and its 6
+    T uc[ZC + 2], lc[ZC + 2], ac[ZC + 2];
+    T uw[ZC], ue[ZC], us[ZC], un[ZC], lw[ZC], le[ZC], ls[ZC], ln[ZC], aw[ZC], ae[ZC], as_[ZC], an[ZC];
+    T xv[ZC][kMaxExtra];
 #pragma unroll
-    for (int q = 0; q < ZC + 2; ++q) { uc[q] = T(0); ac[q] = T(0); }
-    if (inside) {
-#pragma unroll
-        for (int q = 0; q < ZC + 2; ++q) {
-            const int z = z0 - 1 + q;                  // interior plane index, -1 and n3 are boundary
-            if (DIM == 2 && q != 1) continue;
-            if (DIM == 3 && z > n3) continue;
-            const long long za = (DIM == 3) ? (long long)(z + 1) * plane_a : 0;
-            ac[q] = __ldg(p.a + za + row_a);
-            if (DIM == 2 || (z >= 0 && z < n3)) uc[q] = __ldg(p.u + (DIM == 3 ? (long long)z * plane_u : 0) + row_u);
+    for (int q = 0; q < ZC + 2; ++q) {
+        uc[q] = T(0); lc[q] = T(0); ac[q] = T(0);
+        const int z = z0 - 1 + q;                  // interior plane index, -1 and n3 are boundary
+        if (!inside || (DIM == 2 && q != 1) || (DIM == 3 && z > n3)) continue;
+        const long long za = (DIM == 3) ? (long long)(z + 1) * plane_a : 0;
+        ac[q] = __ldg(p.a + za + row_a);
+        if (DIM == 2 || (z >= 0 && z < n3)) {
+            const long long zu = (DIM == 3 ? (long long)z * plane_u : 0) + row_u;
+            uc[q] = __ldg(p.u + zu);
+            if (HASLO) lc[q] = __ldg(p.u_lo + zu);
         }
+    }
 #pragma unroll
-        for (int q = 0; q < ZC; ++q) {
-            const int z = z0 + q;
-            uw[q] = ue[q] = us[q] = un[q] = T(0);
-            aw[q] = ae[q] = as_[q] = an[q] = T(0);
-            if (DIM == 3 && z >= n3) continue;
-            const long long zu = (DIM == 3) ? (long long)z * plane_u : 0;
-            const long long za = (DIM == 3) ? (long long)(z + 1) * plane_a : 0;
-            const T* uz = p.u + zu + row_u;
-            const T* az = p.a + za + row_a;
-            if (i1 > 0) uw[q] = __ldg(uz - 1);
-            if (i1 + 1 < n1) ue[q] = __ldg(uz + 1);
-            if (i2 > 0) us[q] = __ldg(uz - n1);
-            if (i2 + 1 < n2) un[q] = __ldg(uz + n1);
-            aw[q] = __ldg(az - 1);                      // the boundary ring makes these valid
-            ae[q] = __ldg(az + 1);
-            as_[q] = __ldg(az - A1);
-            an[q] = __ldg(az + A1);
+    for (int q = 0; q < ZC; ++q) {
+        const int z = z0 + q;
+        uw[q] = ue[q] = us[q] = un[q] = T(0);
+        lw[q] = le[q] = ls[q] = ln[q] = T(0);
+        aw[q] = ae[q] = as_[q] = an[q] = T(0);
 #pragma unroll
-            for (int e = 0; e < kMaxExtra; ++e) xv[q][e] = (e < p.nx) ? __ldg(p.X[e] + zu + row_u) : T(0);
+        for (int e = 0; e < kMaxExtra; ++e) xv[q][e] = T(0);
+        if (!inside || (DIM == 3 && z >= n3)) continue;
+        const long long zu = (DIM == 3) ? (long long)z * plane_u : 0;
+        const long long za = (DIM == 3) ? (long long)(z + 1) * plane_a : 0;
+        const T* uz = p.u + zu + row_u;
+        const T* az = p.a + za + row_a;
+        if (i1 > 0) uw[q] = __ldg(uz - 1);
+        if (i1 + 1 < n1) ue[q] = __ldg(uz + 1);
+        if (i2 > 0) us[q] = __ldg(uz - n1);
+        if (i2 + 1 < n2) un[q] = __ldg(uz + n1);
+        if (HASLO) {
+            const T* lz = p.u_lo + zu + row_u;
+            if (i1 > 0) lw[q] = __ldg(lz - 1);
+            if (i1 + 1 < n1) le[q] = __ldg(lz + 1);
+            if (i2 > 0) ls[q] = __ldg(lz - n1);
+            if (i2 + 1 < n2) ln[q] = __ldg(lz + n1);
         }
+        aw[q] = __ldg(az - 1);                      // the boundary ring makes these valid
+        ae[q] = __ldg(az + 1);
+        as_[q] = __ldg(az - A1);
+        an[q] = __ldg(az + A1);
+#pragma unroll
+        for (int e = 0; e < kMaxExtra; ++e)
+            if (e < p.nx) xv[q][e] = __ldg(p.X[e] + zu + row_u);
     }
     float outabs[kMaxOut] = {0.f, 0.f};
     float uabs = 0.f;
-    const T half = T(0.5), two = T(2);
 #pragma unroll
     for (int q = 0; q < ZC; ++q) {
         const int z = z0 + q;
         if (!inside || (DIM == 3 && z >= n3)) continue;
-        const T u0 = uc[q + 1], a0 = ac[q + 1];
-        // diffusion remainder (a - abar) in flux form and advection remainder
-        T g = (half * (a0 + ae[q]) * (ue[q] - u0) - half * (a0 + aw[q]) * (u0 - uw[q])) * c.ih2[0]
-            + (half * (a0 + an[q]) * (un[q] - u0) - half * (a0 + as_[q]) * (u0 - us[q])) * c.ih2[1]
-            + c.bmb[0] * (ue[q] - uw[q]) * c.i2h[0] + c.bmb[1] * (un[q] - us[q]) * c.i2h[1];
-        if (DIM == 3) {
-            const T up = uc[q + 2], um = uc[q], ap = ac[q + 2], am = ac[q];
-            g += (half * (a0 + ap) * (up - u0) - half * (a0 + am) * (u0 - um)) * c.ih2[2]
-               + c.bmb[2] * (up - um) * c.i2h[2];
-        }
-        g += c.r0 + u0 * (c.r1 + u0 * (c.r2 + u0 * c.r3));
+        const T u0 = uc[q + 1], l0 = lc[q + 1], a0 = ac[q + 1];
+        // one-sided differences; with a low part, (hi difference) + (lo difference)
+        const T dE = (ue[q] - u0) + (le[q] - l0), dW = (u0 - uw[q]) + (l0 - lw[q]);
+        const T dN = (un[q] - u0) + (ln[q] - l0), dS = (u0 - us[q]) + (l0 - ls[q]);
+        const T dP = DIM == 3 ? (uc[q + 2] - u0) + (lc[q + 2] - l0) : T(0);
+        const T dM = DIM == 3 ? (u0 - uc[q]) + (l0 - lc[q]) : T(0);
+        const T uC = u0 + l0;
         T F = T(0);
-        if (needF) {
-            F = g + c.abar * ((ue[q] - two * u0 + uw[q]) * c.ih2[0] + (un[q] - two * u0 + us[q]) * c.ih2[1])
-                  + c.beta[0] * (ue[q] - uw[q]) * c.i2h[0] + c.beta[1] * (un[q] - us[q]) * c.i2h[1];
-            if (DIM == 3)
-                F += c.abar * (uc[q + 2] - two * u0 + uc[q]) * c.ih2[2] + c.beta[2] * (uc[q + 2] - uc[q]) * c.i2h[2];
-        }
+        const T g = stencil_core<T, DIM>(c, uC, dE, dW, dN, dS, dP, dM, a0 + ae[q], a0 + aw[q], a0 + an[q],
+                                         a0 + as_[q], a0 + ac[q + 2], a0 + ac[q], needF, F);
         const long long idx = (DIM == 3 ? (long long)z * plane_u : 0) + row_u;
-        uabs = fmaxf(uabs, (float)absval(u0));
+        uabs = fmaxf(uabs, (float)absval(uC));
 #pragma unroll
         for (int j = 0; j < kMaxOut; ++j) {
             if (j < p.nout) {
-                T v = c.cu[j] * u0 + c.cg[j] * g + c.cF[j] * F;
+                T v = c.cu[j] * uC + c.cg[j] * g + c.cF[j] * F;
 #pragma unroll
                 for (int e = 0; e < kMaxExtra; ++e) v += c.cx[j][e] * xv[q][e];
                 p.out[j][idx] = v;
@@ -139,12 +162,15 @@ __global__ void __launch_bounds__(TX * TY) stencil_kernel(StencilArgs<T> p, Coef
         if (j < p.nout && p.amax[j]) block_amax(outabs[j], p.amax[j]);
 }
 
-
 // FP32, n1 % 4 == 0: each thread computes 4 consecutive x1 nodes of ZV planes with 16-byte
 // loads; the x1 neighbours of the 4-node group come from the adjacent lanes (shuffles), the
 // warp edges load them. A warp covers 128 consecutive x1 nodes of one (x2, x3) row.
 constexpr int ZV = 2;
-template <int DIM>
+
+__device__ __forceinline__ void f4arr(const float4& v, float (&a)[4]) { a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w; }
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+
+template <int DIM, bool HASLO>
 __global__ void __launch_bounds__(256) stencil_vec4_kernel(StencilArgs<float> p, Coefs<float> c, bool needF) {
     const int n1 = p.n1, n2 = p.n2, n3 = p.n3;
     const int A1 = p.apitch, A2 = n2 + 2;
@@ -155,22 +181,23 @@ __global__ void __launch_bounds__(256) stencil_vec4_kernel(StencilArgs<float> p,
     const int i2 = blockIdx.y * 8 + int(threadIdx.x >> 5);
     const int z0 = (DIM == 3) ? int(blockIdx.z) * ZV : 0;
     const bool inside = (i1 < n1) && (i2 < n2);      // n1 % 4 == 0: all 4 nodes or none
-    const bool row_ok = i2 < n2;
     const long long row_u = (long long)i2 * n1 + i1;
     const long long row_a = (long long)(i2 + 1) * A1 + (i1 + 4);
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
 
-    float4 uc[ZV + 2], ac[ZV + 2];
+    float4 uc[ZV + 2], lc[ZV + 2], ac[ZV + 2];
 #pragma unroll
     for (int q = 0; q < ZV + 2; ++q) {
-        uc[q] = zero4;
-        ac[q] = zero4;
+        uc[q] = lc[q] = ac[q] = zero4;
         const int z = z0 - 1 + q;
         if (!inside || (DIM == 2 && q != 1) || (DIM == 3 && z > n3)) continue;
         const long long za = (DIM == 3) ? (long long)(z + 1) * plane_a : 0;
-        ac[q] = __ldg(reinterpret_cast<const float4*>(p.a + za + row_a));
-        if (DIM == 2 || (z >= 0 && z < n3))
-            uc[q] = __ldg(reinterpret_cast<const float4*>(p.u + (DIM == 3 ? (long long)z * plane_u : 0) + row_u));
+        ac[q] = ld4(p.a + za + row_a);
+        if (DIM == 2 || (z >= 0 && z < n3)) {
+            const long long zu = (DIM == 3 ? (long long)z * plane_u : 0) + row_u;
+            uc[q] = ld4(p.u + zu);
+            if (HASLO) lc[q] = ld4(p.u_lo + zu);
+        }
     }
     float outabs[kMaxOut] = {0.f, 0.f};
     float uabs = 0.f;
@@ -180,64 +207,72 @@ __global__ void __launch_bounds__(256) stencil_vec4_kernel(StencilArgs<float> p,
         const bool plane_ok = (DIM == 2) ? (q == 0) : (z < n3);   // 2-D: a single plane
         const long long zu = (DIM == 3) ? (long long)z * plane_u : 0;
         const long long za = (DIM == 3) ? (long long)(z + 1) * plane_a : 0;
-        float4 us = zero4, un = zero4, as4 = zero4, an4 = zero4;
-        float xw = 0.f, xe = 0.f, aw = 0.f, ae = 0.f;
+        float4 us = zero4, un = zero4, ls4 = zero4, ln4 = zero4, as4 = zero4, an4 = zero4;
+        float xw = 0.f, xe = 0.f, yw = 0.f, ye = 0.f, aw = 0.f, ae = 0.f;
         float4 xv[kMaxExtra];
+#pragma unroll
+        for (int e = 0; e < kMaxExtra; ++e) xv[e] = zero4;
+        // warp edges, and a group whose right neighbour is the boundary, load their halo
+        const bool load_e = (lane == 31) || (i1 + 4 >= n1);
         if (inside && plane_ok) {
             const float* uz = p.u + zu + row_u;
             const float* az = p.a + za + row_a;
-            if (i2 > 0) us = __ldg(reinterpret_cast<const float4*>(uz - n1));
-            if (i2 + 1 < n2) un = __ldg(reinterpret_cast<const float4*>(uz + n1));
-            as4 = __ldg(reinterpret_cast<const float4*>(az - A1));
-            an4 = __ldg(reinterpret_cast<const float4*>(az + A1));
-            // warp edges, and a group whose right neighbour is the boundary, load their halo
-            const bool load_e = (lane == 31) || (i1 + 4 >= n1);
+            if (i2 > 0) us = ld4(uz - n1);
+            if (i2 + 1 < n2) un = ld4(uz + n1);
+            as4 = ld4(az - A1);
+            an4 = ld4(az + A1);
             if (lane == 0 && i1 > 0) xw = __ldg(uz - 1);
             if (load_e && i1 + 4 < n1) xe = __ldg(uz + 4);
             if (lane == 0) aw = __ldg(az - 1);
             if (load_e) ae = __ldg(az + 4);
+            if (HASLO) {
+                const float* lz = p.u_lo + zu + row_u;
+                if (i2 > 0) ls4 = ld4(lz - n1);
+                if (i2 + 1 < n2) ln4 = ld4(lz + n1);
+                if (lane == 0 && i1 > 0) yw = __ldg(lz - 1);
+                if (load_e && i1 + 4 < n1) ye = __ldg(lz + 4);
+            }
 #pragma unroll
             for (int e = 0; e < kMaxExtra; ++e)
-                xv[e] = (e < p.nx) ? __ldg(reinterpret_cast<const float4*>(p.X[e] + zu + row_u)) : zero4;
+                if (e < p.nx) xv[e] = ld4(p.X[e] + zu + row_u);
         }
-        const float4 u0 = uc[q + 1], a0 = ac[q + 1];
+        const float4 u0 = uc[q + 1], l0 = lc[q + 1], a0 = ac[q + 1];
         // x1 halo of the group from the neighbouring lanes (all lanes take part)
         const float sw_u = __shfl_up_sync(0xffffffffu, u0.w, 1), se_u = __shfl_down_sync(0xffffffffu, u0.x, 1);
         const float sw_a = __shfl_up_sync(0xffffffffu, a0.w, 1), se_a = __shfl_down_sync(0xffffffffu, a0.x, 1);
+        float sw_l = 0.f, se_l = 0.f;
+        if (HASLO) {
+            sw_l = __shfl_up_sync(0xffffffffu, l0.w, 1);
+            se_l = __shfl_down_sync(0xffffffffu, l0.x, 1);
+        }
         if (!inside || !plane_ok) continue;
-        if (lane != 0) { xw = sw_u; aw = sw_a; }
-        if (lane != 31 && i1 + 4 < n1) { xe = se_u; ae = se_a; }
-        const float uu[6] = {xw, u0.x, u0.y, u0.z, u0.w, xe};
-        const float aa[6] = {aw, a0.x, a0.y, a0.z, a0.w, ae};
-        const float uS[4] = {us.x, us.y, us.z, us.w}, uN[4] = {un.x, un.y, un.z, un.w};
-        const float aS[4] = {as4.x, as4.y, as4.z, as4.w}, aN[4] = {an4.x, an4.y, an4.z, an4.w};
-        const float uM[4] = {uc[q].x, uc[q].y, uc[q].z, uc[q].w}, uP[4] = {uc[q + 2].x, uc[q + 2].y, uc[q + 2].z, uc[q + 2].w};
-        const float aM[4] = {ac[q].x, ac[q].y, ac[q].z, ac[q].w}, aP[4] = {ac[q + 2].x, ac[q + 2].y, ac[q + 2].z, ac[q + 2].w};
+        if (lane != 0) { xw = sw_u; aw = sw_a; yw = sw_l; }
+        if (lane != 31 && i1 + 4 < n1) { xe = se_u; ae = se_a; ye = se_l; }
+        float U[4], L[4], Aa[4], US[4], UN[4], LS[4], LN[4], AS[4], AN[4], UM[4], UP[4], LM[4], LP[4], AM[4], AP[4];
+        f4arr(u0, U); f4arr(l0, L); f4arr(a0, Aa);
+        f4arr(us, US); f4arr(un, UN); f4arr(ls4, LS); f4arr(ln4, LN); f4arr(as4, AS); f4arr(an4, AN);
+        f4arr(uc[q], UM); f4arr(uc[q + 2], UP); f4arr(lc[q], LM); f4arr(lc[q + 2], LP); f4arr(ac[q], AM); f4arr(ac[q + 2], AP);
+        const float UX[6] = {xw, U[0], U[1], U[2], U[3], xe}, LX[6] = {yw, L[0], L[1], L[2], L[3], ye};
+        const float AX[6] = {aw, Aa[0], Aa[1], Aa[2], Aa[3], ae};
         float res[kMaxOut][4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const float uC = uu[k + 1], aC = aa[k + 1];
-            const float uW = uu[k], uE = uu[k + 2], aW = aa[k], aE = aa[k + 2];
-            float g = (0.5f * (aC + aE) * (uE - uC) - 0.5f * (aC + aW) * (uC - uW)) * c.ih2[0]
-                    + (0.5f * (aC + aN[k]) * (uN[k] - uC) - 0.5f * (aC + aS[k]) * (uC - uS[k])) * c.ih2[1]
-                    + c.bmb[0] * (uE - uW) * c.i2h[0] + c.bmb[1] * (uN[k] - uS[k]) * c.i2h[1];
-            if (DIM == 3)
-                g += (0.5f * (aC + aP[k]) * (uP[k] - uC) - 0.5f * (aC + aM[k]) * (uC - uM[k])) * c.ih2[2]
-                   + c.bmb[2] * (uP[k] - uM[k]) * c.i2h[2];
-            g += c.r0 + uC * (c.r1 + uC * (c.r2 + uC * c.r3));
+            const float uC = U[k], lC = L[k], aC = Aa[k];
+            const float dE = (UX[k + 2] - uC) + (LX[k + 2] - lC), dW = (uC - UX[k]) + (lC - LX[k]);
+            const float dN = (UN[k] - uC) + (LN[k] - lC), dS = (uC - US[k]) + (lC - LS[k]);
+            const float dP = (UP[k] - uC) + (LP[k] - lC), dM = (uC - UM[k]) + (lC - LM[k]);
+            const float uF = uC + lC;
             float F = 0.f;
-            if (needF) {
-                F = g + c.abar * ((uE - 2.f * uC + uW) * c.ih2[0] + (uN[k] - 2.f * uC + uS[k]) * c.ih2[1])
-                      + c.beta[0] * (uE - uW) * c.i2h[0] + c.beta[1] * (uN[k] - uS[k]) * c.i2h[1];
-                if (DIM == 3) F += c.abar * (uP[k] - 2.f * uC + uM[k]) * c.ih2[2] + c.beta[2] * (uP[k] - uM[k]) * c.i2h[2];
-            }
-            uabs = fmaxf(uabs, fabsf(uC));
+            const float g = stencil_core<float, DIM>(c, uF, dE, dW, dN, dS, dP, dM, aC + AX[k + 2], aC + AX[k],
+                                                     aC + AN[k], aC + AS[k], aC + AP[k], aC + AM[k], needF, F);
+            uabs = fmaxf(uabs, fabsf(uF));
 #pragma unroll
             for (int j = 0; j < kMaxOut; ++j) {
-                float v = c.cu[j] * uC + c.cg[j] * g + c.cF[j] * F;
+                float v = c.cu[j] * uF + c.cg[j] * g + c.cF[j] * F;
 #pragma unroll
                 for (int e = 0; e < kMaxExtra; ++e) {
-                    const float xe4[4] = {xv[e].x, xv[e].y, xv[e].z, xv[e].w};
+                    float xe4[4];
+                    f4arr(xv[e], xe4);
                     v += c.cx[j][e] * xe4[k];
                 }
                 res[j][k] = v;
@@ -251,7 +286,6 @@ __global__ void __launch_bounds__(256) stencil_vec4_kernel(StencilArgs<float> p,
             }
         }
     }
-    (void)row_ok;
     if (p.amax_u) block_amax(uabs, p.amax_u);
 #pragma unroll
     for (int j = 0; j < kMaxOut; ++j)
@@ -281,16 +315,28 @@ cudaError_t launch_impl(const StencilArgs<T>& p, cudaStream_t s) {
                        (reinterpret_cast<uintptr_t>(p.a) % 16 == 0);
         for (int j = 0; j < p.nout; ++j) aligned = aligned && (reinterpret_cast<uintptr_t>(p.out[j]) % 16 == 0);
         for (int e = 0; e < p.nx; ++e) aligned = aligned && (reinterpret_cast<uintptr_t>(p.X[e]) % 16 == 0);
+        if (p.u_lo) aligned = aligned && (reinterpret_cast<uintptr_t>(p.u_lo) % 16 == 0);
         if (aligned) {
             dim3 g4((p.n1 / 4 + 31) / 32, (p.n2 + 7) / 8, p.dim == 3 ? (p.n3 + ZV - 1) / ZV : 1);
-            if (p.dim == 3) stencil_vec4_kernel<3><<<g4, 256, 0, s>>>(p, c, needF);
-            else            stencil_vec4_kernel<2><<<g4, 256, 0, s>>>(p, c, needF);
+            if (p.dim == 3) {
+                if (p.u_lo) stencil_vec4_kernel<3, true><<<g4, 256, 0, s>>>(p, c, needF);
+                else        stencil_vec4_kernel<3, false><<<g4, 256, 0, s>>>(p, c, needF);
+            } else {
+                if (p.u_lo) stencil_vec4_kernel<2, true><<<g4, 256, 0, s>>>(p, c, needF);
+                else        stencil_vec4_kernel<2, false><<<g4, 256, 0, s>>>(p, c, needF);
+            }
             return cudaGetLastError();
         }
     }
     dim3 grid((p.n1 + TX - 1) / TX, (p.n2 + TY - 1) / TY, p.dim == 3 ? (p.n3 + ZCHUNK - 1) / ZCHUNK : 1);
-    if (p.dim == 3) stencil_kernel<T, 3, ZCHUNK><<<grid, block, 0, s>>>(p, c, needF);
-    else            stencil_kernel<T, 2, 1><<<grid, block, 0, s>>>(p, c, needF);
+    const bool lo = std::is_same<T, float>::value && p.u_lo != nullptr;
+    if (p.dim == 3) {
+        if (lo) stencil_kernel<T, 3, ZCHUNK, true><<<grid, block, 0, s>>>(p, c, needF);
+        else    stencil_kernel<T, 3, ZCHUNK, false><<<grid, block, 0, s>>>(p, c, needF);
+    } else {
+        if (lo) stencil_kernel<T, 2, 1, true><<<grid, block, 0, s>>>(p, c, needF);
+        else    stencil_kernel<T, 2, 1, false><<<grid, block, 0, s>>>(p, c, needF);
+    }
     return cudaGetLastError();
 }
 
