@@ -141,6 +141,26 @@ adr_status adr_get_info(const adr_ctx* ctx, double kappa[3], double* abar, doubl
  * has more than max_ops operations. */
 adr_status adr_profile_step(adr_ctx* ctx, void* u_dev, int max_ops, float* ms, int* kind, int* n_ops);
 
+/* The FP64 mu-mode chain y = v x_1 M_1 x_2 M_2 (x_3 M_3) -- with M_mu = e^{c tau A_mu} this is
+ * e^{c tau A} v -- for callers that must not allocate device memory: a host application that
+ * reserves all of its device memory up front in its own pool, or a pipeline in which a
+ * cudaMalloc would synchronise the device. The paper has no counterpart; it exists for
+ * such callers. It allocates nothing (no cudaMalloc / cudaFree, no allocating library
+ * call) and needs no context:
+ *   dim:      2 or 3; n: interior points per direction, x1 first;
+ *   factors:  host array of dim device pointers, factor mu row-major n_mu x n_mu (FP64);
+ *   v_dev, y_dev: device arrays of n1*n2(*n3) doubles, x1 fastest; must not alias;
+ *   cuda_stream:  cudaStream_t of the launches (NULL = legacy stream). Asynchronous.
+ * The intermediates live in a library-owned static device array of 2 x 1,048,576 doubles
+ * (16 MiB, held on every GPU that loads the library until the process exits): grids with
+ * more than 1,048,576 points return ADR_ERR_ARG. All calls share that array, so calls that
+ * overlap on the GPU race with each other. The first call on a device looks up the array's
+ * address (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture. Returns ADR_ERR_ARG for invalid arguments, ADR_ERR_CUDA if a CUDA call
+ * or launch fails; no message is kept (adr_last_error does not cover this call). */
+adr_status adr_mumode_apply_static(int dim, const int n[3], const double* const factors[3],
+                                   const double* v_dev, double* y_dev, void* cuda_stream);
+
 /* Number of kernels one adr_step launches (for launch accounting). */
 int adr_kernels_per_step(const adr_ctx* ctx);
 

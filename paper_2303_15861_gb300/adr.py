@@ -61,6 +61,7 @@ def load_library(path: str = LIB_PATH):
         "adr_synchronize": (ip, [vp]),
         "adr_profile_step": (ip, [vp, vp, ip, C.POINTER(C.c_float), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "adr_get_info": (ip, [vp, dp, dp, dp]),
+        "adr_mumode_apply_static": (ip, [ip, C.POINTER(C.c_int), C.POINTER(vp), vp, vp, vp]),
         "adr_kernels_per_step": (ip, [vp]),
         "adr_last_error": (C.c_char_p, [vp]),
         "adr_destroy": (None, [vp]),
@@ -174,6 +175,19 @@ def adr_profile_step(ctx, u, max_ops=256):
     n = C.c_int()
     _check(_lib.adr_profile_step(ctx, _ptr(u), int(max_ops), ms, kind, C.byref(n)), ctx)
     return [(int(kind[i]), float(ms[i])) for i in range(n.value)]
+
+
+def adr_mumode_apply_static(factors, v, y, stream=None):
+    """y = v x_1 M_1 x_2 M_2 (x_3 M_3) in FP64 without any device allocation (see adr.h).
+    factors: list of contiguous CUDA float64 tensors (n_mu x n_mu); v, y: CUDA float64
+    tensors of numpy shape (n3, n2, n1) or (n2, n1)."""
+    load_library()
+    dims = tuple(int(f.shape[0]) for f in factors)
+    n = (C.c_int * 3)(*(list(dims) + [1] * (3 - len(dims))))
+    fp = (C.c_void_p * 3)(*([f.data_ptr() for f in factors] + [None] * (3 - len(factors))))
+    st = _lib.adr_mumode_apply_static(len(dims), n, fp, _ptr(v), _ptr(y), _stream_handle(stream))
+    if st != ADR_OK:
+        raise AdrError(st, "adr_mumode_apply_static failed")
 
 
 def adr_get_info(ctx):
