@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--m", type=int, default=40)
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison run")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--ncu-steps", type=int, default=0,
+                   help="profiling mode: run this many untimed time steps (adr_step) and exit")
     return p.parse_args()
 
 
@@ -309,10 +311,32 @@ def ours(args):
     return 0
 
 
+def ncu_steps(args):
+    """Untimed time steps of the workload, for capturing kernels under a profiler."""
+    import torch
+    from paper_2303_15861_gb300 import adr, build_lib
+    torch.cuda.set_device(0)
+    build_lib.build()
+    adr.load_library()
+    w = workload(args)
+    stream = torch.cuda.Stream()
+    dt = torch.float64 if args.precision == "fp64" else torch.float32
+    with torch.cuda.stream(stream):
+        ctx = adr.Context(w.dims, w.tau, "lawson4", args.precision, stream=stream)
+        ctx.set_coeffs(w.a_nodes, w.b, w.r_poly)
+        u = torch.tensor(w.u0, dtype=dt, device="cuda")
+        for i in range(args.ncu_steps):
+            ctx.step(u, i * w.tau)
+        ctx.synchronize()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.ncu_steps > 0:
+        return ncu_steps(args)
     return ours(args)
 
 
