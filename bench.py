@@ -268,7 +268,7 @@ def ours(args):
         tflops = flops / (tc_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s",
                 "frac": tflops / bf16_peak, "traffic": None,
-                "kernel": "tc_contract_kernel (mu-mode contraction, tcgen05 kind::f16)",
+                "kernel": "tma_contract_kernel (mu-mode contraction, TMA-fed tcgen05 kind::f16)",
                 "launch_ms": tc_ms, "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / hbm_peak,
                 "peak_source": f"{peak_src} bf16 sustained"}
     else:

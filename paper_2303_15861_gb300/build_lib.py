@@ -73,7 +73,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for s, log in zip(srcs, logs):
             print(f"== {os.path.basename(s)}\n{log}", file=sys.stderr)
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-lcuda"]
+    cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")

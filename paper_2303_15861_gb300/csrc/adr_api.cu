@@ -77,6 +77,8 @@ struct adr_ctx {
     bool tc = false;
     uint8_t* d_img[5][3] = {{nullptr}};    // 0: E(0.5), 1: E(1), 2: V, 3: V^-1, 4: E(0.5) precise
     float* d_fsc[5][3] = {{nullptr}};
+    uint8_t* d_img2[5][3] = {{nullptr}};   // the same for the TMA-fed kernel (K chunks of 32)
+    float* d_fsc2[5][3] = {{nullptr}};
     float* d_zt[3] = {nullptr};            // tau * lambda_mu[j] (FP32)
     unsigned* d_slots = nullptr;           // max-abs slots of the arrays a step produces
     int* d_err = nullptr;                  // device error word (bounded waits)
@@ -136,6 +138,15 @@ cudaError_t upload_tc(adr_ctx* c, int kind, int m, const std::vector<double>& M)
     if (e == cudaSuccess) e = cudaMemcpy(c->d_img[kind][m], f.img.data(), f.img.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(c->d_fsc[kind][m], f.fscale.data(), f.fscale.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    // TMA-fed kernel: 128-row output tiles, K chunks of 32
+    const adr::TcFactor f2 = adr::make_tc_factor(M, c->n[m], 128, precise, 32);
+    if (!c->d_img2[kind][m]) e = cudaMalloc(reinterpret_cast<void**>(&c->d_img2[kind][m]), f2.img.size());
+    if (e == cudaSuccess && !c->d_fsc2[kind][m])
+        e = cudaMalloc(reinterpret_cast<void**>(&c->d_fsc2[kind][m]), f2.fscale.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_img2[kind][m], f2.img.data(), f2.img.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_fsc2[kind][m], f2.fscale.data(), f2.fscale.size() * sizeof(float), cudaMemcpyHostToDevice);
     return e;
 }
 
@@ -254,6 +265,20 @@ void push_mode(Sched& S, int mu, int kind, const T* x, T* y, int epi = adr::EPI_
     a.amax_in = S.consume(x);
     a.amax_out = S.produce(y);
     a.err = c->d_err;
+    if (adr::tma_supported(n, Q, x, xlo)) {
+        // TMA-fed kernel: position tiles of 128 consecutive q of one p, 128-row output tiles
+        adr::TmaArgs t;
+        static_cast<adr::TcArgs&>(t) = a;
+        t.fimg = c->d_img2[kind][mu - 1];
+        t.fscale = c->d_fsc2[kind][mu - 1];
+        t.nK = (n + 31) / 32;
+        t.nOut = (n + 127) / 128;
+        t.nqt = (mu >= 2) ? (Q + 127) / 128 : 1;
+        t.ntiles = ((mu >= 2) ? P * t.nqt : (P + 127) / 128) * t.nOut;
+        const long long PP = P;
+        S.ops.push_back({[t, PP](cudaStream_t s) { return adr::launch_contract_tma(t, PP, s); }, OP_CONTRACT_TC});
+        return;
+    }
     S.ops.push_back({[a](cudaStream_t s) { return adr::launch_contract_tc(a, s); }, OP_CONTRACT_TC});
 }
 
@@ -773,6 +798,8 @@ void adr_destroy(adr_ctx* c) {
     free_dev(c->d_host_state);
     for (auto& row : c->d_img) for (auto& p : row) { void* q = p; free_dev(q); p = nullptr; }  // 5 kinds
     for (auto& row : c->d_fsc) for (auto& p : row) { void* q = p; free_dev(q); p = nullptr; }
+    for (auto& row : c->d_img2) for (auto& p : row) { void* q = p; free_dev(q); p = nullptr; }
+    for (auto& row : c->d_fsc2) for (auto& p : row) { void* q = p; free_dev(q); p = nullptr; }
     for (auto& p : c->d_zt) { void* q = p; free_dev(q); p = nullptr; }
     { void* q = c->d_slots; free_dev(q); c->d_slots = nullptr; }
     { void* q = c->d_err; free_dev(q); c->d_err = nullptr; }

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libadr.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
@@ -126,13 +127,25 @@ struct TcArgs {
     int* err = nullptr;                                 // bounded-wait timeout flags
 };
 
-// Host: slice an FP64 factor into the tensor-core image (see contract_tc.cu), with output
-// tiles of `rows` rows; standard slices F0, F1, 2^-8 F1, 2^-8 F2 or precise F0..F3.
+// The TMA-fed form (contract_tma.cu): the same arguments plus tensor maps of the FP32 state
+// (and of its low part), encoded at launch; position tiles are (p, 128 consecutive q).
+struct TmaArgs : TcArgs {
+    alignas(64) CUtensorMap map_x;
+    alignas(64) CUtensorMap map_xlo;
+    long long nqt = 1;          // position tiles per p: ceil(Q / 128) (modes >= 2)
+    bool has_lo = false;
+};
+bool tma_supported(int n, long long Q, const void* x, const void* xlo);
+cudaError_t launch_contract_tma(TmaArgs a, long long P, cudaStream_t s);
+
+// Host: slice an FP64 factor into the tensor-core image, with output tiles of `rows` rows
+// and K chunks of `chunk` (64: 128-byte swizzle, contract_tc.cu; 32: 64-byte swizzle,
+// contract_tma.cu); standard slices F0, F1, 2^-8 F1, 2^-8 F2 or precise F0..F3.
 struct TcFactor {
     std::vector<uint8_t> img;
     std::vector<float> fscale;
 };
-TcFactor make_tc_factor(const std::vector<double>& M, int n, int rows, bool precise);
+TcFactor make_tc_factor(const std::vector<double>& M, int n, int rows, bool precise, int chunk = 64);
 int tc_out_rows(bool state_is_a, bool precise);   // rows of an output tile of a kernel variant
 int tc_pos_rows(bool state_is_a, bool precise);   // rows of a position / fibre tile
 

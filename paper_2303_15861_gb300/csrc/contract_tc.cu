@@ -48,6 +48,7 @@
 
 #include "adr_internal.h"
 #include "phi_device.cuh"
+#include "tc_common.cuh"
 
 namespace adr {
 namespace {
@@ -58,7 +59,7 @@ constexpr int kProducerWarps = 8;
 constexpr int kMmaWarp = kProducerWarps + 4;
 constexpr int kThreads = (kMmaWarp + 1) * 32;   // 416
 constexpr uint32_t kTmemCols = 512;
-constexpr long long kWaitCycles = 4000000000LL; // bounded waits (~2 s)
+using namespace tc;
 
 // Compile-time shape of one kernel variant. SA: the state is the A operand (modes >= 2);
 // PR: precise configuration.
@@ -83,86 +84,6 @@ struct Cfg {
     static_assert(NACC * N == 256, "one accumulator set is 256 TMEM columns");
     static_assert(2 * STAGE + 1024 <= 227 * 1024, "shared memory budget");
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    return uint64_t((saddr & 0x3FFFFu) >> 4) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) |
-           (uint64_t(1) << 46) | (uint64_t(2) << 61);
-}
-
-// byte offset of the 16-byte chunk j (8 bf16 along K) of row r in a 128B-swizzled tile
-__device__ __forceinline__ uint32_t swz(int r, int j) {
-    return uint32_t((r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on phase `parity`; false on timeout (error recorded) or when the CTA aborts.
-// backoff_ns > 0 sleeps between polls so waiting warps leave issue slots to working ones.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code, volatile int* abort_flag,
-                          unsigned backoff_ns = 0) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (backoff_ns) __nanosleep(backoff_ns);
-        if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitCycles) {
-            if (err) atomicOr(err, code);
-            *abort_flag = 1;
-            return false;
-        }
-    }
-    return true;
-}
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
-                 : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                       uint32_t accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
 
 // Load 16 columns of two accumulators for this warp's 32 lanes, then wait.
 __device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float (&a)[16], float (&b)[16]) {

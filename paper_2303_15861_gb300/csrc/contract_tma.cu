@@ -1,0 +1,621 @@
+// K2 (tensor cores), TMA-fed form of the mixed-precision mu-mode contraction. Same
+// exact-slice arithmetic as contract_tc.cu (see there); what changes is how the FP32 state
+// reaches the slicers and how shared memory is spent:
+//   * a loader thread brings FP32 state tiles with cp.async.bulk.tensor (TMA) into a
+//     staging ring several chunks ahead, so the producer warps only slice shared -> shared;
+//   * K chunks of 32 with the 64-byte swizzle halve every slice tile, which leaves room for
+//     N = 128 output columns in the precise configuration too (no re-slicing of a state
+//     tile per 64 outputs; the precise form keeps one TMEM accumulator set of 4 x 128).
+// Used when the x1 extent is a multiple of 4 and the arrays are 16-byte aligned (TMA
+// stride and address rules); other shapes use contract_tc.cu.
+//
+// Tiles. Modes >= 2 (state is A): a position tile is 128 consecutive q of one p (the state
+// seen as [P][n][Q]); mode 1 (state is B): 128 consecutive fibres. Output tiles are 128 rows
+// of the factor. Warps: 0-7 producers, 8-15 epilogue, 16 MMA issuer, 17 TMA and factor loader.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "adr_internal.h"
+#include "phi_device.cuh"
+#include "tc_common.cuh"
+
+namespace adr {
+namespace {
+using namespace tc;
+
+constexpr int kM = 128;          // UMMA M, TMEM lanes
+constexpr int kN = 128;          // UMMA N
+constexpr int kKc = 32;          // K per stage: one 64-byte bf16 row (64-byte swizzle)
+constexpr int kProducerWarps = 8;
+constexpr int kEpiWarp0 = 8;      // warps 8-15: two per TMEM lane quarter, each half the columns
+constexpr int kEpiWarps = 8;
+constexpr int kMmaWarp = 16;
+constexpr int kLoadWarp = 17;
+constexpr int kThreads = 18 * 32;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kN >> 3) << 17) | (uint32_t(kM >> 4) << 24);
+
+template <bool PR>
+struct Cfg {
+    static constexpr int SS = PR ? 4 : 3;              // state slices
+    static constexpr int FS = 4;                       // factor slices
+    static constexpr int NACC = PR ? 4 : 2;            // accumulators (128 columns each)
+    static constexpr int NSETS = PR ? 1 : 2;           // TMEM accumulator sets
+    static constexpr int TILE = kM * kKc * 2;          // one bf16 slice tile: 8 KB
+    static constexpr int SBYTES = SS * TILE;           // one state-slice stage
+    static constexpr int FBYTES = FS * TILE;           // one factor stage (32 KB)
+    static constexpr int NSLICE = 2;                   // state-slice ring
+    static constexpr int NF = PR ? 3 : 4;              // factor ring (the loader runs it ahead)
+    static constexpr int XTILE = kM * kKc * 4;         // one FP32 staging tile: 16 KB
+    static constexpr int XSTAGE = PR ? 2 * XTILE : XTILE;   // hi (+ lo)
+    static constexpr int NX = 2;
+    static constexpr int SMEM = NSLICE * SBYTES + NF * FBYTES + NX * XSTAGE + 1024;
+    static_assert(NACC * kN * NSETS <= 512, "TMEM");
+    static_assert(SMEM <= 227 * 1024, "shared memory budget");
+};
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float (&a)[16], float (&b)[16]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%33];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(ta), "r"(tb)
+        : "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        a[j] = __uint_as_float(r[j]);
+        b[j] = __uint_as_float(r[16 + j]);
+    }
+}
+
+__device__ __forceinline__ void tmem_ld8x4(uint32_t t0, uint32_t stride, float (&d)[4][8]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%32];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%33];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%34];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%35];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(t0), "r"(t0 + stride), "r"(t0 + 2 * stride), "r"(t0 + 3 * stride)
+        : "memory");
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) d[k][j] = __uint_as_float(r[8 * k + j]);
+}
+
+// Integer slices of y (+ ylo); see split<> in contract_tc.cu.
+template <bool PR>
+__device__ __forceinline__ void split(float y, float ylo, uint32_t (&b)[4]) {
+    const float s0 = rintf(y);
+    const float r0 = PR ? (y - s0) + ylo : (y - s0);
+    const float y1 = r0 * 256.f;
+    const float s1 = rintf(y1);
+    const float y2 = (y1 - s1) * 256.f;
+    const float s2 = rintf(y2);
+    b[0] = __float_as_uint(s0);
+    b[1] = __float_as_uint(s1);
+    if (PR) {
+        b[2] = __float_as_uint(s2);
+        b[3] = __float_as_uint(rintf((y2 - s2) * 256.f));
+    } else {
+        b[2] = __float_as_uint(s2 * 0.00390625f);
+        b[3] = 0u;
+    }
+}
+
+// Slice 8 values (+ low parts) and store them as 16-byte chunk j of row r of the SS tiles.
+template <bool PR>
+__device__ __forceinline__ void slice_store8(const float (&v)[8], const float (&vl)[8], float sc, uint32_t tile0, int r,
+                                             int j) {
+    constexpr int SS = PR ? 4 : 3;
+    uint32_t w[4][4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        uint32_t a[4], c[4];
+        split<PR>(v[2 * e] * sc, vl[2 * e] * sc, a);
+        split<PR>(v[2 * e + 1] * sc, vl[2 * e + 1] * sc, c);
+#pragma unroll
+        for (int q = 0; q < SS; ++q) w[q][e] = __byte_perm(a[q], c[q], 0x7632);
+    }
+    const uint32_t off = swz64(r, j);
+#pragma unroll
+    for (int q = 0; q < SS; ++q)
+        st_shared_v4(tile0 + q * (kM * kKc * 2) + off, make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]));
+}
+
+__device__ __forceinline__ float lds(uint32_t a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float4 lds4(uint32_t a) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+template <bool SA, bool PR>
+__device__ __forceinline__ void mma_kstep(uint32_t d, const uint64_t (&S)[4], const uint64_t (&F)[4], uint64_t adv,
+                                          uint32_t first) {
+    auto mma = [&](int acc, int si, int fi, uint32_t accumulate) {
+        const uint32_t dd = d + uint32_t(acc * kN);
+        if (SA) tc_mma(dd, S[si] + adv, F[fi] + adv, kIdesc, accumulate);
+        else    tc_mma(dd, F[fi] + adv, S[si] + adv, kIdesc, accumulate);
+    };
+    const uint32_t acc = first ? 0u : 1u;
+    if (!PR) {
+        mma(0, 0, 0, acc);
+        mma(1, 0, 1, acc);
+        mma(1, 1, 0, 1u);
+        mma(1, 0, 3, 1u);
+        mma(1, 2, 0, 1u);
+        mma(1, 1, 2, 1u);
+    } else {
+        mma(0, 0, 0, acc);
+        mma(1, 0, 1, acc);
+        mma(1, 1, 0, 1u);
+        mma(2, 0, 2, acc);
+        mma(2, 1, 1, 1u);
+        mma(2, 2, 0, 1u);
+        mma(3, 0, 3, acc);
+        mma(3, 1, 2, 1u);
+        mma(3, 2, 1, 1u);
+        mma(3, 3, 0, 1u);
+    }
+}
+
+template <bool SA, bool PR, int EPI>
+__global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_constant__ TmaArgs p) {
+    using C = Cfg<PR>;
+    extern __shared__ uint8_t smem_raw[];
+    // barriers: xfull[2] xempty[2] sfull[2] sempty[2] ffull[4] fempty[4] accf[2] acce[2] drain
+    __shared__ __align__(8) uint64_t bars[21];
+    __shared__ uint32_t tmem_base_s;
+    __shared__ volatile int abort_s;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;   // state-slice ring
+    const uint32_t fbase = sbase + C::NSLICE * C::SBYTES;             // factor ring
+    const uint32_t xbase = fbase + C::NF * C::FBYTES;                 // FP32 staging ring
+    const uint32_t bar0 = smem_u32(&bars[0]);
+    auto xfull = [&](int s) { return bar0 + 8u * s; };
+    auto xempty = [&](int s) { return bar0 + 16u + 8u * s; };
+    auto sfull = [&](int s) { return bar0 + 32u + 8u * s; };
+    auto sempty = [&](int s) { return bar0 + 48u + 8u * s; };
+    auto ffull = [&](int s) { return bar0 + 64u + 8u * s; };
+    auto fempty = [&](int s) { return bar0 + 96u + 8u * s; };
+    auto accf = [&](int a) { return bar0 + 128u + 8u * a; };
+    auto acce = [&](int a) { return bar0 + 144u + 8u * a; };
+    const uint32_t drain_bar = bar0 + 160u;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::NX; ++s) {
+            mbar_init(xfull(s), 1);                         // loader's expect_tx arrival
+            mbar_init(xempty(s), kProducerWarps * 32);      // producers have read the tile
+        }
+        for (int s = 0; s < C::NSLICE; ++s) {
+            mbar_init(sfull(s), kProducerWarps * 32);       // producers
+            mbar_init(sempty(s), 1);                        // tcgen05.commit
+        }
+        for (int s = 0; s < C::NF; ++s) {
+            mbar_init(ffull(s), 1);                         // loader's expect_tx arrival
+            mbar_init(fempty(s), 1);                        // tcgen05.commit
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(accf(a), 1);
+            mbar_init(acce(a), kEpiWarps * 32);
+        }
+        mbar_init(drain_bar, 1);
+        abort_s = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_s;
+
+    const float amax = __uint_as_float(*p.amax_in);
+    int es = 0;
+    if (amax > 0.f) frexpf(amax, &es);
+    const float sc = ldexpf(1.f, 7 - es);
+    const float sback = ldexpf(1.f, es - 7);
+    const int n = p.n;
+    const long long Q = p.Q;
+    const long long my_tiles = (p.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
+    const long long items = my_tiles * p.nK;
+
+    // tile -> (position tile, output tile); position tile -> (p, q0) or fibre f0
+    auto tile_of = [&](long long it) { return blockIdx.x + (it / p.nK) * gridDim.x; };
+
+    if (warp == kLoadWarp) {
+        // ------------------------------------------------------------ TMA loader
+        // Fills the factor ring (pre-sliced factor tiles, consumed directly by the MMA; the
+        // slot of item i frees when the MMA of item i - NF retires, so each copy has NF - 1
+        // chunks of lead time) and the FP32 staging ring (state tiles for the producers).
+        if (lane == 0) {
+            for (long long it = 0; it < items && !abort_s; ++it) {
+                const long long tile = tile_of(it);
+                {
+                    const int s = int(it % C::NF);
+                    const uint32_t ph = uint32_t(it / C::NF) & 1u;
+                    if (!mbar_wait(fempty(s), ph ^ 1u, p.err, 64, &abort_s, 32)) break;
+                    mbar_arrive_expect_tx(ffull(s), C::FBYTES);
+                    const uint8_t* src = p.fimg + (size_t(tile % p.nOut) * p.nK + it % p.nK) * C::FBYTES;
+                    const uint32_t dst = fbase + s * C::FBYTES;
+#pragma unroll
+                    for (int q = 0; q < C::FS; ++q) bulk_g2s(dst + q * C::TILE, src + q * C::TILE, C::TILE, ffull(s));
+                }
+                {
+                    const int s = int(it % C::NX);
+                    const uint32_t ph = uint32_t(it / C::NX) & 1u;
+                    if (!mbar_wait(xempty(s), ph ^ 1u, p.err, 16, &abort_s, 32)) break;
+                    const long long pt = tile / p.nOut;
+                    const int k0 = int(it % p.nK) * kKc;
+                    const uint32_t dst = xbase + s * C::XSTAGE;
+                    const bool lo = PR && p.has_lo;
+                    mbar_arrive_expect_tx(xfull(s), lo ? 2 * C::XTILE : C::XTILE);
+                    if (SA) {
+                        const int pidx = int(pt / p.nqt), q0 = int(pt % p.nqt) * kM;
+                        tma_load_3d(dst, &p.map_x, q0, k0, pidx, xfull(s));
+                        if (lo) tma_load_3d(dst + C::XTILE, &p.map_xlo, q0, k0, pidx, xfull(s));
+                    } else {
+                        const int f0 = int(pt * kN);
+                        tma_load_2d(dst, &p.map_x, k0, f0, xfull(s));
+                        if (lo) tma_load_2d(dst + C::XTILE, &p.map_xlo, k0, f0, xfull(s));
+                    }
+                }
+            }
+        }
+    } else if (warp < kProducerWarps) {
+        // ------------------------------------------------------------ producers (shared -> shared)
+        const int t = threadIdx.x;
+        for (long long it = 0; it < items; ++it) {
+            const int ss = int(it % C::NSLICE);
+            const uint32_t sph = uint32_t(it / C::NSLICE) & 1u;
+            if (!mbar_wait(sempty(ss), sph ^ 1u, p.err, 1, &abort_s, 32)) break;
+            const uint32_t sA = sbase + ss * C::SBYTES;
+            const int xs = int(it % C::NX);
+            const uint32_t xph = uint32_t(it / C::NX) & 1u;
+            if (!mbar_wait(xfull(xs), xph, p.err, 32, &abort_s)) break;
+            const uint32_t xt = xbase + xs * C::XSTAGE;
+            float v[2][8], vl[2][8];
+            if (SA) {
+                // staging tile [k][q] (32 rows of 128 floats); thread: position row, 16 K values
+                const int row = t & (kM - 1), half = t >> 7;
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const uint32_t a = xt + uint32_t(((16 * half + 8 * h + e) * kM + row) * 4);
+                        v[h][e] = lds(a);
+                        vl[h][e] = (PR && p.has_lo) ? lds(a + C::XTILE) : 0.f;
+                    }
+            } else {
+                // staging tile [f][k] (128 rows of 32 floats); thread: chunk j of rows r0, r0 + 64
+                const int j = t & 3, r0 = t >> 2;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t a = xt + uint32_t(((r0 + 64 * h) * kKc + 8 * j) * 4);
+                    const float4 x0 = lds4(a), x1 = lds4(a + 16);
+                    v[h][0] = x0.x; v[h][1] = x0.y; v[h][2] = x0.z; v[h][3] = x0.w;
+                    v[h][4] = x1.x; v[h][5] = x1.y; v[h][6] = x1.z; v[h][7] = x1.w;
+                    if (PR && p.has_lo) {
+                        const float4 y0 = lds4(a + C::XTILE), y1 = lds4(a + C::XTILE + 16);
+                        vl[h][0] = y0.x; vl[h][1] = y0.y; vl[h][2] = y0.z; vl[h][3] = y0.w;
+                        vl[h][4] = y1.x; vl[h][5] = y1.y; vl[h][6] = y1.z; vl[h][7] = y1.w;
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) vl[h][e] = 0.f;
+                    }
+                }
+            }
+            mbar_arrive(xempty(xs));      // the staging tile may be refilled
+            if (SA) {
+                const int row = t & (kM - 1), half = t >> 7;
+                slice_store8<PR>(v[0], vl[0], sc, sA, row, 2 * half);
+                slice_store8<PR>(v[1], vl[1], sc, sA, row, 2 * half + 1);
+            } else {
+                const int j = t & 3, r0 = t >> 2;
+                slice_store8<PR>(v[0], vl[0], sc, sA, r0, j);
+                slice_store8<PR>(v[1], vl[1], sc, sA, r0 + 64, j);
+            }
+            fence_proxy_async();
+            mbar_arrive(sfull(ss));
+        }
+    } else if (warp < kEpiWarp0 + kEpiWarps) {
+        // ------------------------------------------------------------ epilogue
+        const int ew = (warp - kEpiWarp0) & 3;          // TMEM lane quarter (warp % 4)
+        const int half = (warp - kEpiWarp0) >> 2;       // column half
+        const int row = ew * 32 + lane;
+        long long tl = 0;
+        for (long long tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, ++tl) {
+            const int a = int(tl % C::NSETS);
+            const uint32_t ph = uint32_t(tl / C::NSETS) & 1u;
+            const bool waited = mbar_wait(accf(a), ph, p.err, 2, &abort_s, 64);
+            if (!__all_sync(0xffffffffu, waited)) break;
+            tc_fence_after();
+            const long long pt = tile / p.nOut;
+            const int ot = int(tile % p.nOut);
+            float vmax = 0.f;
+            bool rvalid;
+            long long off0, cstep;
+            float zrow = 0.f, rscale = 0.f;
+            int ncol;
+            if (SA) {
+                const long long pp = pt / p.nqt, qq = (pt % p.nqt) * kM + row;
+                rvalid = qq < Q;
+                off0 = (pp * n + ot * kN) * Q + qq;
+                cstep = Q;
+                ncol = min(kN, n - ot * kN);
+                if (EPI == EPI_PHI && rvalid) {
+                    zrow = __ldg(p.zq_a + qq % p.na);
+                    if (p.zq_b) zrow += __ldg(p.zq_b + qq / p.na);
+                    if (p.zp) zrow += __ldg(p.zp + pp);
+                }
+            } else {
+                const int irow = ot * kM + row;
+                rvalid = irow < n;
+                if (rvalid) rscale = sback * __ldg(p.fscale + irow);
+                off0 = pt * kN * (long long)n + irow;
+                cstep = n;
+                ncol = int(min((long long)kN, p.npos - pt * kN));
+            }
+            const float* fsc = p.fscale + ot * kN;
+            const float* zc = p.zmu + ot * kN;
+            float* yrow = p.Y + off0;
+            float* ylo = (EPI == EPI_STORE2) ? p.Ylo + off0 : nullptr;
+            const float* brow = (EPI == EPI_AXPY) ? p.base + off0 : nullptr;
+            const uint32_t tbase = tmem + (uint32_t(ew * 32) << 16) + uint32_t(a) * 256u;
+            auto emit = [&](int col, float hi, float lo) {
+                const float scale = SA ? sback * __ldg(fsc + col) : rscale;
+                const long long o = (long long)col * cstep;
+                if (EPI == EPI_STORE2) {
+                    yrow[o] = hi * scale;
+                    ylo[o] = lo * scale;
+                    vmax = fmaxf(vmax, fabsf(hi * scale));
+                    return;
+                }
+                float v = (hi + lo) * scale;
+                if (EPI == EPI_PHI) v *= phi_eval(p.phik, zrow + __ldg(zc + col));
+                if (EPI == EPI_AXPY) v = fmaf(p.alpha, v, __ldg(brow + o));
+                yrow[o] = v;
+                vmax = fmaxf(vmax, fabsf(v));
+            };
+            const int jlo = half * (kN / 2), jhi = jlo + kN / 2;
+            if (!PR) {
+#pragma unroll 1
+                for (int j0 = jlo; j0 < jhi; j0 += 16) {
+                    float d0[16], d1[16];
+                    __syncwarp();
+                    tmem_ld16x2(tbase + j0, tbase + uint32_t(kN) + j0, d0, d1);
+                    if (!rvalid || j0 >= ncol) continue;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        if (j0 + j >= ncol) break;
+                        const float t1 = d1[j] * 0.00390625f;
+                        if (EPI == EPI_STORE2) {
+                            float hi, lo;
+                            two_sum(d0[j], t1, hi, lo);
+                            emit(j0 + j, hi, lo);
+                        } else {
+                            emit(j0 + j, d0[j] + t1, 0.f);
+                        }
+                    }
+                }
+            } else {
+#pragma unroll 1
+                for (int j0 = jlo; j0 < jhi; j0 += 8) {
+                    float d[4][8];
+                    __syncwarp();
+                    tmem_ld8x4(tbase + j0, uint32_t(kN), d);
+                    if (!rvalid || j0 >= ncol) continue;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (j0 + j >= ncol) break;
+                        float hi, lo;
+                        two_sum(d[0][j], d[1][j] * 0.00390625f, hi, lo);
+                        lo += fmaf(d[3][j], 5.9604644775390625e-08f, d[2][j] * 1.52587890625e-05f);
+                        const float s = hi + lo;
+                        lo = lo - (s - hi);
+                        emit(j0 + j, s, lo);
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(acce(a));
+            for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+            if (lane == 0 && p.amax_out && vmax > 0.f) atomicMax(p.amax_out, __float_as_uint(vmax));
+        }
+    } else if (warp == kMmaWarp && lane == 0) {
+        // ------------------------------------------------------------ MMA issuer (warp 12)
+        long long g = 0, tl = 0;
+        for (long long tile = blockIdx.x; tile < p.ntiles && !abort_s; tile += gridDim.x, ++tl) {
+            const int a = int(tl % C::NSETS);
+            const uint32_t aph = uint32_t(tl / C::NSETS) & 1u;
+            if (!mbar_wait(acce(a), aph ^ 1u, p.err, 4, &abort_s)) break;
+            tc_fence_after();
+            const uint32_t d = tmem + uint32_t(a) * 256u;
+            bool ok = true;
+            for (int c = 0; c < p.nK; ++c, ++g) {
+                const int s = int(g % C::NSLICE);
+                const uint32_t ph = uint32_t(g / C::NSLICE) & 1u;
+                const int fs = int(g % C::NF);
+                const uint32_t fph = uint32_t(g / C::NF) & 1u;
+                if (!mbar_wait(ffull(fs), fph, p.err, 128, &abort_s)) { ok = false; break; }
+                if (!mbar_wait(sfull(s), ph, p.err, 8, &abort_s)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t sS = sbase + s * C::SBYTES;
+                const uint32_t sF = fbase + fs * C::FBYTES;
+                uint64_t S[4], F[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    S[q] = sdesc64(sS + (q < C::SS ? q : 0) * C::TILE);
+                    F[q] = sdesc64(sF + q * C::TILE);
+                }
+#pragma unroll
+                for (int kk = 0; kk < kKc / 16; ++kk)
+                    mma_kstep<SA, PR>(d, S, F, uint64_t(kk * 32) >> 4, (c == 0 && kk == 0) ? 1u : 0u);
+                tc_commit(sempty(s));
+                tc_commit(fempty(fs));
+            }
+            if (!ok) break;
+            tc_commit(accf(a));
+        }
+        tc_commit(drain_bar);
+        const long long t0 = clock64();
+        while (!mbar_try_wait(drain_bar, 0) && clock64() - t0 < kWaitCycles) {}
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+int g_sms = 0;
+
+template <bool SA, bool PR, int EPI>
+cudaError_t launch_variant(const TmaArgs& a, unsigned grid, cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(tma_contract_kernel<SA, PR, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             Cfg<PR>::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    tma_contract_kernel<SA, PR, EPI><<<grid, kThreads, Cfg<PR>::SMEM, s>>>(a);
+    return cudaGetLastError();
+}
+
+// FP32 tensor map over the state seen as [P][n][Q] (modes >= 2; box 128 q x 32 k x 1 p) or
+// as [P][n] rows of n (mode 1; box 32 k x 128 fibres).
+// cuTensorMapEncodeTiled is a driver-API call; the library takes it through the runtime's
+// driver entry-point query so that it does not link libcuda itself and still loads (for
+// symbol checks) on a machine without a GPU driver.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled_fn() {
+    static EncodeTiledFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return EncodeTiledFn(nullptr);
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+bool encode_map(CUtensorMap* m, const float* x, bool state_is_a, long long n, long long Q, long long P) {
+    if (!x) return true;
+    const EncodeTiledFn cuTensorMapEncodeTiled = encode_tiled_fn();
+    if (!cuTensorMapEncodeTiled) return false;
+    CUresult r;
+    if (state_is_a) {
+        cuuint64_t dims[3] = {cuuint64_t(Q), cuuint64_t(n), cuuint64_t(P)};
+        cuuint64_t strides[2] = {cuuint64_t(Q * 4), cuuint64_t(n * Q * 4)};
+        cuuint32_t box[3] = {cuuint32_t(kM), cuuint32_t(kKc), 1u};
+        cuuint32_t es[3] = {1u, 1u, 1u};
+        r = cuTensorMapEncodeTiled(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(x), dims, strides, box, es,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        cuuint64_t dims[2] = {cuuint64_t(n), cuuint64_t(P)};
+        cuuint64_t strides[1] = {cuuint64_t(n * 4)};
+        cuuint32_t box[2] = {cuuint32_t(kKc), cuuint32_t(kN)};
+        cuuint32_t es[2] = {1u, 1u};
+        r = cuTensorMapEncodeTiled(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(x), dims, strides, box, es,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool tma_supported(int n, long long Q, const void* x, const void* xlo) {
+    // TMA: 16-byte aligned base addresses and row strides (Q * 4 or n * 4 bytes)
+    if (reinterpret_cast<uintptr_t>(x) % 16 != 0) return false;
+    if (xlo && reinterpret_cast<uintptr_t>(xlo) % 16 != 0) return false;
+    if (Q == 1) return n % 4 == 0;
+    return Q % 4 == 0;
+}
+
+cudaError_t launch_contract_tma(TmaArgs a, long long P, cudaStream_t s) {
+    if (g_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    if (a.n > 512 || a.n < 1) return cudaErrorInvalidValue;
+    if (!encode_map(&a.map_x, a.X, a.state_is_a, a.n, a.Q, P)) return cudaErrorInvalidValue;
+    a.has_lo = a.precise && a.Xlo != nullptr;
+    if (a.has_lo && !encode_map(&a.map_xlo, a.Xlo, a.state_is_a, a.n, a.Q, P)) return cudaErrorInvalidValue;
+    const long long grid = a.ntiles < g_sms ? a.ntiles : g_sms;
+    if (grid <= 0) return cudaSuccess;
+    const unsigned g = unsigned(grid);
+    if (a.precise) {
+        if (a.epi != EPI_STORE2 && a.epi != EPI_STORE) return cudaErrorInvalidValue;
+        if (a.state_is_a) return a.epi == EPI_STORE2 ? launch_variant<true, true, EPI_STORE2>(a, g, s)
+                                                     : launch_variant<true, true, EPI_STORE>(a, g, s);
+        return a.epi == EPI_STORE2 ? launch_variant<false, true, EPI_STORE2>(a, g, s)
+                                   : launch_variant<false, true, EPI_STORE>(a, g, s);
+    }
+    if (a.state_is_a) {
+        if (a.epi == EPI_PHI) return launch_variant<true, false, EPI_PHI>(a, g, s);
+        if (a.epi == EPI_AXPY) return launch_variant<true, false, EPI_AXPY>(a, g, s);
+        if (a.epi == EPI_STORE2) return launch_variant<true, false, EPI_STORE2>(a, g, s);
+        return launch_variant<true, false, EPI_STORE>(a, g, s);
+    }
+    if (a.epi == EPI_PHI || a.epi == EPI_STORE2) return cudaErrorInvalidValue;
+    if (a.epi == EPI_AXPY) return launch_variant<false, false, EPI_AXPY>(a, g, s);
+    return launch_variant<false, false, EPI_STORE>(a, g, s);
+}
+
+}  // namespace adr

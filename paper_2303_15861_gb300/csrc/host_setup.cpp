@@ -176,14 +176,15 @@ uint16_t bf16_bits_exact(double v) {
 }
 }  // namespace
 
-TcFactor make_tc_factor(const std::vector<double>& M, int n, int rows, bool precise) {
+TcFactor make_tc_factor(const std::vector<double>& M, int n, int rows, bool precise, int chunk) {
     // Each row i of M (an output index) is written as 2^(e_i-7) sum_j 2^(-8j) f_j with
     // integer slices |f_j| <= 128 and max_k |M[i][k]| < 2^e_i. The image stores, per
     // (output tile of `rows` rows, K chunk of 64), four slice tiles in the 128-byte-swizzled
     // K-major layout the tensor cores read (8-row groups of 1024 B; 16-byte chunk j of row r
     // at position j ^ (r mod 8)): F0, F1, 2^-8 F1, 2^-8 F2 (standard) or F0, F1, F2, F3
-    // (precise).
-    const int chunk = 64, tile = rows * chunk * 2;
+    // (precise). With chunks of 32 the tiles use the 64-byte swizzle (8-row groups of 512 B;
+    // chunk j of row r at position j ^ ((r / 2) mod 4)).
+    const int tile = rows * chunk * 2;
     const int nK = (n + chunk - 1) / chunk, nOut = (n + rows - 1) / rows;
     TcFactor out;
     out.img.assign(size_t(nOut) * nK * 4 * tile, 0);
@@ -218,12 +219,14 @@ TcFactor make_tc_factor(const std::vector<double>& M, int n, int rows, bool prec
                 for (int r = 0; r < rows; ++r) {
                     const int i = ot * rows + r;
                     if (i >= n) continue;
-                    for (int j = 0; j < 8; ++j)
+                    for (int j = 0; j < chunk / 8; ++j)
                         for (int e2 = 0; e2 < 8; ++e2) {
                             const int k = c * chunk + 8 * j + e2;
                             if (k >= n) continue;
                             const uint16_t b = bf16_bits_exact(slices[(size_t(i) * n + k) * 4 + q]);
-                            const size_t off = size_t((r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4) + 2 * e2);
+                            const size_t off = chunk == 64
+                                ? size_t((r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4) + 2 * e2)
+                                : size_t((r >> 3) * 512 + (r & 7) * 64 + ((j ^ ((r >> 1) & 3)) << 4) + 2 * e2);
                             t[off] = uint8_t(b & 0xFF);
                             t[off + 1] = uint8_t(b >> 8);
                         }
