@@ -137,7 +137,8 @@ adr_status adr_get_info(const adr_ctx* ctx, double kappa[3], double* abar, doubl
 /* One adr_step with a CUDA event recorded on the context stream around every enqueued
  * operation (no graph). Writes, for the i-th operation, its duration in ms[i] and its kind
  * in kind[i] (0 memset, 1 max-abs reduction, 2 stencil, 3 SIMT contraction,
- * 4 tensor-core contraction) and the count in *n_ops. Synchronous. ADR_ERR_ARG if the step
+ * 4 tensor-core contraction, 5 tensor-core contraction in the precise four-slice
+ * configuration) and the count in *n_ops. Synchronous. ADR_ERR_ARG if the step
  * has more than max_ops operations. */
 adr_status adr_profile_step(adr_ctx* ctx, void* u_dev, int max_ops, float* ms, int* kind, int* n_ops);
 

@@ -35,7 +35,8 @@ using adr::StencilArgs;
 namespace {
 
 // One enqueued operation of a schedule and the kind of kernel it launches.
-enum OpKind { OP_MEMSET = 0, OP_AMAX = 1, OP_STENCIL = 2, OP_CONTRACT_SIMT = 3, OP_CONTRACT_TC = 4 };
+enum OpKind { OP_MEMSET = 0, OP_AMAX = 1, OP_STENCIL = 2, OP_CONTRACT_SIMT = 3, OP_CONTRACT_TC = 4,
+              OP_CONTRACT_TC_PRECISE = 5 };
 struct Op {
     std::function<cudaError_t(cudaStream_t)> fn;
     int kind;
@@ -265,6 +266,7 @@ void push_mode(Sched& S, int mu, int kind, const T* x, T* y, int epi = adr::EPI_
     a.amax_in = S.consume(x);
     a.amax_out = S.produce(y);
     a.err = c->d_err;
+    const int tc_kind = a.precise ? OP_CONTRACT_TC_PRECISE : OP_CONTRACT_TC;
     if (adr::tma_supported(n, Q, x, xlo)) {
         // TMA-fed kernel: position tiles of 128 consecutive q of one p, 128-row output tiles
         adr::TmaArgs t;
@@ -276,10 +278,10 @@ void push_mode(Sched& S, int mu, int kind, const T* x, T* y, int epi = adr::EPI_
         t.nqt = (mu >= 2) ? (Q + 127) / 128 : 1;
         t.ntiles = ((mu >= 2) ? P * t.nqt : (P + 127) / 128) * t.nOut;
         const long long PP = P;
-        S.ops.push_back({[t, PP](cudaStream_t s) { return adr::launch_contract_tma(t, PP, s); }, OP_CONTRACT_TC});
+        S.ops.push_back({[t, PP](cudaStream_t s) { return adr::launch_contract_tma(t, PP, s); }, tc_kind});
         return;
     }
-    S.ops.push_back({[a](cudaStream_t s) { return adr::launch_contract_tc(a, s); }, OP_CONTRACT_TC});
+    S.ops.push_back({[a](cudaStream_t s) { return adr::launch_contract_tc(a, s); }, tc_kind});
 }
 
 // y = e^{c tau A} x, optionally finished by y = base + alpha * (e^{c tau A} x).
