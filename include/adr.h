@@ -82,14 +82,29 @@ typedef struct {
     double kappa_tol;      /* eigen route guard: fail with ADR_ERR_ILL_CONDITIONED when
                               prod_mu kappa(V_mu) * unit roundoff > kappa_tol; <= 0 selects
                               1e-2. Only schemes that need phi_k (ADR_ETD2RK) check it.  */
+    int batch;             /* 0: one grid (dim, n). > 0: that many independent 2-D
+                              instances of uneven size in one context (dim must be 2;
+                              ADR_FP64 or ADR_FP32)                                       */
+    const int* n_batch;    /* batch > 0: host, 2*batch ints (n1, n2) of instance i at
+                              [2i], [2i+1]; copied by adr_create                          */
+    int batch_tile;        /* batch > 0: 0 = tile shapes and grid chosen by the autotuner;
+                              32, 64 or 128 = that square tile for every instance          */
 } adr_params;
 
-/* Create a context for one grid. cuda_stream is a cudaStream_t (NULL = legacy default
- * stream) on the current device. Validates params, allocates the device workspace.
- * The factors are built by adr_set_coeffs. On failure *out is NULL. */
+/* Create a context for one grid, or for a batch of independent 2-D instances.
+ * cuda_stream is a cudaStream_t (NULL = legacy default stream) on the current device.
+ * Validates params, allocates the device workspace. The factors are built by
+ * adr_set_coeffs. On failure *out is NULL.
+ *
+ * Batched contexts. Every state-sized array (the state u of adr_step / adr_integrate,
+ * the inputs and outputs of the building blocks) packs the instances one after another:
+ * instance i occupies n1_i*n2_i elements (x1 fastest) starting at element
+ * sum_{j<i} n1_j*n2_j. Every stage of a step is one persistent kernel launch over all
+ * instances. All instances share tau and the scheme. */
 adr_status adr_create(const adr_params* p, void* cuda_stream, adr_ctx** out);
 
-/* Set the coefficients of Eq. (adr) (instance must be 0).
+/* Set the coefficients of Eq. (adr) of one instance (0 for a single-grid context,
+ * 0..batch-1 for a batched one).
  *   a_nodes: host, (n3+2)*(n2+2)*(n1+2) doubles (2-D: (n2+2)*(n1+2)), the diffusion
  *            coefficient at every node including the boundary ring, x1 fastest.
  *   b:       host, 3 doubles, constant velocity (b3 ignored in 2-D).
@@ -98,7 +113,13 @@ adr_status adr_create(const adr_params* p, void* cuda_stream, adr_ctx** out);
  * e^{c tau A_mu} (Pade-13 scaling and squaring) and the closed-form eigenpairs of
  * A_mu; uploads them. Synchronous with respect to the host data (it may be freed on
  * return). Returns ADR_ERR_COMPLEX_SPECTRUM / ADR_ERR_ILL_CONDITIONED for ADR_ETD2RK
- * when the eigen route is unavailable or fails the kappa guard. */
+ * when the eigen route is unavailable or fails the kappa guard.
+ * Batched contexts build only the factors their scheme uses (e^{tau A_mu} for
+ * ADR_LAWSON_EULER, e^{tau A_mu / 2} for ADR_LAWSON4, the eigenpairs for ADR_ETD2RK).
+ * Steps are refused (ADR_ERR_STATE) until every instance is set. The call that sets
+ * the last unset instance uploads the batch and runs the autotuner: it times candidate
+ * tile shapes per instance size and grid sizes on the context stream, synchronously.
+ * It must not be made while the stream is being captured. */
 adr_status adr_set_coeffs(adr_ctx* ctx, int instance, const double* a_nodes,
                           const double b[3], const double r_poly[4]);
 
@@ -133,6 +154,18 @@ adr_status adr_synchronize(adr_ctx* ctx);
 /* Host-side facts of the current operator: kappa(V_mu) per direction (0 when the
  * spectrum is complex), lambda*a_max, and beta. Any pointer may be NULL. */
 adr_status adr_get_info(const adr_ctx* ctx, double kappa[3], double* abar, double beta[3]);
+
+/* The same facts for one instance of a batched context (instance 0 of a single-grid
+ * context gives adr_get_info's values). ADR_ERR_STATE if the instance is not set. */
+adr_status adr_get_instance_info(const adr_ctx* ctx, int instance, double kappa[3], double* abar,
+                                 double beta[3]);
+
+/* The contraction schedule of a batched context, as chosen by the autotuner (or forced
+ * by batch_tile), for mode 1 (contraction along x1) or mode 2: the tile edge (32, 64 or
+ * 128) of every instance in tile_edge[0..batch-1] (may be NULL) and the number of
+ * persistent CTAs of the launch in *grid (may be NULL). ADR_ERR_STATE before every
+ * instance is set; ADR_ERR_ARG for a single-grid context. */
+adr_status adr_get_batch_plan(const adr_ctx* ctx, int mode, int* tile_edge, int* grid);
 
 /* One adr_step with a CUDA event recorded on the context stream around every enqueued
  * operation (no graph). Writes, for the i-th operation, its duration in ms[i] and its kind

@@ -33,7 +33,8 @@ class AdrError(RuntimeError):
 class adr_params(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("lambda_", C.c_double),
                 ("abar_override", C.c_double), ("tau", C.c_double), ("scheme", C.c_int),
-                ("precision", C.c_int), ("kappa_tol", C.c_double)]
+                ("precision", C.c_int), ("kappa_tol", C.c_double), ("batch", C.c_int),
+                ("n_batch", C.POINTER(C.c_int)), ("batch_tile", C.c_int)]
 
 
 _lib = None
@@ -61,6 +62,8 @@ def load_library(path: str = LIB_PATH):
         "adr_synchronize": (ip, [vp]),
         "adr_profile_step": (ip, [vp, vp, ip, C.POINTER(C.c_float), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "adr_get_info": (ip, [vp, dp, dp, dp]),
+        "adr_get_instance_info": (ip, [vp, ip, dp, dp, dp]),
+        "adr_get_batch_plan": (ip, [vp, ip, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "adr_mumode_apply_static": (ip, [ip, C.POINTER(C.c_int), C.POINTER(vp), vp, vp, vp]),
         "adr_kernels_per_step": (ip, [vp]),
         "adr_last_error": (C.c_char_p, [vp]),
@@ -105,10 +108,22 @@ def _stream_handle(stream):
 
 # ------------------------------------------------------------------- C entry points
 def adr_create(dims, tau, scheme="lawson4", precision="fp64", lam=1.0, abar_override=0.0,
-               kappa_tol=0.0, stream=None):
+               kappa_tol=0.0, stream=None, batch_dims=None, batch_tile=0):
+    """dims: grid of a single-grid context; batch_dims: [(n1, n2), ...] of a batched 2-D
+    context (dims is then ignored)."""
     lib = load_library()
     p = adr_params()
-    p.dim = len(dims)
+    nb = None
+    if batch_dims is not None:
+        flat = [int(v) for d in batch_dims for v in d]
+        nb = (C.c_int * len(flat))(*flat)
+        p.dim = 2
+        p.batch = len(batch_dims)
+        p.n_batch = C.cast(nb, C.POINTER(C.c_int))
+        p.batch_tile = int(batch_tile)
+        dims = ()
+    else:
+        p.dim = len(dims)
     for i, n in enumerate(dims):
         p.n[i] = int(n)
     p.lambda_ = float(lam)
@@ -198,6 +213,21 @@ def adr_get_info(ctx):
     return {"kappa": list(kappa), "abar": abar.value, "beta": list(beta)}
 
 
+def adr_get_instance_info(ctx, instance):
+    kappa = (C.c_double * 3)()
+    abar = C.c_double()
+    beta = (C.c_double * 3)()
+    _check(_lib.adr_get_instance_info(ctx, int(instance), kappa, C.byref(abar), beta), ctx)
+    return {"kappa": list(kappa), "abar": abar.value, "beta": list(beta)}
+
+
+def adr_get_batch_plan(ctx, mode, batch):
+    edges = (C.c_int * int(batch))()
+    grid = C.c_int()
+    _check(_lib.adr_get_batch_plan(ctx, int(mode), edges, C.byref(grid)), ctx)
+    return list(edges), grid.value
+
+
 def adr_kernels_per_step(ctx):
     return int(_lib.adr_kernels_per_step(ctx))
 
@@ -216,13 +246,27 @@ class Context:
     """Owns one adr_ctx; methods forward to the C entry points above."""
 
     def __init__(self, dims, tau, scheme="lawson4", precision="fp64", stream=None, **kw):
-        self.dims = tuple(int(n) for n in dims)
+        self.batch_dims = [tuple(int(v) for v in d) for d in kw["batch_dims"]] if kw.get("batch_dims") else None
+        self.dims = tuple(int(n) for n in dims) if dims is not None else ()
         self.precision = precision
         self.ctx = adr_create(self.dims, tau, scheme, precision, stream=stream, **kw)
 
-    def set_coeffs(self, a_nodes, b, r_poly):
-        adr_set_coeffs(self.ctx, 0, a_nodes, b, r_poly)
+    def set_coeffs(self, a_nodes, b, r_poly, instance=0):
+        adr_set_coeffs(self.ctx, instance, a_nodes, b, r_poly)
         return self
+
+    def offsets(self):
+        """Element offsets of the instances in a packed batched state (plus the total)."""
+        out = [0]
+        for n1, n2 in self.batch_dims:
+            out.append(out[-1] + n1 * n2)
+        return out
+
+    def instance_info(self, i):
+        return adr_get_instance_info(self.ctx, i)
+
+    def batch_plan(self, mode):
+        return adr_get_batch_plan(self.ctx, mode, len(self.batch_dims))
 
     def step(self, u, t=0.0):
         adr_step(self.ctx, u, t)

@@ -18,6 +18,7 @@
 //                               W = E X (= U4),  X = E ACC                [K2 x 2d]
 //                               u = X + tau/6 g(W)                        [K1]
 //     using E(u + tau/6 k1) = 2/3 Eu + 1/3 U2, so a step costs four E actions.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -46,6 +47,37 @@ struct Op {
 thread_local std::string g_create_error;
 
 }  // namespace
+
+// Host side of a batched context: the packing of the instances (fixed at adr_create),
+// FP64 staging of their coefficients, factors and eigenvalues (filled by adr_set_coeffs),
+// the device copies, and the contraction schedule chosen by the autotuner.
+struct adr_batch_state {
+    int B = 0;
+    int tile_force = -1;                   // BatchTile forced by batch_tile, -1: autotune
+    std::vector<int> n1, n2, apitch;
+    std::vector<long long> off, row0, a_off;
+    std::vector<long long> f_off;          // [i][role][dir] -> 8 per instance, -1 if absent
+    std::vector<long long> lam_off;        // [i][dir] -> 2 per instance, -1 if absent
+    long long rows = 0, a_len = 0, f_len = 0, lam_len = 0;
+    bool roles[4] = {false, false, false, false};
+    std::vector<char> set;
+    int nset = 0;
+    std::vector<double> hA, hF, hLam;      // FP64 staging, packed like the device copies
+    std::vector<double> coef;              // [i] -> ih2[2] i2h[2] bmb[2] beta[2] abar r[4]
+    std::vector<double> kappa;             // [i][dir]
+    // device
+    void* d_inst = nullptr;                // BatchInst<T>[B]
+    long long* d_row_start = nullptr;      // B + 1
+    void* d_a = nullptr;
+    void* d_f = nullptr;
+    double* d_lam = nullptr;
+    int4* d_items[2] = {nullptr, nullptr};
+    int nitems[2] = {0, 0};
+    int grid[2] = {0, 0};                  // persistent CTAs of the contraction, per mode
+    int sgrid = 0;                         // persistent CTAs of the stencil
+    std::vector<int> tile[2];              // BatchTile per instance, per mode
+    bool uploaded = false, tuned = false;
+};
 
 struct adr_ctx {
     adr_params p{};
@@ -83,6 +115,9 @@ struct adr_ctx {
     float* d_zt[3] = {nullptr};            // tau * lambda_mu[j] (FP32)
     unsigned* d_slots = nullptr;           // max-abs slots of the arrays a step produces
     int* d_err = nullptr;                  // device error word (bounded waits)
+
+    // batched 2-D instances (p.batch > 0)
+    std::unique_ptr<adr_batch_state> bs;
 
     // graph cache for adr_integrate
     cudaGraph_t graph = nullptr;
@@ -214,6 +249,59 @@ ContractArgs<T> mode_args(const adr_ctx* c, int mu, const T* M, const T* X, T* Y
 }
 
 enum FactorKind { FK_EXP_HALF = 0, FK_EXP_ONE = 1, FK_V = 2, FK_VINV = 3, FK_EXP_HALF_PRECISE = 4 };
+static_assert(int(FK_EXP_HALF) == adr::BR_EXP_HALF && int(FK_EXP_ONE) == adr::BR_EXP_ONE && int(FK_V) == adr::BR_V &&
+                  int(FK_VINV) == adr::BR_VINV,
+              "factor kinds and batch roles share their numbering");
+
+// Batched context: one pass over every instance (one persistent launch).
+template <typename T>
+void push_mode_batch(Sched& S, int mu, int kind, const T* x, T* y, int epi, const T* base, double alpha, int phik) {
+    const adr_ctx* c = S.c;
+    const adr_batch_state& b = *c->bs;
+    adr::BatchContractArgs<T> a;
+    a.inst = static_cast<const adr::BatchInst<T>*>(b.d_inst);
+    a.items = b.d_items[mu - 1];
+    a.nitems = b.nitems[mu - 1];
+    a.mode = mu;
+    a.role = kind;
+    a.factors = static_cast<const T*>(b.d_f);
+    a.lam = b.d_lam;
+    a.X = x;
+    a.Y = y;
+    a.epi = epi;
+    a.base = base;
+    a.alpha = alpha;
+    a.phik = phik;
+    a.tau = c->p.tau;
+    a.grid = b.grid[mu - 1];
+    S.ops.push_back({[a](cudaStream_t s) { return adr::launch_batch_contract(a, s); }, OP_CONTRACT_SIMT});
+}
+
+// Batched context: the stage combination of s over every instance, with each instance's
+// own coefficients (the grid and coefficient fields of s are not used).
+template <typename T>
+adr::BatchStencilArgs<T> batch_stencil_args(const adr_ctx* c, const StencilArgs<T>& s) {
+    const adr_batch_state& b = *c->bs;
+    adr::BatchStencilArgs<T> a;
+    a.inst = static_cast<const adr::BatchInst<T>*>(b.d_inst);
+    a.row_start = b.d_row_start;
+    a.ninst = b.B;
+    a.rows = b.rows;
+    a.a = static_cast<const T*>(b.d_a);
+    a.u = s.u;
+    a.nx = s.nx;
+    a.nout = s.nout;
+    for (int e = 0; e < adr::kMaxExtra; ++e) a.X[e] = s.X[e];
+    for (int j = 0; j < adr::kMaxOut; ++j) {
+        a.out[j] = s.out[j];
+        a.cu[j] = s.cu[j];
+        a.cg[j] = s.cg[j];
+        a.cF[j] = s.cF[j];
+        for (int e = 0; e < adr::kMaxExtra; ++e) a.cx[j][e] = s.cx[j][e];
+    }
+    a.grid = b.sgrid;
+    return a;
+}
 
 // One mu-mode pass y = x x_mu M_kind with epilogue (epi, base, alpha, phik).
 template <typename T>
@@ -221,6 +309,10 @@ void push_mode(Sched& S, int mu, int kind, const T* x, T* y, int epi = adr::EPI_
                const T* base = nullptr, double alpha = 0.0, int phik = 0, T* ylo = nullptr,
                const T* xlo = nullptr) {
     const adr_ctx* c = S.c;
+    if (c->bs) {
+        push_mode_batch<T>(S, mu, kind, x, y, epi, base, alpha, phik);
+        return;
+    }
     if (!c->tc) {
         const void* M = kind == FK_EXP_HALF ? c->d_E[0][mu - 1] : kind == FK_EXP_ONE ? c->d_E[1][mu - 1]
                       : kind == FK_V ? c->d_V[mu - 1] : c->d_Vi[mu - 1];
@@ -366,6 +458,11 @@ StencilArgs<T> stencil_base(const adr_ctx* c, const T* u) {
 // Push a stencil op; on the mixed path its outputs (and, if asked, its input) get slots.
 template <typename T>
 void push_stencil(Sched& S, StencilArgs<T> s, bool record_input = false) {
+    if (S.c->bs) {
+        const auto a = batch_stencil_args(S.c, s);
+        S.ops.push_back({[a](cudaStream_t st) { return adr::launch_batch_stencil(a, st); }, OP_STENCIL});
+        return;
+    }
     if (S.c->tc) {
         if (record_input) s.amax_u = S.produce(s.u);
         for (int j = 0; j < s.nout; ++j) s.amax[j] = S.produce(s.out[j]);
@@ -457,7 +554,409 @@ bool needs_phi(int scheme) { return scheme == ADR_ETD2RK; }
 
 adr_status check_ready(adr_ctx* c) {
     if (!c) return ADR_ERR_ARG;
-    if (!c->coeffs_set) return fail(c, ADR_ERR_STATE, "adr_set_coeffs has not been called");
+    if (!c->coeffs_set)
+        return fail(c, ADR_ERR_STATE, c->bs ? "adr_set_coeffs has not been called for every instance"
+                                            : "adr_set_coeffs has not been called");
+    return ADR_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// ------------------------------------------------------------------ batched contexts
+constexpr int kCoef = 13;   // per instance: ih2[2] i2h[2] bmb[2] beta[2] abar r[4]
+
+int device_sms() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+// Copy src[off, off + len) (FP64 staging) to the same elements of a device array of the
+// working precision.
+cudaError_t upload_range(const adr_ctx* c, void* dst, const std::vector<double>& src, long long off, long long len) {
+    if (len <= 0) return cudaSuccess;
+    char* d = static_cast<char*>(dst) + off * static_cast<long long>(c->esize);
+    if (c->fp64) return cudaMemcpy(d, src.data() + off, size_t(len) * 8, cudaMemcpyHostToDevice);
+    std::vector<float> tmp(src.begin() + off, src.begin() + off + len);
+    return cudaMemcpy(d, tmp.data(), size_t(len) * 4, cudaMemcpyHostToDevice);
+}
+
+template <typename T>
+cudaError_t upload_instances(const adr_ctx* c) {
+    const adr_batch_state& b = *c->bs;
+    std::vector<adr::BatchInst<T>> h(b.B);
+    for (int i = 0; i < b.B; ++i) {
+        auto& d = h[i];
+        const double* k = &b.coef[size_t(i) * kCoef];
+        d.n1 = b.n1[i];
+        d.n2 = b.n2[i];
+        d.off = b.off[i];
+        d.row0 = b.row0[i];
+        d.a_off = b.a_off[i];
+        d.apitch = b.apitch[i];
+        for (int m = 0; m < 2; ++m) {
+            d.ih2[m] = T(k[m]);
+            d.i2h[m] = T(k[2 + m]);
+            d.bmb[m] = T(k[4 + m]);
+            d.beta[m] = T(k[6 + m]);
+            d.lam_off[m] = b.lam_off[size_t(i) * 2 + m];
+        }
+        d.abar = T(k[8]);
+        for (int j = 0; j < 4; ++j) d.r[j] = T(k[9 + j]);
+        for (int r = 0; r < 4; ++r)
+            for (int m = 0; m < 2; ++m) d.f_off[r][m] = b.f_off[size_t(i) * 8 + r * 2 + m];
+    }
+    return cudaMemcpy(b.d_inst, h.data(), h.size() * sizeof(adr::BatchInst<T>), cudaMemcpyHostToDevice);
+}
+
+// Upload everything (first time) or the regions of instance i (later changes).
+cudaError_t batch_upload(adr_ctx* c, int i) {
+    adr_batch_state& b = *c->bs;
+    cudaError_t e = c->fp64 ? upload_instances<double>(c) : upload_instances<float>(c);
+    if (e != cudaSuccess) return e;
+    if (!b.uploaded) {
+        e = upload_range(c, b.d_a, b.hA, 0, b.a_len);
+        if (e == cudaSuccess) e = upload_range(c, b.d_f, b.hF, 0, b.f_len);
+        if (e == cudaSuccess && b.lam_len > 0)
+            e = cudaMemcpy(b.d_lam, b.hLam.data(), size_t(b.lam_len) * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) b.uploaded = true;
+        return e;
+    }
+    e = upload_range(c, b.d_a, b.hA, b.a_off[i], (long long)b.apitch[i] * (b.n2[i] + 2));
+    for (int r = 0; r < 4 && e == cudaSuccess; ++r)
+        for (int m = 0; m < 2 && e == cudaSuccess; ++m) {
+            const long long o = b.f_off[size_t(i) * 8 + r * 2 + m];
+            const long long nm = m == 0 ? b.n1[i] : b.n2[i];
+            if (o >= 0) e = upload_range(c, b.d_f, b.hF, o, nm * nm);
+        }
+    for (int m = 0; m < 2 && e == cudaSuccess; ++m) {
+        const long long o = b.lam_off[size_t(i) * 2 + m];
+        const long long nm = m == 0 ? b.n1[i] : b.n2[i];
+        if (o >= 0) e = cudaMemcpy(b.d_lam + o, b.hLam.data() + o, size_t(nm) * 8, cudaMemcpyHostToDevice);
+    }
+    return e;
+}
+
+// Work items of the instances `insts` with tile shape t: {instance, tile row, tile column, t}.
+void append_items(const adr_batch_state& b, const std::vector<int>& insts, int t, std::vector<int4>& out) {
+    const int edge = adr::batch_tile_edge(t);
+    for (int i : insts)
+        for (int ty = 0; ty < (b.n2[i] + edge - 1) / edge; ++ty)
+            for (int tx = 0; tx < (b.n1[i] + edge - 1) / edge; ++tx) out.push_back(make_int4(i, ty, tx, t));
+}
+
+// Autotuner. Per instance size (n1, n2) and mode it times each candidate tile shape on the
+// items of that size class and keeps the fastest; the full item list of a mode is then
+// ordered by the measured cost per item, largest first (longest-processing-time order for
+// the persistent CTAs that take items round robin); last it times the full list at 1-4
+// CTAs per SM, and the stencil at 4, 8 and 16 CTAs per SM.
+template <typename T>
+adr_status batch_tune(adr_ctx* c) {
+    adr_batch_state& b = *c->bs;
+    const int sms = device_sms();
+    std::vector<std::pair<std::pair<int, int>, std::vector<int>>> classes;
+    for (int i = 0; i < b.B; ++i) {
+        const std::pair<int, int> key(b.n1[i], b.n2[i]);
+        auto it = classes.begin();
+        while (it != classes.end() && it->first != key) ++it;
+        if (it == classes.end()) classes.push_back({key, {i}});
+        else it->second.push_back(i);
+    }
+    int role = 0;
+    while (role < 4 && !b.roles[role]) ++role;
+    long long max_items = 0;
+    for (int i = 0; i < b.B; ++i) max_items += (long long)((b.n1[i] + 31) / 32) * ((b.n2[i] + 31) / 32);
+    int4* d_tmp = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&d_tmp), size_t(max_items) * sizeof(int4));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    auto cleanup = [&]() {
+        if (d_tmp) cudaFree(d_tmp);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "autotuner set-up"); }
+    // the fastest of 3 timed launches after 2 untimed ones
+    auto best_of = [&](const std::function<cudaError_t(cudaStream_t)>& launch, float& ms) -> cudaError_t {
+        ms = 1e30f;
+        for (int r = 0; r < 5; ++r) {
+            cudaError_t le = cudaEventRecord(e0, c->stream);
+            if (le == cudaSuccess) le = launch(c->stream);
+            if (le == cudaSuccess) le = cudaEventRecord(e1, c->stream);
+            if (le == cudaSuccess) le = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (le == cudaSuccess) le = cudaEventElapsedTime(&t, e0, e1);
+            if (le != cudaSuccess) return le;
+            if (r >= 2 && t < ms) ms = t;
+        }
+        return cudaSuccess;
+    };
+    adr::BatchContractArgs<T> base;
+    base.inst = static_cast<const adr::BatchInst<T>*>(b.d_inst);
+    base.role = role;
+    base.factors = static_cast<const T*>(b.d_f);
+    base.lam = b.d_lam;
+    base.X = static_cast<const T*>(c->ws[0]);
+    base.Y = static_cast<T*>(c->ws[1]);
+    base.epi = adr::EPI_STORE;
+    for (int mode = 1; mode <= 2 && e == cudaSuccess; ++mode) {
+        std::vector<std::pair<double, int4>> all;
+        for (const auto& cl : classes) {
+            int best_t = b.tile_force >= 0 ? b.tile_force : adr::BT_64;
+            float best_ms = 1e30f;
+            for (int t = 0; t < adr::kBatchTiles && e == cudaSuccess; ++t) {
+                if (b.tile_force >= 0 && t != b.tile_force) continue;
+                std::vector<int4> items;
+                append_items(b, cl.second, t, items);
+                e = cudaMemcpy(d_tmp, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
+                auto a = base;
+                a.items = d_tmp;
+                a.nitems = int(items.size());
+                a.mode = mode;
+                a.grid = std::min(int(items.size()), 2 * sms);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = best_of([a](cudaStream_t s) { return adr::launch_batch_contract(a, s); }, ms);
+                if (e == cudaSuccess && ms < best_ms) { best_ms = ms; best_t = t; }
+            }
+            std::vector<int4> items;
+            append_items(b, cl.second, best_t, items);
+            const double g = double(std::min(int(items.size()), 2 * sms));
+            const double per_item = double(best_ms) * g / double(items.size());
+            for (int i : cl.second) b.tile[mode - 1][i] = best_t;
+            for (const auto& it : items) all.push_back({per_item, it});
+        }
+        if (e != cudaSuccess) break;
+        std::stable_sort(all.begin(), all.end(), [](const std::pair<double, int4>& x, const std::pair<double, int4>& y) {
+            return x.first > y.first;
+        });
+        std::vector<int4> items(all.size());
+        for (size_t k = 0; k < all.size(); ++k) items[k] = all[k].second;
+        if (b.d_items[mode - 1]) cudaFree(b.d_items[mode - 1]);
+        b.d_items[mode - 1] = nullptr;
+        e = cudaMalloc(reinterpret_cast<void**>(&b.d_items[mode - 1]), items.size() * sizeof(int4));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b.d_items[mode - 1], items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
+        b.nitems[mode - 1] = int(items.size());
+        float best_ms = 1e30f;
+        b.grid[mode - 1] = std::min(b.nitems[mode - 1], 2 * sms);
+        for (int per_sm = 1; per_sm <= 4 && e == cudaSuccess; ++per_sm) {
+            auto a = base;
+            a.items = b.d_items[mode - 1];
+            a.nitems = b.nitems[mode - 1];
+            a.mode = mode;
+            a.grid = std::min(a.nitems, per_sm * sms);
+            float ms = 0.f;
+            e = best_of([a](cudaStream_t s) { return adr::launch_batch_contract(a, s); }, ms);
+            if (e == cudaSuccess && ms < best_ms) { best_ms = ms; b.grid[mode - 1] = a.grid; }
+        }
+    }
+    if (e == cudaSuccess) {
+        adr::BatchStencilArgs<T> s;
+        s.inst = static_cast<const adr::BatchInst<T>*>(b.d_inst);
+        s.row_start = b.d_row_start;
+        s.ninst = b.B;
+        s.rows = b.rows;
+        s.a = static_cast<const T*>(b.d_a);
+        s.u = static_cast<const T*>(c->ws[0]);
+        s.nout = 1;
+        s.out[0] = static_cast<T*>(c->ws[1]);
+        s.cg[0] = 1.0;
+        float best_ms = 1e30f;
+        b.sgrid = 8 * sms;
+        for (int per_sm : {4, 8, 16}) {
+            s.grid = per_sm * sms;
+            float ms = 0.f;
+            e = best_of([s](cudaStream_t st) { return adr::launch_batch_stencil(s, st); }, ms);
+            if (e != cudaSuccess) break;
+            if (ms < best_ms) { best_ms = ms; b.sgrid = s.grid; }
+        }
+    }
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(c, e, "autotuner");
+    b.tuned = true;
+    return ADR_OK;
+}
+
+adr_status create_batch(const adr_params* p, void* cuda_stream, adr_ctx** out) {
+    if (p->dim != 2) return fail(nullptr, ADR_ERR_ARG, "a batched context is 2-D: dim must be 2");
+    if (!p->n_batch) return fail(nullptr, ADR_ERR_ARG, "n_batch is NULL");
+    if (p->batch > (1 << 20)) return fail(nullptr, ADR_ERR_ARG, "batch must be <= 2^20");
+    if (!(p->tau > 0.0) || !std::isfinite(p->tau)) return fail(nullptr, ADR_ERR_ARG, "tau must be positive");
+    if (p->scheme < ADR_LAWSON_EULER || p->scheme > ADR_LAWSON4) return fail(nullptr, ADR_ERR_ARG, "unknown scheme");
+    if (p->precision == ADR_MIXED_BF16X3 || p->precision == ADR_MIXED_TF32X3)
+        return fail(nullptr, ADR_ERR_UNSUPPORTED,
+                    "batched contexts run in ADR_FP64 or ADR_FP32 (the fixed-point slices of the mixed "
+                    "path lose the small entries of ill-scaled eigenvector factors)");
+    if (p->precision != ADR_FP64 && p->precision != ADR_FP32) return fail(nullptr, ADR_ERR_ARG, "unknown precision");
+    int force = -1;
+    if (p->batch_tile == 32) force = adr::BT_32;
+    else if (p->batch_tile == 64) force = adr::BT_64;
+    else if (p->batch_tile == 128) force = adr::BT_128;
+    else if (p->batch_tile != 0) return fail(nullptr, ADR_ERR_ARG, "batch_tile must be 0, 32, 64 or 128");
+
+    auto bs = std::make_unique<adr_batch_state>();
+    adr_batch_state& b = *bs;
+    b.B = p->batch;
+    b.tile_force = force;
+    if (p->scheme == ADR_LAWSON_EULER) b.roles[adr::BR_EXP_ONE] = true;
+    if (p->scheme == ADR_LAWSON4) b.roles[adr::BR_EXP_HALF] = true;
+    if (p->scheme == ADR_ETD2RK) b.roles[adr::BR_V] = b.roles[adr::BR_VINV] = true;
+    b.n1.resize(b.B); b.n2.resize(b.B); b.apitch.resize(b.B);
+    b.off.resize(b.B); b.row0.resize(b.B); b.a_off.resize(b.B);
+    b.f_off.assign(size_t(b.B) * 8, -1);
+    b.lam_off.assign(size_t(b.B) * 2, -1);
+    long long N = 0;
+    for (int i = 0; i < b.B; ++i) {
+        const int n1 = p->n_batch[2 * i], n2 = p->n_batch[2 * i + 1];
+        if (n1 < 2 || n1 > 4096 || n2 < 2 || n2 > 4096)
+            return fail(nullptr, ADR_ERR_ARG, "instance sizes must be in [2, 4096]");
+        b.n1[i] = n1; b.n2[i] = n2;
+        b.off[i] = N; N += (long long)n1 * n2;
+        b.row0[i] = b.rows; b.rows += n2;
+        b.apitch[i] = ((n1 + 5) + 3) / 4 * 4;
+        b.a_off[i] = b.a_len; b.a_len += (long long)b.apitch[i] * (n2 + 2);
+        for (int r = 0; r < 4; ++r)
+            for (int m = 0; m < 2; ++m) {
+                if (!b.roles[r]) continue;
+                const long long nm = m == 0 ? n1 : n2;
+                b.f_off[size_t(i) * 8 + r * 2 + m] = b.f_len;
+                b.f_len += nm * nm;
+            }
+        if (b.roles[adr::BR_V])
+            for (int m = 0; m < 2; ++m) {
+                b.lam_off[size_t(i) * 2 + m] = b.lam_len;
+                b.lam_len += m == 0 ? n1 : n2;
+            }
+    }
+    if (N > (1LL << 31) - 1) return fail(nullptr, ADR_ERR_ARG, "batch too large (more than 2^31 - 1 nodes)");
+    b.hA.assign(size_t(b.a_len), 0.0);
+    b.hF.assign(size_t(b.f_len), 0.0);
+    b.hLam.assign(size_t(b.lam_len), 0.0);
+    b.coef.assign(size_t(b.B) * kCoef, 0.0);
+    b.kappa.assign(size_t(b.B) * 2, 0.0);
+    b.set.assign(b.B, 0);
+    b.tile[0].assign(b.B, 0);
+    b.tile[1].assign(b.B, 0);
+
+    std::unique_ptr<adr_ctx> c(new adr_ctx);
+    c->p = *p;
+    c->p.n_batch = nullptr;                // the sizes are copied above
+    if (c->p.lambda <= 0.0) c->p.lambda = 1.0;
+    if (c->p.kappa_tol <= 0.0) c->p.kappa_tol = 1e-2;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->dim = 2;
+    c->n[0] = b.n1[0]; c->n[1] = b.n2[0]; c->n[2] = 1;
+    c->N = size_t(N);
+    c->nodes = 0;
+    c->fp64 = (p->precision == ADR_FP64);
+    c->esize = c->fp64 ? 8 : 4;
+    c->tc = false;
+    const size_t inst_bytes = c->fp64 ? sizeof(adr::BatchInst<double>) : sizeof(adr::BatchInst<float>);
+    std::vector<long long> row_start(size_t(b.B) + 1);
+    for (int i = 0; i < b.B; ++i) row_start[i] = b.row0[i];
+    row_start[b.B] = b.rows;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&c->d_err), sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+    for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaMalloc(&c->ws[i], c->N * c->esize);
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_inst, size_t(b.B) * inst_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b.d_row_start), row_start.size() * sizeof(long long));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b.d_row_start, row_start.data(), row_start.size() * sizeof(long long), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_a, size_t(b.a_len) * c->esize);
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_f, size_t(b.f_len) * c->esize);
+    if (e == cudaSuccess && b.lam_len > 0) e = cudaMalloc(reinterpret_cast<void**>(&b.d_lam), size_t(b.lam_len) * 8);
+    c->bs = std::move(bs);
+    if (e != cudaSuccess) {
+        const std::string msg = std::string("batched context: ") + cudaGetErrorString(e);
+        adr_destroy(c.release());
+        return fail(nullptr, ADR_ERR_ALLOC, msg);
+    }
+    *out = c.release();
+    return ADR_OK;
+}
+
+adr_status batch_set_coeffs(adr_ctx* c, int i, const double* a_nodes, const double bvec[3], const double r_poly[4]) {
+    adr_batch_state& b = *c->bs;
+    if (i < 0 || i >= b.B) return fail(c, ADR_ERR_ARG, "instance out of range");
+    if (!a_nodes || !bvec || !r_poly) return fail(c, ADR_ERR_ARG, "NULL coefficient pointer");
+    const int n[3] = {b.n1[i], b.n2[i], 1};
+    const size_t nodes = size_t(n[0] + 2) * (n[1] + 2);
+    for (size_t k = 0; k < nodes; ++k)
+        if (!std::isfinite(a_nodes[k])) return fail(c, ADR_ERR_ARG, "a_nodes has a non-finite value");
+    drop_graph(c);
+    c->coeffs_set = false;
+    // Eq. (amaxbeta), per instance
+    const double abar = c->p.abar_override > 0 ? c->p.abar_override : c->p.lambda * adr::nodal_max(a_nodes, nodes);
+    if (!(abar > 0)) return fail(c, ADR_ERR_ARG, "lambda * a_max must be positive");
+    double beta[2];
+    for (int m = 0; m < 2; ++m) beta[m] = bvec[m] + adr::mean_face_jump(a_nodes, 2, n, m + 1);
+    for (int j2 = 0; j2 < n[1] + 2; ++j2)
+        for (int j1 = 0; j1 < n[0] + 2; ++j1)
+            b.hA[size_t(b.a_off[i] + (long long)j2 * b.apitch[i] + j1 + 3)] = a_nodes[size_t(j2) * (n[0] + 2) + j1] - abar;
+    double* k = &b.coef[size_t(i) * kCoef];
+    for (int m = 0; m < 2; ++m) {
+        const double h = 1.0 / (n[m] + 1);
+        k[m] = 1.0 / (h * h);
+        k[2 + m] = 1.0 / (2.0 * h);
+        k[4 + m] = bvec[m] - beta[m];
+        k[6 + m] = beta[m];
+    }
+    k[8] = abar;
+    for (int j = 0; j < 4; ++j) k[9 + j] = r_poly[j];
+    // factors of the scheme, on the host in FP64
+    for (int m = 0; m < 2; ++m) {
+        const adr::Factor1D f = adr::make_factor(n[m], abar, beta[m]);
+        const long long nm = n[m];
+        for (int ci = 0; ci < 2; ++ci) {
+            const int role = ci == 0 ? adr::BR_EXP_HALF : adr::BR_EXP_ONE;
+            if (!b.roles[role]) continue;
+            std::vector<double> sA = adr::factor_dense(f);
+            for (auto& v : sA) v *= (ci == 0 ? 0.5 : 1.0) * c->p.tau;
+            std::vector<double> E;
+            try {
+                E = adr::expm_pade13(sA, n[m]);
+            } catch (const std::exception& ex) {
+                return fail(c, ADR_ERR_ARG, std::string("expm: ") + ex.what());
+            }
+            std::copy(E.begin(), E.end(), b.hF.begin() + b.f_off[size_t(i) * 8 + role * 2 + m]);
+        }
+        if (b.roles[adr::BR_V]) {
+            const adr::Eigen1D eg = adr::eigen_closed_form(f);
+            if (!eg.real) {
+                char buf[128];
+                std::snprintf(buf, sizeof buf, "instance %d: cell Peclet number >= 1: A_mu has no real eigenbasis", i);
+                return fail(c, ADR_ERR_COMPLEX_SPECTRUM, buf);
+            }
+            b.kappa[size_t(i) * 2 + m] = eg.kappa;
+            std::copy(eg.V.begin(), eg.V.end(), b.hF.begin() + b.f_off[size_t(i) * 8 + adr::BR_V * 2 + m]);
+            std::copy(eg.Vinv.begin(), eg.Vinv.end(), b.hF.begin() + b.f_off[size_t(i) * 8 + adr::BR_VINV * 2 + m]);
+            std::copy(eg.lam.begin(), eg.lam.end(), b.hLam.begin() + b.lam_off[size_t(i) * 2 + m]);
+            (void)nm;
+        }
+    }
+    if (b.roles[adr::BR_V]) {
+        const double kp = b.kappa[size_t(i) * 2] * b.kappa[size_t(i) * 2 + 1];
+        const double unit = c->fp64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+        if (kp * unit > c->p.kappa_tol) {
+            char buf[192];
+            std::snprintf(buf, sizeof buf, "instance %d: eigen route ill-conditioned: prod kappa * u = %.3e > kappa_tol %.3e",
+                          i, kp * unit, c->p.kappa_tol);
+            return fail(c, ADR_ERR_ILL_CONDITIONED, buf);
+        }
+    }
+    if (!b.set[i]) { b.set[i] = 1; ++b.nset; }
+    if (b.nset < b.B) return ADR_OK;
+    cudaError_t e = batch_upload(c, i);
+    if (e != cudaSuccess) return cuda_fail(c, e, "upload batch");
+    if (!b.tuned) {
+        const adr_status st = c->fp64 ? batch_tune<double>(c) : batch_tune<float>(c);
+        if (st != ADR_OK) return st;
+    }
+    c->coeffs_set = true;
     return ADR_OK;
 }
 
@@ -470,6 +969,8 @@ adr_status adr_create(const adr_params* p, void* cuda_stream, adr_ctx** out) {
     if (!out) return fail(nullptr, ADR_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!p) return fail(nullptr, ADR_ERR_ARG, "params is NULL");
+    if (p->batch < 0) return fail(nullptr, ADR_ERR_ARG, "batch must be >= 0");
+    if (p->batch > 0) return create_batch(p, cuda_stream, out);
     if (p->dim != 2 && p->dim != 3) return fail(nullptr, ADR_ERR_ARG, "dim must be 2 or 3");
     for (int m = 0; m < p->dim; ++m)
         if (p->n[m] < 2 || p->n[m] > 4096) return fail(nullptr, ADR_ERR_ARG, "n must be in [2, 4096]");
@@ -522,6 +1023,7 @@ adr_status adr_create(const adr_params* p, void* cuda_stream, adr_ctx** out) {
 
 adr_status adr_set_coeffs(adr_ctx* c, int instance, const double* a_nodes, const double b[3], const double r_poly[4]) {
     if (!c) return ADR_ERR_ARG;
+    if (c->bs) return batch_set_coeffs(c, instance, a_nodes, b, r_poly);
     if (instance != 0) return fail(c, ADR_ERR_ARG, "instance must be 0 for a single-grid context");
     if (!a_nodes || !b || !r_poly) return fail(c, ADR_ERR_ARG, "NULL coefficient pointer");
     for (size_t i = 0; i < c->nodes; ++i)
@@ -705,6 +1207,8 @@ adr_status adr_apply_exp(adr_ctx* c, double cc, const void* v, void* y) {
     if (cc == 0.5) ci = 0;
     if (cc == 1.0) ci = 1;
     if (ci < 0) return fail(c, ADR_ERR_ARG, "c must be 0.5 or 1");
+    if (c->bs && !c->bs->roles[ci])
+        return fail(c, ADR_ERR_STATE, "this batched context's scheme does not build e^{c tau A} for this c");
     Sched S(c);
     if (c->fp64) push_exp<double>(S, ci, static_cast<const double*>(v), static_cast<double*>(y));
     else         push_exp<float>(S, ci, static_cast<const float*>(v), static_cast<float*>(y));
@@ -716,7 +1220,9 @@ adr_status adr_apply_phi(adr_ctx* c, int k, const void* v, void* y) {
     if (st != ADR_OK) return st;
     if (!v || !y || v == y) return fail(c, ADR_ERR_ARG, "NULL or aliased array");
     if (k < 0 || k > 2) return fail(c, ADR_ERR_ARG, "k must be 0, 1 or 2");
-    if (!c->eig_real) return fail(c, ADR_ERR_COMPLEX_SPECTRUM, "A_mu has no real eigenbasis");
+    if (c->bs && !c->bs->roles[FK_V])
+        return fail(c, ADR_ERR_STATE, "this batched context's scheme does not build the eigenbasis");
+    if (!c->bs && !c->eig_real) return fail(c, ADR_ERR_COMPLEX_SPECTRUM, "A_mu has no real eigenbasis");
     Sched S(c);
     if (c->fp64) push_phi<double>(S, k, static_cast<const double*>(v), static_cast<double*>(y));
     else         push_phi<float>(S, k, static_cast<const float*>(v), static_cast<float*>(y));
@@ -765,9 +1271,45 @@ adr_status adr_synchronize(adr_ctx* c) {
 
 adr_status adr_get_info(const adr_ctx* c, double kappa[3], double* abar, double beta[3]) {
     if (!c) return ADR_ERR_ARG;
+    if (c->bs) {
+        // the largest kappa per direction over the instances; a_max and beta of instance 0
+        const adr_batch_state& b = *c->bs;
+        if (kappa) {
+            kappa[0] = kappa[1] = kappa[2] = 0.0;
+            for (int i = 0; i < b.B; ++i)
+                for (int m = 0; m < 2; ++m) kappa[m] = std::max(kappa[m], b.kappa[size_t(i) * 2 + m]);
+        }
+        return adr_get_instance_info(c, 0, nullptr, abar, beta);
+    }
     if (kappa) for (int m = 0; m < 3; ++m) kappa[m] = c->kappa[m];
     if (abar) *abar = c->abar;
     if (beta) for (int m = 0; m < 3; ++m) beta[m] = c->beta[m];
+    return ADR_OK;
+}
+
+adr_status adr_get_instance_info(const adr_ctx* c, int instance, double kappa[3], double* abar, double beta[3]) {
+    if (!c) return ADR_ERR_ARG;
+    if (!c->bs) {
+        if (instance != 0) return ADR_ERR_ARG;
+        return adr_get_info(c, kappa, abar, beta);
+    }
+    const adr_batch_state& b = *c->bs;
+    if (instance < 0 || instance >= b.B) return ADR_ERR_ARG;
+    if (!b.set[instance]) return ADR_ERR_STATE;
+    const double* k = &b.coef[size_t(instance) * kCoef];
+    if (kappa) { kappa[0] = b.kappa[size_t(instance) * 2]; kappa[1] = b.kappa[size_t(instance) * 2 + 1]; kappa[2] = 0.0; }
+    if (abar) *abar = k[8];
+    if (beta) { beta[0] = k[6]; beta[1] = k[7]; beta[2] = 0.0; }
+    return ADR_OK;
+}
+
+adr_status adr_get_batch_plan(const adr_ctx* c, int mode, int* tile_edge, int* grid) {
+    if (!c || !c->bs || (mode != 1 && mode != 2)) return ADR_ERR_ARG;
+    const adr_batch_state& b = *c->bs;
+    if (!b.tuned) return ADR_ERR_STATE;
+    if (tile_edge)
+        for (int i = 0; i < b.B; ++i) tile_edge[i] = adr::batch_tile_edge(b.tile[mode - 1][i]);
+    if (grid) *grid = b.grid[mode - 1];
     return ADR_OK;
 }
 
@@ -791,6 +1333,15 @@ void adr_destroy(adr_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     drop_graph(c);
+    if (c->bs) {
+        adr_batch_state& b = *c->bs;
+        free_dev(b.d_inst);
+        free_dev(b.d_a);
+        free_dev(b.d_f);
+        { void* q = b.d_row_start; free_dev(q); b.d_row_start = nullptr; }
+        { void* q = b.d_lam; free_dev(q); b.d_lam = nullptr; }
+        for (auto& it : b.d_items) { void* q = it; free_dev(q); it = nullptr; }
+    }
     free_dev(c->d_a);
     for (auto& row : c->d_E) for (auto& p : row) free_dev(p);
     for (auto& p : c->d_V) free_dev(p);

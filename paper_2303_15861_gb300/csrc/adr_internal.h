@@ -158,4 +158,78 @@ cudaError_t launch_contract(const ContractArgs<double>& a, cudaStream_t s);
 cudaError_t launch_contract(const ContractArgs<float>& a, cudaStream_t s);
 cudaError_t launch_convert_f64_to_f32(const double* in, float* out, size_t n, cudaStream_t s);
 
+// ---------------------------------------------------------------- batched 2-D instances
+// Many independent 2-D problems of uneven size advance together: every state-sized array
+// of a batched context packs the instances one after another (instance i at element
+// offset off, n2 rows of n1), and each stage is one persistent launch over all of them.
+template <typename T>
+struct BatchInst {
+    int n1 = 0, n2 = 0;
+    long long off = 0;             // element offset of the instance in every packed state array
+    long long row0 = 0;            // first row of the instance in the concatenated row list
+    long long a_off = 0;           // offset of its padded (a - abar), layout as StencilArgs::a
+    int apitch = 0;
+    T ih2[2] = {0, 0}, i2h[2] = {0, 0}, bmb[2] = {0, 0}, beta[2] = {0, 0};
+    T abar = 0, r[4] = {0, 0, 0, 0};
+    long long f_off[4][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};  // factor role x direction
+    long long lam_off[2] = {-1, -1};                                   // eigenvalues per direction
+};
+
+// Factor roles of a batched context (the same numbering as the single-grid factor kinds).
+enum BatchRole { BR_EXP_HALF = 0, BR_EXP_ONE = 1, BR_V = 2, BR_VINV = 3 };
+
+// One stencil stage over all instances: packed arrays, per-instance coefficients from
+// `inst`, the stage combination (cu, cx, cg, cF) shared by all instances. Work unit: one
+// row (i2) of one instance, found through the row prefix `row_start` (ninst + 1 entries).
+template <typename T>
+struct BatchStencilArgs {
+    const BatchInst<T>* inst = nullptr;
+    const long long* row_start = nullptr;
+    int ninst = 0;
+    long long rows = 0;
+    const T* a = nullptr;          // all instances' padded (a - abar)
+    const T* u = nullptr;
+    const T* X[kMaxExtra] = {nullptr, nullptr, nullptr};
+    int nx = 0;
+    T* out[kMaxOut] = {nullptr, nullptr};
+    int nout = 0;
+    double cu[kMaxOut] = {0, 0};
+    double cx[kMaxOut][kMaxExtra] = {{0, 0, 0}, {0, 0, 0}};
+    double cg[kMaxOut] = {0, 0};
+    double cF[kMaxOut] = {0, 0};
+    int grid = 0;                  // persistent CTAs (0: the launcher picks)
+};
+
+// Tile shapes of the batched contraction (256 threads each): 32x32, 64x64, 128x128.
+enum BatchTile { BT_32 = 0, BT_64 = 1, BT_128 = 2 };
+constexpr int kBatchTiles = 3;
+inline int batch_tile_edge(int t) { return t == BT_32 ? 32 : t == BT_64 ? 64 : 128; }
+
+// One mu-mode pass over all instances. items[i] = {instance, tile row, tile column, tile
+// shape}; mode 1: Y_i = X_i M_i^T (rows of x1), mode 2: Y_i = M_i X_i. Epilogues as
+// ContractArgs, with the phi argument tau (lambda_1[i1] + lambda_2[i2]) of each instance.
+template <typename T>
+struct BatchContractArgs {
+    const BatchInst<T>* inst = nullptr;
+    const int4* items = nullptr;
+    int nitems = 0;
+    int mode = 1;
+    int role = BR_VINV;
+    const T* factors = nullptr;    // all instances' dense factors
+    const double* lam = nullptr;   // all instances' eigenvalues
+    const T* X = nullptr;
+    T* Y = nullptr;
+    int epi = EPI_STORE;
+    const T* base = nullptr;
+    double alpha = 0;
+    int phik = 1;
+    double tau = 0;
+    int grid = 0;
+};
+
+cudaError_t launch_batch_stencil(const BatchStencilArgs<double>& a, cudaStream_t s);
+cudaError_t launch_batch_stencil(const BatchStencilArgs<float>& a, cudaStream_t s);
+cudaError_t launch_batch_contract(const BatchContractArgs<double>& a, cudaStream_t s);
+cudaError_t launch_batch_contract(const BatchContractArgs<float>& a, cudaStream_t s);
+
 }  // namespace adr

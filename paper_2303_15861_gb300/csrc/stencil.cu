@@ -16,6 +16,7 @@
 #include <type_traits>
 
 #include "adr_internal.h"
+#include "stencil_core.cuh"
 
 namespace adr {
 namespace {
@@ -23,41 +24,6 @@ namespace {
 constexpr int TX = 32;   // x1 extent of a CTA tile (one warp wide: coalesced rows)
 constexpr int TY = 8;    // x2 extent
 constexpr int ZCHUNK = 4;   // x3 planes per thread
-
-template <typename T>
-struct Coefs {
-    T ih2[3], i2h[3], bmb[3], beta[3], abar, r0, r1, r2, r3;
-    T cu[kMaxOut], cx[kMaxOut][kMaxExtra], cg[kMaxOut], cF[kMaxOut];
-};
-
-template <typename T>
-__device__ __forceinline__ T absval(T v) { return v < T(0) ? -v : v; }
-
-__device__ __forceinline__ void block_amax(float v, unsigned* slot) {
-    // Warp max then one atomic per warp; |out| as float bits (monotone for v >= 0).
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0 && v > 0.f) atomicMax(slot, __float_as_uint(v));
-}
-
-
-// The stencil at one node from its one-sided differences dE = u_E - u_C, dW = u_C - u_W
-// (and N/S, P/M for x2, x3), the centre value and the face-coefficient sums
-// sE = (a - abar)_C + (a - abar)_E etc. Returns g; F = g + A u when needF.
-template <typename T, int DIM>
-__device__ __forceinline__ T stencil_core(const Coefs<T>& c, T uC, T dE, T dW, T dN, T dS, T dP, T dM, T sE, T sW,
-                                          T sN, T sS, T sP, T sM, bool needF, T& F) {
-    const T h = T(0.5);
-    T g = (h * sE * dE - h * sW * dW) * c.ih2[0] + (h * sN * dN - h * sS * dS) * c.ih2[1]
-        + c.bmb[0] * (dE + dW) * c.i2h[0] + c.bmb[1] * (dN + dS) * c.i2h[1];
-    if (DIM == 3) g += (h * sP * dP - h * sM * dM) * c.ih2[2] + c.bmb[2] * (dP + dM) * c.i2h[2];
-    g += c.r0 + uC * (c.r1 + uC * (c.r2 + uC * c.r3));
-    if (needF) {
-        F = g + c.abar * ((dE - dW) * c.ih2[0] + (dN - dS) * c.ih2[1]) + c.beta[0] * (dE + dW) * c.i2h[0]
-              + c.beta[1] * (dN + dS) * c.i2h[1];
-        if (DIM == 3) F += c.abar * (dP - dM) * c.ih2[2] + c.beta[2] * (dP + dM) * c.i2h[2];
-    }
-    return g;
-}
 
 // One pass over the grid. Each thread owns the nodes (i1, i2, z0 .. z0+ZC-1): it issues
 // every load of its column up front (centre column with its x3 halo, the four x1/x2

@@ -149,3 +149,22 @@ def config4(count=512, m=30, T=0.1, seed=2303):
             u0=smooth_initial_state(dims, noise=1e-3, rng=np.random.default_rng((seed, i))),
             tau=T / m, m=m, scheme="etd2rk", extra=d))
     return out
+
+
+def batch_instances(sizes, m=30, T=0.1, scheme="etd2rk", seed=2303):
+    """Independent 2-D instances with the given (n1, n2), each drawn like the batched
+    workload above: c ~ U[0.1, 0.9], k in {1, 2, 3}, b ~ U[0, 20]^2, reaction u^2(1-u)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, (n1, n2) in enumerate(sizes):
+        c = float(rng.uniform(0.1, 0.9))
+        k = int(rng.integers(1, 4))
+        b = rng.uniform(0.0, 20.0, size=2)
+        dims = (int(n1), int(n2))
+        out.append(Workload(
+            name=f"inst{i}_{n1}x{n2}", dims=dims,
+            a_nodes=sine_product_coefficient(dims, c, k),
+            b=(float(b[0]), float(b[1]), 0.0), r_poly=REACTION_U2_1MU,
+            u0=smooth_initial_state(dims, noise=1e-3, rng=np.random.default_rng((seed, i))),
+            tau=T / m, m=int(m), scheme=scheme, extra=dict(c=c, k=k, b=(float(b[0]), float(b[1])))))
+    return out

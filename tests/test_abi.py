@@ -72,3 +72,38 @@ def test_null_arguments(lib):
     assert lib.adr_create(None, None, None) == 1
     assert lib.adr_kernels_per_step(None) == -1
     lib.adr_destroy(None)
+
+
+def _batch_params(sizes, **kw):
+    p = _params(dim=kw.get("dim", 2), n=(0, 0, 0), scheme=kw.get("scheme", 1), precision=kw.get("precision", 1))
+    flat = [v for d in sizes for v in d]
+    arr = (C.c_int * max(1, len(flat)))(*flat)
+    p.batch = kw.get("batch", len(sizes))
+    p.n_batch = C.cast(arr, C.POINTER(C.c_int)) if kw.get("with_sizes", True) else None
+    p.batch_tile = kw.get("batch_tile", 0)
+    return p, arr
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(dim=3), 1),                       # batched contexts are 2-D
+    (dict(with_sizes=False), 1),            # n_batch missing
+    (dict(batch=-1), 1),
+    (dict(precision=3), 8),                 # the mixed path is not offered for batches
+    (dict(precision=2), 8),
+    (dict(batch_tile=48), 1),
+    (dict(sizes=[(48, 48), (1, 64)]), 1),   # an instance below the minimum size
+])
+def test_create_batch_rejects_invalid_params_on_host(lib, kw, status):
+    """Batched contexts validate their parameters before any CUDA call."""
+    sizes = kw.pop("sizes", [(48, 48), (64, 32)])
+    p, keep = _batch_params(sizes, **kw)
+    ctx = C.c_void_p()
+    assert lib.adr_create(C.byref(p), None, C.byref(ctx)) == status
+    assert not ctx.value
+    assert len(lib.adr_last_error(None)) > 0
+    del keep
+
+
+def test_batch_plan_needs_a_context(lib):
+    assert lib.adr_get_batch_plan(None, 1, None, None) == 1
+    assert lib.adr_get_instance_info(None, 0, None, None, None) == 1

@@ -1,0 +1,225 @@
+"""Batched 2-D contexts: many independent instances of uneven size in one context, each
+stage one persistent launch (through the C ABI), against the FP64 oracle per instance.
+
+Tolerances: FP64 1e-12 relative l2 per instance; FP32 1e-5 per instance, the tolerance of
+the batched workload (512 instances, n in {48..256}, ETD2RK, 30 steps). Instance sizes
+include ragged ones (not multiples of any tile edge) and ones spanning several 128-tiles.
+Packed states carry NaN guard bands that must survive every call.
+"""
+import numpy as np
+import pytest
+
+from oracle import adr_oracle as O
+from paper_2303_15861_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2303_15861_gb300 import adr, build_lib  # noqa: E402
+
+build_lib.build()
+adr.load_library()
+
+GUARD = 512
+SIZES = [(33, 45), (48, 48), (64, 40), (96, 96), (130, 70), (40, 129)]
+DT = {"fp64": torch.float64, "fp32": torch.float32}
+
+
+def batch_context(ws, prec, scheme, stream=None, tile=0, kappa_tol=0.0):
+    ctx = adr.Context(None, ws[0].tau, scheme, prec, stream=stream, batch_dims=[w.dims for w in ws],
+                      batch_tile=tile, kappa_tol=kappa_tol)
+    for i, w in enumerate(ws):
+        ctx.set_coeffs(w.a_nodes, w.b, w.r_poly, instance=i)
+    return ctx
+
+
+def packed(ws, prec, arrays=None):
+    """Packed device state (instance after instance) inside NaN guard bands."""
+    arrays = [w.u0 for w in ws] if arrays is None else arrays
+    flat = np.concatenate([np.ascontiguousarray(x).ravel() for x in arrays])
+    full = torch.full((flat.size + 2 * GUARD,), float("nan"), dtype=DT[prec], device="cuda")
+    view = full[GUARD:GUARD + flat.size]
+    view.copy_(torch.as_tensor(flat, dtype=DT[prec]))
+    return full, view
+
+
+def unpack(ws, view):
+    out, o = [], 0
+    h = view.double().cpu().numpy()
+    for w in ws:
+        n = w.dof
+        out.append(h[o:o + n].reshape(w.dims[::-1]))
+        o += n
+    return out
+
+
+def check_guards(full):
+    g = torch.cat([full[:GUARD], full[-GUARD:]])
+    assert torch.isnan(g).all(), "write outside the packed array"
+
+
+@pytest.mark.parametrize("scheme", ["lawson_euler", "etd2rk", "lawson4"])
+def test_batch_fp64_schemes_match_oracle(scheme):
+    ws = W.batch_instances(SIZES, scheme=scheme)
+    m = 4
+    ctx = batch_context(ws, "fp64", scheme)
+    full, u = packed(ws, "fp64")
+    ctx.integrate(u, 0.0, m * ws[0].tau, m)
+    ctx.synchronize()
+    check_guards(full)
+    for w, got in zip(ws, unpack(ws, u)):
+        ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, m, scheme)
+        assert O.rel_l2(got, ref) < 1e-12, w.name
+
+
+def test_batch_fp32_etd2rk_full_horizon_matches_oracle():
+    ws = W.batch_instances(SIZES, scheme="etd2rk")
+    ctx = batch_context(ws, "fp32", "etd2rk")
+    full, u = packed(ws, "fp32")
+    ctx.integrate(u, 0.0, ws[0].m * ws[0].tau, ws[0].m)
+    ctx.synchronize()
+    check_guards(full)
+    for w, got in zip(ws, unpack(ws, u)):
+        ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, w.m, "etd2rk")
+        assert O.rel_l2(got, ref) < 1e-5, w.name
+
+
+def test_batch_building_blocks_match_oracle():
+    """F, g and phi_k actions of every instance in one call each (FP64)."""
+    ws = W.batch_instances(SIZES, scheme="etd2rk")
+    ctx = batch_context(ws, "fp64", "etd2rk")
+    rng = np.random.default_rng(11)
+    vs = [rng.standard_normal(w.dims[::-1]) for w in ws]
+    _, u = packed(ws, "fp64")
+    fF, F = packed(ws, "fp64", [np.zeros(w.dims[::-1]) for w in ws])
+    fg, g = packed(ws, "fp64", [np.zeros(w.dims[::-1]) for w in ws])
+    ctx.eval_rhs(u, F, g)
+    _, v = packed(ws, "fp64", vs)
+    ys = {}
+    for k in (0, 1, 2):
+        fy, y = packed(ws, "fp64", [np.zeros(w.dims[::-1]) for w in ws])
+        ctx.apply_phi(k, v, y)
+        ys[k] = (fy, y)
+    ctx.synchronize()
+    for full in (fF, fg) + tuple(f for f, _ in ys.values()):
+        check_guards(full)
+    Fs, gs = unpack(ws, F), unpack(ws, g)
+    for i, w in enumerate(ws):
+        prob = O.ADRProblem(w.dims, w.a_nodes, w.b, w.r_poly)
+        assert O.rel_l2(Fs[i], prob.F(w.u0)) < 1e-12, w.name
+        assert O.rel_l2(gs[i], prob.g(w.u0)) < 1e-12, w.name
+        mf = O.MatrixFunctions(prob, w.tau)
+        for k, (_, y) in ys.items():
+            ref = mf.exp_action(1.0, vs[i]) if k == 0 else mf.phi_action(k, 1.0, vs[i])
+            assert O.rel_l2(unpack(ws, y)[i], ref) < 1e-12, (w.name, k)
+
+
+def test_batch_result_does_not_depend_on_tile_shapes():
+    """Every output accumulates its products in the same order for every tile shape, so
+    forced 32/64/128 tiles and the autotuner's plan give identical bits."""
+    ws = W.batch_instances(SIZES, scheme="etd2rk")
+    outs = []
+    for tile in (0, 32, 64, 128):
+        ctx = batch_context(ws, "fp32", "etd2rk", tile=tile)
+        _, u = packed(ws, "fp32")
+        ctx.integrate(u, 0.0, 3 * ws[0].tau, 3)
+        ctx.synchronize()
+        outs.append(u.clone())
+        if tile:
+            edges, grid = ctx.batch_plan(1)
+            assert edges == [tile] * len(ws) and grid > 0
+        ctx.close()
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+
+
+def test_batch_plan_is_a_valid_schedule():
+    ws = W.batch_instances(SIZES + [(48, 48), (96, 96)], scheme="etd2rk")
+    ctx = batch_context(ws, "fp32", "etd2rk")
+    for mode in (1, 2):
+        edges, grid = ctx.batch_plan(mode)
+        assert all(e in (32, 64, 128) for e in edges)
+        assert grid > 0
+        by_size = {}
+        for w, e in zip(ws, edges):
+            by_size.setdefault(w.dims, set()).add(e)
+        assert all(len(s) == 1 for s in by_size.values())   # one choice per size class
+
+
+def test_batch_graph_replay_equals_direct_steps():
+    ws = W.batch_instances(SIZES, scheme="etd2rk")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = batch_context(ws, "fp32", "etd2rk", stream=s)
+        _, u1 = packed(ws, "fp32")
+        _, u2 = packed(ws, "fp32")
+        ctx.integrate(u1, 0.0, 3 * ws[0].tau, 3)
+        for i in range(3):
+            ctx.step(u2, i * ws[0].tau)
+        ctx.synchronize()
+    assert torch.equal(u1, u2)
+
+
+def test_batch_integrate_host_equals_device():
+    ws = W.batch_instances(SIZES[:3], scheme="etd2rk")
+    ctx = batch_context(ws, "fp32", "etd2rk")
+    _, u = packed(ws, "fp32")
+    host = u.cpu().pin_memory()
+    ctx.integrate(u, 0.0, 2 * ws[0].tau, 2)
+    ctx.integrate_host(host, 0.0, 2 * ws[0].tau, 2)
+    ctx.synchronize()
+    assert torch.equal(u.cpu(), host)
+
+
+def test_batch_refuses_steps_until_every_instance_is_set():
+    ws = W.batch_instances(SIZES[:2], scheme="etd2rk")
+    ctx = adr.Context(None, ws[0].tau, "etd2rk", "fp32", batch_dims=[w.dims for w in ws])
+    ctx.set_coeffs(ws[0].a_nodes, ws[0].b, ws[0].r_poly, instance=0)
+    _, u = packed(ws, "fp32")
+    with pytest.raises(adr.AdrError) as e:
+        ctx.step(u)
+    assert e.value.status == 7
+    with pytest.raises(adr.AdrError):
+        ctx.set_coeffs(ws[1].a_nodes, ws[1].b, ws[1].r_poly, instance=2)
+    ctx.set_coeffs(ws[1].a_nodes, ws[1].b, ws[1].r_poly, instance=1)
+    ctx.step(u)
+    ctx.synchronize()
+    info = ctx.instance_info(1)
+    assert info["abar"] == pytest.approx(ws[1].a_nodes.max())
+
+
+def test_batch_coefficient_update_of_one_instance():
+    """Changing one instance's coefficients after set-up re-uploads that instance only."""
+    ws = W.batch_instances(SIZES[:3], scheme="etd2rk")
+    ctx = batch_context(ws, "fp64", "etd2rk")
+    other = W.batch_instances(SIZES[:3], scheme="etd2rk", seed=7)
+    ws2 = [ws[0], other[1], ws[2]]
+    ctx.set_coeffs(other[1].a_nodes, other[1].b, other[1].r_poly, instance=1)
+    _, u = packed(ws2, "fp64")
+    ctx.integrate(u, 0.0, 2 * ws[0].tau, 2)
+    ctx.synchronize()
+    for w, got in zip(ws2, unpack(ws2, u)):
+        ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, 2, "etd2rk")
+        assert O.rel_l2(got, ref) < 1e-12, w.name
+
+
+def test_batched_workload_512_instances_sampled_against_oracle():
+    """The full batched workload (512 instances, n in {48, ..., 256}, ETD2RK, 30 steps, FP32):
+    one graph-replayed integration, then the oracle on sampled instances, including the
+    most ill-conditioned eigenbases of the draw (prod kappa up to 1e7, hence kappa_tol = 1)."""
+    ws = W.config4()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = batch_context(ws, "fp32", "etd2rk", stream=s, kappa_tol=1.0)
+        full, u = packed(ws, "fp32")
+        ctx.integrate(u, 0.0, ws[0].m * ws[0].tau, ws[0].m)
+        ctx.synchronize()
+    check_guards(full)
+    res = unpack(ws, u)
+    for i in (0, 1, 31, 146, 255, 349, 448, 511):
+        w = ws[i]
+        ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, w.m, "etd2rk")
+        assert O.rel_l2(res[i], ref) < 1e-5, (i, w.dims)
