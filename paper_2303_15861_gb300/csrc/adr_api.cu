@@ -57,12 +57,12 @@ struct adr_batch_state {
     std::vector<int> n1, n2, apitch;
     std::vector<long long> off, row0, a_off;
     std::vector<long long> f_off;          // [i][role][dir] -> 8 per instance, -1 if absent
-    std::vector<long long> lam_off;        // [i][dir] -> 2 per instance, -1 if absent
-    long long rows = 0, a_len = 0, f_len = 0, lam_len = 0;
+    std::vector<long long> zt_off;         // [i][dir] -> 2 per instance, -1 if absent
+    long long rows = 0, a_len = 0, f_len = 0, zt_len = 0;
     bool roles[4] = {false, false, false, false};
     std::vector<char> set;
     int nset = 0;
-    std::vector<double> hA, hF, hLam;      // FP64 staging, packed like the device copies
+    std::vector<double> hA, hF, hZt;       // FP64 staging, packed like the device copies
     std::vector<double> coef;              // [i] -> ih2[2] i2h[2] bmb[2] beta[2] abar r[4]
     std::vector<double> kappa;             // [i][dir]
     // device
@@ -70,7 +70,7 @@ struct adr_batch_state {
     long long* d_row_start = nullptr;      // B + 1
     void* d_a = nullptr;
     void* d_f = nullptr;
-    double* d_lam = nullptr;
+    void* d_zt = nullptr;                  // tau * eigenvalues, working precision
     int4* d_items[2] = {nullptr, nullptr};
     int nitems[2] = {0, 0};
     int grid[2] = {0, 0};                  // persistent CTAs of the contraction, per mode
@@ -253,6 +253,8 @@ static_assert(int(FK_EXP_HALF) == adr::BR_EXP_HALF && int(FK_EXP_ONE) == adr::BR
                   int(FK_VINV) == adr::BR_VINV,
               "factor kinds and batch roles share their numbering");
 
+bool aligned16(const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
+
 // Batched context: one pass over every instance (one persistent launch).
 template <typename T>
 void push_mode_batch(Sched& S, int mu, int kind, const T* x, T* y, int epi, const T* base, double alpha, int phik) {
@@ -265,14 +267,14 @@ void push_mode_batch(Sched& S, int mu, int kind, const T* x, T* y, int epi, cons
     a.mode = mu;
     a.role = kind;
     a.factors = static_cast<const T*>(b.d_f);
-    a.lam = b.d_lam;
+    a.zt = static_cast<const T*>(b.d_zt);
     a.X = x;
     a.Y = y;
     a.epi = epi;
     a.base = base;
     a.alpha = alpha;
     a.phik = phik;
-    a.tau = c->p.tau;
+    a.aligned = aligned16(x) && aligned16(y) && aligned16(base);
     a.grid = b.grid[mu - 1];
     S.ops.push_back({[a](cudaStream_t s) { return adr::launch_batch_contract(a, s); }, OP_CONTRACT_SIMT});
 }
@@ -602,12 +604,17 @@ cudaError_t upload_instances(const adr_ctx* c) {
             d.i2h[m] = T(k[2 + m]);
             d.bmb[m] = T(k[4 + m]);
             d.beta[m] = T(k[6 + m]);
-            d.lam_off[m] = b.lam_off[size_t(i) * 2 + m];
+            d.zt_off[m] = b.zt_off[size_t(i) * 2 + m];
         }
+        bool vec = (b.n1[i] % 4 == 0) && (b.n2[i] % 4 == 0) && (b.off[i] % 4 == 0);
         d.abar = T(k[8]);
         for (int j = 0; j < 4; ++j) d.r[j] = T(k[9 + j]);
         for (int r = 0; r < 4; ++r)
-            for (int m = 0; m < 2; ++m) d.f_off[r][m] = b.f_off[size_t(i) * 8 + r * 2 + m];
+            for (int m = 0; m < 2; ++m) {
+                d.f_off[r][m] = b.f_off[size_t(i) * 8 + r * 2 + m];
+                if (d.f_off[r][m] >= 0 && d.f_off[r][m] % 4 != 0) vec = false;
+            }
+        d.vec = vec ? 1 : 0;
     }
     return cudaMemcpy(b.d_inst, h.data(), h.size() * sizeof(adr::BatchInst<T>), cudaMemcpyHostToDevice);
 }
@@ -620,8 +627,7 @@ cudaError_t batch_upload(adr_ctx* c, int i) {
     if (!b.uploaded) {
         e = upload_range(c, b.d_a, b.hA, 0, b.a_len);
         if (e == cudaSuccess) e = upload_range(c, b.d_f, b.hF, 0, b.f_len);
-        if (e == cudaSuccess && b.lam_len > 0)
-            e = cudaMemcpy(b.d_lam, b.hLam.data(), size_t(b.lam_len) * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = upload_range(c, b.d_zt, b.hZt, 0, b.zt_len);
         if (e == cudaSuccess) b.uploaded = true;
         return e;
     }
@@ -633,9 +639,9 @@ cudaError_t batch_upload(adr_ctx* c, int i) {
             if (o >= 0) e = upload_range(c, b.d_f, b.hF, o, nm * nm);
         }
     for (int m = 0; m < 2 && e == cudaSuccess; ++m) {
-        const long long o = b.lam_off[size_t(i) * 2 + m];
+        const long long o = b.zt_off[size_t(i) * 2 + m];
         const long long nm = m == 0 ? b.n1[i] : b.n2[i];
-        if (o >= 0) e = cudaMemcpy(b.d_lam + o, b.hLam.data() + o, size_t(nm) * 8, cudaMemcpyHostToDevice);
+        if (o >= 0) e = upload_range(c, b.d_zt, b.hZt, o, nm);
     }
     return e;
 }
@@ -699,7 +705,8 @@ adr_status batch_tune(adr_ctx* c) {
     base.inst = static_cast<const adr::BatchInst<T>*>(b.d_inst);
     base.role = role;
     base.factors = static_cast<const T*>(b.d_f);
-    base.lam = b.d_lam;
+    base.zt = static_cast<const T*>(b.d_zt);
+    base.aligned = aligned16(c->ws[0]) && aligned16(c->ws[1]);
     base.X = static_cast<const T*>(c->ws[0]);
     base.Y = static_cast<T*>(c->ws[1]);
     base.epi = adr::EPI_STORE;
@@ -808,7 +815,7 @@ adr_status create_batch(const adr_params* p, void* cuda_stream, adr_ctx** out) {
     b.n1.resize(b.B); b.n2.resize(b.B); b.apitch.resize(b.B);
     b.off.resize(b.B); b.row0.resize(b.B); b.a_off.resize(b.B);
     b.f_off.assign(size_t(b.B) * 8, -1);
-    b.lam_off.assign(size_t(b.B) * 2, -1);
+    b.zt_off.assign(size_t(b.B) * 2, -1);
     long long N = 0;
     for (int i = 0; i < b.B; ++i) {
         const int n1 = p->n_batch[2 * i], n2 = p->n_batch[2 * i + 1];
@@ -828,14 +835,14 @@ adr_status create_batch(const adr_params* p, void* cuda_stream, adr_ctx** out) {
             }
         if (b.roles[adr::BR_V])
             for (int m = 0; m < 2; ++m) {
-                b.lam_off[size_t(i) * 2 + m] = b.lam_len;
-                b.lam_len += m == 0 ? n1 : n2;
+                b.zt_off[size_t(i) * 2 + m] = b.zt_len;
+                b.zt_len += ((m == 0 ? n1 : n2) + 3) / 4 * 4;
             }
     }
     if (N > (1LL << 31) - 1) return fail(nullptr, ADR_ERR_ARG, "batch too large (more than 2^31 - 1 nodes)");
     b.hA.assign(size_t(b.a_len), 0.0);
     b.hF.assign(size_t(b.f_len), 0.0);
-    b.hLam.assign(size_t(b.lam_len), 0.0);
+    b.hZt.assign(size_t(b.zt_len), 0.0);
     b.coef.assign(size_t(b.B) * kCoef, 0.0);
     b.kappa.assign(size_t(b.B) * 2, 0.0);
     b.set.assign(b.B, 0);
@@ -868,7 +875,7 @@ adr_status create_batch(const adr_params* p, void* cuda_stream, adr_ctx** out) {
         e = cudaMemcpy(b.d_row_start, row_start.data(), row_start.size() * sizeof(long long), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&b.d_a, size_t(b.a_len) * c->esize);
     if (e == cudaSuccess) e = cudaMalloc(&b.d_f, size_t(b.f_len) * c->esize);
-    if (e == cudaSuccess && b.lam_len > 0) e = cudaMalloc(reinterpret_cast<void**>(&b.d_lam), size_t(b.lam_len) * 8);
+    if (e == cudaSuccess && b.zt_len > 0) e = cudaMalloc(&b.d_zt, size_t(b.zt_len) * c->esize);
     c->bs = std::move(bs);
     if (e != cudaSuccess) {
         const std::string msg = std::string("batched context: ") + cudaGetErrorString(e);
@@ -934,8 +941,7 @@ adr_status batch_set_coeffs(adr_ctx* c, int i, const double* a_nodes, const doub
             b.kappa[size_t(i) * 2 + m] = eg.kappa;
             std::copy(eg.V.begin(), eg.V.end(), b.hF.begin() + b.f_off[size_t(i) * 8 + adr::BR_V * 2 + m]);
             std::copy(eg.Vinv.begin(), eg.Vinv.end(), b.hF.begin() + b.f_off[size_t(i) * 8 + adr::BR_VINV * 2 + m]);
-            std::copy(eg.lam.begin(), eg.lam.end(), b.hLam.begin() + b.lam_off[size_t(i) * 2 + m]);
-            (void)nm;
+            for (long long j = 0; j < nm; ++j) b.hZt[size_t(b.zt_off[size_t(i) * 2 + m] + j)] = c->p.tau * eg.lam[size_t(j)];
         }
     }
     if (b.roles[adr::BR_V]) {
@@ -1339,7 +1345,7 @@ void adr_destroy(adr_ctx* c) {
         free_dev(b.d_a);
         free_dev(b.d_f);
         { void* q = b.d_row_start; free_dev(q); b.d_row_start = nullptr; }
-        { void* q = b.d_lam; free_dev(q); b.d_lam = nullptr; }
+        free_dev(b.d_zt);
         for (auto& it : b.d_items) { void* q = it; free_dev(q); it = nullptr; }
     }
     free_dev(c->d_a);

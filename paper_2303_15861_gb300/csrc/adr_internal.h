@@ -172,7 +172,8 @@ struct BatchInst {
     T ih2[2] = {0, 0}, i2h[2] = {0, 0}, bmb[2] = {0, 0}, beta[2] = {0, 0};
     T abar = 0, r[4] = {0, 0, 0, 0};
     long long f_off[4][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};  // factor role x direction
-    long long lam_off[2] = {-1, -1};                                   // eigenvalues per direction
+    long long zt_off[2] = {-1, -1};                                    // tau * eigenvalues per direction
+    int vec = 0;                   // n1, n2, off and factor offsets multiples of 4 (16-byte rows)
 };
 
 // Factor roles of a batched context (the same numbering as the single-grid factor kinds).
@@ -216,14 +217,14 @@ struct BatchContractArgs {
     int mode = 1;
     int role = BR_VINV;
     const T* factors = nullptr;    // all instances' dense factors
-    const double* lam = nullptr;   // all instances' eigenvalues
+    const T* zt = nullptr;         // all instances' tau * eigenvalues (working precision)
     const T* X = nullptr;
     T* Y = nullptr;
     int epi = EPI_STORE;
     const T* base = nullptr;
     double alpha = 0;
     int phik = 1;
-    double tau = 0;
+    bool aligned = false;          // X, Y (and base) 16-byte aligned: vector loads where vec
     int grid = 0;
 };
 

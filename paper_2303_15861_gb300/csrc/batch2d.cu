@@ -90,109 +90,247 @@ __global__ void __launch_bounds__(256) batch_stencil_kernel(BatchStencilArgs<T> 
 }
 
 // --------------------------------------------------------------------------- contraction
-constexpr int kThreads = 256;
-constexpr int kBK = 16;
+constexpr int kThreads = 256;      // 16 x 16 threads per tile of every shape
+constexpr int kBK = 16;            // K per shared-memory stage
+constexpr int kPad = 4;            // row padding: keeps 16-byte alignment of 4-wide groups
 constexpr int kMaxEdge = 128;
 
 template <typename T>
 struct TileSmem {
-    T A[kBK][kMaxEdge + 1];
-    T B[kBK][kMaxEdge + 1];
+    alignas(16) T A[kBK][kMaxEdge + kPad];   // A^T slice: [k][m]
+    alignas(16) T B[kBK][kMaxEdge + kPad];   // B slice:   [k][n]
+};
+
+// G consecutive values from shared or global memory (16-byte aligned when G * sizeof(T) >= 16).
+template <int G>
+__device__ __forceinline__ void ld_group(const float* p, float (&r)[G]) {
+    if constexpr (G == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+    } else if constexpr (G == 2) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        r[0] = v.x; r[1] = v.y;
+    } else {
+        r[0] = p[0];
+    }
+}
+template <int G>
+__device__ __forceinline__ void ld_group(const double* p, double (&r)[G]) {
+    if constexpr (G >= 2) {
+#pragma unroll
+        for (int h = 0; h < G / 2; ++h) {
+            const double2 v = reinterpret_cast<const double2*>(p)[h];
+            r[2 * h] = v.x; r[2 * h + 1] = v.y;
+        }
+    } else {
+        r[0] = p[0];
+    }
+}
+__device__ __forceinline__ void st4(float* p, const float* v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double* v) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void ldg4(const float* p, float* v) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+__device__ __forceinline__ void ldg4(const double* p, double* v) {
+    const double2 x = __ldg(reinterpret_cast<const double2*>(p)), y = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+}
+
+// One kBK-deep slice of an operand tile of edge E, staged through E/16 registers per
+// thread. Element (e, k) of the operand (e the row of A or the column of B) sits at
+// P[e * s + k] when KFAST (k contiguous), else at P[k * s + e]. VEC: 16-byte loads of 4
+// elements along the contiguous index (every row start and extent a multiple of 4).
+template <typename T, int E, bool KFAST, bool VEC>
+struct Slice {
+    static constexpr int R = E / 16;
+    T v[R];
+
+    __device__ __forceinline__ void load(const T* __restrict__ P, long long s, int e0, int k0, int Ne, int K) {
+        const int tid = threadIdx.x;
+        if constexpr (VEC) {
+#pragma unroll
+            for (int q = 0; q < R / 4; ++q) {
+                const int c = tid + kThreads * q;
+                const int e = KFAST ? c / (kBK / 4) : (c % (E / 4)) * 4;
+                const int k = KFAST ? (c % (kBK / 4)) * 4 : c / (E / 4);
+                const int ge = e0 + e, gk = k0 + k;
+                if (ge < Ne && gk < K) ldg4(KFAST ? P + (long long)ge * s + gk : P + (long long)gk * s + ge, v + 4 * q);
+                else v[4 * q] = v[4 * q + 1] = v[4 * q + 2] = v[4 * q + 3] = T(0);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int c = tid + kThreads * q;
+                const int e = KFAST ? c / kBK : c % E;
+                const int k = KFAST ? c % kBK : c / E;
+                const int ge = e0 + e, gk = k0 + k;
+                v[q] = (ge < Ne && gk < K) ? __ldg(KFAST ? P + (long long)ge * s + gk : P + (long long)gk * s + ge) : T(0);
+            }
+        }
+    }
+
+    __device__ __forceinline__ void store(T (*S)[kMaxEdge + kPad]) const {
+        const int tid = threadIdx.x;
+        if constexpr (VEC) {
+#pragma unroll
+            for (int q = 0; q < R / 4; ++q) {
+                const int c = tid + kThreads * q;
+                if constexpr (KFAST) {
+                    const int e = c / (kBK / 4), k = (c % (kBK / 4)) * 4;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) S[k + j][e] = v[4 * q + j];
+                } else {
+                    const int e = (c % (E / 4)) * 4, k = c / (E / 4);
+                    st4(&S[k][e], v + 4 * q);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int c = tid + kThreads * q;
+                const int e = KFAST ? c / kBK : c % E;
+                const int k = KFAST ? c % kBK : c / E;
+                S[k][e] = v[q];
+            }
+        }
+    }
 };
 
 // The phi factor of one output, kept out of line: the series branch would otherwise take
 // registers from the accumulator tile of every shape.
 template <typename T>
-__device__ __noinline__ T phi_factor(int k, double z) { return phi_eval(k, T(z)); }
+__device__ __noinline__ T phi_factor(int k, T z) { return phi_eval(k, z); }
 
-// One BM x BN output tile of C = A B (K = the contracted extent) with the fused epilogue.
-// A(m, k) = A[m * sam + k] (k contiguous in both modes); B(k, n) = B[k * sbk + n * sbn].
-template <typename T, int BM, int BN>
-__device__ __forceinline__ void tile_gemm(TileSmem<T>& sm, const T* __restrict__ A, long long sam, const T* __restrict__ B,
-                                          long long sbk, long long sbn, int M, int N, int K, int m0, int n0,
+// One E x E output tile of C = A B (K = the contracted extent) with the fused epilogue.
+// A(m, k) = A[m * sam + k]; B(k, n) = B[n * sb + k] in mode 1 (the factor, k contiguous)
+// and B[k * sb + n] in mode 2 (the state, n contiguous). A thread owns TM x TM outputs in
+// groups of G consecutive rows and columns: row (i / G) * 16G + ty G + i % G.
+template <typename T, int E, int MODE, bool VEC>
+__device__ __forceinline__ void tile_gemm(TileSmem<T>& sm, const T* __restrict__ A, long long sam,
+                                          const T* __restrict__ B, long long sb, int M, int N, int K, int m0, int n0,
                                           const BatchContractArgs<T>& p, const BatchInst<T>& in) {
-    constexpr int TM = BM / 16, TN = BN / 16;    // 16 x 16 threads
+    constexpr int TM = E / 16;
+    constexpr int G = TM < 4 ? TM : 4;
+    constexpr int H = TM / G;
+    constexpr bool VA = VEC && E >= 64;          // vector staging needs E/16 >= 4 registers
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    const bool b_kfast = (sbk == 1);
-    T acc[TM][TN];
+    T acc[TM][TM];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+        for (int j = 0; j < TM; ++j) acc[i][j] = T(0);
 
+    Slice<T, E, true, VA> sa;
+    Slice<T, E, MODE == 1, VA> sbl;
+    sa.load(A, sam, m0, 0, M, K);
+    sbl.load(B, sb, n0, 0, N, K);
     for (int k0 = 0; k0 < K; k0 += kBK) {
-        for (int e = tid; e < BM * kBK; e += kThreads) {
-            const int kk = e % kBK, mm = e / kBK;
-            const int gm = m0 + mm, gk = k0 + kk;
-            sm.A[kk][mm] = (gm < M && gk < K) ? __ldg(A + (long long)gm * sam + gk) : T(0);
-        }
-        for (int e = tid; e < BN * kBK; e += kThreads) {
-            int nn, kk;
-            if (b_kfast) { kk = e % kBK; nn = e / kBK; } else { nn = e % BN; kk = e / BN; }
-            const int gn = n0 + nn, gk = k0 + kk;
-            sm.B[kk][nn] = (gn < N && gk < K) ? __ldg(B + (long long)gk * sbk + (long long)gn * sbn) : T(0);
-        }
+        sa.store(sm.A);
+        sbl.store(sm.B);
         __syncthreads();
+        if (k0 + kBK < K) {                      // the next slice is in flight during the FMAs
+            sa.load(A, sam, m0, k0 + kBK, M, K);
+            sbl.load(B, sb, n0, k0 + kBK, N, K);
+        }
 #pragma unroll
         for (int kk = 0; kk < kBK; ++kk) {
-            T ra[TM], rb[TN];
+            T ra[TM], rb[TM];
 #pragma unroll
-            for (int i = 0; i < TM; ++i) ra[i] = sm.A[kk][ty + 16 * i];
+            for (int h = 0; h < H; ++h) {
+                T ga[G], gb[G];
+                ld_group<G>(&sm.A[kk][h * 16 * G + ty * G], ga);
+                ld_group<G>(&sm.B[kk][h * 16 * G + tx * G], gb);
 #pragma unroll
-            for (int j = 0; j < TN; ++j) rb[j] = sm.B[kk][tx + 16 * j];
+                for (int g = 0; g < G; ++g) { ra[h * G + g] = ga[g]; rb[h * G + g] = gb[g]; }
+            }
 #pragma unroll
             for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) acc[i][j] = fma(ra[i], rb[j], acc[i][j]);
+                for (int j = 0; j < TM; ++j) acc[i][j] = fma(ra[i], rb[j], acc[i][j]);
         }
         __syncthreads();
     }
 
     // C(m, n) is node (i1 = n, i2 = m) of the instance in both modes
-    const double* l1 = (p.epi == EPI_PHI) ? p.lam + in.lam_off[0] : nullptr;
-    const double* l2 = (p.epi == EPI_PHI) ? p.lam + in.lam_off[1] : nullptr;
+    const T* z1 = (MODE == 2 && p.epi == EPI_PHI) ? p.zt + in.zt_off[0] : nullptr;
+    const T* z2 = (MODE == 2 && p.epi == EPI_PHI) ? p.zt + in.zt_off[1] : nullptr;
+    constexpr bool VOUT = (G == 4);
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
-        const int gm = m0 + ty + 16 * i;
+        const int gm = m0 + (i / G) * 16 * G + ty * G + (i % G);
         if (gm >= M) continue;
+        const long long row = in.off + (long long)gm * in.n1;
+        const T zr = (MODE == 2 && p.epi == EPI_PHI) ? __ldg(z2 + gm) : T(0);
 #pragma unroll
-        for (int j = 0; j < TN; ++j) {
-            const int gn = n0 + tx + 16 * j;
-            if (gn >= N) continue;
-            const long long off = in.off + (long long)gm * in.n1 + gn;
-            T v = acc[i][j];
-            if (p.epi == EPI_PHI) {
-                v *= phi_factor<T>(p.phik, p.tau * (__ldg(l1 + gn) + __ldg(l2 + gm)));
+        for (int h = 0; h < H; ++h) {
+            const int gn0 = n0 + h * 16 * G + tx * G;
+            if (gn0 >= N) continue;
+            T v[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) v[g] = acc[i][h * G + g];
+            const bool full = VOUT && VEC && p.aligned && (gn0 + G <= N);
+            if (MODE == 2 && p.epi == EPI_PHI) {      // the last forward pass of a 2-D phi action
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    if (gn0 + g < N) v[g] *= phi_factor<T>(p.phik, zr + __ldg(z1 + gn0 + g));
             } else if (p.epi == EPI_AXPY) {
-                v = __ldg(p.base + off) + T(p.alpha) * v;
+                T bv[G];
+                if constexpr (VOUT) {
+                    if (full) ldg4(p.base + row + gn0, bv);
+                    else
+#pragma unroll
+                        for (int g = 0; g < G; ++g) bv[g] = gn0 + g < N ? __ldg(p.base + row + gn0 + g) : T(0);
+                } else {
+#pragma unroll
+                    for (int g = 0; g < G; ++g) bv[g] = gn0 + g < N ? __ldg(p.base + row + gn0 + g) : T(0);
+                }
+#pragma unroll
+                for (int g = 0; g < G; ++g) v[g] = bv[g] + T(p.alpha) * v[g];
             }
-            p.Y[off] = v;
+            if constexpr (VOUT) {
+                if (full) { st4(p.Y + row + gn0, v); continue; }
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+                if (gn0 + g < N) p.Y[row + gn0 + g] = v[g];
         }
     }
 }
 
-template <typename T>
+template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) batch_contract_kernel(BatchContractArgs<T> p) {
     __shared__ TileSmem<T> sm;
     for (int it = blockIdx.x; it < p.nitems; it += gridDim.x) {
         const int4 item = __ldg(p.items + it);
         const BatchInst<T>& in = p.inst[item.x];
         const int n1 = in.n1, n2 = in.n2;
-        const T* F = p.factors + in.f_off[p.role][p.mode - 1];
+        const T* F = p.factors + in.f_off[p.role][MODE - 1];
         const T* X = p.X + in.off;
         const int edge = item.w == BT_32 ? 32 : item.w == BT_64 ? 64 : 128;
         const int m0 = item.y * edge, n0 = item.z * edge;
         // mode 1: C (n2 x n1) = X (n2 x n1) * M1^T, K = n1; mode 2: C = M2 (n2 x n2) * X, K = n2
-        const T* A = p.mode == 1 ? X : F;
-        const long long sam = p.mode == 1 ? n1 : n2;
-        const T* B = p.mode == 1 ? F : X;
-        const long long sbk = p.mode == 1 ? 1 : n1;
-        const long long sbn = p.mode == 1 ? n1 : 1;
-        const int K = p.mode == 1 ? n1 : n2;
-        if (item.w == BT_32)      tile_gemm<T, 32, 32>(sm, A, sam, B, sbk, sbn, n2, n1, K, m0, n0, p, in);
-        else if (item.w == BT_64) tile_gemm<T, 64, 64>(sm, A, sam, B, sbk, sbn, n2, n1, K, m0, n0, p, in);
-        else                      tile_gemm<T, 128, 128>(sm, A, sam, B, sbk, sbn, n2, n1, K, m0, n0, p, in);
+        const T* A = MODE == 1 ? X : F;
+        const long long sam = MODE == 1 ? n1 : n2;
+        const T* B = MODE == 1 ? F : X;
+        const long long sb = n1;
+        const int K = MODE == 1 ? n1 : n2;
+        const bool vec = in.vec && p.aligned;
+        if (item.w == BT_32) {
+            tile_gemm<T, 32, MODE, false>(sm, A, sam, B, sb, n2, n1, K, m0, n0, p, in);
+        } else if (item.w == BT_64) {
+            if (vec) tile_gemm<T, 64, MODE, true>(sm, A, sam, B, sb, n2, n1, K, m0, n0, p, in);
+            else     tile_gemm<T, 64, MODE, false>(sm, A, sam, B, sb, n2, n1, K, m0, n0, p, in);
+        } else {
+            if (vec) tile_gemm<T, 128, MODE, true>(sm, A, sam, B, sb, n2, n1, K, m0, n0, p, in);
+            else     tile_gemm<T, 128, MODE, false>(sm, A, sam, B, sb, n2, n1, K, m0, n0, p, in);
+        }
     }
 }
 
@@ -232,11 +370,12 @@ cudaError_t contract_launch(const BatchContractArgs<T>& p, cudaStream_t s) {
     if (p.nitems <= 0) return cudaSuccess;
     if (!p.inst || !p.items || !p.factors || !p.X || !p.Y || (p.mode != 1 && p.mode != 2)) return cudaErrorInvalidValue;
     if (p.role < 0 || p.role > BR_VINV) return cudaErrorInvalidValue;
-    if (p.epi == EPI_PHI && !p.lam) return cudaErrorInvalidValue;
+    if (p.epi == EPI_PHI && (!p.zt || p.mode != 2)) return cudaErrorInvalidValue;
     if (p.epi == EPI_AXPY && !p.base) return cudaErrorInvalidValue;
     long long grid = p.grid > 0 ? p.grid : 2LL * sm_count();
     if (grid > p.nitems) grid = p.nitems;
-    batch_contract_kernel<T><<<unsigned(grid), kThreads, 0, s>>>(p);
+    if (p.mode == 1) batch_contract_kernel<T, 1><<<unsigned(grid), kThreads, 0, s>>>(p);
+    else             batch_contract_kernel<T, 2><<<unsigned(grid), kThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 

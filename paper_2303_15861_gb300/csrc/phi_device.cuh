@@ -7,15 +7,25 @@
 
 namespace adr {
 
+// 1/m! for the series coefficients, evaluated by the compiler.
+constexpr double inv_factorial(int m) {
+    double f = 1.0;
+    for (int j = 2; j <= m; ++j) f *= j;
+    return 1.0 / f;
+}
+
+// sum_{j=0}^{19} z^j / (j+K)! by Horner's rule, FP64 (|z| < 1: the first omitted term is
+// below 1/20! = 4e-19). Multiplications only: FP64 division is slow on this GPU.
+template <int K>
+__device__ __forceinline__ double phi_series_k(double z) {
+    double s = inv_factorial(19 + K);
+#pragma unroll
+    for (int j = 18; j >= 0; --j) s = fma(s, z, inv_factorial(j + K));
+    return s;
+}
+
 __device__ __forceinline__ double phi_series(int k, double z) {
-    double fact = 1.0;
-    for (int j = 2; j <= k; ++j) fact *= j;
-    double term = 1.0 / fact, sum = 0.0;
-    for (int j = 0; j < 22; ++j) {   // |z| < 1: the 22nd term is below 1e-21
-        sum += term;
-        term *= z / double(j + k + 1);
-    }
-    return sum;
+    return k == 1 ? phi_series_k<1>(z) : k == 2 ? phi_series_k<2>(z) : phi_series_k<0>(z);
 }
 
 __device__ __forceinline__ double phi_eval(int k, double z) {
