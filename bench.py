@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--m", type=int, default=40)
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison run")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--workload", choices=["3d", "batch2d"], default="3d",
+                   help="3d: the 256^3 Lawson4 workload (default); batch2d: 512 uneven 2-D ETD2RK instances")
     p.add_argument("--ncu-steps", type=int, default=0,
                    help="profiling mode: run this many untimed time steps (adr_step) and exit")
     return p.parse_args()
@@ -362,8 +364,195 @@ def ncu_steps(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- batched 2-D
+BATCH_METRIC = "DOF*steps/s, 512 batched 2-D ETD2RK instances (FP32, tol 1e-5 vs FP64 oracle)"
+FP32_LANES_PER_SM = 128        # FP32 FMA lanes per SM (4 SMSPs x 32)
+SMS = 152
+
+
+def batch_oracle_sample(ws, stride=16):
+    """The oracle's ETD2RK step on every stride-th instance: (seconds, DOF) of one step each,
+    factors and eigenpairs built before timing."""
+    from oracle import adr_oracle as O
+    total_t, total_dof = 0.0, 0
+    for w in ws[::stride]:
+        ops = O.GridOps(O.ADRProblem(w.dims, w.a_nodes, w.b, w.r_poly), w.tau)
+        ops.mf.eig()
+        t0 = time.perf_counter()
+        O.SCHEMES["etd2rk"](ops, w.u0)
+        total_t += time.perf_counter() - t0
+        total_dof += w.dof
+    return total_t, total_dof
+
+
+def reference_batch(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    from paper_2303_15861_gb300 import workloads as W
+    ws = W.config4()
+    for _ in range(args.warmup):
+        batch_oracle_sample(ws, stride=4)
+    ts, dofs = 0.0, 0
+    for _ in range(args.steps):
+        t, d = batch_oracle_sample(ws, stride=4)
+        ts += t
+        dofs += d
+    value = dofs / ts
+    line = {
+        "impl": "reference", "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * ts / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "2d_batch512_etd2rk_T0.1_m30", "instances": len(ws), "precision": "fp64-numpy-oracle",
+                   "step": "one ETD2RK time step of every 4th instance"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": _CORES, "kind": "oracle",
+                         "sample": "one ETD2RK step of every 4th instance (128 of 512) per bench step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ours_batch(args):
+    import numpy as np
+    import torch
+    from paper_2303_15861_gb300 import adr, build_lib, workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    build_lib.build()
+    adr.load_library()
+    prec = "fp64" if args.precision == "fp64" else "fp32"
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    ws = W.config4()
+    N = sum(w.dof for w in ws)
+    m = ws[0].m
+    stream = torch.cuda.Stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        ctx = adr.Context(None, ws[0].tau, "etd2rk", prec, stream=stream, batch_dims=[w.dims for w in ws],
+                          kappa_tol=1.0)
+        for i, w in enumerate(ws):
+            ctx.set_coeffs(w.a_nodes, w.b, w.r_poly, instance=i)
+        setup_s = time.perf_counter() - t0
+        u0 = torch.tensor(np.concatenate([w.u0.ravel() for w in ws]), dtype=dt, device="cuda")
+        u = u0.clone()
+        for _ in range(args.warmup):
+            u.copy_(u0)
+            ctx.integrate(u, 0.0, m * ws[0].tau, m)
+        ctx.synchronize()
+        sampler = ClockSampler(local)
+        sampler.start()
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ctx.integrate(u, 0.0, m * ws[0].tau, m)
+        ev1.record(stream)
+        barrier()
+        sampler.stop()
+        ms = ev0.elapsed_time(ev1)
+        ctx.synchronize()
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        value = world * N * m * args.steps / (ms_max * 1e-3)
+
+        # per-op durations of one step: contractions (kind 3) and stencils (kind 2)
+        kinds = {}
+        for _ in range(3):
+            for kind, kms in ctx.profile_step(u):
+                kinds.setdefault(kind, []).append(kms)
+        plan = {mode: ctx.batch_plan(mode) for mode in (1, 2)}
+
+        # end to end: pinned host state in, result out, every integration
+        host = u0.cpu().pin_memory()
+        barrier()
+        te = time.perf_counter()
+        e2e_steps = max(1, args.steps // 2)
+        for _ in range(e2e_steps):
+            ctx.integrate_host(host, 0.0, m * ws[0].tau, m)
+        e2e_s = time.perf_counter() - te
+        e2e_value = world * N * m * e2e_steps / e2e_s
+
+        acc = {}
+        if rank == 0 and not args.no_fp64:
+            from oracle import adr_oracle as O
+            u.copy_(u0)
+            ctx.integrate(u, 0.0, m * ws[0].tau, m)
+            ctx.synchronize()
+            h = u.double().cpu().numpy()
+            offs = np.cumsum([0] + [w.dof for w in ws])
+            errs = []
+            for i in (0, 146, 349, 511):
+                w = ws[i]
+                ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, m, "etd2rk")
+                errs.append(O.rel_l2(h[offs[i]:offs[i + 1]].reshape(w.dims[::-1]), ref))
+            acc = {"rel_l2_vs_oracle_max_sampled": max(errs), "sampled_instances": [0, 146, 349, 511]}
+        launches = ctx.kernels_per_step() * m * args.steps
+        ctx.close()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel: the batched contraction on the FP32 FMA pipes
+    flops_pass = sum(2.0 * w.dims[0] * w.dims[1] * (w.dims[0] + w.dims[1]) / 2.0 for w in ws)
+    c_ms = statistics.mean(kinds.get(3, [float("nan")]))
+    clk = sampler.summary()
+    mhz = clk["sm_mhz"] or 2070.0
+    peak = SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12 if prec == "fp32" else None
+    achieved = flops_pass / (c_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if peak else None, "traffic": None,
+            "kernel": "batch_contract_kernel (mu-mode pass over all instances, FP32 FMA)",
+            "launch_ms": c_ms, "stencil_launch_ms": statistics.mean(kinds.get(2, [float("nan")])),
+            "peak_source": f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flops x {mhz:.0f} MHz"}
+    cpu = None
+    if not args.no_cpu:
+        t_cpu, d_cpu = batch_oracle_sample(ws, stride=1)
+        cpu = {"value": d_cpu / t_cpu, "unit": UNIT, "cores": _CORES, "kind": "oracle",
+               "sample": f"one ETD2RK step of all 512 instances ({t_cpu:.1f} s)"}
+    edges = {f"mode{mode}": {f"{w.dims[0]}": e for w, e in zip(ws, plan[mode][0])} for mode in (1, 2)}
+    line = {
+        "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": "2d_batch512_etd2rk_T0.1_m30", "instances": len(ws), "dof": N, "precision": prec,
+                   "time_steps_per_bench_step": m, "parallelism": f"replicas{world}",
+                   "l2": "working set > L2 (factors and six packed state arrays)",
+                   "autotuned_tiles": edges, "grid": {f"mode{k}": plan[k][1] for k in (1, 2)}},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * (8 if prec == "fp64" else 4),
+                "d2h_bytes_per_step": N * (8 if prec == "fp64" else 4)},
+        "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "setup_s": setup_s,
+        "kernel_ms_per_time_step": {str(k): sum(v) / 3.0 for k, v in kinds.items()},
+    }
+    line.update(acc)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "batch2d":
+        return reference_batch(args) if args.impl == "reference" else ours_batch(args)
     if args.impl == "reference":
         return reference_arm(args)
     if args.ncu_steps > 0:
