@@ -37,16 +37,19 @@ constexpr int kThreads = 18 * 32;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kN >> 3) << 17) | (uint32_t(kM >> 4) << 24);
 
+// Standard: state slices S0, S1, 2^-8 S2, 2^-8 S1 and factor slices F0, F1, 2^-8 F2 (the
+// product S1 (2^-8 F1) of the split is formed as (2^-8 S1) F1, the same exact value, so
+// each K chunk moves three factor tiles from L2 instead of four). Precise: four of each.
 template <bool PR>
 struct Cfg {
-    static constexpr int SS = PR ? 4 : 3;              // state slices
-    static constexpr int FS = 4;                       // factor slices
+    static constexpr int SS = 4;                       // state slices
+    static constexpr int FS = PR ? 4 : 3;              // factor slices
     static constexpr int NACC = PR ? 4 : 2;            // accumulators (128 columns each)
     static constexpr int NSETS = PR ? 1 : 2;           // TMEM accumulator sets
     static constexpr int TILE = kM * kKc * 2;          // one bf16 slice tile: 8 KB
     static constexpr int SBYTES = SS * TILE;           // one state-slice stage
-    static constexpr int FBYTES = FS * TILE;           // one factor stage (32 KB)
-    static constexpr int NSLICE = 2;                   // state-slice ring
+    static constexpr int FBYTES = FS * TILE;           // one factor stage (24 or 32 KB)
+    static constexpr int NSLICE = PR ? 2 : 3;          // state-slice ring
     static constexpr int NF = PR ? 3 : 4;              // factor ring (the loader runs it ahead)
     static constexpr int XTILE = kM * kKc * 4;         // one FP32 staging tile: 16 KB
     static constexpr int XSTAGE = PR ? 2 * XTILE : XTILE;   // hi (+ lo)
@@ -127,7 +130,7 @@ __device__ __forceinline__ void split(float y, float ylo, uint32_t (&b)[4]) {
         b[3] = __float_as_uint(rintf((y2 - s2) * 256.f));
     } else {
         b[2] = __float_as_uint(s2 * 0.00390625f);
-        b[3] = 0u;
+        b[3] = __float_as_uint(s1 * 0.00390625f);
     }
 }
 
@@ -135,7 +138,7 @@ __device__ __forceinline__ void split(float y, float ylo, uint32_t (&b)[4]) {
 template <bool PR>
 __device__ __forceinline__ void slice_store8(const float (&v)[8], const float (&vl)[8], float sc, uint32_t tile0, int r,
                                              int j) {
-    constexpr int SS = PR ? 4 : 3;
+    constexpr int SS = 4;
     uint32_t w[4][4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -177,13 +180,13 @@ __device__ __forceinline__ void mma_kstep(uint32_t d, const uint64_t (&S)[4], co
         else    tc_mma(dd, F[fi] + adv, S[si] + adv, kIdesc, accumulate);
     };
     const uint32_t acc = first ? 0u : 1u;
-    if (!PR) {
+    if (!PR) {                       // S = {S0, S1, 2^-8 S2, 2^-8 S1}, F = {F0, F1, 2^-8 F2}
         mma(0, 0, 0, acc);
         mma(1, 0, 1, acc);
         mma(1, 1, 0, 1u);
-        mma(1, 0, 3, 1u);
+        mma(1, 0, 2, 1u);
         mma(1, 2, 0, 1u);
-        mma(1, 1, 2, 1u);
+        mma(1, 3, 1, 1u);
     } else {
         mma(0, 0, 0, acc);
         mma(1, 0, 1, acc);
@@ -202,8 +205,11 @@ template <bool SA, bool PR, int EPI>
 __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_constant__ TmaArgs p) {
     using C = Cfg<PR>;
     extern __shared__ uint8_t smem_raw[];
-    // barriers: xfull[2] xempty[2] sfull[2] sempty[2] ffull[4] fempty[4] accf[2] acce[2] drain
-    __shared__ __align__(8) uint64_t bars[21];
+    // barriers: xfull[NX] xempty[NX] sfull[NSLICE] sempty[NSLICE] ffull[NF] fempty[NF] accf[2] acce[2] drain
+    constexpr uint32_t kXF = 0, kXE = kXF + 8 * C::NX, kSF = kXE + 8 * C::NX, kSE = kSF + 8 * C::NSLICE;
+    constexpr uint32_t kFF = kSE + 8 * C::NSLICE, kFE = kFF + 8 * C::NF, kAF = kFE + 8 * C::NF, kAE = kAF + 16;
+    constexpr uint32_t kDR = kAE + 16;
+    __shared__ __align__(8) uint64_t bars[kDR / 8 + 1];
     __shared__ uint32_t tmem_base_s;
     __shared__ volatile int abort_s;
 
@@ -212,23 +218,23 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
     const uint32_t fbase = sbase + C::NSLICE * C::SBYTES;             // factor ring
     const uint32_t xbase = fbase + C::NF * C::FBYTES;                 // FP32 staging ring
     const uint32_t bar0 = smem_u32(&bars[0]);
-    auto xfull = [&](int s) { return bar0 + 8u * s; };
-    auto xempty = [&](int s) { return bar0 + 16u + 8u * s; };
-    auto sfull = [&](int s) { return bar0 + 32u + 8u * s; };
-    auto sempty = [&](int s) { return bar0 + 48u + 8u * s; };
-    auto ffull = [&](int s) { return bar0 + 64u + 8u * s; };
-    auto fempty = [&](int s) { return bar0 + 96u + 8u * s; };
-    auto accf = [&](int a) { return bar0 + 128u + 8u * a; };
-    auto acce = [&](int a) { return bar0 + 144u + 8u * a; };
-    const uint32_t drain_bar = bar0 + 160u;
+    auto xfull = [&](int s) { return bar0 + kXF + 8u * s; };
+    auto xempty = [&](int s) { return bar0 + kXE + 8u * s; };
+    auto sfull = [&](int s) { return bar0 + kSF + 8u * s; };
+    auto sempty = [&](int s) { return bar0 + kSE + 8u * s; };
+    auto ffull = [&](int s) { return bar0 + kFF + 8u * s; };
+    auto fempty = [&](int s) { return bar0 + kFE + 8u * s; };
+    auto accf = [&](int a) { return bar0 + kAF + 8u * a; };
+    auto acce = [&](int a) { return bar0 + kAE + 8u * a; };
+    const uint32_t drain_bar = bar0 + kDR;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::NX; ++s) {
             mbar_init(xfull(s), 1);                         // loader's expect_tx arrival
-            mbar_init(xempty(s), kProducerWarps * 32);      // producers have read the tile
+            mbar_init(xempty(s), kProducerWarps);           // one arrival per producer warp
         }
         for (int s = 0; s < C::NSLICE; ++s) {
-            mbar_init(sfull(s), kProducerWarps * 32);       // producers
+            mbar_init(sfull(s), kProducerWarps);            // one arrival per producer warp
             mbar_init(sempty(s), 1);                        // tcgen05.commit
         }
         for (int s = 0; s < C::NF; ++s) {
@@ -237,7 +243,7 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(accf(a), 1);
-            mbar_init(acce(a), kEpiWarps * 32);
+            mbar_init(acce(a), kEpiWarps);                  // one arrival per epilogue warp
         }
         mbar_init(drain_bar, 1);
         abort_s = 0;
@@ -312,11 +318,12 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
         for (long long it = 0; it < items; ++it) {
             const int ss = int(it % C::NSLICE);
             const uint32_t sph = uint32_t(it / C::NSLICE) & 1u;
-            if (!mbar_wait(sempty(ss), sph ^ 1u, p.err, 1, &abort_s, 32)) break;
+            // waits decide warp-uniformly: the per-warp arrivals below need every lane
+            if (!__all_sync(0xffffffffu, mbar_wait(sempty(ss), sph ^ 1u, p.err, 1, &abort_s, 32))) break;
             const uint32_t sA = sbase + ss * C::SBYTES;
             const int xs = int(it % C::NX);
             const uint32_t xph = uint32_t(it / C::NX) & 1u;
-            if (!mbar_wait(xfull(xs), xph, p.err, 32, &abort_s)) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(xfull(xs), xph, p.err, 32, &abort_s))) break;
             const uint32_t xt = xbase + xs * C::XSTAGE;
             float v[2][8], vl[2][8];
             if (SA) {
@@ -349,7 +356,10 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
                     }
                 }
             }
-            mbar_arrive(xempty(xs));      // the staging tile may be refilled
+            // the staging tile may be refilled: one arrival per warp once every lane has read
+            // (256 single-thread arrivals on one barrier word serialise for ~1000 cycles)
+            __syncwarp();
+            if (lane == 0) mbar_arrive(xempty(xs));
             if (SA) {
                 const int row = t & (kM - 1), half = t >> 7;
                 slice_store8<PR>(v[0], vl[0], sc, sA, row, 2 * half);
@@ -360,7 +370,8 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
                 slice_store8<PR>(v[1], vl[1], sc, sA, r0 + 64, j);
             }
             fence_proxy_async();
-            mbar_arrive(sfull(ss));
+            __syncwarp();
+            if (lane == 0) mbar_arrive(sfull(ss));
         }
     } else if (warp < kEpiWarp0 + kEpiWarps) {
         // ------------------------------------------------------------ epilogue
@@ -462,7 +473,8 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
                 }
             }
             tc_fence_before();
-            mbar_arrive(acce(a));
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce(a));
             for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
             if (lane == 0 && p.amax_out && vmax > 0.f) atomicMax(p.amax_out, __float_as_uint(vmax));
         }
@@ -490,7 +502,7 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     S[q] = sdesc64(sS + (q < C::SS ? q : 0) * C::TILE);
-                    F[q] = sdesc64(sF + q * C::TILE);
+                    F[q] = sdesc64(sF + (q < C::FS ? q : 0) * C::TILE);
                 }
 #pragma unroll
                 for (int kk = 0; kk < kKc / 16; ++kk)

@@ -183,11 +183,14 @@ TcFactor make_tc_factor(const std::vector<double>& M, int n, int rows, bool prec
     // K-major layout the tensor cores read (8-row groups of 1024 B; 16-byte chunk j of row r
     // at position j ^ (r mod 8)): F0, F1, 2^-8 F1, 2^-8 F2 (standard) or F0, F1, F2, F3
     // (precise). With chunks of 32 the tiles use the 64-byte swizzle (8-row groups of 512 B;
-    // chunk j of row r at position j ^ ((r / 2) mod 4)).
+    // chunk j of row r at position j ^ ((r / 2) mod 4)), and the standard image holds three
+    // tiles F0, F1, 2^-8 F2: that kernel forms S1 (2^-8 F1) as (2^-8 S1) F1 from a scaled
+    // state slice, the same exact product, so one factor tile less crosses from L2.
     const int tile = rows * chunk * 2;
     const int nK = (n + chunk - 1) / chunk, nOut = (n + rows - 1) / rows;
+    const int nq = (precise || chunk == 64) ? 4 : 3;
     TcFactor out;
-    out.img.assign(size_t(nOut) * nK * 4 * tile, 0);
+    out.img.assign(size_t(nOut) * nK * nq * tile, 0);
     out.fscale.assign(size_t(nOut) * rows, 0.0f);
     std::vector<double> slices(size_t(n) * n * 4, 0.0);
     for (int i = 0; i < n; ++i) {
@@ -207,15 +210,17 @@ TcFactor make_tc_factor(const std::vector<double>& M, int n, int rows, bool prec
             double* sl = &slices[(size_t(i) * n + k) * 4];
             if (precise) {
                 sl[0] = f0; sl[1] = f1; sl[2] = f2; sl[3] = f3;
-            } else {
+            } else if (nq == 4) {
                 sl[0] = f0; sl[1] = f1; sl[2] = f1 / 256.0; sl[3] = f2 / 256.0;
+            } else {
+                sl[0] = f0; sl[1] = f1; sl[2] = f2 / 256.0; sl[3] = 0.0;
             }
         }
     }
     for (int ot = 0; ot < nOut; ++ot)
         for (int c = 0; c < nK; ++c)
-            for (int q = 0; q < 4; ++q) {
-                uint8_t* t = &out.img[((size_t(ot) * nK + c) * 4 + q) * tile];
+            for (int q = 0; q < nq; ++q) {
+                uint8_t* t = &out.img[((size_t(ot) * nK + c) * nq + q) * tile];
                 for (int r = 0; r < rows; ++r) {
                     const int i = ot * rows + r;
                     if (i >= n) continue;

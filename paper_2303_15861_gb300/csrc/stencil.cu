@@ -132,6 +132,7 @@ __global__ void __launch_bounds__(TX * TY) stencil_kernel(StencilArgs<T> p, Coef
 // loads; the x1 neighbours of the 4-node group come from the adjacent lanes (shuffles), the
 // warp edges load them. A warp covers 128 consecutive x1 nodes of one (x2, x3) row.
 constexpr int ZV = 2;
+constexpr int kMarchPlanes = 12;   // x3 planes walked by one CTA of the z-marching kernel
 
 __device__ __forceinline__ void f4arr(const float4& v, float (&a)[4]) { a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w; }
 __device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
@@ -258,6 +259,171 @@ __global__ void __launch_bounds__(256) stencil_vec4_kernel(StencilArgs<float> p,
         if (j < p.nout && p.amax[j]) block_amax(outabs[j], p.amax[j]);
 }
 
+// FP32, 3-D, n1 % 4 == 0: z-marching form. A thread owns 4 consecutive x1 nodes of one
+// (x2) row and walks ZB planes of x3: the planes below, at and above the current one stay
+// in registers and rotate, and the next plane's centre values (u, its low part, a, the extra
+// stage inputs) are loaded one iteration ahead, so each value is read from memory about once
+// and the loads of plane z+1 are in flight while plane z is computed. The x1 neighbours come
+// from the adjacent lanes (shuffles), the x2 neighbours from the rows of the adjacent warps
+// (L1/L2 hits).
+template <bool HASLO, int NX, int NOUT>
+__global__ void __launch_bounds__(256, HASLO ? 2 : 3) stencil_march_kernel(StencilArgs<float> p, Coefs<float> c, bool needF, int zb) {
+    const int n1 = p.n1, n2 = p.n2, n3 = p.n3;
+    const int A1 = p.apitch, A2 = n2 + 2;
+    const long long plane_u = (long long)n1 * n2;
+    const long long plane_a = (long long)A1 * A2;
+    const int lane = threadIdx.x & 31;
+    const int i1 = (blockIdx.x * 32 + lane) * 4;
+    const int i2 = blockIdx.y * 8 + int(threadIdx.x >> 5);
+    const int z0 = int(blockIdx.z) * zb;
+    const int z1 = min(z0 + zb, n3);
+    const bool inside = (i1 < n1) && (i2 < n2);      // n1 % 4 == 0: all 4 nodes or none
+    const long long row_u = (long long)i2 * n1 + i1;
+    const long long row_a = (long long)(i2 + 1) * A1 + (i1 + 4);
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool load_e = (lane == 31) || (i1 + 4 >= n1);
+
+    // planes z-1 (M), z (C), z+1 (P) of u (+ low part) and of a; x1 ghosts of u are 0
+    float4 uM = zero4, uC = zero4, uP = zero4, lM = zero4, lC = zero4, lP = zero4;
+    float4 aM = zero4, aC = zero4, aP = zero4;
+    float4 xC[NX > 0 ? NX : 1], xP[NX > 0 ? NX : 1];
+#pragma unroll
+    for (int e = 0; e < (NX > 0 ? NX : 1); ++e) xC[e] = xP[e] = zero4;
+    if (inside) {
+        aM = ld4(p.a + (long long)z0 * plane_a + row_a);              // a plane index z + 1
+        aC = ld4(p.a + (long long)(z0 + 1) * plane_a + row_a);
+        if (z0 > 0) {
+            uM = ld4(p.u + (long long)(z0 - 1) * plane_u + row_u);
+            if (HASLO) lM = ld4(p.u_lo + (long long)(z0 - 1) * plane_u + row_u);
+        }
+        uC = ld4(p.u + (long long)z0 * plane_u + row_u);
+        if (HASLO) lC = ld4(p.u_lo + (long long)z0 * plane_u + row_u);
+#pragma unroll
+        for (int e = 0; e < NX; ++e) xC[e] = ld4(p.X[e] + (long long)z0 * plane_u + row_u);
+    }
+    float outabs[NOUT];
+#pragma unroll
+    for (int j = 0; j < NOUT; ++j) outabs[j] = 0.f;
+    float uabs = 0.f;
+    for (int z = z0; z < z1; ++z) {
+        const long long zu = (long long)z * plane_u;
+        const long long za = (long long)(z + 1) * plane_a;
+        // next plane (in flight during this one)
+        if (inside) {
+            aP = ld4(p.a + za + plane_a + row_a);                     // a at z + 1 (ring: z + 2 <= n3 + 1)
+            if (z + 1 < n3) {
+                uP = ld4(p.u + zu + plane_u + row_u);
+                if (HASLO) lP = ld4(p.u_lo + zu + plane_u + row_u);
+                if (z + 1 < z1) {
+#pragma unroll
+                    for (int e = 0; e < NX; ++e) xP[e] = ld4(p.X[e] + zu + plane_u + row_u);
+                }
+            } else {
+                uP = zero4;
+                lP = zero4;
+            }
+        }
+        float4 us = zero4, un = zero4, ls4 = zero4, ln4 = zero4, as4 = zero4, an4 = zero4;
+        float xw = 0.f, xe = 0.f, yw = 0.f, ye = 0.f, aw = 0.f, ae = 0.f;
+        if (inside) {
+            const float* uz = p.u + zu + row_u;
+            const float* az = p.a + za + row_a;
+            if (i2 > 0) us = ld4(uz - n1);
+            if (i2 + 1 < n2) un = ld4(uz + n1);
+            as4 = ld4(az - A1);
+            an4 = ld4(az + A1);
+            if (lane == 0 && i1 > 0) xw = __ldg(uz - 1);
+            if (load_e && i1 + 4 < n1) xe = __ldg(uz + 4);
+            if (lane == 0) aw = __ldg(az - 1);
+            if (load_e) ae = __ldg(az + 4);
+            if (HASLO) {
+                const float* lz = p.u_lo + zu + row_u;
+                if (i2 > 0) ls4 = ld4(lz - n1);
+                if (i2 + 1 < n2) ln4 = ld4(lz + n1);
+                if (lane == 0 && i1 > 0) yw = __ldg(lz - 1);
+                if (load_e && i1 + 4 < n1) ye = __ldg(lz + 4);
+            }
+        }
+        // x1 halo of the group from the neighbouring lanes (all lanes take part)
+        const float sw_u = __shfl_up_sync(0xffffffffu, uC.w, 1), se_u = __shfl_down_sync(0xffffffffu, uC.x, 1);
+        const float sw_a = __shfl_up_sync(0xffffffffu, aC.w, 1), se_a = __shfl_down_sync(0xffffffffu, aC.x, 1);
+        float sw_l = 0.f, se_l = 0.f;
+        if (HASLO) {
+            sw_l = __shfl_up_sync(0xffffffffu, lC.w, 1);
+            se_l = __shfl_down_sync(0xffffffffu, lC.x, 1);
+        }
+        if (inside) {
+            if (lane != 0) { xw = sw_u; aw = sw_a; yw = sw_l; }
+            if (lane != 31 && i1 + 4 < n1) { xe = se_u; ae = se_a; ye = se_l; }
+            float U[4], L[4], Aa[4], US[4], UN[4], LS[4], LN[4], AS[4], AN[4], UM[4], UP[4], LM[4], LP[4], AM[4], AP[4];
+            f4arr(uC, U); f4arr(lC, L); f4arr(aC, Aa);
+            f4arr(us, US); f4arr(un, UN); f4arr(ls4, LS); f4arr(ln4, LN); f4arr(as4, AS); f4arr(an4, AN);
+            f4arr(uM, UM); f4arr(uP, UP); f4arr(lM, LM); f4arr(lP, LP); f4arr(aM, AM); f4arr(aP, AP);
+            const float UX[6] = {xw, U[0], U[1], U[2], U[3], xe}, LX[6] = {yw, L[0], L[1], L[2], L[3], ye};
+            const float AX[6] = {aw, Aa[0], Aa[1], Aa[2], Aa[3], ae};
+            float res[NOUT][4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float uk = U[k], lk = L[k], ak = Aa[k];
+                const float dE = (UX[k + 2] - uk) + (LX[k + 2] - lk), dW = (uk - UX[k]) + (lk - LX[k]);
+                const float dN = (UN[k] - uk) + (LN[k] - lk), dS = (uk - US[k]) + (lk - LS[k]);
+                const float dP = (UP[k] - uk) + (LP[k] - lk), dM = (uk - UM[k]) + (lk - LM[k]);
+                const float uF = uk + lk;
+                float F = 0.f;
+                const float g = stencil_core<float, 3>(c, uF, dE, dW, dN, dS, dP, dM, ak + AX[k + 2], ak + AX[k],
+                                                       ak + AN[k], ak + AS[k], ak + AP[k], ak + AM[k], needF, F);
+                uabs = fmaxf(uabs, fabsf(uF));
+#pragma unroll
+                for (int j = 0; j < NOUT; ++j) {
+                    float v = c.cu[j] * uF + c.cg[j] * g + c.cF[j] * F;
+#pragma unroll
+                    for (int e = 0; e < NX; ++e) {
+                        float xe4[4];
+                        f4arr(xC[e], xe4);
+                        v += c.cx[j][e] * xe4[k];
+                    }
+                    res[j][k] = v;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NOUT; ++j) {
+                *reinterpret_cast<float4*>(p.out[j] + zu + row_u) = make_float4(res[j][0], res[j][1], res[j][2], res[j][3]);
+                outabs[j] = fmaxf(outabs[j], fmaxf(fmaxf(fabsf(res[j][0]), fabsf(res[j][1])), fmaxf(fabsf(res[j][2]), fabsf(res[j][3]))));
+            }
+        }
+        uM = uC; uC = uP; lM = lC; lC = lP; aM = aC; aC = aP;
+#pragma unroll
+        for (int e = 0; e < NX; ++e) xC[e] = xP[e];
+    }
+    if (p.amax_u) block_amax(uabs, p.amax_u);
+#pragma unroll
+    for (int j = 0; j < NOUT; ++j)
+        if (p.amax[j]) block_amax(outabs[j], p.amax[j]);
+}
+
+template <bool HASLO, int NX>
+void launch_march_nout(const StencilArgs<float>& p, const Coefs<float>& c, bool needF, int zb, dim3 g, cudaStream_t s) {
+    if (p.nout == 1) stencil_march_kernel<HASLO, NX, 1><<<g, 256, 0, s>>>(p, c, needF, zb);
+    else             stencil_march_kernel<HASLO, NX, 2><<<g, 256, 0, s>>>(p, c, needF, zb);
+}
+
+template <bool HASLO>
+void launch_march_nx(const StencilArgs<float>& p, const Coefs<float>& c, bool needF, int zb, dim3 g, cudaStream_t s) {
+    switch (p.nx) {
+    case 0: launch_march_nout<HASLO, 0>(p, c, needF, zb, g, s); break;
+    case 1: launch_march_nout<HASLO, 1>(p, c, needF, zb, g, s); break;
+    case 2: launch_march_nout<HASLO, 2>(p, c, needF, zb, g, s); break;
+    default: launch_march_nout<HASLO, 3>(p, c, needF, zb, g, s); break;
+    }
+}
+
+cudaError_t launch_march(const StencilArgs<float>& p, const Coefs<float>& c, bool needF, int zb, dim3 g, cudaStream_t s) {
+    if (p.nout < 1 || p.nout > kMaxOut || p.nx < 0 || p.nx > kMaxExtra) return cudaErrorInvalidValue;
+    if (p.u_lo) launch_march_nx<true>(p, c, needF, zb, g, s);
+    else        launch_march_nx<false>(p, c, needF, zb, g, s);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_impl(const StencilArgs<T>& p, cudaStream_t s) {
     Coefs<T> c;
@@ -285,8 +451,9 @@ cudaError_t launch_impl(const StencilArgs<T>& p, cudaStream_t s) {
         if (aligned) {
             dim3 g4((p.n1 / 4 + 31) / 32, (p.n2 + 7) / 8, p.dim == 3 ? (p.n3 + ZV - 1) / ZV : 1);
             if (p.dim == 3) {
-                if (p.u_lo) stencil_vec4_kernel<3, true><<<g4, 256, 0, s>>>(p, c, needF);
-                else        stencil_vec4_kernel<3, false><<<g4, 256, 0, s>>>(p, c, needF);
+                const int zb = kMarchPlanes;
+                dim3 gm((p.n1 / 4 + 31) / 32, (p.n2 + 7) / 8, (p.n3 + zb - 1) / zb);
+                return launch_march(p, c, needF, zb, gm, s);
             } else {
                 if (p.u_lo) stencil_vec4_kernel<2, true><<<g4, 256, 0, s>>>(p, c, needF);
                 else        stencil_vec4_kernel<2, false><<<g4, 256, 0, s>>>(p, c, needF);
