@@ -43,8 +43,11 @@ def parse():
     p.add_argument("--m", type=int, default=40)
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison run")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    p.add_argument("--workload", choices=["3d", "batch2d"], default="3d",
-                   help="3d: the 256^3 Lawson4 workload (default); batch2d: 512 uneven 2-D ETD2RK instances")
+    p.add_argument("--workload", choices=["3d", "batch2d"] + sorted(GRID_WORKLOADS), default="3d",
+                   help="3d: the 256^3 Lawson4 workload (default); batch2d: 512 uneven 2-D ETD2RK instances; "
+                        "c1-*, c2, c5-*: the other single-grid workloads")
+    p.add_argument("--check", action="store_true",
+                   help="single-grid workloads: also measure the error (oracle for c1/c2, FP64 GPU at tau/4 for c5)")
     p.add_argument("--ncu-steps", type=int, default=0,
                    help="profiling mode: run this many untimed time steps (adr_step) and exit")
     return p.parse_args()
@@ -364,6 +367,129 @@ def ncu_steps(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- other single grids
+# name -> (workload factory, default precision)
+GRID_WORKLOADS = {
+    "c1-le": (lambda W: W.config1("lawson_euler"), "fp64"),
+    "c1-etd2rk": (lambda W: W.config1("etd2rk"), "fp64"),
+    "c2": (lambda W: W.config2(), "fp64"),
+    "c5-lawson4": (lambda W: W.config5(scheme="lawson4"), "bf16x3"),
+    "c5-etd2rk": (lambda W: W.config5(scheme="etd2rk"), "bf16x3"),
+}
+FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (nominal; no measured figure on this machine)
+
+
+def ours_grid(args):
+    """One of the single-grid workloads: device-timed integrations through adr_integrate,
+    per-op kernel times, e2e through adr_integrate_host, and with --check the error."""
+    import numpy as np
+    import torch
+    from paper_2303_15861_gb300 import adr, build_lib, workloads as W
+
+    torch.cuda.set_device(0)
+    build_lib.build()
+    adr.load_library()
+    make, default_prec = GRID_WORKLOADS[args.workload]
+    w = make(W)
+    prec = args.precision if args.precision != "bf16x3" or default_prec == "bf16x3" else default_prec
+    if args.workload.startswith(("c1", "c2")):
+        prec = "fp64" if args.precision == "bf16x3" else args.precision
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    N = w.dof
+    stream = torch.cuda.Stream()
+    base = {"metric": f"DOF*steps/s, {args.workload}", "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3+f32"}[prec], "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.dims), "scheme": w.scheme, "precision": prec,
+                       "tau": w.tau, "time_steps_per_bench_step": w.m, "b": list(w.b[:len(w.dims)])}}
+    with torch.cuda.stream(stream):
+        try:
+            ctx = adr.Context(w.dims, w.tau, w.scheme, prec, stream=stream)
+            ctx.set_coeffs(w.a_nodes, w.b, w.r_poly)
+        except adr.AdrError as e:
+            line = dict(base, unavailable=str(e))
+            print(json.dumps(line), flush=True)
+            return 0
+        u0 = torch.tensor(w.u0, dtype=dt, device="cuda")
+        u = u0.clone()
+        for _ in range(args.warmup):
+            ctx.integrate(u, 0.0, 0.0, w.m)
+        ctx.synchronize()
+        sampler = ClockSampler(0)
+        sampler.start()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ctx.integrate(u, 0.0, 0.0, w.m)
+        ev1.record(stream)
+        ev1.synchronize()
+        sampler.stop()
+        ms = ev0.elapsed_time(ev1)
+        ctx.synchronize()
+        kinds = {}
+        for _ in range(3):
+            for kind, kms in ctx.profile_step(u):
+                kinds.setdefault(kind, []).append(kms)
+        host = u0.cpu().pin_memory()
+        ctx.integrate_host(host, 0.0, 0.0, w.m)
+        t0 = time.perf_counter()
+        e2e_n = max(1, min(args.steps, 5))
+        for _ in range(e2e_n):
+            ctx.integrate_host(host, 0.0, 0.0, w.m)
+        e2e_s = time.perf_counter() - t0
+        acc = {}
+        if args.check:
+            u.copy_(u0)
+            ctx.integrate(u, 0.0, 0.0, w.m)
+            ctx.synchronize()
+            got = u.double().cpu().numpy()
+            from oracle import adr_oracle as O
+            if args.workload.startswith("c5"):
+                # reference: the FP64 GPU path at tau / 4 (four times the steps)
+                rc = adr.Context(w.dims, w.tau / 4, w.scheme, "fp64", stream=stream)
+                rc.set_coeffs(w.a_nodes, w.b, w.r_poly)
+                ur = torch.tensor(w.u0, dtype=torch.float64, device="cuda")
+                rc.integrate(ur, 0.0, 0.0, 4 * w.m)
+                rc.synchronize()
+                ref = ur.cpu().numpy()
+                rc.close()
+                acc = {"reference": "FP64 GPU path at tau/4"}
+            else:
+                ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, w.m, w.scheme)
+                acc = {"reference": "FP64 oracle"}
+            acc.update({"rel_l2": O.rel_l2(got, ref), "rel_inf": O.rel_inf(got, ref)})
+        launches = ctx.kernels_per_step() * w.m * args.steps
+        ctx.close()
+    value = N * w.m * args.steps / (ms * 1e-3)
+    per_step_us = 1e3 * ms / (args.steps * w.m)
+    n = w.dims[0]
+    if prec == "bf16x3":
+        c_ms = statistics.mean(kinds.get(4, [float("nan")]))
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = json.load(f)["bf16_tflops_sustained"] / 6.0
+        ach = 2.0 * n * N / (c_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": "tma_contract_kernel standard pass", "launch_ms": c_ms,
+                "peak_source": "measured bf16 sustained / 6 products"}
+    else:
+        c_ms = statistics.mean(kinds.get(3, [float("nan")]))
+        ach = 2.0 * n * N / (c_ms * 1e-3) / 1e12
+        peak = FP64_NOMINAL_TFLOPS if prec == "fp64" else SMS * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": "contract_kernel (SIMT mu-mode pass)", "launch_ms": c_ms,
+                "peak_source": "nominal FP64 (not measured on this pool)" if prec == "fp64"
+                else "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    line = dict(base, value=value, ms_per_step=ms / args.steps, us_per_time_step=per_step_us,
+                e2e={"value": N * w.m * e2e_n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * dt.itemsize,
+                     "d2h_bytes_per_step": N * dt.itemsize},
+                gpu_launches=launches, roofline=roof, cpu_baseline=None, clocks=sampler.summary(),
+                kernel_ms_per_time_step={str(k): sum(v) / 3.0 for k, v in kinds.items()})
+    line.update(acc)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- batched 2-D
 BATCH_METRIC = "DOF*steps/s, 512 batched 2-D ETD2RK instances (FP32, tol 1e-5 vs FP64 oracle)"
 FP32_LANES_PER_SM = 128        # FP32 FMA lanes per SM (4 SMSPs x 32)
@@ -553,6 +679,12 @@ def main():
     args = parse()
     if args.workload == "batch2d":
         return reference_batch(args) if args.impl == "reference" else ours_batch(args)
+    if args.workload in GRID_WORKLOADS:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm is timed on the "
+                              "default 3d and batch2d workloads"}), flush=True)
+            return 0
+        return ours_grid(args)
     if args.impl == "reference":
         return reference_arm(args)
     if args.ncu_steps > 0:

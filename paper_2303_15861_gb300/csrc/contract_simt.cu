@@ -104,14 +104,43 @@ cudaError_t launch_tiled(const ContractArgs<T>& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+int g_sms = 0;
+
+// Output tiles of a bm x bn tiling of the pass.
+template <typename T>
+long long ctas(const ContractArgs<T>& p, int bm, int bn) {
+    return (long long)((p.N + bn - 1) / bn) * ((p.M + bm - 1) / bm) * p.batch;
+}
+
+int sm_count() {
+    if (g_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sms <= 0) g_sms = 1;
+    }
+    return g_sms;
+}
+
 }  // namespace
 
+// The largest tile that still gives every SM work: a small grid in one big tile would run on
+// one SM (and mostly on padding), which the FP64 pipes of this GPU make very slow. Every
+// output accumulates its K products in the same order for every tile shape.
 cudaError_t launch_contract(const ContractArgs<double>& p, cudaStream_t s) {
-    return launch_tiled<double, 64, 64, 16, 4, 4>(p, s);
+    const long long want = 2LL * sm_count();
+    if (ctas(p, 64, 64) >= want) return launch_tiled<double, 64, 64, 16, 4, 4>(p, s);
+    if (ctas(p, 32, 32) >= want) return launch_tiled<double, 32, 32, 16, 2, 2>(p, s);
+    if (ctas(p, 16, 16) >= want / 2) return launch_tiled<double, 16, 16, 16, 1, 1>(p, s);
+    return launch_tiled<double, 8, 8, 16, 1, 1>(p, s);
 }
 
 cudaError_t launch_contract(const ContractArgs<float>& p, cudaStream_t s) {
-    return launch_tiled<float, 128, 128, 8, 8, 8>(p, s);
+    const long long want = 2LL * sm_count();
+    if (ctas(p, 128, 128) >= want) return launch_tiled<float, 128, 128, 8, 8, 8>(p, s);
+    if (ctas(p, 64, 64) >= want) return launch_tiled<float, 64, 64, 16, 4, 4>(p, s);
+    if (ctas(p, 32, 32) >= want) return launch_tiled<float, 32, 32, 16, 2, 2>(p, s);
+    return launch_tiled<float, 16, 16, 16, 1, 1>(p, s);
 }
 
 }  // namespace adr
