@@ -68,7 +68,14 @@ typedef enum {
 typedef enum {
     ADR_LAWSON_EULER = 0,  /* u+ = e^{tau A}(u + tau g(u))                 (Appendix)     */
     ADR_ETD2RK = 1,        /* exponential RK2 with phi_2, c2 = 1           (Appendix)     */
-    ADR_LAWSON4 = 2        /* Lawson's construction on classical RK4 (Section 1)          */
+    ADR_LAWSON4 = 2,       /* Lawson's construction on classical RK4 (Section 1)          */
+    ADR_EXPONENTIAL_EULER = 3,        /* u+ = u + tau phi_1(tau A) F(u)    (Appendix)     */
+    ADR_ERK2P1 = 4,                   /* exponential RK2, phi_1 only, c2 = 1 (Appendix)   */
+    ADR_STABILIZED_LAWSON_EULER = 5,  /* u+ = u + tau e^{tau A} F(u)       (Appendix)     */
+    ADR_LAWSON2A = 6,                 /* second-order Lawson, midpoint form (Appendix)    */
+    ADR_LAWSON2B = 7,                 /* second-order Lawson, trapezoidal form (Appendix) */
+    ADR_STABILIZED_LAWSON2 = 8        /* stabilized second-order Lawson, alpha = 0.327
+                                         (Appendix)                                       */
 } adr_scheme;
 
 typedef struct {
@@ -81,7 +88,8 @@ typedef struct {
     int precision;         /* adr_precision                                              */
     double kappa_tol;      /* eigen route guard: fail with ADR_ERR_ILL_CONDITIONED when
                               prod_mu kappa(V_mu) * unit roundoff > kappa_tol; <= 0 selects
-                              1e-2. Only schemes that need phi_k (ADR_ETD2RK) check it.  */
+                              1e-2. Only schemes that need phi_k (ADR_ETD2RK,
+                              ADR_EXPONENTIAL_EULER, ADR_ERK2P1) check it.               */
     int batch;             /* 0: one grid (dim, n). > 0: that many independent 2-D
                               instances of uneven size in one context (dim must be 2;
                               ADR_FP64 or ADR_FP32)                                       */

@@ -21,7 +21,8 @@ STATUS = {0: "ADR_OK", 1: "ADR_ERR_ARG", 2: "ADR_ERR_ALLOC", 3: "ADR_ERR_CUDA",
           4: "ADR_ERR_ILL_CONDITIONED", 5: "ADR_ERR_COMPLEX_SPECTRUM", 6: "ADR_ERR_TIMEOUT",
           7: "ADR_ERR_STATE", 8: "ADR_ERR_UNSUPPORTED"}
 PRECISION = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x3": 3}
-SCHEME = {"lawson_euler": 0, "etd2rk": 1, "lawson4": 2}
+SCHEME = {"lawson_euler": 0, "etd2rk": 1, "lawson4": 2, "exponential_euler": 3, "erk2p1": 4,
+          "stabilized_lawson_euler": 5, "lawson2a": 6, "lawson2b": 7, "stabilized_lawson2": 8}
 
 
 class AdrError(RuntimeError):

@@ -56,10 +56,10 @@ struct adr_batch_state {
     int tile_force = -1;                   // BatchTile forced by batch_tile, -1: autotune
     std::vector<int> n1, n2, apitch;
     std::vector<long long> off, row0, a_off;
-    std::vector<long long> f_off;          // [i][role][dir] -> 8 per instance, -1 if absent
+    std::vector<long long> f_off;          // [i][role][dir] -> 2 * kBatchRoles per instance, -1 if absent
     std::vector<long long> zt_off;         // [i][dir] -> 2 per instance, -1 if absent
     long long rows = 0, a_len = 0, f_len = 0, zt_len = 0;
-    bool roles[4] = {false, false, false, false};
+    bool roles[adr::kBatchRoles] = {false, false, false, false, false};
     std::vector<char> set;
     int nset = 0;
     std::vector<double> hA, hF, hZt;       // FP64 staging, packed like the device copies
@@ -99,7 +99,7 @@ struct adr_ctx {
 
     // device memory (library-owned)
     void* d_a = nullptr;                   // nodal (a - abar)
-    void* d_E[2][3] = {{nullptr}};         // e^{c tau A_mu}, c = 0.5 (0) and 1 (1)
+    void* d_E[3][3] = {{nullptr}};         // e^{c tau A_mu}, c = 0.5 (0), 1 (1), alpha (2)
     void* d_V[3] = {nullptr};
     void* d_Vi[3] = {nullptr};
     double* d_lam[3] = {nullptr};
@@ -108,10 +108,10 @@ struct adr_ctx {
 
     // mixed precision (tensor cores): sliced factor images, per-row scales, c tau lambda
     bool tc = false;
-    uint8_t* d_img[5][3] = {{nullptr}};    // 0: E(0.5), 1: E(1), 2: V, 3: V^-1, 4: E(0.5) precise
-    float* d_fsc[5][3] = {{nullptr}};
-    uint8_t* d_img2[5][3] = {{nullptr}};   // the same for the TMA-fed kernel (K chunks of 32)
-    float* d_fsc2[5][3] = {{nullptr}};
+    uint8_t* d_img[6][3] = {{nullptr}};    // 0: E(0.5), 1: E(1), 2: V, 3: V^-1, 4: E(0.5) precise, 5: E(alpha)
+    float* d_fsc[6][3] = {{nullptr}};
+    uint8_t* d_img2[6][3] = {{nullptr}};   // the same for the TMA-fed kernel (K chunks of 32)
+    float* d_fsc2[6][3] = {{nullptr}};
     float* d_zt[3] = {nullptr};            // tau * lambda_mu[j] (FP32)
     unsigned* d_slots = nullptr;           // max-abs slots of the arrays a step produces
     int* d_err = nullptr;                  // device error word (bounded waits)
@@ -248,7 +248,7 @@ ContractArgs<T> mode_args(const adr_ctx* c, int mu, const T* M, const T* X, T* Y
     return a;
 }
 
-enum FactorKind { FK_EXP_HALF = 0, FK_EXP_ONE = 1, FK_V = 2, FK_VINV = 3, FK_EXP_HALF_PRECISE = 4 };
+enum FactorKind { FK_EXP_HALF = 0, FK_EXP_ONE = 1, FK_V = 2, FK_VINV = 3, FK_EXP_HALF_PRECISE = 4, FK_EXP_ALPHA = 5 };
 static_assert(int(FK_EXP_HALF) == adr::BR_EXP_HALF && int(FK_EXP_ONE) == adr::BR_EXP_ONE && int(FK_V) == adr::BR_V &&
                   int(FK_VINV) == adr::BR_VINV,
               "factor kinds and batch roles share their numbering");
@@ -265,7 +265,7 @@ void push_mode_batch(Sched& S, int mu, int kind, const T* x, T* y, int epi, cons
     a.items = b.d_items[mu - 1];
     a.nitems = b.nitems[mu - 1];
     a.mode = mu;
-    a.role = kind;
+    a.role = kind == FK_EXP_ALPHA ? adr::BR_EXP_ALPHA : kind;
     a.factors = static_cast<const T*>(b.d_f);
     a.zt = static_cast<const T*>(b.d_zt);
     a.X = x;
@@ -317,6 +317,7 @@ void push_mode(Sched& S, int mu, int kind, const T* x, T* y, int epi = adr::EPI_
     }
     if (!c->tc) {
         const void* M = kind == FK_EXP_HALF ? c->d_E[0][mu - 1] : kind == FK_EXP_ONE ? c->d_E[1][mu - 1]
+                      : kind == FK_EXP_ALPHA ? c->d_E[2][mu - 1]
                       : kind == FK_V ? c->d_V[mu - 1] : c->d_Vi[mu - 1];
         auto a = mode_args<T>(c, mu, static_cast<const T*>(M), x, y);
         a.epi = epi; a.base = base; a.alpha = alpha; a.phik = phik; a.ctau = c->p.tau;
@@ -534,6 +535,74 @@ std::vector<Op> build_step(const adr_ctx* c, T* u) {
         push_stencil(S, s4);
         break;
     }
+    case ADR_EXPONENTIAL_EULER: {
+        auto s = stencil_base<T>(c, u);
+        s.nout = 1; s.out[0] = B0; s.cF[0] = 1.0;                       // F(u)
+        push_stencil(S, s);
+        push_phi<T>(S, 1, B0, u, u, tau);                                // u = u + tau phi1 F
+        break;
+    }
+    case ADR_ERK2P1: {
+        auto s1 = stencil_base<T>(c, u);
+        s1.nout = 2; s1.out[0] = B0; s1.cF[0] = 1.0;                    // F(u)
+        s1.out[1] = B1; s1.cg[1] = 1.0;                                 // G0 = g(u)
+        push_stencil(S, s1);
+        push_phi<T>(S, 1, B0, B2, u, tau);                               // U = u + tau phi1 F
+        auto s2 = stencil_base<T>(c, B2);
+        s2.nx = 1; s2.X[0] = B1;
+        s2.nout = 1; s2.out[0] = B0; s2.cg[0] = 1.0; s2.cx[0][0] = -1.0; // D = g(U) - G0
+        push_stencil(S, s2);
+        push_phi<T>(S, 1, B0, u, B2, 0.5 * tau);                         // u = U + tau/2 phi1 D
+        break;
+    }
+    case ADR_STABILIZED_LAWSON_EULER: {
+        auto s = stencil_base<T>(c, u);
+        s.nout = 1; s.out[0] = B0; s.cF[0] = 1.0;                       // F(u)
+        push_stencil(S, s);
+        push_exp<T>(S, FK_EXP_ONE, B0, u, u, tau);                       // u = u + tau e^{tau A} F
+        break;
+    }
+    case ADR_LAWSON2A: {
+        auto s1 = stencil_base<T>(c, u);
+        s1.nout = 1; s1.out[0] = B0; s1.cu[0] = 1.0; s1.cg[0] = 0.5 * tau; // u + tau/2 g(u)
+        push_stencil(S, s1);
+        push_exp<T>(S, FK_EXP_HALF, B0, B1);                             // U = e^{tau A/2}(...)
+        push_exp<T>(S, FK_EXP_ONE, u, B2);                               // e^{tau A} u
+        auto s2 = stencil_base<T>(c, B1);
+        s2.nout = 1; s2.out[0] = B0; s2.cg[0] = 1.0;                     // g(U)
+        push_stencil(S, s2);
+        push_exp<T>(S, FK_EXP_HALF, B0, u, B2, tau);                     // u = e^{tau A} u + tau e^{tau A/2} g(U)
+        break;
+    }
+    case ADR_LAWSON2B: {
+        auto s1 = stencil_base<T>(c, u);
+        s1.nout = 2;
+        s1.out[0] = B0; s1.cu[0] = 1.0; s1.cg[0] = tau;                  // u + tau g(u)
+        s1.out[1] = B1; s1.cu[1] = 1.0; s1.cg[1] = 0.5 * tau;            // u + tau/2 g(u)
+        push_stencil(S, s1);
+        push_exp<T>(S, FK_EXP_ONE, B0, B2);                              // U = e^{tau A}(u + tau g(u))
+        push_exp<T>(S, FK_EXP_ONE, B1, B3);                              // e^{tau A}(u + tau/2 g(u))
+        auto s2 = stencil_base<T>(c, B2);
+        s2.nx = 1; s2.X[0] = B3;
+        s2.nout = 1; s2.out[0] = u; s2.cx[0][0] = 1.0; s2.cg[0] = 0.5 * tau; // u = ... + tau/2 g(U)
+        push_stencil(S, s2);
+        break;
+    }
+    case ADR_STABILIZED_LAWSON2: {
+        const double al = adr::kLawsonAlpha;
+        auto s1 = stencil_base<T>(c, u);
+        s1.nout = 2; s1.out[0] = B0; s1.cF[0] = 1.0;                    // F(u)
+        s1.out[1] = B1; s1.cg[1] = 1.0;                                 // G0 = g(u)
+        push_stencil(S, s1);
+        push_exp<T>(S, FK_EXP_ALPHA, B0, B2, u, al * tau);               // U = u + alpha tau e^{alpha tau A} F
+        push_exp<T>(S, FK_EXP_HALF, B0, B3, u, tau);                     // u + tau e^{tau A/2} F
+        auto s2 = stencil_base<T>(c, B2);
+        s2.nx = 1; s2.X[0] = B1;
+        s2.nout = 1; s2.out[0] = B0; s2.cg[0] = 1.0; s2.cx[0][0] = -1.0; // D = g(U) - G0
+        push_stencil(S, s2);
+        push_exp<T>(S, FK_EXP_ONE, B0, u, B3, tau / (2.0 * al));         // u = ... + tau/(2 alpha) e^{tau A} D
+        break;
+    }
     default:
         break;
     }
@@ -552,7 +621,9 @@ adr_status run_ops(adr_ctx* c, const std::vector<Op>& ops, const char* where) {
     return ADR_OK;
 }
 
-bool needs_phi(int scheme) { return scheme == ADR_ETD2RK; }
+bool needs_phi(int scheme) {
+    return scheme == ADR_ETD2RK || scheme == ADR_EXPONENTIAL_EULER || scheme == ADR_ERK2P1;
+}
 
 adr_status check_ready(adr_ctx* c) {
     if (!c) return ADR_ERR_ARG;
@@ -609,9 +680,9 @@ cudaError_t upload_instances(const adr_ctx* c) {
         bool vec = (b.n1[i] % 4 == 0) && (b.n2[i] % 4 == 0) && (b.off[i] % 4 == 0);
         d.abar = T(k[8]);
         for (int j = 0; j < 4; ++j) d.r[j] = T(k[9 + j]);
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < adr::kBatchRoles; ++r)
             for (int m = 0; m < 2; ++m) {
-                d.f_off[r][m] = b.f_off[size_t(i) * 8 + r * 2 + m];
+                d.f_off[r][m] = b.f_off[size_t(i) * 2 * adr::kBatchRoles + r * 2 + m];
                 if (d.f_off[r][m] >= 0 && d.f_off[r][m] % 4 != 0) vec = false;
             }
         d.vec = vec ? 1 : 0;
@@ -632,9 +703,9 @@ cudaError_t batch_upload(adr_ctx* c, int i) {
         return e;
     }
     e = upload_range(c, b.d_a, b.hA, b.a_off[i], (long long)b.apitch[i] * (b.n2[i] + 2));
-    for (int r = 0; r < 4 && e == cudaSuccess; ++r)
+    for (int r = 0; r < adr::kBatchRoles && e == cudaSuccess; ++r)
         for (int m = 0; m < 2 && e == cudaSuccess; ++m) {
-            const long long o = b.f_off[size_t(i) * 8 + r * 2 + m];
+            const long long o = b.f_off[size_t(i) * 2 * adr::kBatchRoles + r * 2 + m];
             const long long nm = m == 0 ? b.n1[i] : b.n2[i];
             if (o >= 0) e = upload_range(c, b.d_f, b.hF, o, nm * nm);
         }
@@ -672,7 +743,7 @@ adr_status batch_tune(adr_ctx* c) {
         else it->second.push_back(i);
     }
     int role = 0;
-    while (role < 4 && !b.roles[role]) ++role;
+    while (role < adr::kBatchRoles && !b.roles[role]) ++role;
     long long max_items = 0;
     for (int i = 0; i < b.B; ++i) max_items += (long long)((b.n1[i] + 31) / 32) * ((b.n2[i] + 31) / 32);
     int4* d_tmp = nullptr;
@@ -793,7 +864,7 @@ adr_status create_batch(const adr_params* p, void* cuda_stream, adr_ctx** out) {
     if (!p->n_batch) return fail(nullptr, ADR_ERR_ARG, "n_batch is NULL");
     if (p->batch > (1 << 20)) return fail(nullptr, ADR_ERR_ARG, "batch must be <= 2^20");
     if (!(p->tau > 0.0) || !std::isfinite(p->tau)) return fail(nullptr, ADR_ERR_ARG, "tau must be positive");
-    if (p->scheme < ADR_LAWSON_EULER || p->scheme > ADR_LAWSON4) return fail(nullptr, ADR_ERR_ARG, "unknown scheme");
+    if (p->scheme < ADR_LAWSON_EULER || p->scheme > ADR_STABILIZED_LAWSON2) return fail(nullptr, ADR_ERR_ARG, "unknown scheme");
     if (p->precision == ADR_MIXED_BF16X3 || p->precision == ADR_MIXED_TF32X3)
         return fail(nullptr, ADR_ERR_UNSUPPORTED,
                     "batched contexts run in ADR_FP64 or ADR_FP32 (the fixed-point slices of the mixed "
@@ -809,12 +880,20 @@ adr_status create_batch(const adr_params* p, void* cuda_stream, adr_ctx** out) {
     adr_batch_state& b = *bs;
     b.B = p->batch;
     b.tile_force = force;
-    if (p->scheme == ADR_LAWSON_EULER) b.roles[adr::BR_EXP_ONE] = true;
-    if (p->scheme == ADR_LAWSON4) b.roles[adr::BR_EXP_HALF] = true;
-    if (p->scheme == ADR_ETD2RK) b.roles[adr::BR_V] = b.roles[adr::BR_VINV] = true;
+    switch (p->scheme) {
+    case ADR_LAWSON_EULER:
+    case ADR_STABILIZED_LAWSON_EULER:
+    case ADR_LAWSON2B: b.roles[adr::BR_EXP_ONE] = true; break;
+    case ADR_LAWSON4: b.roles[adr::BR_EXP_HALF] = true; break;
+    case ADR_LAWSON2A: b.roles[adr::BR_EXP_HALF] = b.roles[adr::BR_EXP_ONE] = true; break;
+    case ADR_STABILIZED_LAWSON2:
+        b.roles[adr::BR_EXP_HALF] = b.roles[adr::BR_EXP_ONE] = b.roles[adr::BR_EXP_ALPHA] = true;
+        break;
+    default: b.roles[adr::BR_V] = b.roles[adr::BR_VINV] = true; break;   // the phi_k schemes
+    }
     b.n1.resize(b.B); b.n2.resize(b.B); b.apitch.resize(b.B);
     b.off.resize(b.B); b.row0.resize(b.B); b.a_off.resize(b.B);
-    b.f_off.assign(size_t(b.B) * 8, -1);
+    b.f_off.assign(size_t(b.B) * 2 * adr::kBatchRoles, -1);
     b.zt_off.assign(size_t(b.B) * 2, -1);
     long long N = 0;
     for (int i = 0; i < b.B; ++i) {
@@ -826,11 +905,11 @@ adr_status create_batch(const adr_params* p, void* cuda_stream, adr_ctx** out) {
         b.row0[i] = b.rows; b.rows += n2;
         b.apitch[i] = ((n1 + 5) + 3) / 4 * 4;
         b.a_off[i] = b.a_len; b.a_len += (long long)b.apitch[i] * (n2 + 2);
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < adr::kBatchRoles; ++r)
             for (int m = 0; m < 2; ++m) {
                 if (!b.roles[r]) continue;
                 const long long nm = m == 0 ? n1 : n2;
-                b.f_off[size_t(i) * 8 + r * 2 + m] = b.f_len;
+                b.f_off[size_t(i) * 2 * adr::kBatchRoles + r * 2 + m] = b.f_len;
                 b.f_len += nm * nm;
             }
         if (b.roles[adr::BR_V])
@@ -918,18 +997,18 @@ adr_status batch_set_coeffs(adr_ctx* c, int i, const double* a_nodes, const doub
     for (int m = 0; m < 2; ++m) {
         const adr::Factor1D f = adr::make_factor(n[m], abar, beta[m]);
         const long long nm = n[m];
-        for (int ci = 0; ci < 2; ++ci) {
-            const int role = ci == 0 ? adr::BR_EXP_HALF : adr::BR_EXP_ONE;
+        for (int ci = 0; ci < 3; ++ci) {
+            const int role = ci == 0 ? adr::BR_EXP_HALF : ci == 1 ? adr::BR_EXP_ONE : adr::BR_EXP_ALPHA;
             if (!b.roles[role]) continue;
             std::vector<double> sA = adr::factor_dense(f);
-            for (auto& v : sA) v *= (ci == 0 ? 0.5 : 1.0) * c->p.tau;
+            for (auto& v : sA) v *= (ci == 0 ? 0.5 : ci == 1 ? 1.0 : adr::kLawsonAlpha) * c->p.tau;
             std::vector<double> E;
             try {
                 E = adr::expm_pade13(sA, n[m]);
             } catch (const std::exception& ex) {
                 return fail(c, ADR_ERR_ARG, std::string("expm: ") + ex.what());
             }
-            std::copy(E.begin(), E.end(), b.hF.begin() + b.f_off[size_t(i) * 8 + role * 2 + m]);
+            std::copy(E.begin(), E.end(), b.hF.begin() + b.f_off[size_t(i) * 2 * adr::kBatchRoles + role * 2 + m]);
         }
         if (b.roles[adr::BR_V]) {
             const adr::Eigen1D eg = adr::eigen_closed_form(f);
@@ -939,8 +1018,8 @@ adr_status batch_set_coeffs(adr_ctx* c, int i, const double* a_nodes, const doub
                 return fail(c, ADR_ERR_COMPLEX_SPECTRUM, buf);
             }
             b.kappa[size_t(i) * 2 + m] = eg.kappa;
-            std::copy(eg.V.begin(), eg.V.end(), b.hF.begin() + b.f_off[size_t(i) * 8 + adr::BR_V * 2 + m]);
-            std::copy(eg.Vinv.begin(), eg.Vinv.end(), b.hF.begin() + b.f_off[size_t(i) * 8 + adr::BR_VINV * 2 + m]);
+            std::copy(eg.V.begin(), eg.V.end(), b.hF.begin() + b.f_off[size_t(i) * 2 * adr::kBatchRoles + adr::BR_V * 2 + m]);
+            std::copy(eg.Vinv.begin(), eg.Vinv.end(), b.hF.begin() + b.f_off[size_t(i) * 2 * adr::kBatchRoles + adr::BR_VINV * 2 + m]);
             for (long long j = 0; j < nm; ++j) b.hZt[size_t(b.zt_off[size_t(i) * 2 + m] + j)] = c->p.tau * eg.lam[size_t(j)];
         }
     }
@@ -981,7 +1060,7 @@ adr_status adr_create(const adr_params* p, void* cuda_stream, adr_ctx** out) {
     for (int m = 0; m < p->dim; ++m)
         if (p->n[m] < 2 || p->n[m] > 4096) return fail(nullptr, ADR_ERR_ARG, "n must be in [2, 4096]");
     if (!(p->tau > 0.0) || !std::isfinite(p->tau)) return fail(nullptr, ADR_ERR_ARG, "tau must be positive");
-    if (p->scheme < ADR_LAWSON_EULER || p->scheme > ADR_LAWSON4) return fail(nullptr, ADR_ERR_ARG, "unknown scheme");
+    if (p->scheme < ADR_LAWSON_EULER || p->scheme > ADR_STABILIZED_LAWSON2) return fail(nullptr, ADR_ERR_ARG, "unknown scheme");
     if (p->precision == ADR_MIXED_TF32X3)
         return fail(nullptr, ADR_ERR_UNSUPPORTED, "ADR_MIXED_TF32X3 is not implemented");
     if (p->precision != ADR_FP64 && p->precision != ADR_FP32 && p->precision != ADR_MIXED_BF16X3)
@@ -1059,12 +1138,13 @@ adr_status adr_set_coeffs(adr_ctx* c, int instance, const double* a_nodes, const
     c->eig_real = true;
     struct CachedE { int n; double beta, c; std::vector<double> E; };
     std::vector<CachedE> cache;
-    cache.reserve(6);
+    cache.reserve(9);
     for (int m = 0; m < c->dim; ++m) {
         c->f[m] = adr::make_factor(c->n[m], c->abar, c->beta[m]);
         const auto A = adr::factor_dense(c->f[m]);
-        for (int ci = 0; ci < 2; ++ci) {
-            const double cc = ci == 0 ? 0.5 : 1.0;
+        for (int ci = 0; ci < 3; ++ci) {
+            if (ci == 2 && c->p.scheme != ADR_STABILIZED_LAWSON2) continue;   // e^{alpha tau A_mu}
+            const double cc = ci == 0 ? 0.5 : ci == 1 ? 1.0 : adr::kLawsonAlpha;
             // directions with the same (n, beta) share one host computation of e^{c tau A_mu}
             const std::vector<double>* E = nullptr;
             for (const auto& hit : cache)
@@ -1082,8 +1162,8 @@ adr_status adr_set_coeffs(adr_ctx* c, int instance, const double* a_nodes, const
             e = upload(c, &c->d_E[ci][m], *E);
             if (e != cudaSuccess) return cuda_fail(c, e, "upload E");
             if (c->tc) {
-                e = upload_tc(c, ci, m, *E);
-                if (e == cudaSuccess && ci == 0) e = upload_tc(c, 4, m, *E);   // precise E(0.5)
+                e = upload_tc(c, ci == 2 ? FK_EXP_ALPHA : ci, m, *E);
+                if (e == cudaSuccess && ci == 0) e = upload_tc(c, FK_EXP_HALF_PRECISE, m, *E);
                 if (e != cudaSuccess) return cuda_fail(c, e, "upload sliced E");
             }
         }
@@ -1326,6 +1406,12 @@ int adr_kernels_per_step(const adr_ctx* c) {
     case ADR_LAWSON_EULER: return 1 + d;
     case ADR_ETD2RK: return 2 + 4 * d;
     case ADR_LAWSON4: return 4 + 4 * d;
+    case ADR_EXPONENTIAL_EULER: return 1 + 2 * d;
+    case ADR_ERK2P1: return 2 + 4 * d;
+    case ADR_STABILIZED_LAWSON_EULER: return 1 + d;
+    case ADR_LAWSON2A: return 2 + 3 * d;
+    case ADR_LAWSON2B: return 2 + 2 * d;
+    case ADR_STABILIZED_LAWSON2: return 2 + 3 * d;
     default: return -1;
     }
 }

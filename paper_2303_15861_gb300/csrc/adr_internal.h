@@ -171,13 +171,16 @@ struct BatchInst {
     int apitch = 0;
     T ih2[2] = {0, 0}, i2h[2] = {0, 0}, bmb[2] = {0, 0}, beta[2] = {0, 0};
     T abar = 0, r[4] = {0, 0, 0, 0};
-    long long f_off[4][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};  // factor role x direction
+    long long f_off[5][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};  // factor role x direction
     long long zt_off[2] = {-1, -1};                                    // tau * eigenvalues per direction
     int vec = 0;                   // n1, n2, off and factor offsets multiples of 4 (16-byte rows)
 };
 
 // Factor roles of a batched context (the same numbering as the single-grid factor kinds).
-enum BatchRole { BR_EXP_HALF = 0, BR_EXP_ONE = 1, BR_V = 2, BR_VINV = 3 };
+enum BatchRole { BR_EXP_HALF = 0, BR_EXP_ONE = 1, BR_V = 2, BR_VINV = 3, BR_EXP_ALPHA = 4 };
+constexpr int kBatchRoles = 5;
+// alpha of the stabilized second-order Lawson scheme (Appendix)
+constexpr double kLawsonAlpha = 0.327;
 
 // One stencil stage over all instances: packed arrays, per-instance coefficients from
 // `inst`, the stage combination (cu, cx, cg, cF) shared by all instances. Work unit: one

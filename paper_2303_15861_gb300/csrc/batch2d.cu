@@ -369,7 +369,7 @@ template <typename T>
 cudaError_t contract_launch(const BatchContractArgs<T>& p, cudaStream_t s) {
     if (p.nitems <= 0) return cudaSuccess;
     if (!p.inst || !p.items || !p.factors || !p.X || !p.Y || (p.mode != 1 && p.mode != 2)) return cudaErrorInvalidValue;
-    if (p.role < 0 || p.role > BR_VINV) return cudaErrorInvalidValue;
+    if (p.role < 0 || p.role >= kBatchRoles) return cudaErrorInvalidValue;
     if (p.epi == EPI_PHI && (!p.zt || p.mode != 2)) return cudaErrorInvalidValue;
     if (p.epi == EPI_AXPY && !p.base) return cudaErrorInvalidValue;
     long long grid = p.grid > 0 ? p.grid : 2LL * sm_count();

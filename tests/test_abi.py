@@ -55,7 +55,7 @@ def _params(**kw):
     (dict(n=(1, 8, 8)), 1),
     (dict(tau=0.0), 1),
     (dict(tau=-1.0), 1),
-    (dict(scheme=7), 1),
+    (dict(scheme=42), 1),
     (dict(precision=9), 1),
     (dict(precision=2), 8),
 ])

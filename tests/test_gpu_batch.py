@@ -61,7 +61,8 @@ def check_guards(full):
     assert torch.isnan(g).all(), "write outside the packed array"
 
 
-@pytest.mark.parametrize("scheme", ["lawson_euler", "etd2rk", "lawson4"])
+@pytest.mark.parametrize("scheme", ["lawson_euler", "etd2rk", "lawson4", "exponential_euler", "erk2p1",
+                                    "stabilized_lawson_euler", "lawson2a", "lawson2b", "stabilized_lawson2"])
 def test_batch_fp64_schemes_match_oracle(scheme):
     ws = W.batch_instances(SIZES, scheme=scheme)
     m = 4

@@ -130,6 +130,15 @@ INTEGRATE = [
     ((128, 128), (10.0, 10.0), "lawson4", 0.1, 40, 2e-6),
     ((64, 64), (10.0, 10.0), "etd2rk", 0.1, 30, 1e-5),
     ((32, 32, 32), (10.0, 10.0, 10.0), "etd2rk", 0.04, 8, 3e-5),
+    # the paper's other schemes (Appendix): exp-only ones as Lawson, phi ones as ETD2RK
+    ((64, 64, 64), (10.0, 10.0, 10.0), "stabilized_lawson_euler", 0.05, 20, 2e-6),
+    ((64, 64, 64), (10.0, 10.0, 10.0), "lawson2a", 0.05, 20, 2e-6),
+    # these two end with an unsmoothed stencil term (tau/2 g(U), tau/(2 alpha) e^{tau A} of
+    # g(U) - g(u)), like Lawson4's last stage; plain FP32 itself is at 2.0e-6 / 2.8e-6 here
+    ((64, 64, 64), (10.0, 10.0, 10.0), "lawson2b", 0.05, 20, 5e-6),
+    ((64, 64, 64), (10.0, 10.0, 10.0), "stabilized_lawson2", 0.05, 20, 5e-6),
+    ((64, 64), (10.0, 10.0), "exponential_euler", 0.1, 30, 1e-5),
+    ((64, 64), (10.0, 10.0), "erk2p1", 0.1, 30, 1e-5),
 ]
 
 
@@ -151,7 +160,8 @@ def test_integrate_matches_oracle(dims, b, scheme, T, m, tol):
     torch.cuda.synchronize()
     err32 = O.rel_l2(v.cpu().numpy(), ref)
     assert err < tol, (err, err32)
-    if scheme != "etd2rk":
+    print(f"{scheme} {dims}: mixed {err:.3e}, plain FP32 {err32:.3e}")
+    if scheme not in ("etd2rk", "exponential_euler", "erk2p1"):
         assert err < 2.5 * err32 + 2e-7, (err, err32)
 
 

@@ -129,6 +129,11 @@ INTEGRATE = [
     ((24, 24, 24), (10.0, 10.0, 10.0), "lawson4", 0.04, 8),
     ((19, 26, 33), (3.0, -5.0, 8.0), "lawson_euler", 0.04, 8),
     ((19, 26, 33), (3.0, -5.0, 8.0), "lawson4", 0.04, 8),
+] + [
+    # the paper's other schemes (Appendix) on the same kernels
+    case for scheme in ("exponential_euler", "erk2p1", "stabilized_lawson_euler", "lawson2a", "lawson2b",
+                        "stabilized_lawson2")
+    for case in (((37, 29), (6.0, -9.0), scheme, 0.05, 10), ((19, 26, 33), (3.0, -5.0, 8.0), scheme, 0.04, 8))
 ]
 
 
