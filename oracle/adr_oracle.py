@@ -269,6 +269,23 @@ class MatrixFunctions:
             self._eig = res
         return self._eig
 
+    def phi_action_dense(self, k, c, v):
+        """phi_k(c tau A) v for any conditioning of the eigenbasis (small grids only): the
+        exponential of the augmented matrix Z = [[c tau A, v, 0], [0, 0, 1], [0, 0, 0]] holds
+        e^{c tau A} v, phi_1(c tau A) v and phi_2(c tau A) v in its last columns, with A the
+        full Kronecker sum A_d (+) ... (+) A_1 (Section 5.2), formed densely."""
+        A = kron_sum_dense([self.p.factor(mu) for mu in range(1, self.p.d + 1)])
+        N = v.size
+        Z = np.zeros((N + 2, N + 2))
+        Z[:N, :N] = c * self.tau * A
+        Z[:N, N] = np.ravel(v)
+        Z[N, N + 1] = 1.0
+        big = expm(Z)
+        col = {0: None, 1: N, 2: N + 1}[k]
+        if col is None:
+            return (expm(c * self.tau * A) @ np.ravel(v)).reshape(v.shape)
+        return big[:N, col].reshape(v.shape)
+
     def phi_action(self, k, c, v):
         """phi_k(c tau A) v through the joint eigenbasis of the 1-D factors."""
         eig = self.eig()
@@ -287,12 +304,15 @@ class MatrixFunctions:
 
 
 class GridOps:
-    """The operations every integrator needs, for an ADR grid problem."""
+    """The operations every integrator needs, for an ADR grid problem. phi_route "eigen"
+    (the joint eigenbasis) or "dense" (the augmented-matrix exponential, small grids, any
+    conditioning of the eigenbasis)."""
 
-    def __init__(self, prob: ADRProblem, tau: float):
+    def __init__(self, prob: ADRProblem, tau: float, phi_route: str = "eigen"):
         self.prob = prob
         self.tau = float(tau)
         self.mf = MatrixFunctions(prob, tau)
+        self.phi_route = phi_route
 
     def g(self, u):
         return self.prob.g(u)
@@ -304,6 +324,8 @@ class GridOps:
         return self.mf.exp_action(c, v)
 
     def phi(self, k, c, v):
+        if self.phi_route == "dense":
+            return self.mf.phi_action_dense(k, c, v)
         return self.mf.phi_action(k, c, v)
 
 
@@ -429,10 +451,10 @@ def integrate(ops, u0, m, scheme):
     return u
 
 
-def solve(dims, a_nodes, b, r_poly, u0, tau, m, scheme, lam=1.0, abar=None):
+def solve(dims, a_nodes, b, r_poly, u0, tau, m, scheme, lam=1.0, abar=None, phi_route="eigen"):
     """Convenience: FP64 oracle solution after m steps of `scheme`."""
     prob = ADRProblem(dims, a_nodes, b, r_poly, lam=lam, abar=abar)
-    return integrate(GridOps(prob, tau), u0, m, scheme)
+    return integrate(GridOps(prob, tau, phi_route=phi_route), u0, m, scheme)
 
 
 # ----------------------------------------------------------------------------------

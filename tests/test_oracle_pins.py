@@ -140,6 +140,48 @@ def test_phi_action_matches_augmented_expm(dims, k):
     assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_dense_phi_route_matches_eigen_route_and_closed_forms(k):
+    """The dense route (augmented-matrix exponential of the full Kronecker sum) agrees with
+    the eigen route where that one is well conditioned, and with the scalar closed forms
+    of phi_k on a 1-point-per-direction grid (A is then the scalar sum of the diagonals)."""
+    dims = (5, 4, 3)
+    a = W.sine_product_coefficient(dims)
+    prob = O.ADRProblem(dims, a, (4.0, 2.0, -3.0), W.REACTION_U2_1MU)
+    tau = 4e-3
+    v = np.random.default_rng(9).standard_normal(tuple(dims[::-1]))
+    mf = O.MatrixFunctions(prob, tau)
+    eig = mf.exp_action(1.0, v) if k == 0 else mf.phi_action(k, 1.0, v)
+    dense = mf.phi_action_dense(k, 1.0, v)
+    assert np.linalg.norm(dense - eig) <= 1e-12 * np.linalg.norm(eig)
+    # scalar: one interior node per direction, A = sum of the three diagonal entries
+    one = O.ADRProblem((1, 1, 1), np.ones((3, 3, 3)), (0.0, 0.0, 0.0), W.REACTION_U2_1MU)
+    z = tau * sum(one.factor(mu)[0, 0] for mu in (1, 2, 3))
+    closed = {0: np.exp(z), 1: np.expm1(z) / z, 2: (np.expm1(z) - z) / z**2}[k]
+    got = O.MatrixFunctions(one, tau).phi_action_dense(k, 1.0, np.ones((1, 1, 1)))
+    assert abs(got.item() - closed) <= 1e-12 * abs(closed)
+
+
+def test_dense_phi_route_handles_an_ill_conditioned_eigenbasis():
+    """With strong advection (cell Peclet 0.8) the eigenvector matrices have condition
+    number ~1e13 per direction and the eigen route loses every digit; the dense route
+    still meets the defining identity A phi_1(A) v = (e^A - I) v."""
+    dims = (24, 20)
+    a = np.ones((22, 26))
+    prob = O.ADRProblem(dims, a, (52.0, -42.0), W.REACTION_U2_1MU)
+    tau = 2e-3
+    v = np.random.default_rng(3).standard_normal((20, 24))
+    mf = O.MatrixFunctions(prob, tau)
+    p1 = mf.phi_action_dense(1, 1.0, v)
+    A = O.kron_sum_dense([prob.factor(1), prob.factor(2)])
+    lhs = tau * (A @ p1.ravel())
+    rhs = mf.phi_action_dense(0, 1.0, v).ravel() - v.ravel()
+    assert np.linalg.norm(lhs - rhs) <= 1e-12 * np.linalg.norm(rhs)
+    p2 = mf.phi_action_dense(2, 1.0, v)
+    # phi_1(z) = 1 + z phi_2(z)
+    assert np.linalg.norm(p1.ravel() - v.ravel() - tau * (A @ p2.ravel())) <= 1e-12 * np.linalg.norm(p1)
+
+
 # ----------------------------------------------------------------------------- stencils
 def _polynomial_case(d):
     dims = (9, 8, 7)[:d]
