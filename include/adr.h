@@ -97,7 +97,23 @@ typedef struct {
                               [2i], [2i+1]; copied by adr_create                          */
     int batch_tile;        /* batch > 0: 0 = tile shapes and grid chosen by the autotuner;
                               32, 64 or 128 = that square tile for every instance          */
+    int phi_route;         /* adr_phi_route: how phi_k(tau A) is applied (single grids)     */
 } adr_params;
+
+/* Routes for phi_k(tau A) v.
+ *   ADR_PHI_EIGEN: mu-mode products with V_mu^-1, the pointwise phi_k(tau(l1+l2+l3)), V_mu
+ *     (closed-form eigenpairs). Needs a real spectrum and passes the kappa guard.
+ *   ADR_PHI_DOUBLING: exponentials only, for any conditioning of the eigenbasis. With
+ *     X = tau A / 2^s (s halvings so that ||X||_1 <= 1/2), a Taylor sum of phi_k(X) v through
+ *     the constant-coefficient stencil of A, then s doublings that follow from the phi
+ *     definitions, phi_1(2X) = (e^X + I) phi_1(X) / 2 and
+ *     phi_2(2X) = (phi_1(X) + (e^X + I) phi_2(X)) / 4, each applying e^{2^i X} by mu-mode
+ *     products with dense factors. Per phi_1 action: s exponential actions and 14 stencil
+ *     applications. Per phi_2 action: 2s exponential actions and s + 15 stencil applications.
+ *     Single-grid contexts only; batched contexts use the eigen route.
+ *   ADR_PHI_AUTO: the eigen route when it is available and passes the kappa guard, the
+ *     doubling route otherwise. */
+typedef enum { ADR_PHI_AUTO = 0, ADR_PHI_EIGEN = 1, ADR_PHI_DOUBLING = 2 } adr_phi_route;
 
 /* Create a context for one grid, or for a batch of independent 2-D instances.
  * cuda_stream is a cudaStream_t (NULL = legacy default stream) on the current device.
@@ -205,6 +221,11 @@ adr_status adr_mumode_apply_static(int dim, const int n[3], const double* const 
 
 /* Number of kernels one adr_step launches (for launch accounting). */
 int adr_kernels_per_step(const adr_ctx* ctx);
+
+/* The phi route a context uses after adr_set_coeffs (ADR_PHI_EIGEN or ADR_PHI_DOUBLING; 0
+ * when its scheme needs no phi_k or before adr_set_coeffs), and for the doubling route the
+ * number of halvings s and of Taylor terms in *halvings, *terms (either may be NULL). */
+int adr_phi_route_used(const adr_ctx* ctx, int* halvings, int* terms);
 
 /* Message of the last failed call on ctx (or of the last failed adr_create when ctx
  * is NULL). Valid until the next call on the same context. */

@@ -21,6 +21,7 @@ STATUS = {0: "ADR_OK", 1: "ADR_ERR_ARG", 2: "ADR_ERR_ALLOC", 3: "ADR_ERR_CUDA",
           4: "ADR_ERR_ILL_CONDITIONED", 5: "ADR_ERR_COMPLEX_SPECTRUM", 6: "ADR_ERR_TIMEOUT",
           7: "ADR_ERR_STATE", 8: "ADR_ERR_UNSUPPORTED"}
 PRECISION = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x3": 3}
+PHI_ROUTE = {"auto": 0, "eigen": 1, "doubling": 2}
 SCHEME = {"lawson_euler": 0, "etd2rk": 1, "lawson4": 2, "exponential_euler": 3, "erk2p1": 4,
           "stabilized_lawson_euler": 5, "lawson2a": 6, "lawson2b": 7, "stabilized_lawson2": 8}
 
@@ -35,7 +36,7 @@ class adr_params(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("lambda_", C.c_double),
                 ("abar_override", C.c_double), ("tau", C.c_double), ("scheme", C.c_int),
                 ("precision", C.c_int), ("kappa_tol", C.c_double), ("batch", C.c_int),
-                ("n_batch", C.POINTER(C.c_int)), ("batch_tile", C.c_int)]
+                ("n_batch", C.POINTER(C.c_int)), ("batch_tile", C.c_int), ("phi_route", C.c_int)]
 
 
 _lib = None
@@ -67,6 +68,7 @@ def load_library(path: str = LIB_PATH):
         "adr_get_batch_plan": (ip, [vp, ip, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "adr_mumode_apply_static": (ip, [ip, C.POINTER(C.c_int), C.POINTER(vp), vp, vp, vp]),
         "adr_kernels_per_step": (ip, [vp]),
+        "adr_phi_route_used": (ip, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "adr_last_error": (C.c_char_p, [vp]),
         "adr_destroy": (None, [vp]),
     }
@@ -109,7 +111,7 @@ def _stream_handle(stream):
 
 # ------------------------------------------------------------------- C entry points
 def adr_create(dims, tau, scheme="lawson4", precision="fp64", lam=1.0, abar_override=0.0,
-               kappa_tol=0.0, stream=None, batch_dims=None, batch_tile=0):
+               kappa_tol=0.0, stream=None, batch_dims=None, batch_tile=0, phi_route="auto"):
     """dims: grid of a single-grid context; batch_dims: [(n1, n2), ...] of a batched 2-D
     context (dims is then ignored)."""
     lib = load_library()
@@ -133,6 +135,7 @@ def adr_create(dims, tau, scheme="lawson4", precision="fp64", lam=1.0, abar_over
     p.scheme = SCHEME[scheme] if isinstance(scheme, str) else int(scheme)
     p.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
     p.kappa_tol = float(kappa_tol)
+    p.phi_route = PHI_ROUTE[phi_route] if isinstance(phi_route, str) else int(phi_route)
     ctx = C.c_void_p()
     _check(lib.adr_create(C.byref(p), _stream_handle(stream), C.byref(ctx)))
     return ctx
@@ -229,6 +232,13 @@ def adr_get_batch_plan(ctx, mode, batch):
     return list(edges), grid.value
 
 
+def adr_phi_route_used(ctx):
+    """(route name or None, halvings, Taylor terms) of a context after adr_set_coeffs."""
+    s, p = C.c_int(), C.c_int()
+    r = int(_lib.adr_phi_route_used(ctx, C.byref(s), C.byref(p)))
+    return ({0: None, 1: "eigen", 2: "doubling"}[r], s.value, p.value)
+
+
 def adr_kernels_per_step(ctx):
     return int(_lib.adr_kernels_per_step(ctx))
 
@@ -298,6 +308,9 @@ class Context:
 
     def kernels_per_step(self):
         return adr_kernels_per_step(self.ctx)
+
+    def phi_route(self):
+        return adr_phi_route_used(self.ctx)
 
     def close(self):
         adr_destroy(self.ctx)

@@ -46,6 +46,12 @@ struct Op {
 
 thread_local std::string g_create_error;
 
+// Factor kinds: 0 E(0.5), 1 E(1), 2 V, 3 V^-1, 4 E(0.5) precise, 5 E(alpha); from kLevel0 the
+// factors e^{2^i tau A_mu / 2^s} of the phi doubling route, level i = kind - kLevel0.
+constexpr int kLevel0 = 8;
+constexpr int kMaxLevels = 40;
+constexpr int kFactorKinds = kLevel0 + kMaxLevels;
+
 }  // namespace
 
 // Host side of a batched context: the packing of the instances (fixed at adr_create),
@@ -108,16 +114,23 @@ struct adr_ctx {
 
     // mixed precision (tensor cores): sliced factor images, per-row scales, c tau lambda
     bool tc = false;
-    uint8_t* d_img[6][3] = {{nullptr}};    // 0: E(0.5), 1: E(1), 2: V, 3: V^-1, 4: E(0.5) precise, 5: E(alpha)
-    float* d_fsc[6][3] = {{nullptr}};
-    uint8_t* d_img2[6][3] = {{nullptr}};   // the same for the TMA-fed kernel (K chunks of 32)
-    float* d_fsc2[6][3] = {{nullptr}};
+    uint8_t* d_img[kFactorKinds][3] = {{nullptr}};    // sliced image per factor kind and direction
+    float* d_fsc[kFactorKinds][3] = {{nullptr}};
+    uint8_t* d_img2[kFactorKinds][3] = {{nullptr}};   // the same for the TMA-fed kernel (K chunks of 32)
+    float* d_fsc2[kFactorKinds][3] = {{nullptr}};
     float* d_zt[3] = {nullptr};            // tau * lambda_mu[j] (FP32)
     unsigned* d_slots = nullptr;           // max-abs slots of the arrays a step produces
     int* d_err = nullptr;                  // device error word (bounded waits)
 
     // batched 2-D instances (p.batch > 0)
     std::unique_ptr<adr_batch_state> bs;
+
+    // phi_k route; for the doubling route: X = tau A / 2^s, Taylor terms, level factors
+    int phi_route = 0;                     // adr_phi_route in use (0: no phi_k needed)
+    int dbl_s = 0, dbl_p = 0;
+    void* d_El[kMaxLevels][3] = {{nullptr}};   // e^{2^i tau A_mu / 2^s}, i = 0..s-1
+    void* d_a0 = nullptr;                  // zero (a - abar): the stencil then yields A u
+    void* wsd[3] = {nullptr, nullptr, nullptr};   // doubling-route workspace
 
     // graph cache for adr_integrate
     cudaGraph_t graph = nullptr;
@@ -165,7 +178,7 @@ cudaError_t upload(adr_ctx* c, void** dst, const std::vector<double>& src) {
 // Slice an FP64 factor for the tensor-core kernel and upload image + row scales. Mode 1
 // uses the factor as the A operand (128-row tiles), modes >= 2 as the B operand.
 cudaError_t upload_tc(adr_ctx* c, int kind, int m, const std::vector<double>& M) {
-    const bool precise = (kind == 4);
+    const bool precise = (kind == 4);   // FK_EXP_HALF_PRECISE
     const adr::TcFactor f = adr::make_tc_factor(M, c->n[m], adr::tc_out_rows(m >= 1, precise), precise);
     cudaError_t e = cudaSuccess;
     if (!c->d_img[kind][m]) e = cudaMalloc(reinterpret_cast<void**>(&c->d_img[kind][m]), f.img.size());
@@ -187,7 +200,7 @@ cudaError_t upload_tc(adr_ctx* c, int kind, int m, const std::vector<double>& M)
 }
 
 // ------------------------------------------------------------------ schedule builders
-constexpr int kSlots = 64;
+constexpr int kSlots = 4096;
 
 // The ops of one call, plus the max-abs bookkeeping of the mixed path: every array a
 // step produces gets a fresh slot (zeroed at the start of the step) that its producer
@@ -204,8 +217,10 @@ struct Sched {
             ops.push_back({[sl](cudaStream_t s) { return cudaMemsetAsync(sl, 0, kSlots * sizeof(unsigned), s); }, OP_MEMSET});
         }
     }
+    bool overflow = false;
     unsigned* produce(const void* buf) {
         if (!c->tc) return nullptr;
+        if (next >= kSlots) { overflow = true; return c->d_slots + (kSlots - 1); }
         const int id = next++;
         for (auto& e : slot_of)
             if (e.first == buf) { e.second = id; return c->d_slots + id; }
@@ -316,7 +331,8 @@ void push_mode(Sched& S, int mu, int kind, const T* x, T* y, int epi = adr::EPI_
         return;
     }
     if (!c->tc) {
-        const void* M = kind == FK_EXP_HALF ? c->d_E[0][mu - 1] : kind == FK_EXP_ONE ? c->d_E[1][mu - 1]
+        const void* M = kind >= kLevel0 ? c->d_El[kind - kLevel0][mu - 1]
+                      : kind == FK_EXP_HALF ? c->d_E[0][mu - 1] : kind == FK_EXP_ONE ? c->d_E[1][mu - 1]
                       : kind == FK_EXP_ALPHA ? c->d_E[2][mu - 1]
                       : kind == FK_V ? c->d_V[mu - 1] : c->d_Vi[mu - 1];
         auto a = mode_args<T>(c, mu, static_cast<const T*>(M), x, y);
@@ -413,11 +429,93 @@ void push_exp_precise(Sched& S, const T* x, T* y, T* ylo) {
     }
 }
 
+template <typename T>
+StencilArgs<T> stencil_base(const adr_ctx* c, const T* u);
+template <typename T>
+void push_stencil(Sched& S, StencilArgs<T> s, bool record_input = false);
+
+// The stencil with zero (a - abar), no reaction and b = beta: F is then A u exactly (the
+// constant-coefficient operator of Eq. (linop)), so out = cu u + sum cx X + cF A u.
+template <typename T>
+StencilArgs<T> linear_base(const adr_ctx* c, const T* u) {
+    StencilArgs<T> s = stencil_base<T>(c, u);
+    s.a = static_cast<const T*>(c->d_a0);
+    for (int m = 0; m < 3; ++m) s.bmb[m] = 0.0;
+    for (int i = 0; i < 4; ++i) s.r[i] = 0.0;
+    return s;
+}
+
+double inv_factorial(int m) {
+    double f = 1.0;
+    for (int j = 2; j <= m; ++j) f *= j;
+    return 1.0 / f;
+}
+
+// y = base + alpha phi_k(tau A) x (k = 1, 2) by exponentials only. With X = tau A / 2^s:
+//   Taylor:   t = sum_{j=0}^{p} X^j x / (j+k)!  by Horner's rule, one stencil per term;
+//             for k = 2 also phi_1(X) x = x + X phi_2(X) x.
+//   Doubling: from the definitions of phi_1, phi_2,
+//             phi_1(2X) = (e^X + I) phi_1(X) / 2,  phi_2(2X) = (phi_1(X) + (e^X + I) phi_2(X)) / 4.
+//   Kept unnormalised, W1 = 2^i phi_1(2^i X) x and W2 = 4^i phi_2(2^i X) x obey
+//             W1 <- e^{2^i X} W1 + W1,  W2 <- e^{2^i X} W2 + (W2 + 2^i W1),
+//   so each level is exponential actions with plain axpy epilogues; at the end
+//   phi_1(tau A) x = W1 / 2^s and phi_2(tau A) x = W2 / 4^s.
+template <typename T>
+void push_phi_doubling(Sched& S, int k, const T* x, T* y, const T* base, double alpha) {
+    const adr_ctx* c = S.c;
+    const int sh = c->dbl_s, p = c->dbl_p;
+    const double c0 = std::ldexp(c->p.tau, -sh);
+    T* W1 = static_cast<T*>(c->wsd[0]);
+    T* W2 = static_cast<T*>(c->wsd[1]);
+    T* Z = static_cast<T*>(c->wsd[2]);
+    T* target = (k == 1) ? W1 : W2;
+    const T* prev = x;
+    for (int q = 0; q < p; ++q) {                          // coefficient j = p - 1 - q
+        const int j = p - 1 - q;
+        T* out = ((p - 1 - q) % 2 == 0) ? target : Z;
+        auto st = linear_base<T>(c, prev);
+        st.nx = 1; st.X[0] = x;
+        st.nout = 1; st.out[0] = out;
+        st.cx[0][0] = inv_factorial(j + k);
+        st.cF[0] = (q == 0) ? c0 * inv_factorial(p + k) : c0;   // the first step starts from x / (p+k)!
+        push_stencil(S, st);
+        prev = out;
+    }
+    if (k == 2) {                                          // W1 = x + X W2
+        auto st = linear_base<T>(c, W2);
+        st.nx = 1; st.X[0] = x;
+        st.nout = 1; st.out[0] = W1; st.cx[0][0] = 1.0; st.cF[0] = c0;
+        push_stencil(S, st);
+    }
+    for (int i = 0; i < sh; ++i) {
+        const int kind = kLevel0 + i;
+        if (k == 2) {
+            auto st = linear_base<T>(c, W2);               // Z = W2 + 2^i W1
+            st.nx = 1; st.X[0] = W1;
+            st.nout = 1; st.out[0] = Z; st.cu[0] = 1.0; st.cx[0][0] = std::ldexp(1.0, i);
+            push_stencil(S, st);
+            push_exp<T>(S, kind, W2, W2, Z, 1.0);
+        }
+        push_exp<T>(S, kind, W1, W1, W1, 1.0);
+    }
+    auto st = linear_base<T>(c, target);                   // y = base + alpha W / 2^(k s)
+    st.nout = 1; st.out[0] = y;
+    st.cu[0] = (base ? alpha : 1.0) * std::ldexp(1.0, -k * sh);
+    if (base) { st.nx = 1; st.X[0] = base; st.cx[0][0] = 1.0; }
+    push_stencil(S, st);
+}
+
 // y = phi_k(tau A) x through the eigenbasis (k = 0 gives e^{tau A}), optionally
-// finished by y = base + alpha * (phi_k(tau A) x).
+// finished by y = base + alpha * (phi_k(tau A) x). Contexts on the doubling route apply
+// phi_1, phi_2 by exponentials only (push_phi_doubling) and phi_0 with the dense e^{tau A}.
 template <typename T>
 void push_phi(Sched& S, int k, const T* x, T* y, const T* base = nullptr, double alpha = 0.0) {
     const adr_ctx* c = S.c;
+    if (c->phi_route == ADR_PHI_DOUBLING) {
+        if (k == 0) push_exp<T>(S, FK_EXP_ONE, x, y, base, base ? alpha : 0.0);
+        else push_phi_doubling<T>(S, k, x, y, base, alpha);
+        return;
+    }
     T* tmp[2] = {static_cast<T*>(c->ws[4]), static_cast<T*>(c->ws[5])};
     int flip = 0;
     const T* in = x;
@@ -460,7 +558,7 @@ StencilArgs<T> stencil_base(const adr_ctx* c, const T* u) {
 
 // Push a stencil op; on the mixed path its outputs (and, if asked, its input) get slots.
 template <typename T>
-void push_stencil(Sched& S, StencilArgs<T> s, bool record_input = false) {
+void push_stencil(Sched& S, StencilArgs<T> s, bool record_input) {
     if (S.c->bs) {
         const auto a = batch_stencil_args(S.c, s);
         S.ops.push_back({[a](cudaStream_t st) { return adr::launch_batch_stencil(a, st); }, OP_STENCIL});
@@ -606,6 +704,8 @@ std::vector<Op> build_step(const adr_ctx* c, T* u) {
     default:
         break;
     }
+    if (S.overflow)   // more produced arrays than max-abs slots: refuse the schedule
+        S.ops.push_back({[](cudaStream_t) { return cudaErrorInvalidValue; }, OP_MEMSET});
     return std::move(S.ops);
 }
 
@@ -1047,6 +1147,77 @@ adr_status batch_set_coeffs(adr_ctx* c, int i, const double* a_nodes, const doub
 
 }  // namespace
 
+namespace {
+
+// C = E E for a row-major n x n matrix.
+std::vector<double> square_matrix(const std::vector<double>& E, int n) {
+    std::vector<double> C(size_t(n) * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+            const double e = E[size_t(i) * n + k];
+            if (e == 0.0) continue;
+            const double* row = &E[size_t(k) * n];
+            double* out = &C[size_t(i) * n];
+            for (int j = 0; j < n; ++j) out[j] += e * row[j];
+        }
+    return C;
+}
+
+// The phi doubling route (see adr_phi_route in adr.h): s halvings so that
+// tau ||A||_1 / 2^s <= 1/2 (||A||_1 <= sum_mu ||A_mu||_1 for the Kronecker sum), p = 13 Taylor
+// terms (the remainder 0.5^14 / 15! is below 5e-17), the level factors e^{2^i X_mu} with
+// X_mu = tau A_mu / 2^s (Pade-13 for i = 0, then repeated squaring), a zero coefficient array
+// for the constant-coefficient stencil, and three state-sized work arrays.
+adr_status setup_doubling(adr_ctx* c) {
+    double norm = 0.0;
+    for (int m = 0; m < c->dim; ++m)
+        norm += std::fabs(c->f[m].sub) + std::fabs(c->f[m].diag) + std::fabs(c->f[m].sup);
+    const double x = c->p.tau * norm;
+    int sh = 0;
+    while (x > std::ldexp(0.5, sh)) ++sh;
+    if (sh > kMaxLevels) return fail(c, ADR_ERR_ARG, "tau ||A|| too large for the phi doubling route");
+    c->dbl_s = sh;
+    c->dbl_p = 13;
+    const double c0 = std::ldexp(c->p.tau, -sh);
+    struct Cached { int n; double beta; std::vector<std::vector<double>> E; };
+    std::vector<Cached> cache;
+    cudaError_t e = cudaSuccess;
+    for (int m = 0; m < c->dim && e == cudaSuccess; ++m) {
+        const std::vector<std::vector<double>>* levels = nullptr;
+        for (const auto& hit : cache)
+            if (hit.n == c->n[m] && hit.beta == c->beta[m]) levels = &hit.E;
+        if (!levels) {
+            Cached cc{c->n[m], c->beta[m], {}};
+            std::vector<double> A = adr::factor_dense(c->f[m]);
+            for (auto& v : A) v *= c0;
+            try {
+                cc.E.push_back(adr::expm_pade13(A, c->n[m]));
+            } catch (const std::exception& ex) {
+                return fail(c, ADR_ERR_ARG, std::string("expm: ") + ex.what());
+            }
+            for (int i = 1; i < sh; ++i) cc.E.push_back(square_matrix(cc.E.back(), c->n[m]));
+            cache.push_back(std::move(cc));
+            levels = &cache.back().E;
+        }
+        for (int i = 0; i < sh && e == cudaSuccess; ++i) {
+            e = upload(c, &c->d_El[i][m], (*levels)[size_t(i)]);
+            if (e == cudaSuccess && c->tc) e = upload_tc(c, kLevel0 + i, m, (*levels)[size_t(i)]);
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "upload doubling factors");
+    const size_t abytes = size_t(c->apitch) * (c->n[1] + 2) * (c->dim == 3 ? c->n[2] + 2 : 1) * c->esize;
+    if (!c->d_a0) {
+        e = cudaMalloc(&c->d_a0, abytes);
+        if (e == cudaSuccess) e = cudaMemset(c->d_a0, 0, abytes);
+    }
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+        if (!c->wsd[i]) e = cudaMalloc(&c->wsd[i], c->N * c->esize);
+    if (e != cudaSuccess) return fail(c, ADR_ERR_ALLOC, std::string("doubling route: ") + cudaGetErrorString(e));
+    return ADR_OK;
+}
+
+}  // namespace
+
 // ===================================================================== C ABI
 extern "C" {
 
@@ -1063,6 +1234,7 @@ adr_status adr_create(const adr_params* p, void* cuda_stream, adr_ctx** out) {
     if (p->scheme < ADR_LAWSON_EULER || p->scheme > ADR_STABILIZED_LAWSON2) return fail(nullptr, ADR_ERR_ARG, "unknown scheme");
     if (p->precision == ADR_MIXED_TF32X3)
         return fail(nullptr, ADR_ERR_UNSUPPORTED, "ADR_MIXED_TF32X3 is not implemented");
+    if (p->phi_route < ADR_PHI_AUTO || p->phi_route > ADR_PHI_DOUBLING) return fail(nullptr, ADR_ERR_ARG, "unknown phi route");
     if (p->precision != ADR_FP64 && p->precision != ADR_FP32 && p->precision != ADR_MIXED_BF16X3)
         return fail(nullptr, ADR_ERR_ARG, "unknown precision");
     if (p->precision == ADR_MIXED_BF16X3)
@@ -1184,17 +1356,26 @@ adr_status adr_set_coeffs(adr_ctx* c, int instance, const double* a_nodes, const
         }
         if (e != cudaSuccess) return cuda_fail(c, e, "upload eigenpairs");
     }
+    c->phi_route = 0;
     if (needs_phi(c->p.scheme)) {
-        if (!c->eig_real)
-            return fail(c, ADR_ERR_COMPLEX_SPECTRUM, "cell Peclet number >= 1: A_mu has no real eigenbasis");
         double kp = 1.0;
         for (int m = 0; m < c->dim; ++m) kp *= c->kappa[m];
         const double unit = c->fp64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
-        if (kp * unit > c->p.kappa_tol) {
+        const bool guard_ok = c->eig_real && kp * unit <= c->p.kappa_tol;
+        if (c->p.phi_route == ADR_PHI_EIGEN && !c->eig_real)
+            return fail(c, ADR_ERR_COMPLEX_SPECTRUM, "cell Peclet number >= 1: A_mu has no real eigenbasis");
+        if (c->p.phi_route == ADR_PHI_EIGEN && !guard_ok) {
             char buf[160];
             std::snprintf(buf, sizeof buf, "eigen route ill-conditioned: prod kappa * u = %.3e > kappa_tol %.3e",
                           kp * unit, c->p.kappa_tol);
             return fail(c, ADR_ERR_ILL_CONDITIONED, buf);
+        }
+        if (c->p.phi_route == ADR_PHI_DOUBLING || !guard_ok) {
+            const adr_status st = setup_doubling(c);
+            if (st != ADR_OK) return st;
+            c->phi_route = ADR_PHI_DOUBLING;
+        } else {
+            c->phi_route = ADR_PHI_EIGEN;
         }
     }
     c->coeffs_set = true;
@@ -1308,7 +1489,8 @@ adr_status adr_apply_phi(adr_ctx* c, int k, const void* v, void* y) {
     if (k < 0 || k > 2) return fail(c, ADR_ERR_ARG, "k must be 0, 1 or 2");
     if (c->bs && !c->bs->roles[FK_V])
         return fail(c, ADR_ERR_STATE, "this batched context's scheme does not build the eigenbasis");
-    if (!c->bs && !c->eig_real) return fail(c, ADR_ERR_COMPLEX_SPECTRUM, "A_mu has no real eigenbasis");
+    if (!c->bs && c->phi_route != ADR_PHI_DOUBLING && !c->eig_real)
+        return fail(c, ADR_ERR_COMPLEX_SPECTRUM, "A_mu has no real eigenbasis");
     Sched S(c);
     if (c->fp64) push_phi<double>(S, k, static_cast<const double*>(v), static_cast<double*>(y));
     else         push_phi<float>(S, k, static_cast<const float*>(v), static_cast<float*>(y));
@@ -1399,8 +1581,22 @@ adr_status adr_get_batch_plan(const adr_ctx* c, int mode, int* tile_edge, int* g
     return ADR_OK;
 }
 
+int adr_phi_route_used(const adr_ctx* c, int* halvings, int* terms) {
+    if (!c) return 0;
+    if (halvings) *halvings = c->phi_route == ADR_PHI_DOUBLING ? c->dbl_s : 0;
+    if (terms) *terms = c->phi_route == ADR_PHI_DOUBLING ? c->dbl_p : 0;
+    return c->phi_route;
+}
+
 int adr_kernels_per_step(const adr_ctx* c) {
     if (!c) return -1;
+    if (c->coeffs_set) {   // count the kernels of the schedule itself (the address is never used)
+        static double dummy[1];
+        int n = 0;
+        for (const auto& op : step_ops(c, dummy))
+            if (op.kind != OP_MEMSET) ++n;
+        return n;
+    }
     const int d = c->dim;
     switch (c->p.scheme) {
     case ADR_LAWSON_EULER: return 1 + d;
@@ -1425,6 +1621,9 @@ void adr_destroy(adr_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     drop_graph(c);
+    for (auto& row : c->d_El) for (auto& q : row) free_dev(q);
+    free_dev(c->d_a0);
+    for (auto& q : c->wsd) free_dev(q);
     if (c->bs) {
         adr_batch_state& b = *c->bs;
         free_dev(b.d_inst);

@@ -195,3 +195,24 @@ def test_config3_full_run_vs_fp64_gpu():
     err = O.rel_l2(u.cpu().numpy(), ud.cpu().numpy())
     print(f"256^3 lawson4 40 steps: bf16x3 vs fp64 GPU rel l2 {err:.3e}")
     assert err < 1e-6
+
+
+@pytest.mark.parametrize("scheme", ["etd2rk", "exponential_euler"])
+def test_phi_doubling_route_on_the_tensor_cores(scheme):
+    """The exponentials-only phi route (forced) with the mixed contractions and FP32 Taylor
+    stencils, against the oracle's eigen route on a well-conditioned grid."""
+    dims = (64, 64)
+    a, bb, r = make(dims, b=(10.0, 10.0))
+    u0 = W.smooth_initial_state(dims)
+    tau, m = 0.1 / 30, 30
+    ctx = adr.Context(dims, tau, scheme, "bf16x3", phi_route="doubling")
+    ctx.set_coeffs(a, bb, r)
+    assert ctx.phi_route()[0] == "doubling"
+    fu, u = guarded(u0.shape, u0)
+    ctx.integrate(u, 0.0, m * tau, m)
+    ctx.synchronize()
+    check_guards(fu)
+    ref = O.solve(dims, a, bb, r, u0, tau, m, scheme)
+    err = O.rel_l2(u.cpu().numpy(), ref)
+    print(f"{scheme} doubling route, bf16x3: {err:.3e}")
+    assert err < 1e-5

@@ -203,7 +203,7 @@ def test_config2_full_size_fp64():
 
 def test_state_errors():
     dims = (16, 16)
-    ctx = adr.Context(dims, 1e-3, "etd2rk", "fp64")
+    ctx = adr.Context(dims, 1e-3, "etd2rk", "fp64", phi_route="eigen")
     u = torch.zeros(dims, dtype=torch.float64, device="cuda")
     with pytest.raises(adr.AdrError) as e:
         ctx.step(u)
@@ -216,7 +216,70 @@ def test_state_errors():
     # the same coefficients are fine for an exp-only (Lawson) scheme
     adr.Context(dims, 1e-3, "lawson4", "fp64").set_coeffs(a, (400.0, 0.0), r)
     # kappa guard
-    ctx2 = adr.Context((64, 64), 1e-3, "etd2rk", "fp32", kappa_tol=1e-9)
+    ctx2 = adr.Context((64, 64), 1e-3, "etd2rk", "fp32", kappa_tol=1e-9, phi_route="eigen")
     with pytest.raises(adr.AdrError) as e:
         ctx2.set_coeffs(*make_case((64, 64))[:3])
     assert e.value.status == 4
+
+
+# ----------------------------------------------------------------------------- phi doubling route
+# Exponentials only: for eigenbases too ill-conditioned for the eigen route, or complex
+# spectra (cell Peclet >= 1). The oracle's reference is its dense route (augmented-matrix
+# exponential of the full Kronecker sum), valid for any conditioning on these small grids.
+DOUBLING = [
+    # (dims, b): prod kappa(V_mu) ~ 1e13 (2-D), complex spectrum (3-D, cell Peclet 1.2)
+    ((24, 20), (52.0, -42.0)),
+    ((10, 9, 8), (40.0, -30.0, 35.0)),
+]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 5e-5)])
+@pytest.mark.parametrize("dims,b", DOUBLING)
+@pytest.mark.parametrize("k", [1, 2])
+def test_phi_doubling_action_matches_dense_oracle(dims, b, k, prec, tol):
+    a, bb, r, _ = make_case(dims, b=b)
+    tau = 2e-3
+    ctx = context(dims, tau, "etd2rk", prec, a, bb, r)
+    route, halvings, terms = ctx.phi_route()
+    assert route == "doubling" and halvings > 0 and terms > 0
+    v0 = np.random.default_rng(12).standard_normal(tuple(dims[::-1]))
+    dt = DTYPES[prec]
+    fv, v = guarded(v0.shape, dt, v0)
+    fy, y = guarded(v0.shape, dt)
+    ctx.apply_phi(k, v, y)
+    torch.cuda.synchronize()
+    check_guards(fy)
+    prob = O.ADRProblem(dims, a, bb, r)
+    ref = O.MatrixFunctions(prob, tau).phi_action_dense(k, 1.0, v.double().cpu().numpy())
+    assert O.rel_l2(y.cpu().numpy(), ref) < tol
+
+
+@pytest.mark.parametrize("scheme", ["etd2rk", "exponential_euler", "erk2p1"])
+@pytest.mark.parametrize("dims,b", DOUBLING)
+def test_phi_schemes_on_the_doubling_route_match_dense_oracle(dims, b, scheme):
+    a, bb, r, u0 = make_case(dims, b=b)
+    tau, m = 2e-3, 4
+    ctx = context(dims, tau, scheme, "fp64", a, bb, r)
+    fu, u = guarded(u0.shape, torch.float64, u0)
+    ctx.integrate(u, 0.0, m * tau, m)
+    torch.cuda.synchronize()
+    check_guards(fu)
+    ref = O.solve(dims, a, bb, r, u0, tau, m, scheme, phi_route="dense")
+    # strongly non-normal operators (prod kappa ~ 1e13, or complex spectra): the oracle's
+    # dense exponential of the augmented matrix and the doubling chain both carry errors of
+    # order eps ||tau A|| times the non-normality, ~1e-12 after these steps
+    assert O.rel_l2(u.cpu().numpy(), ref) < 5e-12
+
+
+def test_doubling_route_forced_on_a_well_conditioned_grid_matches_eigen_oracle():
+    dims = (33, 30)
+    a, bb, r, u0 = make_case(dims)
+    tau, m = 3e-3, 6
+    ctx = adr.Context(dims, tau, "etd2rk", "fp64", phi_route="doubling")
+    ctx.set_coeffs(a, bb, r)
+    assert ctx.phi_route()[0] == "doubling"
+    u = torch.tensor(u0, dtype=torch.float64, device="cuda")
+    ctx.integrate(u, 0.0, m * tau, m)
+    ctx.synchronize()
+    ref = O.solve(dims, a, bb, r, u0, tau, m, "etd2rk")
+    assert O.rel_l2(u.cpu().numpy(), ref) < 1e-12
