@@ -219,6 +219,26 @@ adr_status adr_profile_step(adr_ctx* ctx, void* u_dev, int max_ops, float* ms, i
 adr_status adr_mumode_apply_static(int dim, const int n[3], const double* const factors[3],
                                    const double* v_dev, double* y_dev, void* cuda_stream);
 
+/* Table 1 and Theorems 2.1-2.7: the smallest lambda in [0, 1] for which the scheme is
+ * unconditionally stable on the model problem, i.e. |Phi(z, lambda)| <= 1 for all z <= 0,
+ * where Phi is one step of the scheme on u' = lambda z u + (1 - lambda) z u from u = 1.
+ * Computed on the host by bisection over lambda, with z on a logarithmic grid down to -1e9.
+ * ADR_ERR_ARG for an unknown scheme. */
+adr_status adr_stability_bound(int scheme, double* lambda_min);
+
+/* The lambda scan of Section 3 (choice of lambda): integrate a SMALL problem (params p,
+ * coefficients and host initial state u0_host of N doubles as in adr_set_coeffs) for m
+ * steps with each candidate lambda (lambdas[0..n_lambdas-1], or, when lambdas is NULL,
+ * n_lambdas values evenly spaced from adr_stability_bound(p->scheme) to 1), and measure the
+ * relative l2 error against a reference: the same semidiscrete problem integrated by
+ * Lawson4 in FP64 with step tau / ref_substeps (<= 0 selects 8). Writes the errors
+ * (INFINITY where a lambda is refused) and the lambda with the smallest error. Runs on
+ * cuda_stream and synchronises it; allocates its own device buffers. */
+adr_status adr_lambda_scan(const adr_params* p, const double* a_nodes, const double b[3],
+                           const double r_poly[4], const double* u0_host, int m, int n_lambdas,
+                           const double* lambdas, int ref_substeps, void* cuda_stream,
+                           double* errors, double* best_lambda);
+
 /* Number of kernels one adr_step launches (for launch accounting). */
 int adr_kernels_per_step(const adr_ctx* ctx);
 

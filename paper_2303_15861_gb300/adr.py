@@ -69,6 +69,8 @@ def load_library(path: str = LIB_PATH):
         "adr_mumode_apply_static": (ip, [ip, C.POINTER(C.c_int), C.POINTER(vp), vp, vp, vp]),
         "adr_kernels_per_step": (ip, [vp]),
         "adr_phi_route_used": (ip, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "adr_stability_bound": (ip, [ip, dp]),
+        "adr_lambda_scan": (ip, [C.POINTER(adr_params), dp, dp, dp, dp, ip, ip, dp, ip, vp, dp, dp]),
         "adr_last_error": (C.c_char_p, [vp]),
         "adr_destroy": (None, [vp]),
     }
@@ -237,6 +239,45 @@ def adr_phi_route_used(ctx):
     s, p = C.c_int(), C.c_int()
     r = int(_lib.adr_phi_route_used(ctx, C.byref(s), C.byref(p)))
     return ({0: None, 1: "eigen", 2: "doubling"}[r], s.value, p.value)
+
+
+def adr_stability_bound(scheme):
+    """Smallest lambda of unconditional stability on the model problem (Table 1)."""
+    lib = load_library()
+    out = C.c_double()
+    _check(lib.adr_stability_bound(SCHEME[scheme] if isinstance(scheme, str) else int(scheme), C.byref(out)))
+    return out.value
+
+
+def adr_lambda_scan(dims, tau, scheme, precision, a_nodes, b, r_poly, u0, m, lambdas=None, n_lambdas=8,
+                    ref_substeps=8, abar_override=0.0, stream=None):
+    """Section 3's lambda scan on a small problem: returns (best lambda, [(lambda, error)])."""
+    lib = load_library()
+    p = adr_params()
+    p.dim = len(dims)
+    for i, n in enumerate(dims):
+        p.n[i] = int(n)
+    p.abar_override = float(abar_override)
+    p.tau = float(tau)
+    p.scheme = SCHEME[scheme] if isinstance(scheme, str) else int(scheme)
+    p.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    a, ap = _dbl(a_nodes)
+    bb, bp = _dbl(list(b) + [0.0] * (3 - len(b)), 3)
+    rr, rp = _dbl(r_poly, 4)
+    uu, up = _dbl(u0)
+    if lambdas is not None:
+        lam_arr, lamp = _dbl(lambdas)
+        n_lambdas = lam_arr.size
+        lam_list = [float(x) for x in lam_arr]
+    else:
+        lamp = None
+        lo = adr_stability_bound(scheme)
+        lam_list = [1.0] if n_lambdas == 1 else [lo + (1.0 - lo) * i / (n_lambdas - 1) for i in range(n_lambdas)]
+    errs = (C.c_double * int(n_lambdas))()
+    best = C.c_double()
+    _check(lib.adr_lambda_scan(C.byref(p), ap, bp, rp, up, int(m), int(n_lambdas), lamp, int(ref_substeps),
+                               _stream_handle(stream), errs, C.byref(best)))
+    return best.value, list(zip(lam_list, list(errs)))
 
 
 def adr_kernels_per_step(ctx):

@@ -283,3 +283,24 @@ def test_doubling_route_forced_on_a_well_conditioned_grid_matches_eigen_oracle()
     ctx.synchronize()
     ref = O.solve(dims, a, bb, r, u0, tau, m, "etd2rk")
     assert O.rel_l2(u.cpu().numpy(), ref) < 1e-12
+
+
+# ----------------------------------------------------------------------------- lambda scan
+def test_lambda_scan_errors_match_oracle():
+    """Section 3's scan on a small grid: the library's error for each lambda equals the
+    oracle's (the same scheme with that lambda against Lawson4 at tau/8), and the chosen
+    lambda is the argmin."""
+    dims = (24, 20)
+    a, bb, r, u0 = make_case(dims, b=(10.0, -6.0))
+    tau, m = 4e-3, 10
+    lams = [0.25, 0.5, 0.75, 1.0]
+    best, errs = adr.adr_lambda_scan(dims, tau, "lawson_euler", "fp64", a, bb, r, u0, m, lambdas=lams)
+    ref = O.solve(dims, a, bb, r, u0, tau / 8, 8 * m, "lawson4")
+    for lam, err in errs:
+        got = O.solve(dims, a, bb, r, u0, tau, m, "lawson_euler", lam=lam)
+        assert abs(err - O.rel_l2(got, ref)) <= 1e-6 * err, lam
+    assert best == min(errs, key=lambda t: t[1])[0]
+    # default candidates: from the Table 1 bound of the scheme to 1
+    best2, errs2 = adr.adr_lambda_scan(dims, tau, "etd2rk", "fp64", a, bb, r, u0, m, n_lambdas=5)
+    assert abs(errs2[0][0] - adr.adr_stability_bound("etd2rk")) < 1e-12 and errs2[-1][0] == 1.0
+    assert all(np.isfinite(e) for _, e in errs2) and best2 == min(errs2, key=lambda t: t[1])[0]
