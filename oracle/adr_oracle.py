@@ -141,26 +141,38 @@ def kron_sum_dense(factors) -> np.ndarray:
 # ----------------------------------------------------------------------------------
 
 class ADRProblem:
-    """u_t = div(a grad u) + b . grad u + r(u) on (0,1)^d, homogeneous Dirichlet.
+    """u_t = div(a grad u) + b . grad u + r(u) on (0,1)^d, homogeneous Dirichlet (form
+    "flux", bc "dirichlet"); or, as in the paper's three-dimensional experiment (Section 5.2,
+    Eq. (adr3d)), u_t = a Lap u + b . grad u + r(u) (form "adelta") with homogeneous Dirichlet
+    values on the faces x_mu = 0 and homogeneous Neumann values on the faces x_mu = 1
+    (bc "mixed"; only with form "adelta").
 
-    dims: interior points per direction, x1 first. a_nodes: nodal a with the boundary
-    ring, numpy shape (n_d+2, ..., n_1+2). b: constant velocity (length >= d).
+    dims: unknowns per direction, x1 first. Dirichlet: nodes x_i = i h, h = 1/(n+1),
+    i = 1..n. Mixed: h = 1/n, i = 1..n (x_n = 1 is an unknown; the Neumann condition enters
+    through the mirror ghost u_{n+1} = u_{n-1}). a_nodes: nodal a at x_j = j h, j = 0..n+1,
+    numpy shape (n_d+2, ..., n_1+2). b: constant velocity (length >= d).
     r_poly: r(u) = r0 + r1 u + r2 u^2 + r3 u^3. lam: the lambda of Eq. (linop).
     """
 
-    def __init__(self, dims, a_nodes, b, r_poly, lam=1.0, abar=None):
+    def __init__(self, dims, a_nodes, b, r_poly, lam=1.0, abar=None, bc="dirichlet", form="flux"):
         self.dims = tuple(int(n) for n in dims)
         self.d = len(self.dims)
         self.a = np.asarray(a_nodes, dtype=np.float64)
         assert self.a.shape == tuple(n + 2 for n in self.dims[::-1])
+        assert bc in ("dirichlet", "mixed") and form in ("flux", "adelta")
+        assert bc == "dirichlet" or form == "adelta", "Neumann faces are supported for the a Lap u form"
+        self.bc, self.form = bc, form
         self.b = np.asarray(b, dtype=np.float64)[: self.d]
         self.r = tuple(float(c) for c in r_poly)
         self.lam = float(lam)
-        self.h = [1.0 / (n + 1) for n in self.dims]
-        # Eq. (amaxbeta): a_max = max a (nodal samples unless overridden)
-        self.abar = self.lam * float(self.a.max()) if abar is None else float(abar)
-        self.beta = np.array([self.b[mu - 1] + self._mean_face_jump(mu)
-                              for mu in range(1, self.d + 1)])
+        self.h = [1.0 / (n + 1) if bc == "dirichlet" else 1.0 / n for n in self.dims]
+        # Eq. (amaxbeta): a_max = max a over the nodes of the closed domain (unless overridden)
+        dom = self.a if bc == "dirichlet" else self.a[tuple(slice(0, n + 1) for n in self.dims[::-1])]
+        self.abar = self.lam * float(dom.max()) if abar is None else float(abar)
+        if form == "flux":
+            self.beta = np.array([self.b[mu - 1] + self._mean_face_jump(mu) for mu in range(1, self.d + 1)])
+        else:   # a Lap u: A = lambda a_max Lap + b . grad (Eq. (adr3dstab))
+            self.beta = self.b.copy()
 
     # -- Eq. (amaxbeta): the domain mean of d_mu a is the face-mean of a(x_mu=1)-a(x_mu=0)
     def _mean_face_jump(self, mu):
@@ -207,12 +219,46 @@ class ADRProblem:
             out += vel[mu - 1] * (up_ - um) / (2.0 * h)
         return out
 
+    # -- a Lap u + vel . grad u with the ghost values of the boundary conditions
+    def _padded(self, u):
+        up = np.pad(u, 1)                       # Dirichlet ghosts: zero
+        if self.bc == "mixed":                  # Neumann on x_mu = 1: u_{n+1} = u_{n-1}
+            for ax in range(self.d):
+                hi = [slice(None)] * self.d
+                src = [slice(None)] * self.d
+                hi[ax] = -1
+                src[ax] = -3
+                up[tuple(hi)] = up[tuple(src)]
+        return up
+
+    def _adelta_form(self, u, coef, vel):
+        d = self.d
+        up = self._padded(u)
+        inner = (slice(1, -1),) * d
+        lap = np.zeros_like(u)
+        adv = np.zeros_like(u)
+        for mu in range(1, d + 1):
+            ax = d - mu
+            h = self.h[mu - 1]
+            plus = list(inner)
+            minus = list(inner)
+            plus[ax] = slice(2, None)
+            minus[ax] = slice(0, -2)
+            uc, upl, umi = up[inner], up[tuple(plus)], up[tuple(minus)]
+            lap += (upl - 2.0 * uc + umi) / (h * h)
+            adv += vel[mu - 1] * (upl - umi) / (2.0 * h)
+        return coef[inner] * lap + adv
+
     def F(self, u):
-        """Full semidiscrete right-hand side of Eq. (adr)."""
+        """Full semidiscrete right-hand side of Eq. (adr) (or Eq. (adr3d) for form "adelta")."""
+        if self.form == "adelta":
+            return self._adelta_form(u, self.a, self.b) + self.reaction(u)
         return self._flux_form(u, self.a, self.b) + self.reaction(u)
 
     def g(self, u):
         """Remainder of Eq. (nonlin), written directly with (a - a_max) and (b - beta)."""
+        if self.form == "adelta":
+            return self._adelta_form(u, self.a - self.abar, self.b - self.beta) + self.reaction(u)
         return self._flux_form(u, self.a - self.abar, self.b - self.beta) + self.reaction(u)
 
     # -- 1-D factors of the Kronecker sum (Section 5.2)
@@ -223,8 +269,13 @@ class ADRProblem:
         diag = -2.0 * self.abar / (h * h)
         sup = self.abar / (h * h) + self.beta[mu - 1] / (2.0 * h)   # coefficient of u_{i+1}
         sub = self.abar / (h * h) - self.beta[mu - 1] / (2.0 * h)   # coefficient of u_{i-1}
-        return (np.diag(np.full(n, diag)) + np.diag(np.full(n - 1, sup), 1)
-                + np.diag(np.full(n - 1, sub), -1))
+        A = (np.diag(np.full(n, diag)) + np.diag(np.full(n - 1, sup), 1)
+             + np.diag(np.full(n - 1, sub), -1))
+        if self.bc == "mixed":
+            # last node: the mirror ghost u_{n+1} = u_{n-1} turns its row into
+            # a_max (2 u_{n-1} - 2 u_n) / h^2 and cancels the central advection
+            A[n - 1, n - 2] = 2.0 * self.abar / (h * h)
+        return A
 
     def A_apply(self, u):
         """A u through the Kronecker-sum factors: sum_mu U x_mu A_mu."""
@@ -451,9 +502,10 @@ def integrate(ops, u0, m, scheme):
     return u
 
 
-def solve(dims, a_nodes, b, r_poly, u0, tau, m, scheme, lam=1.0, abar=None, phi_route="eigen"):
+def solve(dims, a_nodes, b, r_poly, u0, tau, m, scheme, lam=1.0, abar=None, phi_route="eigen",
+          bc="dirichlet", form="flux"):
     """Convenience: FP64 oracle solution after m steps of `scheme`."""
-    prob = ADRProblem(dims, a_nodes, b, r_poly, lam=lam, abar=abar)
+    prob = ADRProblem(dims, a_nodes, b, r_poly, lam=lam, abar=abar, bc=bc, form=form)
     return integrate(GridOps(prob, tau, phi_route=phi_route), u0, m, scheme)
 
 

@@ -168,3 +168,24 @@ def batch_instances(sizes, m=30, T=0.1, scheme="etd2rk", seed=2303):
             u0=smooth_initial_state(dims, noise=1e-3, rng=np.random.default_rng((seed, i))),
             tau=T / m, m=int(m), scheme=scheme, extra=dict(c=c, k=k, b=(float(b[0]), float(b[1])))))
     return out
+
+
+REACTION_U_1PU2 = (0.0, 1.0, 0.0, 1.0)  # r(u) = u (1 + u^2)
+
+
+def config_e4(n=60, b=-0.01, scheme="lawson2a", m=64, T=0.25):
+    """The paper's three-dimensional experiment (Section 5.2, Eq. (adr3d)): a Lap u +
+    b (d_1 + d_2 + d_3) u + u (1 + u^2) on (0,1)^3, Dirichlet on the faces x_mu = 0 and
+    Neumann on the faces x_mu = 1, a = exp(-|x - 1/2|^2) / 10, the smooth datum
+    (27/4)^3 x1 x2 x3 (1-x1)^2 (1-x2)^2 (1-x3)^2 without noise. Nodes x_j = j / n: the
+    unknowns are j = 1..n (x_n = 1), the coefficient array covers j = 0..n+1."""
+    h = 1.0 / n
+    xs = np.arange(0, n + 2, dtype=np.float64) * h
+    X3, X2, X1 = np.meshgrid(xs, xs, xs, indexing="ij")
+    a = 0.1 * np.exp(-(X1 - 0.5) ** 2 - (X2 - 0.5) ** 2 - (X3 - 0.5) ** 2)
+    xi = np.arange(1, n + 1, dtype=np.float64) * h
+    Y3, Y2, Y1 = np.meshgrid(xi, xi, xi, indexing="ij")
+    u0 = (27.0 / 4.0) ** 3 * Y1 * Y2 * Y3 * (1 - Y1) ** 2 * (1 - Y2) ** 2 * (1 - Y3) ** 2
+    return Workload(name=f"e4_{n}_{scheme}_b{b}", dims=(n, n, n), a_nodes=a, b=(b, b, b),
+                    r_poly=REACTION_U_1PU2, u0=np.ascontiguousarray(u0), tau=T / m, m=int(m), scheme=scheme,
+                    extra=dict(bc="mixed", form="adelta"))

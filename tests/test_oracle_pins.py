@@ -374,3 +374,71 @@ def test_grid_convergence_orders():
     assert 0.8 < slopes["lawson_euler"] < 1.2, slopes
     assert 1.8 < slopes["etd2rk"] < 2.2, slopes
     assert 3.4 < slopes["lawson4"] < 4.4, slopes
+
+
+# ------------------------------------------------ mixed boundary conditions, a Lap u form
+def _mixed_case(dims, seed=4):
+    rng = np.random.default_rng(seed)
+    a = 0.5 + rng.random(tuple(n + 2 for n in dims[::-1]))
+    b = (0.7, -1.3, 2.1)[: len(dims)]
+    return O.ADRProblem(dims, a, b, (0.1, -0.4, 0.3, 0.2), bc="mixed", form="adelta")
+
+
+@pytest.mark.parametrize("dims", [(7, 6, 5), (9, 8)])
+def test_mixed_adelta_stencil_exact_for_mirror_symmetric_quadratics(dims):
+    """u = prod_mu x_mu (2 - x_mu) vanishes on x_mu = 0, has zero normal derivative on x_mu = 1
+    and is even about x_mu = 1, so the centred differences with the mirror ghost are exact:
+    F_h u = a Lap u + b . grad u + r(u) at every node, including the Neumann ones."""
+    prob = _mixed_case(dims)
+    axes = [np.arange(1, n + 1) / n for n in dims]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")[::-1]       # x1, x2, ...
+    q = [x * (2 - x) for x in grids]
+    u = np.prod(q, axis=0)
+    lap = sum(-2.0 * np.prod([q[nu] for nu in range(len(dims)) if nu != mu], axis=0) for mu in range(len(dims)))
+    grad = [(2 - 2 * grids[mu]) * np.prod([q[nu] for nu in range(len(dims)) if nu != mu], axis=0)
+            for mu in range(len(dims))]
+    a_in = prob.a[(slice(1, -1),) * len(dims)]
+    exact = a_in * lap + sum(prob.b[mu] * grad[mu] for mu in range(len(dims))) + prob.reaction(u)
+    assert np.max(np.abs(prob.F(u) - exact)) <= 1e-11 * np.max(np.abs(exact))
+
+
+@pytest.mark.parametrize("dims", [(7, 6, 5), (9, 8)])
+def test_mixed_factors_match_the_stencil_with_constant_coefficient(dims):
+    """With a = a_max everywhere and r = 0, F is the constant-coefficient operator A: the
+    Kronecker sum of the 1-D factors (Neumann rows included) applied densely must agree."""
+    prob0 = _mixed_case(dims)
+    a = np.full(prob0.a.shape, 0.8)
+    prob = O.ADRProblem(dims, a, prob0.b, (0, 0, 0, 0), bc="mixed", form="adelta")
+    u = np.random.default_rng(2).standard_normal(tuple(dims[::-1]))
+    A = O.kron_sum_dense([prob.factor(mu) for mu in range(1, len(dims) + 1)])
+    ref = (A @ u.ravel()).reshape(u.shape)
+    assert np.linalg.norm(prob.F(u) - ref) <= 1e-13 * np.linalg.norm(ref)
+    assert np.linalg.norm(prob.A_apply(u) - ref) <= 1e-13 * np.linalg.norm(ref)
+    # and the splitting identity g = F - A u with a variable coefficient
+    u2 = np.random.default_rng(3).standard_normal(tuple(dims[::-1]))
+    lhs = prob0.g(u2)
+    rhs = prob0.F(u2) - prob0.A_apply(u2)
+    assert np.linalg.norm(lhs - rhs) <= 1e-12 * np.linalg.norm(prob0.F(u2))
+
+
+def test_mixed_exp_action_matches_dense_expm():
+    """e^{tau A} by mu-mode products with the (non-Toeplitz) mixed factors equals the
+    dense exponential of the full Kronecker sum."""
+    dims = (6, 5, 4)
+    prob = _mixed_case(dims)
+    tau = 3e-3
+    v = np.random.default_rng(8).standard_normal(tuple(dims[::-1]))
+    A = O.kron_sum_dense([prob.factor(mu) for mu in range(1, 4)])
+    ref = sla.expm(tau * A) @ v.ravel()
+    got = O.MatrixFunctions(prob, tau).exp_action(1.0, v).ravel()
+    assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+def test_e4_workload_recipe():
+    """The paper's three-dimensional datum and coefficients on the mixed-BC grid."""
+    from paper_2303_15861_gb300 import workloads as W
+    w = W.config_e4(n=16, m=8)
+    assert w.a_nodes.shape == (18, 18, 18) and w.u0.shape == (16, 16, 16)
+    assert abs(w.a_nodes.max() - 0.1) < 1e-3 and w.u0.max() <= 1.0 + 1e-12
+    prob = O.ADRProblem(w.dims, w.a_nodes, w.b, w.r_poly, bc="mixed", form="adelta")
+    assert np.allclose(prob.beta, w.b[:3]) and prob.h[0] == 1.0 / 16
