@@ -45,7 +45,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--workload", choices=["3d", "batch2d"] + sorted(GRID_WORKLOADS), default="3d",
                    help="3d: the 256^3 Lawson4 workload (default); batch2d: 512 uneven 2-D ETD2RK instances; "
-                        "c1-*, c2, c5-*: the other single-grid workloads")
+                        "c1-*, c2, c5-*, e4-*: the other single-grid workloads")
     p.add_argument("--check", action="store_true",
                    help="single-grid workloads: also measure the error (oracle for c1/c2, FP64 GPU at tau/4 for c5)")
     p.add_argument("--ncu-steps", type=int, default=0,
@@ -375,6 +375,9 @@ GRID_WORKLOADS = {
     "c2": (lambda W: W.config2(), "fp64"),
     "c5-lawson4": (lambda W: W.config5(scheme="lawson4"), "bf16x3"),
     "c5-etd2rk": (lambda W: W.config5(scheme="etd2rk"), "bf16x3"),
+    # the paper's three-dimensional experiment: N = 60, T = 1/4, b = -0.01, 2^8 steps
+    "e4-lawson2a": (lambda W: W.config_e4(n=60, b=-0.01, scheme="lawson2a", m=256), "bf16x3"),
+    "e4-stabilized-lawson2": (lambda W: W.config_e4(n=60, b=-0.01, scheme="stabilized_lawson2", m=256), "bf16x3"),
 }
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (nominal; no measured figure on this machine)
 
@@ -394,6 +397,7 @@ def ours_grid(args):
     prec = args.precision if args.precision != "bf16x3" or default_prec == "bf16x3" else default_prec
     if args.workload.startswith(("c1", "c2")):
         prec = "fp64" if args.precision == "bf16x3" else args.precision
+    form_kw = {k: w.extra[k] for k in ("bc", "form") if k in w.extra}
     dt = torch.float64 if prec == "fp64" else torch.float32
     N = w.dof
     stream = torch.cuda.Stream()
@@ -404,7 +408,7 @@ def ours_grid(args):
                        "tau": w.tau, "time_steps_per_bench_step": w.m, "b": list(w.b[:len(w.dims)])}}
     with torch.cuda.stream(stream):
         try:
-            ctx = adr.Context(w.dims, w.tau, w.scheme, prec, stream=stream)
+            ctx = adr.Context(w.dims, w.tau, w.scheme, prec, stream=stream, **form_kw)
             ctx.set_coeffs(w.a_nodes, w.b, w.r_poly)
         except adr.AdrError as e:
             line = dict(base, unavailable=str(e))
@@ -447,7 +451,7 @@ def ours_grid(args):
             from oracle import adr_oracle as O
             if args.workload.startswith("c5"):
                 # reference: the FP64 GPU path at tau / 4 (four times the steps)
-                rc = adr.Context(w.dims, w.tau / 4, w.scheme, "fp64", stream=stream)
+                rc = adr.Context(w.dims, w.tau / 4, w.scheme, "fp64", stream=stream, **form_kw)
                 rc.set_coeffs(w.a_nodes, w.b, w.r_poly)
                 ur = torch.tensor(w.u0, dtype=torch.float64, device="cuda")
                 rc.integrate(ur, 0.0, 0.0, 4 * w.m)
@@ -456,7 +460,7 @@ def ours_grid(args):
                 rc.close()
                 acc = {"reference": "FP64 GPU path at tau/4"}
             else:
-                ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, w.m, w.scheme)
+                ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, w.m, w.scheme, **form_kw)
                 acc = {"reference": "FP64 oracle"}
             acc.update({"rel_l2": O.rel_l2(got, ref), "rel_inf": O.rel_inf(got, ref)})
         launches = ctx.kernels_per_step() * w.m * args.steps

@@ -98,7 +98,20 @@ typedef struct {
     int batch_tile;        /* batch > 0: 0 = tile shapes and grid chosen by the autotuner;
                               32, 64 or 128 = that square tile for every instance          */
     int phi_route;         /* adr_phi_route: how phi_k(tau A) is applied (single grids)     */
+    int bc_hi;             /* adr_bc: the boundary condition on the faces x_mu = 1          */
+    int form;              /* adr_form: the diffusion term                                  */
 } adr_params;
+
+/* Boundary conditions on the faces x_mu = 1 (the faces x_mu = 0 are always homogeneous
+ * Dirichlet). ADR_BC_NEUMANN: homogeneous Neumann, as in the paper's three-dimensional
+ * experiment (Section 5.2, Eq. (adr3d)); the grid is then x_i = i/n, i = 1..n (x_n = 1 is
+ * an unknown, its ghost mirrors u_{n-1}), and a_nodes still covers j = 0..n+1 (the ring
+ * beyond x = 1 is not used). Only with ADR_FORM_ADELTA; single-grid contexts only. */
+typedef enum { ADR_BC_DIRICHLET = 0, ADR_BC_NEUMANN = 1 } adr_bc;
+
+/* The diffusion term: ADR_FORM_FLUX div(a grad u) with arithmetic-mean face coefficients
+ * (Eq. (adr)); ADR_FORM_ADELTA a(x) Lap u (Eq. (adr3d)), for which beta = b. */
+typedef enum { ADR_FORM_FLUX = 0, ADR_FORM_ADELTA = 1 } adr_form;
 
 /* Routes for phi_k(tau A) v.
  *   ADR_PHI_EIGEN: mu-mode products with V_mu^-1, the pointwise phi_k(tau(l1+l2+l3)), V_mu

@@ -22,6 +22,8 @@ STATUS = {0: "ADR_OK", 1: "ADR_ERR_ARG", 2: "ADR_ERR_ALLOC", 3: "ADR_ERR_CUDA",
           7: "ADR_ERR_STATE", 8: "ADR_ERR_UNSUPPORTED"}
 PRECISION = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x3": 3}
 PHI_ROUTE = {"auto": 0, "eigen": 1, "doubling": 2}
+BC = {"dirichlet": 0, "mixed": 1}          # faces x_mu = 1: Dirichlet, or Neumann ("mixed")
+FORM = {"flux": 0, "adelta": 1}
 SCHEME = {"lawson_euler": 0, "etd2rk": 1, "lawson4": 2, "exponential_euler": 3, "erk2p1": 4,
           "stabilized_lawson_euler": 5, "lawson2a": 6, "lawson2b": 7, "stabilized_lawson2": 8}
 
@@ -36,7 +38,8 @@ class adr_params(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("lambda_", C.c_double),
                 ("abar_override", C.c_double), ("tau", C.c_double), ("scheme", C.c_int),
                 ("precision", C.c_int), ("kappa_tol", C.c_double), ("batch", C.c_int),
-                ("n_batch", C.POINTER(C.c_int)), ("batch_tile", C.c_int), ("phi_route", C.c_int)]
+                ("n_batch", C.POINTER(C.c_int)), ("batch_tile", C.c_int), ("phi_route", C.c_int),
+                ("bc_hi", C.c_int), ("form", C.c_int)]
 
 
 _lib = None
@@ -113,7 +116,8 @@ def _stream_handle(stream):
 
 # ------------------------------------------------------------------- C entry points
 def adr_create(dims, tau, scheme="lawson4", precision="fp64", lam=1.0, abar_override=0.0,
-               kappa_tol=0.0, stream=None, batch_dims=None, batch_tile=0, phi_route="auto"):
+               kappa_tol=0.0, stream=None, batch_dims=None, batch_tile=0, phi_route="auto", bc="dirichlet",
+               form="flux"):
     """dims: grid of a single-grid context; batch_dims: [(n1, n2), ...] of a batched 2-D
     context (dims is then ignored)."""
     lib = load_library()
@@ -138,6 +142,8 @@ def adr_create(dims, tau, scheme="lawson4", precision="fp64", lam=1.0, abar_over
     p.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
     p.kappa_tol = float(kappa_tol)
     p.phi_route = PHI_ROUTE[phi_route] if isinstance(phi_route, str) else int(phi_route)
+    p.bc_hi = BC[bc] if isinstance(bc, str) else int(bc)
+    p.form = FORM[form] if isinstance(form, str) else int(form)
     ctx = C.c_void_p()
     _check(lib.adr_create(C.byref(p), _stream_handle(stream), C.byref(ctx)))
     return ctx

@@ -544,8 +544,10 @@ StencilArgs<T> stencil_base(const adr_ctx* c, const T* u) {
     s.n1 = c->n[0];
     s.n2 = c->n[1];
     s.n3 = c->dim == 3 ? c->n[2] : 1;
+    s.neumann = c->p.bc_hi == ADR_BC_NEUMANN;
+    s.adelta = c->p.form == ADR_FORM_ADELTA;
     for (int m = 0; m < c->dim; ++m) {
-        const double h = 1.0 / (c->n[m] + 1);
+        const double h = s.neumann ? 1.0 / c->n[m] : 1.0 / (c->n[m] + 1);
         s.inv_h2[m] = 1.0 / (h * h);
         s.inv_2h[m] = 1.0 / (2.0 * h);
         s.bmb[m] = c->b[m] - c->beta[m];
@@ -961,6 +963,8 @@ adr_status batch_tune(adr_ctx* c) {
 
 adr_status create_batch(const adr_params* p, void* cuda_stream, adr_ctx** out) {
     if (p->dim != 2) return fail(nullptr, ADR_ERR_ARG, "a batched context is 2-D: dim must be 2");
+    if (p->bc_hi != ADR_BC_DIRICHLET || p->form != ADR_FORM_FLUX)
+        return fail(nullptr, ADR_ERR_UNSUPPORTED, "batched contexts are Dirichlet, flux form");
     if (!p->n_batch) return fail(nullptr, ADR_ERR_ARG, "n_batch is NULL");
     if (p->batch > (1 << 20)) return fail(nullptr, ADR_ERR_ARG, "batch must be <= 2^20");
     if (!(p->tau > 0.0) || !std::isfinite(p->tau)) return fail(nullptr, ADR_ERR_ARG, "tau must be positive");
@@ -1169,9 +1173,17 @@ std::vector<double> square_matrix(const std::vector<double>& E, int n) {
 // X_mu = tau A_mu / 2^s (Pade-13 for i = 0, then repeated squaring), a zero coefficient array
 // for the constant-coefficient stencil, and three state-sized work arrays.
 adr_status setup_doubling(adr_ctx* c) {
-    double norm = 0.0;
-    for (int m = 0; m < c->dim; ++m)
-        norm += std::fabs(c->f[m].sub) + std::fabs(c->f[m].diag) + std::fabs(c->f[m].sup);
+    double norm = 0.0;   // sum over mu of the largest absolute row sum of A_mu (Neumann rows included)
+    for (int m = 0; m < c->dim; ++m) {
+        const std::vector<double> A = adr::factor_dense(c->f[m]);
+        double rmax = 0.0;
+        for (int i = 0; i < c->n[m]; ++i) {
+            double r = 0.0;
+            for (int j = 0; j < c->n[m]; ++j) r += std::fabs(A[size_t(i) * c->n[m] + j]);
+            rmax = std::max(rmax, r);
+        }
+        norm += rmax;
+    }
     const double x = c->p.tau * norm;
     int sh = 0;
     while (x > std::ldexp(0.5, sh)) ++sh;
@@ -1235,6 +1247,10 @@ adr_status adr_create(const adr_params* p, void* cuda_stream, adr_ctx** out) {
     if (p->precision == ADR_MIXED_TF32X3)
         return fail(nullptr, ADR_ERR_UNSUPPORTED, "ADR_MIXED_TF32X3 is not implemented");
     if (p->phi_route < ADR_PHI_AUTO || p->phi_route > ADR_PHI_DOUBLING) return fail(nullptr, ADR_ERR_ARG, "unknown phi route");
+    if (p->bc_hi != ADR_BC_DIRICHLET && p->bc_hi != ADR_BC_NEUMANN) return fail(nullptr, ADR_ERR_ARG, "unknown bc_hi");
+    if (p->form != ADR_FORM_FLUX && p->form != ADR_FORM_ADELTA) return fail(nullptr, ADR_ERR_ARG, "unknown form");
+    if (p->bc_hi == ADR_BC_NEUMANN && p->form != ADR_FORM_ADELTA)
+        return fail(nullptr, ADR_ERR_UNSUPPORTED, "Neumann faces are implemented for the a Lap u form");
     if (p->precision != ADR_FP64 && p->precision != ADR_FP32 && p->precision != ADR_MIXED_BF16X3)
         return fail(nullptr, ADR_ERR_ARG, "unknown precision");
     if (p->precision == ADR_MIXED_BF16X3)
@@ -1290,9 +1306,21 @@ adr_status adr_set_coeffs(adr_ctx* c, int instance, const double* a_nodes, const
     for (int m = 0; m < 3; ++m) c->b[m] = (m < c->dim) ? b[m] : 0.0;
     for (int i = 0; i < 4; ++i) c->r[i] = r_poly[i];
     // Eq. (amaxbeta)
-    c->abar = c->p.abar_override > 0 ? c->p.abar_override : c->p.lambda * adr::nodal_max(a_nodes, c->nodes);
+    const bool neumann = c->p.bc_hi == ADR_BC_NEUMANN;
+    double amax = adr::nodal_max(a_nodes, c->nodes);
+    if (neumann) {   // the ring beyond x_mu = 1 lies outside the domain: max over j_mu <= n_mu
+        amax = -INFINITY;
+        const int N1 = c->n[0] + 2, N2 = c->n[1] + 2;
+        const int J3 = c->dim == 3 ? c->n[2] + 1 : 1;
+        for (int j3 = 0; j3 < J3; ++j3)
+            for (int j2 = 0; j2 <= c->n[1]; ++j2)
+                for (int j1 = 0; j1 <= c->n[0]; ++j1)
+                    amax = std::max(amax, a_nodes[(size_t(j3) * N2 + j2) * N1 + j1]);
+    }
+    c->abar = c->p.abar_override > 0 ? c->p.abar_override : c->p.lambda * amax;
     if (!(c->abar > 0)) return fail(c, ADR_ERR_ARG, "lambda * a_max must be positive");
-    for (int m = 0; m < c->dim; ++m) c->beta[m] = c->b[m] + adr::mean_face_jump(a_nodes, c->dim, c->n, m + 1);
+    for (int m = 0; m < c->dim; ++m)   // Eq. (amaxbeta); the a Lap u form of Eq. (adr3dstab) has beta = b
+        c->beta[m] = c->b[m] + (c->p.form == ADR_FORM_ADELTA ? 0.0 : adr::mean_face_jump(a_nodes, c->dim, c->n, m + 1));
 
     // device copy of (a - abar) with padded rows: interior x1 nodes start 16-byte aligned
     const int N1 = c->n[0] + 2, N2 = c->n[1] + 2, N3 = c->dim == 3 ? c->n[2] + 2 : 1;
@@ -1312,7 +1340,7 @@ adr_status adr_set_coeffs(adr_ctx* c, int instance, const double* a_nodes, const
     std::vector<CachedE> cache;
     cache.reserve(9);
     for (int m = 0; m < c->dim; ++m) {
-        c->f[m] = adr::make_factor(c->n[m], c->abar, c->beta[m]);
+        c->f[m] = adr::make_factor(c->n[m], c->abar, c->beta[m], neumann);
         const auto A = adr::factor_dense(c->f[m]);
         for (int ci = 0; ci < 3; ++ci) {
             if (ci == 2 && c->p.scheme != ADR_STABILIZED_LAWSON2) continue;   // e^{alpha tau A_mu}
@@ -1363,7 +1391,8 @@ adr_status adr_set_coeffs(adr_ctx* c, int instance, const double* a_nodes, const
         const double unit = c->fp64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
         const bool guard_ok = c->eig_real && kp * unit <= c->p.kappa_tol;
         if (c->p.phi_route == ADR_PHI_EIGEN && !c->eig_real)
-            return fail(c, ADR_ERR_COMPLEX_SPECTRUM, "cell Peclet number >= 1: A_mu has no real eigenbasis");
+            return fail(c, ADR_ERR_COMPLEX_SPECTRUM,
+                        "no closed-form real eigenbasis of A_mu (cell Peclet number >= 1, or a Neumann face)");
         if (c->p.phi_route == ADR_PHI_EIGEN && !guard_ok) {
             char buf[160];
             std::snprintf(buf, sizeof buf, "eigen route ill-conditioned: prod kappa * u = %.3e > kappa_tol %.3e",

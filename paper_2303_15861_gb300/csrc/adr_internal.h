@@ -15,9 +15,10 @@ namespace adr {
 struct Factor1D {
     int n = 0;
     double h = 0, sub = 0, diag = 0, sup = 0;  // coefficients of u_{i-1}, u_i, u_{i+1}
+    bool neumann = false;                      // homogeneous Neumann end at x = 1 (last row)
 };
 
-Factor1D make_factor(int n, double abar, double beta);
+Factor1D make_factor(int n, double abar, double beta, bool neumann_hi = false);
 std::vector<double> factor_dense(const Factor1D& f);                   // row-major n*n
 std::vector<double> expm_pade13(const std::vector<double>& A, int n);  // e^A, row-major
 
@@ -53,6 +54,8 @@ struct StencilArgs {
                                      // (j3 * (n2 + 2) + j2) * apitch + j1 + 3
     int apitch = 0;                  // row pitch of a: multiple of 4, >= n1 + 5
     int dim = 3, n1 = 1, n2 = 1, n3 = 1;
+    bool neumann = false;            // homogeneous Neumann faces at x_mu = 1: mirror ghosts
+    bool adelta = false;             // (a - abar) Lap u instead of div((a - abar) grad u)
     double inv_h2[3] = {0, 0, 0}, inv_2h[3] = {0, 0, 0};
     double bmb[3] = {0, 0, 0};       // b - beta
     double beta[3] = {0, 0, 0};

@@ -9,12 +9,15 @@
 
 namespace adr {
 
-Factor1D make_factor(int n, double abar, double beta) {
+Factor1D make_factor(int n, double abar, double beta, bool neumann_hi) {
     // Centred second differences of abar*u'' and first differences of beta*u'
-    // with Dirichlet ghosts (Section 5.2); Eq. (linop) restricted to one direction.
+    // with Dirichlet ghosts (Section 5.2); Eq. (linop) restricted to one direction. With a
+    // homogeneous Neumann end at x = 1 (Eq. (adr3d)) the grid is x_i = i/n, i = 1..n, and
+    // the mirror ghost u_{n+1} = u_{n-1} makes the last row abar (2 u_{n-1} - 2 u_n) / h^2.
     Factor1D f;
     f.n = n;
-    f.h = 1.0 / (n + 1);
+    f.neumann = neumann_hi;
+    f.h = neumann_hi ? 1.0 / n : 1.0 / (n + 1);
     const double d2 = abar / (f.h * f.h);
     const double d1 = beta / (2.0 * f.h);
     f.sub = d2 - d1;
@@ -31,6 +34,7 @@ std::vector<double> factor_dense(const Factor1D& f) {
         if (i + 1 < n) A[size_t(i) * n + i + 1] = f.sup;
         if (i > 0) A[size_t(i) * n + i - 1] = f.sub;
     }
+    if (f.neumann && n >= 2) A[size_t(n - 1) * n + n - 2] = -f.diag;   // 2 abar / h^2, no advection
     return A;
 }
 
@@ -138,6 +142,7 @@ std::vector<double> expm_pade13(const std::vector<double>& Ain, int n) {
 Eigen1D eigen_closed_form(const Factor1D& f) {
     Eigen1D e;
     const int n = f.n;
+    if (f.neumann) return e;    // not Toeplitz: no closed form (the exponential-only routes remain)
     const double sp = f.sub * f.sup;
     if (!(sp > 0.0)) return e;  // complex (or defective) spectrum
     e.real = true;

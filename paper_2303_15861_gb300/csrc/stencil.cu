@@ -54,8 +54,9 @@ __global__ void __launch_bounds__(TX * TY) stencil_kernel(StencilArgs<T> p, Coef
         if (!inside || (DIM == 2 && q != 1) || (DIM == 3 && z > n3)) continue;
         const long long za = (DIM == 3) ? (long long)(z + 1) * plane_a : 0;
         ac[q] = __ldg(p.a + za + row_a);
-        if (DIM == 2 || (z >= 0 && z < n3)) {
-            const long long zu = (DIM == 3 ? (long long)z * plane_u : 0) + row_u;
+        const int zs = (DIM == 3 && p.neumann && z == n3) ? n3 - 2 : z;   // Neumann: mirror ghost plane
+        if (DIM == 2 || (zs >= 0 && zs < n3)) {
+            const long long zu = (DIM == 3 ? (long long)zs * plane_u : 0) + row_u;
             uc[q] = __ldg(p.u + zu);
             if (HASLO) lc[q] = __ldg(p.u_lo + zu);
         }
@@ -73,16 +74,21 @@ __global__ void __launch_bounds__(TX * TY) stencil_kernel(StencilArgs<T> p, Coef
         const long long za = (DIM == 3) ? (long long)(z + 1) * plane_a : 0;
         const T* uz = p.u + zu + row_u;
         const T* az = p.a + za + row_a;
+        // Dirichlet ghosts are zero; a Neumann face at x_mu = 1 mirrors u_{n-1} (p.neumann)
         if (i1 > 0) uw[q] = __ldg(uz - 1);
         if (i1 + 1 < n1) ue[q] = __ldg(uz + 1);
+        else if (p.neumann && i1 > 0) ue[q] = uw[q];
         if (i2 > 0) us[q] = __ldg(uz - n1);
         if (i2 + 1 < n2) un[q] = __ldg(uz + n1);
+        else if (p.neumann && i2 > 0) un[q] = us[q];
         if (HASLO) {
             const T* lz = p.u_lo + zu + row_u;
             if (i1 > 0) lw[q] = __ldg(lz - 1);
             if (i1 + 1 < n1) le[q] = __ldg(lz + 1);
+            else if (p.neumann && i1 > 0) le[q] = lw[q];
             if (i2 > 0) ls[q] = __ldg(lz - n1);
             if (i2 + 1 < n2) ln[q] = __ldg(lz + n1);
+            else if (p.neumann && i2 > 0) ln[q] = ls[q];
         }
         aw[q] = __ldg(az - 1);                      // the boundary ring makes these valid
         ae[q] = __ldg(az + 1);
@@ -106,8 +112,12 @@ __global__ void __launch_bounds__(TX * TY) stencil_kernel(StencilArgs<T> p, Coef
         const T dM = DIM == 3 ? (u0 - uc[q]) + (l0 - lc[q]) : T(0);
         const T uC = u0 + l0;
         T F = T(0);
-        const T g = stencil_core<T, DIM>(c, uC, dE, dW, dN, dS, dP, dM, a0 + ae[q], a0 + aw[q], a0 + an[q],
-                                         a0 + as_[q], a0 + ac[q + 2], a0 + ac[q], needF, F);
+        // face sums (a - abar)_C + (a - abar)_nb; the a Lap u form uses 2 (a - abar)_C on every face
+        const T g = p.adelta
+            ? stencil_core<T, DIM>(c, uC, dE, dW, dN, dS, dP, dM, a0 + a0, a0 + a0, a0 + a0, a0 + a0, a0 + a0, a0 + a0,
+                                   needF, F)
+            : stencil_core<T, DIM>(c, uC, dE, dW, dN, dS, dP, dM, a0 + ae[q], a0 + aw[q], a0 + an[q], a0 + as_[q],
+                                   a0 + ac[q + 2], a0 + ac[q], needF, F);
         const long long idx = (DIM == 3 ? (long long)z * plane_u : 0) + row_u;
         uabs = fmaxf(uabs, (float)absval(uC));
 #pragma unroll
@@ -318,6 +328,9 @@ __global__ void __launch_bounds__(256, HASLO ? 2 : 3) stencil_march_kernel(Stenc
 #pragma unroll
                     for (int e = 0; e < NX; ++e) xP[e] = ld4(p.X[e] + zu + plane_u + row_u);
                 }
+            } else if (p.neumann) {          // Neumann face at x3 = 1: mirror ghost plane
+                uP = uM;
+                lP = lM;
             } else {
                 uP = zero4;
                 lP = zero4;
@@ -330,6 +343,7 @@ __global__ void __launch_bounds__(256, HASLO ? 2 : 3) stencil_march_kernel(Stenc
             const float* az = p.a + za + row_a;
             if (i2 > 0) us = ld4(uz - n1);
             if (i2 + 1 < n2) un = ld4(uz + n1);
+            else if (p.neumann && i2 > 0) un = us;          // Neumann face at x2 = 1
             as4 = ld4(az - A1);
             an4 = ld4(az + A1);
             if (lane == 0 && i1 > 0) xw = __ldg(uz - 1);
@@ -340,6 +354,7 @@ __global__ void __launch_bounds__(256, HASLO ? 2 : 3) stencil_march_kernel(Stenc
                 const float* lz = p.u_lo + zu + row_u;
                 if (i2 > 0) ls4 = ld4(lz - n1);
                 if (i2 + 1 < n2) ln4 = ld4(lz + n1);
+                else if (p.neumann && i2 > 0) ln4 = ls4;
                 if (lane == 0 && i1 > 0) yw = __ldg(lz - 1);
                 if (load_e && i1 + 4 < n1) ye = __ldg(lz + 4);
             }
@@ -355,6 +370,7 @@ __global__ void __launch_bounds__(256, HASLO ? 2 : 3) stencil_march_kernel(Stenc
         if (inside) {
             if (lane != 0) { xw = sw_u; aw = sw_a; yw = sw_l; }
             if (lane != 31 && i1 + 4 < n1) { xe = se_u; ae = se_a; ye = se_l; }
+            if (p.neumann && i1 + 4 >= n1) { xe = uC.z; ye = lC.z; }   // Neumann face at x1 = 1: mirror
             float U[4], L[4], Aa[4], US[4], UN[4], LS[4], LN[4], AS[4], AN[4], UM[4], UP[4], LM[4], LP[4], AM[4], AP[4];
             f4arr(uC, U); f4arr(lC, L); f4arr(aC, Aa);
             f4arr(us, US); f4arr(un, UN); f4arr(ls4, LS); f4arr(ln4, LN); f4arr(as4, AS); f4arr(an4, AN);
@@ -370,8 +386,11 @@ __global__ void __launch_bounds__(256, HASLO ? 2 : 3) stencil_march_kernel(Stenc
                 const float dP = (UP[k] - uk) + (LP[k] - lk), dM = (uk - UM[k]) + (lk - LM[k]);
                 const float uF = uk + lk;
                 float F = 0.f;
-                const float g = stencil_core<float, 3>(c, uF, dE, dW, dN, dS, dP, dM, ak + AX[k + 2], ak + AX[k],
-                                                       ak + AN[k], ak + AS[k], ak + AP[k], ak + AM[k], needF, F);
+                const float g = p.adelta
+                    ? stencil_core<float, 3>(c, uF, dE, dW, dN, dS, dP, dM, ak + ak, ak + ak, ak + ak, ak + ak, ak + ak,
+                                             ak + ak, needF, F)
+                    : stencil_core<float, 3>(c, uF, dE, dW, dN, dS, dP, dM, ak + AX[k + 2], ak + AX[k], ak + AN[k],
+                                             ak + AS[k], ak + AP[k], ak + AM[k], needF, F);
                 uabs = fmaxf(uabs, fabsf(uF));
 #pragma unroll
                 for (int j = 0; j < NOUT; ++j) {
@@ -447,6 +466,8 @@ cudaError_t launch_impl(const StencilArgs<T>& p, cudaStream_t s) {
                        (reinterpret_cast<uintptr_t>(p.a) % 16 == 0);
         for (int j = 0; j < p.nout; ++j) aligned = aligned && (reinterpret_cast<uintptr_t>(p.out[j]) % 16 == 0);
         for (int e = 0; e < p.nx; ++e) aligned = aligned && (reinterpret_cast<uintptr_t>(p.X[e]) % 16 == 0);
+        // the vectorised 2-D kernel has Dirichlet ghosts and the flux form only
+        if (p.dim == 2 && (p.neumann || p.adelta)) aligned = false;
         if (p.u_lo) aligned = aligned && (reinterpret_cast<uintptr_t>(p.u_lo) % 16 == 0);
         if (aligned) {
             dim3 g4((p.n1 / 4 + 31) / 32, (p.n2 + 7) / 8, p.dim == 3 ? (p.n3 + ZV - 1) / ZV : 1);

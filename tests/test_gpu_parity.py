@@ -304,3 +304,106 @@ def test_lambda_scan_errors_match_oracle():
     best2, errs2 = adr.adr_lambda_scan(dims, tau, "etd2rk", "fp64", a, bb, r, u0, m, n_lambdas=5)
     assert abs(errs2[0][0] - adr.adr_stability_bound("etd2rk")) < 1e-12 and errs2[-1][0] == 1.0
     assert all(np.isfinite(e) for _, e in errs2) and best2 == min(errs2, key=lambda t: t[1])[0]
+
+
+
+# ------------------------------------------- the paper's 3-D problem form (Eq. (adr3d))
+# a Lap u, Dirichlet faces at x_mu = 0, Neumann faces at x_mu = 1 (mirror ghosts, h = 1/n).
+def mixed_case(dims, seed=21):
+    rng = np.random.default_rng(seed)
+    a = 0.05 + 0.1 * rng.random(tuple(n + 2 for n in dims[::-1]))
+    b = (-1.0, 0.6, -0.3)[: len(dims)] + (0.0,) * (3 - len(dims))
+    u0 = rng.standard_normal(tuple(dims[::-1])) * 0.1 + 0.3
+    return a, b, (0.0, 1.0, 0.0, 1.0), u0
+
+
+def mixed_context(dims, tau, scheme, prec, a, b, r, **kw):
+    ctx = adr.Context(dims, tau, scheme, prec, bc="mixed", form="adelta", **kw)
+    ctx.set_coeffs(a, b, r)
+    return ctx
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+@pytest.mark.parametrize("dims", [(24, 20, 18), (25, 19, 17), (30, 26), (33, 21)])
+def test_mixed_adelta_stencil_F_and_g(dims, prec, tol):
+    a, b, r, u0 = mixed_case(dims)
+    ctx = mixed_context(dims, 1e-3, "lawson4", prec, a, b, r)
+    dt = DTYPES[prec]
+    _, u = guarded(u0.shape, dt, u0)
+    fF, F = guarded(u0.shape, dt)
+    fg, g = guarded(u0.shape, dt)
+    ctx.eval_rhs(u, F, g)
+    torch.cuda.synchronize()
+    check_guards(fF)
+    check_guards(fg)
+    prob = O.ADRProblem(dims, a, b, r, bc="mixed", form="adelta")
+    uin = u.double().cpu().numpy()
+    assert O.rel_l2(F.cpu().numpy(), prob.F(uin)) < tol
+    assert O.rel_l2(g.cpu().numpy(), prob.g(uin)) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+def test_adelta_form_with_dirichlet_faces(prec, tol):
+    dims = (24, 20, 18)
+    a, b, r, u0 = mixed_case(dims)
+    ctx = adr.Context(dims, 1e-3, "lawson4", prec, form="adelta")
+    ctx.set_coeffs(a, b, r)
+    dt = DTYPES[prec]
+    _, u = guarded(u0.shape, dt, u0)
+    _, F = guarded(u0.shape, dt)
+    ctx.eval_rhs(u, F, None)
+    torch.cuda.synchronize()
+    prob = O.ADRProblem(dims, a, b, r, form="adelta")
+    assert O.rel_l2(F.cpu().numpy(), prob.F(u.double().cpu().numpy())) < tol
+
+
+@pytest.mark.parametrize("scheme", ["lawson4", "lawson2a", "lawson2b", "stabilized_lawson2", "lawson_euler"])
+def test_mixed_adelta_lawson_schemes_match_oracle(scheme):
+    dims = (24, 20, 18)
+    a, b, r, u0 = mixed_case(dims)
+    tau, m = 2e-3, 6
+    ctx = mixed_context(dims, tau, scheme, "fp64", a, b, r)
+    fu, u = guarded(u0.shape, torch.float64, u0)
+    ctx.integrate(u, 0.0, m * tau, m)
+    torch.cuda.synchronize()
+    check_guards(fu)
+    ref = O.solve(dims, a, b, r, u0, tau, m, scheme, bc="mixed", form="adelta")
+    assert O.rel_l2(u.cpu().numpy(), ref) < 1e-12
+
+
+@pytest.mark.parametrize("scheme", ["etd2rk", "erk2p1"])
+def test_mixed_adelta_phi_schemes_on_the_doubling_route(scheme):
+    """No closed-form eigenbasis with Neumann rows: the phi schemes take the doubling route."""
+    dims = (10, 9, 8)
+    a, b, r, u0 = mixed_case(dims)
+    tau, m = 2e-3, 4
+    ctx = mixed_context(dims, tau, scheme, "fp64", a, b, r)
+    assert ctx.phi_route()[0] == "doubling"
+    fu, u = guarded(u0.shape, torch.float64, u0)
+    ctx.integrate(u, 0.0, m * tau, m)
+    torch.cuda.synchronize()
+    check_guards(fu)
+    ref = O.solve(dims, a, b, r, u0, tau, m, scheme, bc="mixed", form="adelta", phi_route="dense")
+    assert O.rel_l2(u.cpu().numpy(), ref) < 1e-12
+
+
+def test_e4_workload_fp64_and_mixed_precision_against_oracle():
+    """The paper's three-dimensional experiment at N = 60 (b = -1), a few Lawson2a steps:
+    FP64 to 1e-12, the tensor-core path to 1e-6."""
+    w = W.config_e4(n=60, b=-1.0, scheme="lawson2a", m=32)
+    steps = 4
+    ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, steps, w.scheme, bc="mixed", form="adelta")
+    for prec, tol in (("fp64", 1e-12), ("bf16x3", 1e-6)):
+        ctx = mixed_context(w.dims, w.tau, w.scheme, prec, w.a_nodes, w.b, w.r_poly)
+        u = torch.tensor(w.u0, dtype=torch.float64 if prec == "fp64" else torch.float32, device="cuda")
+        ctx.integrate(u, 0.0, steps * w.tau, steps)
+        ctx.synchronize()
+        err = O.rel_l2(u.double().cpu().numpy(), ref)
+        print(f"E4 N=60 lawson2a {prec}: {err:.3e}")
+        assert err < tol, (prec, err)
+
+
+def test_neumann_faces_need_the_adelta_form():
+    with pytest.raises(adr.AdrError) as e:
+        adr.Context((16, 16), 1e-3, "lawson4", "fp64", bc="mixed", form="flux")
+    assert e.value.status == 8
