@@ -354,6 +354,113 @@ class MatrixFunctions:
         return out
 
 
+def phi_complex(k: int, z):
+    """phi_k of complex arguments (elementwise, FP64): the Taylor series for |z| < 1,
+    the closed forms e^z, (e^z - 1)/z, (e^z - 1 - z)/z^2 elsewhere."""
+    z = np.asarray(z, dtype=np.complex128)
+    if k == 0:
+        return np.exp(z)
+    out = np.empty_like(z)
+    small = np.abs(z) < 1.0
+    zs = z[small]
+    acc = np.zeros_like(zs)
+    term = np.full_like(zs, 1.0 / factorial(k))
+    for j in range(0, 30):
+        acc = acc + term
+        term = term * zs / (j + k + 1)
+    out[small] = acc
+    zl = z[~small]
+    e = np.expm1(zl.real) * np.exp(1j * zl.imag) + (np.exp(1j * zl.imag) - 1.0)   # e^z - 1
+    out[~small] = e / zl if k == 1 else (e - zl) / (zl * zl)
+    return out
+
+
+class PeriodicProblem:
+    """The paper's two-dimensional experiment form (Section 5.1, Eq. (ad2d)):
+    u_t = div(a grad u) + div(b u) + r(u) on a periodic box of side L, with a diagonal
+    diffusion tensor a = diag(a_11, ..., a_dd) and a velocity field b(x), both sampled at the
+    nodes x_j = x0 + j L/n, discretised by the Fourier pseudospectral method (n modes per
+    direction; first derivatives D_mu with the Nyquist wavenumber set to zero).
+
+    A of Eq. (linop) = lambda sum_mu a_mumu^max D_mu^2 + beta . D with a_mumu^max the nodal
+    maximum and beta_mu the mean of b_mu (Eq. (amaxbeta); d_mu a_mumu averages to zero over a
+    period). A is diagonal in Fourier space with symbol
+    s(k) = -lambda sum_mu a^max_mu k_mu^2 + i beta . k.
+    a_diag, b_field: d nodal arrays each, numpy shape (n_d, ..., n_1)."""
+
+    def __init__(self, dims, L, a_diag, b_field, r_poly, lam=1.0):
+        self.dims = tuple(int(n) for n in dims)
+        self.d = len(self.dims)
+        self.L = float(L)
+        shape = self.dims[::-1]
+        self.a = [np.asarray(x, dtype=np.float64).reshape(shape) for x in a_diag]
+        self.bf = [np.asarray(x, dtype=np.float64).reshape(shape) for x in b_field]
+        self.r = tuple(float(c) for c in r_poly)
+        self.lam = float(lam)
+        self.amax = np.array([self.lam * float(x.max()) for x in self.a])
+        self.beta = np.array([float(x.mean()) for x in self.bf])
+        self.k = []
+        for mu in range(1, self.d + 1):
+            n = self.dims[mu - 1]
+            km = np.fft.fftfreq(n, d=1.0 / n) * (2.0 * np.pi / self.L)
+            if n % 2 == 0:
+                km[n // 2] = 0.0                      # Nyquist: no first derivative
+            shp = [1] * self.d
+            shp[self.d - mu] = n
+            self.k.append(km.reshape(shp))
+        self.symbol = sum(-self.amax[mu] * self.k[mu] ** 2 + 1j * self.beta[mu] * self.k[mu]
+                          for mu in range(self.d))
+
+    def D(self, u, mu):
+        """Pseudospectral first derivative along x_mu (mu = 1..d)."""
+        return np.real(np.fft.ifftn(1j * self.k[mu - 1] * np.fft.fftn(u)))
+
+    def reaction(self, u):
+        r0, r1, r2, r3 = self.r
+        return r0 + u * (r1 + u * (r2 + u * r3))
+
+    def F(self, u):
+        """sum_mu D_mu (a_mumu D_mu u + b_mu u) + r(u)."""
+        return sum(self.D(self.a[mu - 1] * self.D(u, mu) + self.bf[mu - 1] * u, mu)
+                   for mu in range(1, self.d + 1)) + self.reaction(u)
+
+    def g(self, u):
+        """Eq. (nonlin): sum_mu D_mu ((a_mumu - lambda a^max) D_mu u + (b_mu - beta_mu) u) + r(u)."""
+        return sum(self.D((self.a[mu - 1] - self.amax[mu - 1]) * self.D(u, mu)
+                          + (self.bf[mu - 1] - self.beta[mu - 1]) * u, mu)
+                   for mu in range(1, self.d + 1)) + self.reaction(u)
+
+    def A_apply(self, u):
+        return np.real(np.fft.ifftn(self.symbol * np.fft.fftn(u)))
+
+
+class PeriodicOps:
+    """The operations every integrator needs, for the periodic pseudospectral problem: the
+    matrix functions of A are pointwise multipliers on the Fourier coefficients."""
+
+    def __init__(self, prob: PeriodicProblem, tau: float):
+        self.prob = prob
+        self.tau = float(tau)
+
+    def g(self, u):
+        return self.prob.g(u)
+
+    def F(self, u):
+        return self.prob.F(u)
+
+    def expA(self, c, v):
+        return np.real(np.fft.ifftn(np.exp(c * self.tau * self.prob.symbol) * np.fft.fftn(v)))
+
+    def phi(self, k, c, v):
+        return np.real(np.fft.ifftn(phi_complex(k, c * self.tau * self.prob.symbol) * np.fft.fftn(v)))
+
+
+def solve_periodic(dims, L, a_diag, b_field, r_poly, u0, tau, m, scheme, lam=1.0):
+    """FP64 oracle solution of the periodic problem after m steps of `scheme`."""
+    prob = PeriodicProblem(dims, L, a_diag, b_field, r_poly, lam=lam)
+    return integrate(PeriodicOps(prob, tau), u0, m, scheme)
+
+
 class GridOps:
     """The operations every integrator needs, for an ADR grid problem. phi_route "eigen"
     (the joint eigenbasis) or "dense" (the augmented-matrix exponential, small grids, any

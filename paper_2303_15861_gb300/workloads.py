@@ -189,3 +189,22 @@ def config_e4(n=60, b=-0.01, scheme="lawson2a", m=64, T=0.25):
     return Workload(name=f"e4_{n}_{scheme}_b{b}", dims=(n, n, n), a_nodes=a, b=(b, b, b),
                     r_poly=REACTION_U_1PU2, u0=np.ascontiguousarray(u0), tau=T / m, m=int(m), scheme=scheme,
                     extra=dict(bc="mixed", form="adelta"))
+
+
+def config_e3(n=256, scheme="lawson2a", m=256, T=4.0):
+    """The paper's two-dimensional experiment (Section 5.1, Eq. (ad2d)): periodic on
+    (-3 pi, 3 pi)^2, a = diag(1/2 + sin^2 x1 sin^2 x2 / 6, 1/2 + cos^2 x1 cos^2 x2 / 6),
+    b = (sin^2 x1 / 5, sin^2 x2 / 5), r(u) = u (1 - u) / 4, u0 = exp(-(x1^2 + x2^2)), on
+    n x n Fourier nodes x_j = -3 pi + j 6 pi / n. Returns (workload, L, a_diag, b_field)."""
+    L = 6.0 * np.pi
+    x = -3.0 * np.pi + np.arange(n, dtype=np.float64) * (L / n)
+    X2, X1 = np.meshgrid(x, x, indexing="ij")
+    a11 = 0.5 + np.sin(X1) ** 2 * np.sin(X2) ** 2 / 6.0
+    a22 = 0.5 + np.cos(X1) ** 2 * np.cos(X2) ** 2 / 6.0
+    b1 = np.sin(X1) ** 2 / 5.0
+    b2 = np.sin(X2) ** 2 / 5.0
+    u0 = np.exp(-(X1 ** 2 + X2 ** 2))
+    w = Workload(name=f"e3_{n}_{scheme}", dims=(n, n), a_nodes=None, b=(0.0, 0.0, 0.0),
+                 r_poly=(0.0, 0.25, -0.25, 0.0), u0=np.ascontiguousarray(u0), tau=T / m, m=int(m),
+                 scheme=scheme, extra=dict(periodic=True, L=L))
+    return w, L, [a11, a22], [b1, b2]

@@ -442,3 +442,77 @@ def test_e4_workload_recipe():
     assert abs(w.a_nodes.max() - 0.1) < 1e-3 and w.u0.max() <= 1.0 + 1e-12
     prob = O.ADRProblem(w.dims, w.a_nodes, w.b, w.r_poly, bc="mixed", form="adelta")
     assert np.allclose(prob.beta, w.b[:3]) and prob.h[0] == 1.0 / 16
+
+
+# ------------------------------------------------ periodic Fourier pseudospectral problem
+def _periodic_case(dims, seed=6):
+    rng = np.random.default_rng(seed)
+    shape = tuple(dims[::-1])
+    a = [0.4 + 0.2 * rng.random(shape) for _ in dims]
+    b = [0.3 * rng.standard_normal(shape) for _ in dims]
+    return a, b
+
+
+@pytest.mark.parametrize("dims", [(16, 12), (8, 6, 10)])
+def test_periodic_derivatives_exact_for_trigonometric_polynomials(dims):
+    """Band-limited u = prod sin(2 pi p_mu x_mu / L + c_mu): D_mu and F with constant a and b
+    (a Lap u + b . grad u) are exact."""
+    L = 5.0
+    d = len(dims)
+    axes = [np.arange(n) * L / n for n in dims]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")[::-1]
+    p = [1, 2, 3][:d]
+    c = [0.3, -1.1, 0.7][:d]
+    f = [np.sin(2 * np.pi * p[m] * grids[m] / L + c[m]) for m in range(d)]
+    fp = [2 * np.pi * p[m] / L * np.cos(2 * np.pi * p[m] * grids[m] / L + c[m]) for m in range(d)]
+    fpp = [-(2 * np.pi * p[m] / L) ** 2 * f[m] for m in range(d)]
+    u = np.prod(f, axis=0)
+    shape = tuple(dims[::-1])
+    a = [np.full(shape, 0.7), np.full(shape, 0.4), np.full(shape, 1.3)][:d]
+    b = [np.full(shape, 0.9), np.full(shape, -0.5), np.full(shape, 0.2)][:d]
+    prob = O.PeriodicProblem(dims, L, a, b, (0.0, 0.0, 0.0, 0.0))
+    others = lambda m, g: np.prod([g[m]] + [f[q] for q in range(d) if q != m], axis=0)
+    for mu in range(1, d + 1):
+        assert np.abs(prob.D(u, mu) - others(mu - 1, fp)).max() < 1e-12
+    exact = sum(a[m][0].flat[0] * others(m, fpp) + b[m].flat[0] * others(m, fp) for m in range(d))
+    assert np.abs(prob.F(u) - exact).max() < 1e-11 * np.abs(exact).max()
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_periodic_matrix_functions_match_dense_exponentials(k):
+    """The Fourier multipliers e^{tau s}, phi_k(tau s) against the dense augmented-matrix
+    exponential of the matrix of A (assembled column by column from A_apply)."""
+    dims = (8, 6)
+    a, b = _periodic_case(dims)
+    prob = O.PeriodicProblem(dims, 4.0, a, b, (0.0, 0.2, 0.1, 0.0), lam=0.8)
+    N = 48
+    A = np.stack([prob.A_apply(np.eye(N)[j].reshape(6, 8)).ravel() for j in range(N)], axis=1)
+    tau = 0.05
+    v = np.random.default_rng(2).standard_normal((6, 8))
+    Z = np.zeros((N + 2, N + 2))
+    Z[:N, :N] = tau * A
+    Z[:N, N] = v.ravel()
+    Z[N, N + 1] = 1.0
+    big = O.expm(Z)
+    ref = (O.expm(tau * A) @ v.ravel()) if k == 0 else big[:N, N + k - 1]
+    ops = O.PeriodicOps(prob, tau)
+    got = (ops.expA(1.0, v) if k == 0 else ops.phi(k, 1.0, v)).ravel()
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_periodic_splitting_and_coefficients():
+    """g = F - A u, a_max = lambda max a_mumu, beta = mean b (the d a term averages out)."""
+    dims = (12, 10)
+    a, b = _periodic_case(dims)
+    prob = O.PeriodicProblem(dims, 3.0, a, b, (0.1, -0.3, 0.2, 0.05), lam=0.6)
+    u = np.random.default_rng(1).standard_normal((10, 12))
+    assert np.linalg.norm(prob.g(u) - (prob.F(u) - prob.A_apply(u))) <= 1e-12 * np.linalg.norm(prob.F(u))
+    assert np.allclose(prob.amax, [0.6 * x.max() for x in a]) and np.allclose(prob.beta, [x.mean() for x in b])
+
+
+def test_e3_workload_recipe():
+    from paper_2303_15861_gb300 import workloads as W
+    w, L, a, b = W.config_e3(n=64, m=16)
+    prob = O.PeriodicProblem(w.dims, L, a, b, w.r_poly)
+    assert abs(prob.amax[0] - (0.5 + 1 / 6)) < 1e-2 and abs(prob.beta[0] - 0.1) < 1e-12
+    assert abs(w.u0.max() - 1.0) < 1e-12
