@@ -45,7 +45,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--workload", choices=["3d", "batch2d"] + sorted(GRID_WORKLOADS), default="3d",
                    help="3d: the 256^3 Lawson4 workload (default); batch2d: 512 uneven 2-D ETD2RK instances; "
-                        "c1-*, c2, c5-*, e4-*: the other single-grid workloads")
+                        "c1-*, c2, c5-*, e4-*, e3-*: the other single-grid workloads")
     p.add_argument("--check", action="store_true",
                    help="single-grid workloads: also measure the error (oracle for c1/c2, FP64 GPU at tau/4 for c5)")
     p.add_argument("--ncu-steps", type=int, default=0,
@@ -378,6 +378,10 @@ GRID_WORKLOADS = {
     # the paper's three-dimensional experiment: N = 60, T = 1/4, b = -0.01, 2^8 steps
     "e4-lawson2a": (lambda W: W.config_e4(n=60, b=-0.01, scheme="lawson2a", m=256), "bf16x3"),
     "e4-stabilized-lawson2": (lambda W: W.config_e4(n=60, b=-0.01, scheme="stabilized_lawson2", m=256), "bf16x3"),
+    # the paper's two-dimensional experiment: periodic, 256 x 256 Fourier nodes, T = 4, 2^8 steps
+    "e3-lawson2a": (lambda W: W.config_e3(n=256, scheme="lawson2a"), "fp64"),
+    "e3-etd2rk": (lambda W: W.config_e3(n=256, scheme="etd2rk"), "fp64"),
+    "e3-lawson4": (lambda W: W.config_e3(n=256, scheme="lawson4"), "fp64"),
 }
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (nominal; no measured figure on this machine)
 
@@ -394,6 +398,9 @@ def ours_grid(args):
     adr.load_library()
     make, default_prec = GRID_WORKLOADS[args.workload]
     w = make(W)
+    periodic = isinstance(w, tuple)      # (workload, L, a_diag, b_field) of a periodic problem
+    if periodic:
+        w, L, a_diag, b_field = w
     prec = args.precision if args.precision != "bf16x3" or default_prec == "bf16x3" else default_prec
     if args.workload.startswith(("c1", "c2")):
         prec = "fp64" if args.precision == "bf16x3" else args.precision
@@ -406,10 +413,16 @@ def ours_grid(args):
             "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3+f32"}[prec], "data": "synthetic",
             "config": {"workload": w.name, "grid": list(w.dims), "scheme": w.scheme, "precision": prec,
                        "tau": w.tau, "time_steps_per_bench_step": w.m, "b": list(w.b[:len(w.dims)])}}
+    if periodic:
+        base["config"].update(periodic=True, length=L)
     with torch.cuda.stream(stream):
         try:
-            ctx = adr.Context(w.dims, w.tau, w.scheme, prec, stream=stream, **form_kw)
-            ctx.set_coeffs(w.a_nodes, w.b, w.r_poly)
+            if periodic:
+                ctx = adr.Context(w.dims, w.tau, w.scheme, prec, stream=stream, periodic=True, length=L)
+                ctx.set_coeffs_periodic(a_diag, b_field, w.r_poly)
+            else:
+                ctx = adr.Context(w.dims, w.tau, w.scheme, prec, stream=stream, **form_kw)
+                ctx.set_coeffs(w.a_nodes, w.b, w.r_poly)
         except adr.AdrError as e:
             line = dict(base, unavailable=str(e))
             print(json.dumps(line), flush=True)
@@ -459,6 +472,9 @@ def ours_grid(args):
                 ref = ur.cpu().numpy()
                 rc.close()
                 acc = {"reference": "FP64 GPU path at tau/4"}
+            elif periodic:
+                ref = O.solve_periodic(w.dims, L, a_diag, b_field, w.r_poly, w.u0, w.tau, w.m, w.scheme)
+                acc = {"reference": "FP64 oracle"}
             else:
                 ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, w.m, w.scheme, **form_kw)
                 acc = {"reference": "FP64 oracle"}
@@ -468,7 +484,18 @@ def ours_grid(args):
     value = N * w.m * args.steps / (ms * 1e-3)
     per_step_us = 1e3 * ms / (args.steps * w.m)
     n = w.dims[0]
-    if prec == "bf16x3":
+    if periodic:
+        # Fourier multiplier op (FFTs, pointwise product, inverse FFTs): its algorithmic bytes are
+        # one read of x and of the complex multiplier (2 words a point) and one write of y
+        c_ms = statistics.mean(kinds.get(7, [float("nan")]))
+        es = dt.itemsize
+        ach = (4 * es * N) / (c_ms * 1e-3) / 1e9
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = json.load(f)["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "kernel": "Fourier multiplier (fft_axis_kernel passes + pointwise)",
+                "launch_ms": c_ms, "peak_source": "measured HBM copy"}
+    elif prec == "bf16x3":
         c_ms = statistics.mean(kinds.get(4, [float("nan")]))
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             peak = json.load(f)["bf16_tflops_sustained"] / 6.0

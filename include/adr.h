@@ -100,7 +100,28 @@ typedef struct {
     int phi_route;         /* adr_phi_route: how phi_k(tau A) is applied (single grids)     */
     int bc_hi;             /* adr_bc: the boundary condition on the faces x_mu = 1          */
     int form;              /* adr_form: the diffusion term                                  */
+    int periodic;          /* 1: periodic Fourier pseudospectral context (see below)        */
+    double length;         /* periodic: side of the periodic box (all directions)           */
 } adr_params;
+
+/* Periodic Fourier pseudospectral contexts (periodic = 1; the discretisation of the paper's
+ * two-dimensional experiment, Section 5.1, Eq. (ad2d)):
+ *     u_t = div(a grad u) + div(b u) + r(u)
+ * on a periodic box of side `length` with a diagonal diffusion tensor a = diag(a_11, ..., a_dd)
+ * and a velocity field b(x), both given at the nodes x_j = x0 + j length / n_mu. Derivatives
+ * are spectral (Nyquist wavenumber 0); A = lambda sum_mu a_mumu^max D_mu^2 + beta . D with
+ * a^max the nodal maxima and beta_mu the mean of b_mu (Eqs. (linop), (amaxbeta)). A is
+ * diagonal in Fourier space, so e^{c tau A} and phi_k(tau A) are multipliers on the Fourier
+ * coefficients (ADR_PHI_FOURIER). n_mu must be powers of two in [2, 1024]; ADR_FP64 or
+ * ADR_FP32; single grids; bc_hi and form at their defaults. The coefficients are set with
+ * adr_set_coeffs_periodic; all other entry points work as for finite-difference contexts. */
+adr_status adr_set_coeffs_periodic(adr_ctx* ctx, const double* a_diag, const double* b_field,
+                                   const double r_poly[4]);
+/*   a_diag:  host, dim arrays of N doubles, a_11 then a_22 (then a_33), x1 fastest.
+ *   b_field: host, dim arrays of N doubles, b_1 then b_2 (then b_3).
+ *   r_poly:  host, 4 doubles, r(u) = r0 + r1 u + r2 u^2 + r3 u^3.
+ * Computes a^max, beta, the symbol of A and the Fourier multipliers e^{c tau s} (c = 1/2, 1,
+ * alpha), phi_1(tau s), phi_2(tau s) on the host in FP64 and uploads them. Synchronous. */
 
 /* Boundary conditions on the faces x_mu = 1 (the faces x_mu = 0 are always homogeneous
  * Dirichlet). ADR_BC_NEUMANN: homogeneous Neumann, as in the paper's three-dimensional
@@ -126,7 +147,8 @@ typedef enum { ADR_FORM_FLUX = 0, ADR_FORM_ADELTA = 1 } adr_form;
  *     Single-grid contexts only; batched contexts use the eigen route.
  *   ADR_PHI_AUTO: the eigen route when it is available and passes the kappa guard, the
  *     doubling route otherwise. */
-typedef enum { ADR_PHI_AUTO = 0, ADR_PHI_EIGEN = 1, ADR_PHI_DOUBLING = 2 } adr_phi_route;
+typedef enum { ADR_PHI_AUTO = 0, ADR_PHI_EIGEN = 1, ADR_PHI_DOUBLING = 2,
+               ADR_PHI_FOURIER = 3 /* periodic contexts: multipliers on Fourier coefficients */ } adr_phi_route;
 
 /* Create a context for one grid, or for a batch of independent 2-D instances.
  * cuda_stream is a cudaStream_t (NULL = legacy default stream) on the current device.
@@ -189,7 +211,8 @@ adr_status adr_apply_phi(adr_ctx* ctx, int k, const void* v_dev, void* y_dev);
 adr_status adr_synchronize(adr_ctx* ctx);
 
 /* Host-side facts of the current operator: kappa(V_mu) per direction (0 when the
- * spectrum is complex), lambda*a_max, and beta. Any pointer may be NULL. */
+ * spectrum is complex), lambda*a_max, and beta. Any pointer may be NULL. Periodic
+ * contexts: kappa = 1 (the Fourier basis is unitary), the largest lambda*a_mumu^max. */
 adr_status adr_get_info(const adr_ctx* ctx, double kappa[3], double* abar, double beta[3]);
 
 /* The same facts for one instance of a batched context (instance 0 of a single-grid
@@ -208,7 +231,8 @@ adr_status adr_get_batch_plan(const adr_ctx* ctx, int mode, int* tile_edge, int*
  * operation (no graph). Writes, for the i-th operation, its duration in ms[i] and its kind
  * in kind[i] (0 memset, 1 max-abs reduction, 2 stencil, 3 SIMT contraction,
  * 4 tensor-core contraction, 5 tensor-core contraction in the precise four-slice
- * configuration) and the count in *n_ops. Synchronous. ADR_ERR_ARG if the step
+ * configuration; periodic contexts: 6 pseudospectral right-hand side, 7 Fourier multiplier,
+ * each several kernels: FFTs and pointwise passes) and the count in *n_ops. Synchronous. ADR_ERR_ARG if the step
  * has more than max_ops operations. */
 adr_status adr_profile_step(adr_ctx* ctx, void* u_dev, int max_ops, float* ms, int* kind, int* n_ops);
 
@@ -246,13 +270,14 @@ adr_status adr_stability_bound(int scheme, double* lambda_min);
  * relative l2 error against a reference: the same semidiscrete problem integrated by
  * Lawson4 in FP64 with step tau / ref_substeps (<= 0 selects 8). Writes the errors
  * (INFINITY where a lambda is refused) and the lambda with the smallest error. Runs on
- * cuda_stream and synchronises it; allocates its own device buffers. */
+ * cuda_stream and synchronises it; allocates its own device buffers. Finite-difference
+ * single grids only (ADR_ERR_ARG for batched or periodic params). */
 adr_status adr_lambda_scan(const adr_params* p, const double* a_nodes, const double b[3],
                            const double r_poly[4], const double* u0_host, int m, int n_lambdas,
                            const double* lambdas, int ref_substeps, void* cuda_stream,
                            double* errors, double* best_lambda);
 
-/* Number of kernels one adr_step launches (for launch accounting). */
+/* Number of kernels one adr_step launches (for launch accounting; memsets not counted). */
 int adr_kernels_per_step(const adr_ctx* ctx);
 
 /* The phi route a context uses after adr_set_coeffs (ADR_PHI_EIGEN or ADR_PHI_DOUBLING; 0

@@ -21,7 +21,7 @@ STATUS = {0: "ADR_OK", 1: "ADR_ERR_ARG", 2: "ADR_ERR_ALLOC", 3: "ADR_ERR_CUDA",
           4: "ADR_ERR_ILL_CONDITIONED", 5: "ADR_ERR_COMPLEX_SPECTRUM", 6: "ADR_ERR_TIMEOUT",
           7: "ADR_ERR_STATE", 8: "ADR_ERR_UNSUPPORTED"}
 PRECISION = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x3": 3}
-PHI_ROUTE = {"auto": 0, "eigen": 1, "doubling": 2}
+PHI_ROUTE = {"auto": 0, "eigen": 1, "doubling": 2, "fourier": 3}
 BC = {"dirichlet": 0, "mixed": 1}          # faces x_mu = 1: Dirichlet, or Neumann ("mixed")
 FORM = {"flux": 0, "adelta": 1}
 SCHEME = {"lawson_euler": 0, "etd2rk": 1, "lawson4": 2, "exponential_euler": 3, "erk2p1": 4,
@@ -39,7 +39,7 @@ class adr_params(C.Structure):
                 ("abar_override", C.c_double), ("tau", C.c_double), ("scheme", C.c_int),
                 ("precision", C.c_int), ("kappa_tol", C.c_double), ("batch", C.c_int),
                 ("n_batch", C.POINTER(C.c_int)), ("batch_tile", C.c_int), ("phi_route", C.c_int),
-                ("bc_hi", C.c_int), ("form", C.c_int)]
+                ("bc_hi", C.c_int), ("form", C.c_int), ("periodic", C.c_int), ("length", C.c_double)]
 
 
 _lib = None
@@ -58,6 +58,7 @@ def load_library(path: str = LIB_PATH):
     sig = {
         "adr_create": (ip, [C.POINTER(adr_params), vp, C.POINTER(vp)]),
         "adr_set_coeffs": (ip, [vp, ip, dp, dp, dp]),
+        "adr_set_coeffs_periodic": (ip, [vp, dp, dp, dp]),
         "adr_step": (ip, [vp, vp, C.c_double]),
         "adr_integrate": (ip, [vp, vp, C.c_double, C.c_double, ip]),
         "adr_integrate_host": (ip, [vp, vp, C.c_double, C.c_double, ip]),
@@ -117,9 +118,10 @@ def _stream_handle(stream):
 # ------------------------------------------------------------------- C entry points
 def adr_create(dims, tau, scheme="lawson4", precision="fp64", lam=1.0, abar_override=0.0,
                kappa_tol=0.0, stream=None, batch_dims=None, batch_tile=0, phi_route="auto", bc="dirichlet",
-               form="flux"):
+               form="flux", periodic=False, length=0.0):
     """dims: grid of a single-grid context; batch_dims: [(n1, n2), ...] of a batched 2-D
-    context (dims is then ignored)."""
+    context (dims is then ignored); periodic=True with the box side `length`: a periodic
+    Fourier pseudospectral context (coefficients through adr_set_coeffs_periodic)."""
     lib = load_library()
     p = adr_params()
     nb = None
@@ -144,6 +146,8 @@ def adr_create(dims, tau, scheme="lawson4", precision="fp64", lam=1.0, abar_over
     p.phi_route = PHI_ROUTE[phi_route] if isinstance(phi_route, str) else int(phi_route)
     p.bc_hi = BC[bc] if isinstance(bc, str) else int(bc)
     p.form = FORM[form] if isinstance(form, str) else int(form)
+    p.periodic = 1 if periodic else 0
+    p.length = float(length)
     ctx = C.c_void_p()
     _check(lib.adr_create(C.byref(p), _stream_handle(stream), C.byref(ctx)))
     return ctx
@@ -154,6 +158,16 @@ def adr_set_coeffs(ctx, instance, a_nodes, b, r_poly):
     bb, bp = _dbl(list(b) + [0.0] * (3 - len(b)), 3)
     rr, rp = _dbl(r_poly, 4)
     _check(_lib.adr_set_coeffs(ctx, int(instance), ap, bp, rp), ctx)
+
+
+def adr_set_coeffs_periodic(ctx, a_diag, b_field, r_poly):
+    """a_diag, b_field: d nodal arrays each (a_11, a_22[, a_33]; b_1, b_2[, b_3]), x1 fastest."""
+    a, ap = _dbl(np.stack([np.ravel(np.asarray(x, dtype=np.float64)) for x in a_diag]))
+    b, bp = _dbl(np.stack([np.ravel(np.asarray(x, dtype=np.float64)) for x in b_field]))
+    if a.shape != b.shape:
+        raise ValueError("a_diag and b_field must hold the same number of nodal arrays")
+    rr, rp = _dbl(r_poly, 4)
+    _check(_lib.adr_set_coeffs_periodic(ctx, ap, bp, rp), ctx)
 
 
 def adr_step(ctx, u, t=0.0):
@@ -311,6 +325,10 @@ class Context:
 
     def set_coeffs(self, a_nodes, b, r_poly, instance=0):
         adr_set_coeffs(self.ctx, instance, a_nodes, b, r_poly)
+        return self
+
+    def set_coeffs_periodic(self, a_diag, b_field, r_poly):
+        adr_set_coeffs_periodic(self.ctx, a_diag, b_field, r_poly)
         return self
 
     def offsets(self):

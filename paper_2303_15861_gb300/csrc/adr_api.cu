@@ -20,6 +20,7 @@
 //     using E(u + tau/6 k1) = 2/3 Eu + 1/3 U2, so a step costs four E actions.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <functional>
@@ -37,10 +38,11 @@ namespace {
 
 // One enqueued operation of a schedule and the kind of kernel it launches.
 enum OpKind { OP_MEMSET = 0, OP_AMAX = 1, OP_STENCIL = 2, OP_CONTRACT_SIMT = 3, OP_CONTRACT_TC = 4,
-              OP_CONTRACT_TC_PRECISE = 5 };
+              OP_CONTRACT_TC_PRECISE = 5, OP_PERIODIC_RHS = 6, OP_FOURIER_MULT = 7 };
 struct Op {
     std::function<cudaError_t(cudaStream_t)> fn;
     int kind;
+    int launches = 1;                      // kernels the op launches (0 for a memset)
     cudaError_t operator()(cudaStream_t s) const { return fn(s); }
 };
 
@@ -124,6 +126,16 @@ struct adr_ctx {
 
     // batched 2-D instances (p.batch > 0)
     std::unique_ptr<adr_batch_state> bs;
+
+    // periodic Fourier pseudospectral contexts (p.periodic)
+    bool periodic = false;
+    void* d_pc[3] = {nullptr, nullptr, nullptr};   // complex work: Cu, Ct, Cs
+    void* d_ptw[3] = {nullptr, nullptr, nullptr};  // twiddles per direction
+    void* d_pk[3] = {nullptr, nullptr, nullptr};   // wavenumbers per direction
+    void* d_pa[3] = {nullptr, nullptr, nullptr};   // a_mumu at the nodes
+    void* d_pb[3] = {nullptr, nullptr, nullptr};   // b_mu at the nodes
+    void* d_psym = nullptr;                        // symbol of A
+    void* d_pm[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // E(1/2), E(1), E(alpha), phi_1, phi_2
 
     // phi_k route; for the doubling route: X = tau A / 2^s, Taylor terms, level factors
     int phi_route = 0;                     // adr_phi_route in use (0: no phi_k needed)
@@ -395,10 +407,48 @@ void push_mode(Sched& S, int mu, int kind, const T* x, T* y, int epi = adr::EPI_
     S.ops.push_back({[a](cudaStream_t s) { return adr::launch_contract_tc(a, s); }, tc_kind});
 }
 
+// The device arrays of a periodic context as the Fourier kernels take them.
+template <typename T>
+adr::PeriodicArgs<T> periodic_args(const adr_ctx* c) {
+    adr::PeriodicArgs<T> P;
+    P.dim = c->dim;
+    for (int m = 0; m < 3; ++m) P.n[m] = c->n[m];
+    P.N = static_cast<long long>(c->N);
+    P.Cu = static_cast<adr::Cplx<T>*>(c->d_pc[0]);
+    P.Ct = static_cast<adr::Cplx<T>*>(c->d_pc[1]);
+    P.Cs = static_cast<adr::Cplx<T>*>(c->d_pc[2]);
+    for (int m = 0; m < c->dim; ++m) {
+        P.tw[m] = static_cast<const adr::Cplx<T>*>(c->d_ptw[m]);
+        P.k[m] = static_cast<const T*>(c->d_pk[m]);
+        P.a[m] = static_cast<const T*>(c->d_pa[m]);
+        P.b[m] = static_cast<const T*>(c->d_pb[m]);
+    }
+    P.sym = static_cast<const adr::Cplx<T>*>(c->d_psym);
+    for (int i = 0; i < 4; ++i) P.r[i] = c->r[i];
+    return P;
+}
+
+// Periodic contexts: y = base + alpha Re(F^-1 (M F x)) for the Fourier multiplier M
+// (y = Re(F^-1 (M F x)) without base); mi indexes d_pm.
+template <typename T>
+void push_fourier(Sched& S, int mi, const T* x, T* y, const T* base, double alpha) {
+    const adr_ctx* c = S.c;
+    const auto P = periodic_args<T>(c);
+    const auto* M = static_cast<const adr::Cplx<T>*>(c->d_pm[mi]);
+    Op op{[P, M, x, y, base, alpha](cudaStream_t st) { return adr::launch_periodic_multiplier(P, M, x, y, base, alpha, st); },
+          OP_FOURIER_MULT};
+    op.launches = adr::periodic_multiplier_launches(c->dim);
+    S.ops.push_back(op);
+}
+
 // y = e^{c tau A} x, optionally finished by y = base + alpha * (e^{c tau A} x).
 template <typename T>
 void push_exp(Sched& S, int ci, const T* x, T* y, const T* base = nullptr, double alpha = 0.0) {
     const adr_ctx* c = S.c;
+    if (c->periodic) {   // multipliers d_pm[0..2]: e^{tau s / 2}, e^{tau s}, e^{alpha tau s}
+        push_fourier<T>(S, ci == FK_EXP_HALF ? 0 : ci == FK_EXP_ONE ? 1 : 2, x, y, base, alpha);
+        return;
+    }
     T* t0 = static_cast<T*>(c->ws[4]);
     T* t1 = static_cast<T*>(c->ws[5]);
     const T* in = x;
@@ -511,6 +561,10 @@ void push_phi_doubling(Sched& S, int k, const T* x, T* y, const T* base, double 
 template <typename T>
 void push_phi(Sched& S, int k, const T* x, T* y, const T* base = nullptr, double alpha = 0.0) {
     const adr_ctx* c = S.c;
+    if (c->periodic) {   // multipliers d_pm[1], d_pm[3], d_pm[4]: phi_0, phi_1, phi_2 of tau s
+        push_fourier<T>(S, k == 0 ? 1 : k == 1 ? 3 : 4, x, y, base, alpha);
+        return;
+    }
     if (c->phi_route == ADR_PHI_DOUBLING) {
         if (k == 0) push_exp<T>(S, FK_EXP_ONE, x, y, base, base ? alpha : 0.0);
         else push_phi_doubling<T>(S, k, x, y, base, alpha);
@@ -561,6 +615,13 @@ StencilArgs<T> stencil_base(const adr_ctx* c, const T* u) {
 // Push a stencil op; on the mixed path its outputs (and, if asked, its input) get slots.
 template <typename T>
 void push_stencil(Sched& S, StencilArgs<T> s, bool record_input) {
+    if (S.c->periodic) {   // the pseudospectral right-hand side (periodic.cu)
+        const auto P = periodic_args<T>(S.c);
+        Op op{[P, s](cudaStream_t st) { return adr::launch_periodic_rhs(P, s, st); }, OP_PERIODIC_RHS};
+        op.launches = adr::periodic_rhs_launches(S.c->dim, s.nout);
+        S.ops.push_back(op);
+        return;
+    }
     if (S.c->bs) {
         const auto a = batch_stencil_args(S.c, s);
         S.ops.push_back({[a](cudaStream_t st) { return adr::launch_batch_stencil(a, st); }, OP_STENCIL});
@@ -1228,6 +1289,92 @@ adr_status setup_doubling(adr_ctx* c) {
     return ADR_OK;
 }
 
+// ------------------------------------------------------------ periodic Fourier contexts
+bool power_of_two(int n) { return n >= 2 && (n & (n - 1)) == 0; }
+
+// phi_k(z), k = 0, 1, 2, of a complex argument from the definitions e^z, (e^z - 1) / z,
+// (e^z - 1 - z) / z^2; for |z| < 1 the power series sum_j z^j / (j + k)! (30 terms, Horner),
+// which avoids the cancellation of the closed forms near 0.
+std::complex<double> phi_complex(int k, std::complex<double> z) {
+    if (k == 0) return std::exp(z);
+    if (std::abs(z) < 1.0) {
+        std::complex<double> acc = 0.0;
+        for (int j = 29; j >= 0; --j) acc = acc * z + inv_factorial(j + k);
+        return acc;
+    }
+    // e^z - 1 = expm1(x) e^{iy} + (e^{iy} - 1), with cos y - 1 = -2 sin^2(y/2)
+    const double x = z.real(), y = z.imag(), sh = std::sin(0.5 * y);
+    const std::complex<double> em1 =
+        std::expm1(x) * std::complex<double>(std::cos(y), std::sin(y)) + std::complex<double>(-2.0 * sh * sh, std::sin(y));
+    return k == 1 ? em1 / z : (em1 - z) / (z * z);
+}
+
+// Wavenumbers of n Fourier modes on a period of length L in FFT order (j, then j - n for
+// j > n/2), the Nyquist mode j = n/2 set to 0: the first derivative of the interpolant of
+// real data has no real Nyquist component.
+std::vector<double> wavenumbers(int n, double L) {
+    std::vector<double> k(static_cast<size_t>(n));
+    for (int j = 0; j < n; ++j) k[size_t(j)] = (2.0 * M_PI / L) * (j < n / 2 ? j : j == n / 2 ? 0 : j - n);
+    return k;
+}
+
+adr_status create_periodic(const adr_params* p, void* cuda_stream, adr_ctx** out) {
+    if (p->periodic != 1) return fail(nullptr, ADR_ERR_ARG, "periodic must be 0 or 1");
+    if (p->batch != 0) return fail(nullptr, ADR_ERR_UNSUPPORTED, "periodic contexts are single grids");
+    if (p->dim != 2 && p->dim != 3) return fail(nullptr, ADR_ERR_ARG, "dim must be 2 or 3");
+    for (int m = 0; m < p->dim; ++m)
+        if (!power_of_two(p->n[m]) || p->n[m] > 1024)
+            return fail(nullptr, ADR_ERR_ARG, "periodic contexts need n a power of two in [2, 1024]");
+    if (!(p->tau > 0.0) || !std::isfinite(p->tau)) return fail(nullptr, ADR_ERR_ARG, "tau must be positive");
+    if (!(p->length > 0.0) || !std::isfinite(p->length)) return fail(nullptr, ADR_ERR_ARG, "length must be positive");
+    if (p->scheme < ADR_LAWSON_EULER || p->scheme > ADR_STABILIZED_LAWSON2) return fail(nullptr, ADR_ERR_ARG, "unknown scheme");
+    if (p->precision != ADR_FP64 && p->precision != ADR_FP32)
+        return fail(nullptr, ADR_ERR_UNSUPPORTED, "periodic contexts run in ADR_FP64 or ADR_FP32");
+    if (p->phi_route != ADR_PHI_AUTO && p->phi_route != ADR_PHI_FOURIER)
+        return fail(nullptr, ADR_ERR_ARG, "periodic contexts apply phi_k as Fourier multipliers");
+    if (p->bc_hi != ADR_BC_DIRICHLET || p->form != ADR_FORM_FLUX)
+        return fail(nullptr, ADR_ERR_ARG, "bc_hi and form do not apply to periodic contexts");
+    size_t N = 1;
+    for (int m = 0; m < p->dim; ++m) N *= size_t(p->n[m]);
+    if (N > (size_t(1) << 31) - 1) return fail(nullptr, ADR_ERR_ARG, "grid too large");
+
+    std::unique_ptr<adr_ctx> c(new adr_ctx);
+    c->p = *p;
+    if (c->p.lambda <= 0.0) c->p.lambda = 1.0;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->periodic = true;
+    c->dim = p->dim;
+    for (int m = 0; m < 3; ++m) c->n[m] = (m < p->dim) ? p->n[m] : 1;
+    c->N = N;
+    c->nodes = N;
+    c->fp64 = (p->precision == ADR_FP64);
+    c->esize = c->fp64 ? 8 : 4;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&c->d_err), sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+    for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaMalloc(&c->ws[i], N * c->esize);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMalloc(&c->d_pc[i], 2 * N * c->esize);
+    if (e != cudaSuccess) {
+        adr_destroy(c.release());
+        return fail(nullptr, ADR_ERR_ALLOC, std::string("periodic context: ") + cudaGetErrorString(e));
+    }
+    for (int m = 0; m < c->dim && e == cudaSuccess; ++m) {
+        const int n = c->n[m];
+        std::vector<double> tw(static_cast<size_t>(n));   // e^{-2 pi i j / n}, j < n/2, interleaved (re, im)
+        for (int j = 0; j < n / 2; ++j) {
+            tw[2 * size_t(j)] = std::cos(2.0 * M_PI * j / n);
+            tw[2 * size_t(j) + 1] = -std::sin(2.0 * M_PI * j / n);
+        }
+        e = upload(c.get(), &c->d_ptw[m], tw);
+        if (e == cudaSuccess) e = upload(c.get(), &c->d_pk[m], wavenumbers(n, p->length));
+    }
+    if (e != cudaSuccess) {
+        adr_destroy(c.release());
+        return fail(nullptr, ADR_ERR_ALLOC, std::string("periodic tables: ") + cudaGetErrorString(e));
+    }
+    *out = c.release();
+    return ADR_OK;
+}
+
 }  // namespace
 
 // ===================================================================== C ABI
@@ -1238,6 +1385,7 @@ adr_status adr_create(const adr_params* p, void* cuda_stream, adr_ctx** out) {
     *out = nullptr;
     if (!p) return fail(nullptr, ADR_ERR_ARG, "params is NULL");
     if (p->batch < 0) return fail(nullptr, ADR_ERR_ARG, "batch must be >= 0");
+    if (p->periodic) return create_periodic(p, cuda_stream, out);
     if (p->batch > 0) return create_batch(p, cuda_stream, out);
     if (p->dim != 2 && p->dim != 3) return fail(nullptr, ADR_ERR_ARG, "dim must be 2 or 3");
     for (int m = 0; m < p->dim; ++m)
@@ -1297,6 +1445,7 @@ adr_status adr_create(const adr_params* p, void* cuda_stream, adr_ctx** out) {
 adr_status adr_set_coeffs(adr_ctx* c, int instance, const double* a_nodes, const double b[3], const double r_poly[4]) {
     if (!c) return ADR_ERR_ARG;
     if (c->bs) return batch_set_coeffs(c, instance, a_nodes, b, r_poly);
+    if (c->periodic) return fail(c, ADR_ERR_ARG, "periodic contexts take adr_set_coeffs_periodic");
     if (instance != 0) return fail(c, ADR_ERR_ARG, "instance must be 0 for a single-grid context");
     if (!a_nodes || !b || !r_poly) return fail(c, ADR_ERR_ARG, "NULL coefficient pointer");
     for (size_t i = 0; i < c->nodes; ++i)
@@ -1411,6 +1560,72 @@ adr_status adr_set_coeffs(adr_ctx* c, int instance, const double* a_nodes, const
     return ADR_OK;
 }
 
+adr_status adr_set_coeffs_periodic(adr_ctx* c, const double* a_diag, const double* b_field, const double r_poly[4]) {
+    if (!c) return ADR_ERR_ARG;
+    if (!c->periodic) return fail(c, ADR_ERR_ARG, "adr_set_coeffs_periodic needs a periodic context");
+    if (!a_diag || !b_field || !r_poly) return fail(c, ADR_ERR_ARG, "NULL coefficient pointer");
+    const size_t N = c->N;
+    const int d = c->dim;
+    for (size_t i = 0; i < size_t(d) * N; ++i)
+        if (!std::isfinite(a_diag[i]) || !std::isfinite(b_field[i]))
+            return fail(c, ADR_ERR_ARG, "a_diag or b_field has a non-finite value");
+    for (int i = 0; i < 4; ++i)
+        if (!std::isfinite(r_poly[i])) return fail(c, ADR_ERR_ARG, "r_poly has a non-finite value");
+    drop_graph(c);
+    c->coeffs_set = false;
+    for (int i = 0; i < 4; ++i) c->r[i] = r_poly[i];
+    // Eq. (amaxbeta): a^max_mu = lambda max a_mumu, beta_mu = mean of b_mu (the mean of d_mu a_mumu
+    // over a period is zero)
+    double amax[3] = {0, 0, 0};
+    c->abar = 0.0;
+    for (int m = 0; m < d; ++m) {
+        const double* a = a_diag + size_t(m) * N;
+        const double* b = b_field + size_t(m) * N;
+        amax[m] = c->p.abar_override > 0 ? c->p.abar_override : c->p.lambda * adr::nodal_max(a, N);
+        if (!(amax[m] > 0)) return fail(c, ADR_ERR_ARG, "lambda * a_max must be positive");
+        double sum = 0.0;
+        for (size_t i = 0; i < N; ++i) sum += b[i];
+        c->b[m] = c->beta[m] = sum / double(N);
+        c->abar = std::max(c->abar, amax[m]);
+        c->kappa[m] = 1.0;   // the Fourier basis is unitary
+        cudaError_t e = upload(c, &c->d_pa[m], std::vector<double>(a, a + N));
+        if (e == cudaSuccess) e = upload(c, &c->d_pb[m], std::vector<double>(b, b + N));
+        if (e != cudaSuccess) return cuda_fail(c, e, "upload a, b");
+    }
+    // symbol s = sum_mu (-a^max_mu k_mu^2 + i beta_mu k_mu) and the multipliers of tau s
+    std::vector<double> k[3];
+    for (int m = 0; m < d; ++m) k[m] = wavenumbers(c->n[m], c->p.length);
+    std::vector<double> sym(2 * N), mult[5];
+    for (auto& v : mult) v.resize(2 * N);
+    const double cexp[3] = {0.5, 1.0, adr::kLawsonAlpha};
+    for (size_t i = 0; i < N; ++i) {
+        size_t r = i;
+        std::complex<double> sv = 0.0;
+        for (int m = 0; m < d; ++m) {
+            const double km = k[m][r % size_t(c->n[m])];
+            r /= size_t(c->n[m]);
+            sv += std::complex<double>(-amax[m] * km * km, c->beta[m] * km);
+        }
+        sym[2 * i] = sv.real();
+        sym[2 * i + 1] = sv.imag();
+        const std::complex<double> z = c->p.tau * sv;
+        std::complex<double> v[5];
+        for (int q = 0; q < 3; ++q) v[q] = std::exp(cexp[q] * z);
+        v[3] = phi_complex(1, z);
+        v[4] = phi_complex(2, z);
+        for (int q = 0; q < 5; ++q) {
+            mult[q][2 * i] = v[q].real();
+            mult[q][2 * i + 1] = v[q].imag();
+        }
+    }
+    cudaError_t e = upload(c, &c->d_psym, sym);
+    for (int q = 0; q < 5 && e == cudaSuccess; ++q) e = upload(c, &c->d_pm[q], mult[q]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "upload Fourier multipliers");
+    c->phi_route = needs_phi(c->p.scheme) ? ADR_PHI_FOURIER : 0;
+    c->coeffs_set = true;
+    return ADR_OK;
+}
+
 adr_status adr_step(adr_ctx* c, void* u, double t) {
     (void)t;
     adr_status st = check_ready(c);
@@ -1518,7 +1733,7 @@ adr_status adr_apply_phi(adr_ctx* c, int k, const void* v, void* y) {
     if (k < 0 || k > 2) return fail(c, ADR_ERR_ARG, "k must be 0, 1 or 2");
     if (c->bs && !c->bs->roles[FK_V])
         return fail(c, ADR_ERR_STATE, "this batched context's scheme does not build the eigenbasis");
-    if (!c->bs && c->phi_route != ADR_PHI_DOUBLING && !c->eig_real)
+    if (!c->bs && !c->periodic && c->phi_route != ADR_PHI_DOUBLING && !c->eig_real)
         return fail(c, ADR_ERR_COMPLEX_SPECTRUM, "A_mu has no real eigenbasis");
     Sched S(c);
     if (c->fp64) push_phi<double>(S, k, static_cast<const double*>(v), static_cast<double*>(y));
@@ -1619,11 +1834,11 @@ int adr_phi_route_used(const adr_ctx* c, int* halvings, int* terms) {
 
 int adr_kernels_per_step(const adr_ctx* c) {
     if (!c) return -1;
-    if (c->coeffs_set) {   // count the kernels of the schedule itself (the address is never used)
+    if (c->coeffs_set || c->periodic) {   // count the kernels of the schedule itself (the address is never used)
         static double dummy[1];
         int n = 0;
         for (const auto& op : step_ops(c, dummy))
-            if (op.kind != OP_MEMSET) ++n;
+            if (op.kind != OP_MEMSET) n += op.launches;
         return n;
     }
     const int d = c->dim;
@@ -1669,6 +1884,13 @@ void adr_destroy(adr_ctx* c) {
     for (auto& p : c->d_lam) { void* q = p; free_dev(q); p = nullptr; }
     for (auto& p : c->ws) free_dev(p);
     free_dev(c->d_host_state);
+    for (auto& q : c->d_pc) free_dev(q);
+    for (auto& q : c->d_ptw) free_dev(q);
+    for (auto& q : c->d_pk) free_dev(q);
+    for (auto& q : c->d_pa) free_dev(q);
+    for (auto& q : c->d_pb) free_dev(q);
+    free_dev(c->d_psym);
+    for (auto& q : c->d_pm) free_dev(q);
     for (auto& row : c->d_img) for (auto& p : row) { void* q = p; free_dev(q); p = nullptr; }  // 5 kinds
     for (auto& row : c->d_fsc) for (auto& p : row) { void* q = p; free_dev(q); p = nullptr; }
     for (auto& row : c->d_img2) for (auto& p : row) { void* q = p; free_dev(q); p = nullptr; }

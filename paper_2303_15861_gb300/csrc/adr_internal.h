@@ -239,4 +239,41 @@ cudaError_t launch_batch_stencil(const BatchStencilArgs<float>& a, cudaStream_t 
 cudaError_t launch_batch_contract(const BatchContractArgs<double>& a, cudaStream_t s);
 cudaError_t launch_batch_contract(const BatchContractArgs<float>& a, cudaStream_t s);
 
+// ---------------------------------------------------------------- periodic Fourier contexts
+// The pseudospectral form of the paper's two-dimensional experiment (Section 5.1): the state
+// lives on n_1 x ... x n_d Fourier nodes (n_mu a power of two, <= 1024); derivatives and the
+// matrix functions of A are applied to Fourier coefficients (periodic.cu).
+template <typename T>
+struct Cplx {
+    T x, y;
+};
+
+template <typename T>
+struct PeriodicArgs {
+    int dim = 2;
+    int n[3] = {1, 1, 1};
+    long long N = 0;
+    Cplx<T>* Cu = nullptr;                 // FFT of the stage input
+    Cplx<T>* Ct = nullptr;                 // work
+    Cplx<T>* Cs = nullptr;                 // spectral divergence of the fluxes
+    const Cplx<T>* tw[3] = {nullptr, nullptr, nullptr};   // e^{-2 pi i j / n_mu}, j < n_mu / 2
+    const T* k[3] = {nullptr, nullptr, nullptr};          // wavenumbers (Nyquist 0)
+    const T* a[3] = {nullptr, nullptr, nullptr};          // a_mumu at the nodes
+    const T* b[3] = {nullptr, nullptr, nullptr};          // b_mu at the nodes
+    const Cplx<T>* sym = nullptr;          // symbol of A at every Fourier point
+    double r[4] = {0, 0, 0, 0};
+};
+
+// One stage: out_j = cu u + sum_e cx X_e + cg g(u) + cF F(u), F(u) = sum_mu D_mu(a_mumu D_mu u +
+// b_mu u) + r(u), g = F - A u (the grid fields of s are not used). Number of kernel launches:
+int periodic_rhs_launches(int dim, int nout);
+cudaError_t launch_periodic_rhs(const PeriodicArgs<double>& P, const StencilArgs<double>& s, cudaStream_t st);
+cudaError_t launch_periodic_rhs(const PeriodicArgs<float>& P, const StencilArgs<float>& s, cudaStream_t st);
+// y = base + alpha Re(IFFT(M FFT(x))) (y = Re(...) when base is null). Number of launches:
+int periodic_multiplier_launches(int dim);
+cudaError_t launch_periodic_multiplier(const PeriodicArgs<double>& P, const Cplx<double>* M, const double* x, double* y,
+                                       const double* base, double alpha, cudaStream_t st);
+cudaError_t launch_periodic_multiplier(const PeriodicArgs<float>& P, const Cplx<float>* M, const float* x, float* y,
+                                       const float* base, double alpha, cudaStream_t st);
+
 }  // namespace adr

@@ -102,7 +102,7 @@ extern "C" adr_status adr_lambda_scan(const adr_params* p, const double* a_nodes
                                       const double* lambdas, int ref_substeps, void* cuda_stream,
                                       double* errors, double* best_lambda) {
     if (!p || !a_nodes || !b || !r_poly || !u0_host || !errors || !best_lambda) return ADR_ERR_ARG;
-    if (m < 1 || n_lambdas < 1 || p->batch != 0 || (p->dim != 2 && p->dim != 3)) return ADR_ERR_ARG;
+    if (m < 1 || n_lambdas < 1 || p->batch != 0 || p->periodic || (p->dim != 2 && p->dim != 3)) return ADR_ERR_ARG;
     if (ref_substeps <= 0) ref_substeps = 8;
     size_t N = 1;
     for (int d = 0; d < p->dim; ++d) {

@@ -208,3 +208,34 @@ def config_e3(n=256, scheme="lawson2a", m=256, T=4.0):
                  r_poly=(0.0, 0.25, -0.25, 0.0), u0=np.ascontiguousarray(u0), tau=T / m, m=int(m),
                  scheme=scheme, extra=dict(periodic=True, L=L))
     return w, L, [a11, a22], [b1, b2]
+
+
+def periodic_instance(dims, L=2.0 * np.pi, scheme="lawson2a", m=8, T=0.05, seed=5):
+    """A seeded periodic instance of the form of config_e3 in 2-D or 3-D on (0, L)^d with
+    n_mu Fourier nodes x_j = j L / n_mu: a_mumu = 1/2 + (1/6) prod_nu sin^2(x_nu + phase),
+    b_mu = (1/5) sin^2(x_mu + phase) (random phases), r(u) = u (1 - u) / 4 and a smooth
+    random datum (the lowest three modes per direction with N(0,1) amplitudes, plus 1/2).
+    Returns (workload, L, a_diag, b_field)."""
+    rng = np.random.default_rng(seed)
+    d = len(dims)
+    axes = [np.arange(n, dtype=np.float64) * (L / n) for n in dims]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")[::-1]     # grids[mu] varies along x_(mu+1)
+    w0 = 2.0 * np.pi / L
+    a_diag, b_field = [], []
+    for mu in range(d):
+        ph = rng.uniform(0, 2 * np.pi, size=d)
+        prod = np.ones(grids[0].shape)
+        for nu in range(d):
+            prod = prod * np.sin(w0 * grids[nu] + ph[nu]) ** 2
+        a_diag.append(0.5 + prod / 6.0)
+        b_field.append(np.sin(w0 * grids[mu] + rng.uniform(0, 2 * np.pi)) ** 2 / 5.0)
+    u0 = np.full(grids[0].shape, 0.5)
+    for mu in range(d):
+        for kk in range(1, 4):
+            if kk < dims[mu] // 2:
+                c, s = rng.standard_normal(2) * 0.1
+                u0 = u0 + c * np.cos(kk * w0 * grids[mu]) + s * np.sin(kk * w0 * grids[mu])
+    w = Workload(name="periodic_" + "x".join(str(n) for n in dims) + f"_{scheme}", dims=tuple(dims), a_nodes=None,
+                 b=(0.0, 0.0, 0.0), r_poly=(0.0, 0.25, -0.25, 0.0), u0=np.ascontiguousarray(u0), tau=T / m,
+                 m=int(m), scheme=scheme, extra=dict(periodic=True, L=L))
+    return w, L, a_diag, b_field

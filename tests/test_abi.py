@@ -107,3 +107,41 @@ def test_create_batch_rejects_invalid_params_on_host(lib, kw, status):
 def test_batch_plan_needs_a_context(lib):
     assert lib.adr_get_batch_plan(None, 1, None, None) == 1
     assert lib.adr_get_instance_info(None, 0, None, None, None) == 1
+
+
+def _periodic_params(**kw):
+    p = _params(dim=kw.get("dim", 2), n=kw.get("n", (16, 16, 1)), precision=kw.get("precision", 0),
+                scheme=kw.get("scheme", 6))
+    p.periodic = kw.get("periodic", 1)
+    p.length = kw.get("length", 1.0)
+    p.phi_route = kw.get("phi_route", 0)
+    p.bc_hi = kw.get("bc_hi", 0)
+    p.form = kw.get("form", 0)
+    p.batch = kw.get("batch", 0)
+    return p
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(n=(12, 16, 1)), 1),          # not a power of two
+    (dict(n=(2048, 16, 1)), 1),        # beyond one shared-memory line
+    (dict(n=(1, 16, 1)), 1),
+    (dict(length=0.0), 1),
+    (dict(length=float("inf")), 1),
+    (dict(precision=3), 8),            # the Fourier path runs in FP64 or FP32
+    (dict(phi_route=1), 1),
+    (dict(bc_hi=1, form=1), 1),
+    (dict(periodic=2), 1),
+    (dict(batch=2), 8),
+    (dict(scheme=42), 1),
+])
+def test_create_rejects_invalid_periodic_params_on_host(lib, kw, status):
+    ctx = C.c_void_p()
+    p = _periodic_params(**kw)
+    assert lib.adr_create(C.byref(p), None, C.byref(ctx)) == status
+    assert not ctx.value
+    assert len(lib.adr_last_error(None)) > 0
+
+
+def test_periodic_entry_points_reject_null_contexts(lib):
+    dp = C.POINTER(C.c_double)
+    assert lib.adr_set_coeffs_periodic(None, dp(), dp(), dp()) == 1

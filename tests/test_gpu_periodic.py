@@ -1,0 +1,185 @@
+"""Periodic Fourier pseudospectral contexts (the paper's two-dimensional experiment form,
+Section 5.1, Eq. (ad2d)) through the C ABI against the FP64 oracle's PeriodicProblem.
+
+Tolerances (relative l2):
+  * FP64 matrix-function actions 1e-12; F and g 1e-11: the spectral derivative multiplies
+    the FFT's rounding (about 1e-16 log2 N relative to the coefficients) by up to k_max^2,
+    k_max = (n/2)(2 pi / L), which is 1e2 to 1e3 on these grids.
+  * FP64 time integration 1e-11 (the same amplification, once per step, damped by e^{tau A}).
+  * FP32: 2e-5 on the full E3 horizon (256 steps at n = 256): single precision rounding of
+    the FFTs (about 6e-8 log2 N) amplified the same way.
+Grids include the largest line (n = 1024), the degenerate n = 2 direction (modes 0 and
+Nyquist only), non-square 2-D and 3-D shapes.
+"""
+import numpy as np
+import pytest
+
+from oracle import adr_oracle as O
+from paper_2303_15861_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2303_15861_gb300 import adr, build_lib  # noqa: E402
+
+build_lib.build()
+adr.load_library()
+
+DT = {"fp64": torch.float64, "fp32": torch.float32}
+SCHEMES = ["lawson_euler", "etd2rk", "lawson4", "exponential_euler", "erk2p1", "stabilized_lawson_euler",
+           "lawson2a", "lawson2b", "stabilized_lawson2"]
+
+
+def context(w, L, a_diag, b_field, prec="fp64", scheme=None, stream=None, lam=1.0):
+    ctx = adr.Context(w.dims, w.tau, scheme or w.scheme, prec, stream=stream, periodic=True, length=L, lam=lam)
+    ctx.set_coeffs_periodic(a_diag, b_field, w.r_poly)
+    return ctx
+
+
+def dev(x, prec="fp64"):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=DT[prec], device="cuda")
+
+
+def host(t):
+    return t.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("dims", [(32, 64), (1024, 4), (2, 64), (16, 8, 32), (4, 4, 4)])
+def test_building_blocks_match_oracle(dims):
+    """F, g, e^{c tau A} and phi_k(tau A) of a random state."""
+    w, L, a, b = W.periodic_instance(dims, T=0.05, m=4)
+    ctx = context(w, L, a, b, scheme="etd2rk")
+    prob = O.PeriodicProblem(dims, L, a, b, w.r_poly)
+    ops = O.PeriodicOps(prob, w.tau)
+    v = np.random.default_rng(3).standard_normal(w.u0.shape)
+    u = dev(w.u0)
+    F = torch.empty_like(u)
+    g = torch.empty_like(u)
+    ctx.eval_rhs(u, F, g)
+    y = {}
+    for c in (0.5, 1.0):
+        y[("exp", c)] = torch.empty_like(u)
+        ctx.apply_exp(c, dev(v), y[("exp", c)])
+    for k in (0, 1, 2):
+        y[("phi", k)] = torch.empty_like(u)
+        ctx.apply_phi(k, dev(v), y[("phi", k)])
+    ctx.synchronize()
+    assert O.rel_l2(host(F), ops.F(w.u0)) < 1e-11
+    assert O.rel_l2(host(g), ops.g(w.u0)) < 1e-11
+    for c in (0.5, 1.0):
+        assert O.rel_l2(host(y[("exp", c)]), ops.expA(c, v)) < 1e-12, c
+    for k in (0, 1, 2):
+        assert O.rel_l2(host(y[("phi", k)]), ops.phi(k, 1.0, v)) < 1e-12, k
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_fp64_schemes_match_oracle(scheme):
+    w, L, a, b = W.periodic_instance((32, 16), scheme=scheme, T=0.2, m=6)
+    ctx = context(w, L, a, b)
+    u = dev(w.u0)
+    ctx.integrate(u, 0.0, w.m * w.tau, w.m)
+    ctx.synchronize()
+    ref = O.solve_periodic(w.dims, L, a, b, w.r_poly, w.u0, w.tau, w.m, scheme)
+    assert O.rel_l2(host(u), ref) < 1e-11
+
+
+@pytest.mark.parametrize("scheme", ["lawson4", "etd2rk", "stabilized_lawson2"])
+def test_fp64_3d_matches_oracle(scheme):
+    w, L, a, b = W.periodic_instance((16, 32, 8), scheme=scheme, T=0.1, m=4)
+    ctx = context(w, L, a, b, lam=0.8)
+    u = dev(w.u0)
+    ctx.integrate(u, 0.0, w.m * w.tau, w.m)
+    ctx.synchronize()
+    ref = O.solve_periodic(w.dims, L, a, b, w.r_poly, w.u0, w.tau, w.m, scheme, lam=0.8)
+    assert O.rel_l2(host(u), ref) < 1e-11
+
+
+def test_e3_workload_fp64_matches_oracle():
+    """The paper's 2-D experiment at n = 128, 64 steps to T = 1 (Lawson2a)."""
+    w, L, a, b = W.config_e3(n=128, scheme="lawson2a", m=64, T=1.0)
+    ctx = context(w, L, a, b)
+    u = dev(w.u0)
+    ctx.integrate(u, 0.0, w.m * w.tau, w.m)
+    ctx.synchronize()
+    ref = O.solve_periodic(w.dims, L, a, b, w.r_poly, w.u0, w.tau, w.m, "lawson2a")
+    assert O.rel_l2(host(u), ref) < 1e-11
+
+
+@pytest.mark.parametrize("scheme", ["lawson2a", "etd2rk"])
+def test_e3_workload_fp32_full_horizon(scheme):
+    """The full E3 workload (n = 256, 256 steps to T = 4) in FP32 against the FP64 oracle."""
+    w, L, a, b = W.config_e3(n=256, scheme=scheme)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = context(w, L, a, b, prec="fp32", stream=s)
+        u = dev(w.u0, "fp32")
+        ctx.integrate(u, 0.0, w.m * w.tau, w.m)
+        ctx.synchronize()
+    ref = O.solve_periodic(w.dims, L, a, b, w.r_poly, w.u0, w.tau, w.m, scheme)
+    err = O.rel_l2(host(u), ref)
+    print(f"E3 n=256 {scheme} fp32: rel l2 {err:.3e}")
+    assert err < 2e-5
+
+
+def test_graph_replay_equals_direct_steps():
+    w, L, a, b = W.periodic_instance((64, 32), scheme="lawson4", m=3)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = context(w, L, a, b, prec="fp32", stream=s)
+        u1 = dev(w.u0, "fp32")
+        u2 = u1.clone()
+        ctx.integrate(u1, 0.0, 3 * w.tau, 3)
+        for i in range(3):
+            ctx.step(u2, i * w.tau)
+        ctx.synchronize()
+    assert torch.equal(u1, u2)
+
+
+def test_integrate_host_equals_device():
+    w, L, a, b = W.periodic_instance((64, 32), scheme="etd2rk", m=2)
+    ctx = context(w, L, a, b)
+    u = dev(w.u0)
+    h = u.cpu().pin_memory()
+    ctx.integrate(u, 0.0, 2 * w.tau, 2)
+    ctx.integrate_host(h, 0.0, 2 * w.tau, 2)
+    ctx.synchronize()
+    assert torch.equal(u.cpu(), h)
+
+
+def test_context_facts_and_launch_count():
+    w, L, a, b = W.periodic_instance((32, 16), scheme="etd2rk")
+    ctx = context(w, L, a, b)
+    assert ctx.phi_route() == 3
+    info = ctx.info()
+    assert info["kappa"][:2] == [1.0, 1.0]
+    assert info["abar"] == pytest.approx(max(x.max() for x in a))
+    assert info["beta"][0] == pytest.approx(b[0].mean()) and info["beta"][1] == pytest.approx(b[1].mean())
+    d = 2
+    rhs = lambda nout: 1 + d + d * (2 * d + 3) + nout * (d + 2)   # noqa: E731
+    mult = 2 * d + 3
+    assert ctx.kernels_per_step() == rhs(2) + mult + rhs(1) + mult   # ETD2RK: 2 stages, 2 phi actions
+    ops = ctx.profile_step(dev(w.u0))
+    assert [k for k, _ in ops] == [6, 7, 6, 7]
+
+
+def test_periodic_context_refuses_grid_coefficients_and_unset_steps():
+    w, L, a, b = W.periodic_instance((16, 16), scheme="lawson2a")
+    ctx = adr.Context(w.dims, w.tau, "lawson2a", "fp64", periodic=True, length=L)
+    u = dev(w.u0)
+    with pytest.raises(adr.AdrError) as e:
+        ctx.step(u)
+    assert e.value.status == 7
+    with pytest.raises(adr.AdrError) as e:
+        ctx.set_coeffs(np.ones((18, 18)), (0.0, 0.0), w.r_poly)
+    assert e.value.status == 1
+    with pytest.raises(adr.AdrError) as e:   # non-finite coefficient
+        bad = [a[0].copy(), a[1]]
+        bad[0][3, 4] = np.nan
+        ctx.set_coeffs_periodic(bad, b, w.r_poly)
+    assert e.value.status == 1
+    ctx.set_coeffs_periodic(a, b, w.r_poly)
+    ctx.step(u)
+    ctx.synchronize()
