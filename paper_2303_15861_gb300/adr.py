@@ -258,7 +258,7 @@ def adr_phi_route_used(ctx):
     """(route name or None, halvings, Taylor terms) of a context after adr_set_coeffs."""
     s, p = C.c_int(), C.c_int()
     r = int(_lib.adr_phi_route_used(ctx, C.byref(s), C.byref(p)))
-    return ({0: None, 1: "eigen", 2: "doubling"}[r], s.value, p.value)
+    return ({0: None, 1: "eigen", 2: "doubling", 3: "fourier"}[r], s.value, p.value)
 
 
 def adr_stability_bound(scheme):

@@ -129,7 +129,7 @@ struct adr_ctx {
 
     // periodic Fourier pseudospectral contexts (p.periodic)
     bool periodic = false;
-    void* d_pc[3] = {nullptr, nullptr, nullptr};   // complex work: Cu, Ct, Cs
+    void* d_pc[4] = {nullptr, nullptr, nullptr, nullptr};   // complex work: Cu, C[0..dim-1]
     void* d_ptw[3] = {nullptr, nullptr, nullptr};  // twiddles per direction
     void* d_pk[3] = {nullptr, nullptr, nullptr};   // wavenumbers per direction
     void* d_pa[3] = {nullptr, nullptr, nullptr};   // a_mumu at the nodes
@@ -415,8 +415,7 @@ adr::PeriodicArgs<T> periodic_args(const adr_ctx* c) {
     for (int m = 0; m < 3; ++m) P.n[m] = c->n[m];
     P.N = static_cast<long long>(c->N);
     P.Cu = static_cast<adr::Cplx<T>*>(c->d_pc[0]);
-    P.Ct = static_cast<adr::Cplx<T>*>(c->d_pc[1]);
-    P.Cs = static_cast<adr::Cplx<T>*>(c->d_pc[2]);
+    for (int m = 0; m < c->dim; ++m) P.C[m] = static_cast<adr::Cplx<T>*>(c->d_pc[m + 1]);
     for (int m = 0; m < c->dim; ++m) {
         P.tw[m] = static_cast<const adr::Cplx<T>*>(c->d_ptw[m]);
         P.k[m] = static_cast<const T*>(c->d_pk[m]);
@@ -1352,7 +1351,8 @@ adr_status create_periodic(const adr_params* p, void* cuda_stream, adr_ctx** out
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&c->d_err), sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
     for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaMalloc(&c->ws[i], N * c->esize);
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMalloc(&c->d_pc[i], 2 * N * c->esize);
+    for (int i = 0; i <= c->dim && e == cudaSuccess; ++i) e = cudaMalloc(&c->d_pc[i], 2 * N * c->esize);
+    if (e == cudaSuccess) e = adr::periodic_prepare(c->fp64);
     if (e != cudaSuccess) {
         adr_destroy(c.release());
         return fail(nullptr, ADR_ERR_ALLOC, std::string("periodic context: ") + cudaGetErrorString(e));

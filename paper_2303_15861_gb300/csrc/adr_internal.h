@@ -253,9 +253,8 @@ struct PeriodicArgs {
     int dim = 2;
     int n[3] = {1, 1, 1};
     long long N = 0;
-    Cplx<T>* Cu = nullptr;                 // FFT of the stage input
-    Cplx<T>* Ct = nullptr;                 // work
-    Cplx<T>* Cs = nullptr;                 // spectral divergence of the fluxes
+    Cplx<T>* Cu = nullptr;                 // transform of the stage input
+    Cplx<T>* C[3] = {nullptr, nullptr, nullptr};   // work: derivatives, fluxes, outputs (d of them)
     const Cplx<T>* tw[3] = {nullptr, nullptr, nullptr};   // e^{-2 pi i j / n_mu}, j < n_mu / 2
     const T* k[3] = {nullptr, nullptr, nullptr};          // wavenumbers (Nyquist 0)
     const T* a[3] = {nullptr, nullptr, nullptr};          // a_mumu at the nodes
@@ -264,8 +263,12 @@ struct PeriodicArgs {
     double r[4] = {0, 0, 0, 0};
 };
 
+// Sets the shared-memory limits of the Fourier kernels of one precision (once, before any
+// launch or stream capture).
+cudaError_t periodic_prepare(bool fp64);
 // One stage: out_j = cu u + sum_e cx X_e + cg g(u) + cF F(u), F(u) = sum_mu D_mu(a_mumu D_mu u +
-// b_mu u) + r(u), g = F - A u (the grid fields of s are not used). Number of kernel launches:
+// b_mu u) + r(u), g = F - A u (the grid fields of s are not used; out_j must not alias u).
+// Number of kernel launches:
 int periodic_rhs_launches(int dim, int nout);
 cudaError_t launch_periodic_rhs(const PeriodicArgs<double>& P, const StencilArgs<double>& s, cudaStream_t st);
 cudaError_t launch_periodic_rhs(const PeriodicArgs<float>& P, const StencilArgs<float>& s, cudaStream_t st);

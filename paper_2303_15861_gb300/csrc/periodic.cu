@@ -2,16 +2,26 @@
 // experiment (Section 5.1, Eq. (ad2d)), where A of Eq. (linop) is diagonal in Fourier space and
 // its matrix functions are multipliers on the Fourier coefficients (Section 5.1).
 //
-// FFT: a batched complex radix-2 FFT along one axis at a time, in the Stockham autosort
-// formulation (each stage reads one buffer and writes the other in natural order, so no bit
-// reversal is needed). A block takes one line of n points (n a power of two <= 1024) into
-// shared memory, runs the log2(n) stages there and writes it back; the twiddles
-// e^{-2 pi i j / n}, j < n/2, come from a table computed on the host in FP64.
+// FFT: complex radix-2 transforms along one axis at a time in the Stockham autosort form (each
+// stage reads one shared-memory buffer and writes the other in natural order, so no bit
+// reversal is needed), twiddles e^{-2 pi i j / n}, j < n/2, from a host FP64 table. A block
+// takes G lines of one axis into shared memory: along x1 the lines are contiguous; along the
+// other axes it takes G neighbouring lines, so that every global access moves G consecutive
+// elements. The inverse transform is unscaled inside the stages; its 1/n is applied once per
+// axis where the result is consumed.
 //
-// Right-hand side: F(u) = sum_mu D_mu (a_mumu D_mu u + b_mu u) + r(u) with D_mu the spectral
-// first derivative (i k_mu; the Nyquist wavenumber is 0), g(u) = F(u) - A u with A u the
-// inverse transform of symbol * u^. A stage output cu u + sum cx X + cg g + cF F is one inverse
-// transform of (cg + cF) S - cg symbol u^, S = sum_mu i k_mu (flux_mu)^, plus pointwise terms.
+// Fusion. A d-dimensional transform is d passes. The last axis d is the pivot: there all other
+// axes are already transformed, so the pivot pass does the forward transform, the pointwise
+// work in Fourier space and the inverse transform in one kernel. The passes along x1 take the
+// real-space prologue (a real input) or epilogue (the stage combination).
+//   Multiplier y = base + alpha Re F^-1(M F x):   x1 fwd | (x2 fwd) | pivot: F, M, F^-1 |
+//                                                (x2 inv) | x1 inv + axpy.          2-D: 3 kernels
+//   Right-hand side, F(u) = sum_mu D_mu (a_mumu D_mu u + b_mu u) + r(u), g = F - A u, with the
+//   spectral first derivative D_mu = F^-1 i k_mu F (Nyquist wavenumber 0):
+//     x1 fwd u | (x2 fwd) | pivot: u^, i k_mu u^ -> d arrays | (x2 inv) |
+//     x1: D_mu u -> flux f_mu = a_mumu D_mu u + b_mu u -> forward | (x2 fwd) |
+//     pivot: S = sum_mu i k_mu f_mu^, O_j = (cg_j + cF_j) S - cg_j s u^ | (x2 inv) |
+//     x1 inv + out_j = cu_j u + sum_e cx_je X_e + Re O_j + (cg_j + cF_j) r(u).      2-D: 5 kernels
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,121 +36,230 @@ __device__ __forceinline__ Cplx<T> cmul(Cplx<T> a, Cplx<T> b) {
     return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
 
-// Every line along one axis: element j of line (p, q) sits at p n Q + j Q + q.
-template <typename T>
-__global__ void __launch_bounds__(256) fft_axis_kernel(Cplx<T>* data, int n, int logn, long long Q, long long lines,
-                                                       const Cplx<T>* __restrict__ tw, int inverse) {
-    extern __shared__ __align__(16) unsigned char fft_smem[];
-    Cplx<T>* b0 = reinterpret_cast<Cplx<T>*>(fft_smem);
-    Cplx<T>* b1 = b0 + n;
-    const int half = n >> 1;
-    const T scale = inverse ? T(1) / T(n) : T(1);
-    for (long long line = blockIdx.x; line < lines; line += gridDim.x) {
-        const long long p = line / Q, q = line % Q;
-        Cplx<T>* base = data + p * n * Q + q;
-        for (int j = threadIdx.x; j < n; j += blockDim.x) b0[j] = base[(long long)j * Q];
-        __syncthreads();
-        Cplx<T>* src = b0;
-        Cplx<T>* dst = b1;
-        for (int s = 0, Ns = 1; s < logn; ++s, Ns <<= 1) {
-            for (int j = threadIdx.x; j < half; j += blockDim.x) {
-                const int r = j & (Ns - 1);                   // position inside the current sub-transforms
-                Cplx<T> w = tw[r * (half / Ns)];              // e^{-2 pi i r / (2 Ns)}
-                if (inverse) w.y = -w.y;
-                const Cplx<T> v0 = src[j];
-                const Cplx<T> v1 = cmul(src[j + half], w);
-                const int o = ((j - r) << 1) + r;             // (j / Ns) 2 Ns + r
-                dst[o] = {v0.x + v1.x, v0.y + v1.y};
-                dst[o + Ns] = {v0.x - v1.x, v0.y - v1.y};
-            }
-            __syncthreads();
-            Cplx<T>* t = src;
-            src = dst;
-            dst = t;
-        }
-        for (int j = threadIdx.x; j < n; j += blockDim.x) base[(long long)j * Q] = {src[j].x * scale, src[j].y * scale};
-        __syncthreads();
-    }
-}
-
-// --------------------------------------------------------------------- pointwise kernels
-template <typename T>
-__global__ void to_cplx_kernel(const T* __restrict__ x, Cplx<T>* c, long long N) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-        c[i] = {x[i], T(0)};
-}
-
-// out = i k_mu in (the spectral derivative along mu); Q, n of that axis
-template <typename T>
-__global__ void deriv_kernel(const Cplx<T>* __restrict__ in, Cplx<T>* out, const T* __restrict__ k, int n,
-                             long long Q, long long N) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const T km = k[(i / Q) % n];
-        const Cplx<T> v = in[i];
-        out[i] = {-km * v.y, km * v.x};
-    }
-}
-
-// c = a Re(c) + b u (the flux of direction mu, real)
-template <typename T>
-__global__ void flux_kernel(Cplx<T>* c, const T* __restrict__ a, const T* __restrict__ b, const T* __restrict__ u,
-                            long long N) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-        c[i] = {a[i] * c[i].x + b[i] * u[i], T(0)};
-}
-
-// S (=|+=) i k_mu c
-template <typename T>
-__global__ void divacc_kernel(const Cplx<T>* __restrict__ c, Cplx<T>* S, const T* __restrict__ k, int n, long long Q,
-                              long long N, int first) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const T km = k[(i / Q) % n];
-        const Cplx<T> v = c[i];
-        const Cplx<T> d = {-km * v.y, km * v.x};
-        S[i] = first ? d : Cplx<T>{S[i].x + d.x, S[i].y + d.y};
-    }
-}
-
-// out = cgF S - cg sym u^
-template <typename T>
-__global__ void spec_out_kernel(const Cplx<T>* __restrict__ S, const Cplx<T>* __restrict__ U, const Cplx<T>* __restrict__ sym,
-                                Cplx<T>* out, T cgF, T cg, long long N) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const Cplx<T> au = cmul(sym[i], U[i]);
-        out[i] = {cgF * S[i].x - cg * au.x, cgF * S[i].y - cg * au.y};
-    }
-}
-
-template <typename T>
-struct RealOut {
-    const T* u;
-    const T* X[kMaxExtra];
-    int nx;
-    T cu, cx[kMaxExtra], cgF, r[4];
+enum PassMode {
+    PM_FWD_REAL = 0,     // x1: C[0] = F_1 x (x real)
+    PM_PLAIN = 1,        // C[a] = F_mu C[a] or F_mu^-1 C[a], a < na
+    PM_PIVOT_MULT = 2,   // C[0] = F_d^-1 (M F_d C[0])
+    PM_FINAL_AXPY = 3,   // x1: y = base + alpha Re F_1^-1 C[0]  (y = Re ... without base)
+    PM_PIVOT_DERIV = 4,  // Cu = F_d Cu (= u^); C[mu] = F_d^-1 (i k_mu u^)
+    PM_FLUX = 5,         // x1: C[mu] = F_1 (a_mu Re F_1^-1 C[mu] + b_mu u)
+    PM_PIVOT_DIV = 6,    // S = sum_mu i k_mu F_d C[mu]; C[j] = F_d^-1 (cgF_j S - cg_j M Cu)
+    PM_FINAL_OUT = 7,    // x1: out_j = cu_j u + sum cx_je X_e + Re F_1^-1 C[j] + cgF_j r(u)
 };
 
-// out = cu u + sum cx X + Re(c) + cgF r(u)
+constexpr int kPassThreads = 256;
+constexpr size_t kPassSmemMax = 200 * 1024;
+
 template <typename T>
-__global__ void real_out_kernel(RealOut<T> a, const Cplx<T>* __restrict__ c, T* out, long long N) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const T u = a.u[i];
-        T v = a.cu * u + c[i].x + a.cgF * (a.r[0] + u * (a.r[1] + u * (a.r[2] + u * a.r[3])));
-        for (int e = 0; e < a.nx; ++e) v += a.cx[e] * a.X[e][i];
-        out[i] = v;
+struct Pass {
+    // the pass: axis, its length n = 2^logn, G = 2^logG lines per block, shared-memory row pitch
+    int axis, n, logn, G, logG, pitch;
+    int logQ;                 // stride of the axis, Q = 2^logQ
+    int log_gpp;              // line groups per outer index p (Q > 1): Q / G = 2^log_gpp
+    long long groups;         // line groups in the grid
+    // all axes (wavenumber lookup)
+    int dim, nn[3], logQs[3];
+    const Cplx<T>* tw;
+    const T* k[3];
+    // arrays
+    Cplx<T>* Cu;
+    Cplx<T>* C[3];
+    int na, inverse;
+    const Cplx<T>* M;         // multiplier (PM_PIVOT_MULT) or symbol of A (PM_PIVOT_DIV)
+    const T* x;               // real input: x (PM_FWD_REAL) or the stage input u
+    T* y;
+    const T* base;
+    T alpha;
+    const T* a[3];
+    const T* b[3];
+    int nout, nx;
+    const T* X[kMaxExtra];
+    T* out[kMaxOut];
+    T cu[kMaxOut], cx[kMaxOut][kMaxExtra], cgF[kMaxOut], cg[kMaxOut], r[4];
+};
+
+// Global index of element j of line g of line group grp.
+template <typename T>
+__device__ __forceinline__ long long elem_index(const Pass<T>& P, long long grp, int g, int j) {
+    if (P.logQ == 0) return (((grp << P.logG) + g) << P.logn) + j;
+    const long long p = grp >> P.log_gpp;
+    const long long q0 = (grp & ((1LL << P.log_gpp) - 1)) << P.logG;
+    return (p << (P.logn + P.logQ)) + ((long long)j << P.logQ) + q0 + g;
+}
+
+// Call f(smem offset, global index) for every element of the block's G lines, in the order that
+// makes consecutive threads touch consecutive global elements.
+template <typename T, typename F>
+__device__ __forceinline__ void for_elems(const Pass<T>& P, long long grp, F f) {
+    const int total = P.G << P.logn;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int g, j;
+        if (P.logQ == 0) { g = idx >> P.logn; j = idx & (P.n - 1); }
+        else             { g = idx & (P.G - 1); j = idx >> P.logG; }
+        f(g * P.pitch + j, elem_index(P, grp, g, j), j);
     }
 }
 
+// Wavenumber of axis mu at global index i (j: position along the pass axis).
 template <typename T>
-__global__ void mul_kernel(Cplx<T>* c, const Cplx<T>* __restrict__ M, long long N) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-        c[i] = cmul(c[i], M[i]);
+__device__ __forceinline__ T wavenumber(const Pass<T>& P, int mu, long long i, int j) {
+    if (mu == P.axis) return P.k[mu][j];
+    return P.k[mu][(i >> P.logQs[mu]) & (P.nn[mu] - 1)];
 }
 
-// y = base + alpha Re(c)  (y = Re(c) without base)
+// Stockham radix-2 transform of the G lines in src (destroys src and dst); returns the buffer
+// that holds the result (unscaled).
 template <typename T>
-__global__ void axpy_out_kernel(const Cplx<T>* __restrict__ c, const T* base, T* y, T alpha, long long N) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-        y[i] = base ? base[i] + alpha * c[i].x : c[i].x;
+__device__ Cplx<T>* fft_lines(const Pass<T>& P, const Cplx<T>* tws, Cplx<T>* src, Cplx<T>* dst, bool inverse) {
+    const int half = P.n >> 1;
+    const int total = P.G * half;
+    for (int s = 0, Ns = 1; s < P.logn; ++s, Ns <<= 1) {
+        for (int bf = threadIdx.x; bf < total; bf += blockDim.x) {
+            const int g = bf >> (P.logn - 1), jj = bf & (half - 1);
+            const int r = jj & (Ns - 1);                  // position inside the current sub-transforms
+            Cplx<T> w = tws[r << (P.logn - 1 - s)];       // e^{-2 pi i r / (2 Ns)}
+            if (inverse) w.y = -w.y;
+            const Cplx<T>* sl = src + g * P.pitch;
+            Cplx<T>* dl = dst + g * P.pitch;
+            const Cplx<T> v0 = sl[jj];
+            const Cplx<T> v1 = cmul(sl[jj + half], w);
+            const int o = ((jj - r) << 1) + r;            // (jj / Ns) 2 Ns + r
+            dl[o] = {v0.x + v1.x, v0.y + v1.y};
+            dl[o + Ns] = {v0.x - v1.x, v0.y - v1.y};
+        }
+        __syncthreads();
+        Cplx<T>* t = src;
+        src = dst;
+        dst = t;
+    }
+    return src;
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kPassThreads) fourier_pass_kernel(const __grid_constant__ Pass<T> P) {
+    extern __shared__ __align__(16) unsigned char fourier_smem[];
+    Cplx<T>* tws = reinterpret_cast<Cplx<T>*>(fourier_smem);
+    Cplx<T>* B0 = tws + (P.n >> 1);
+    const int bsize = P.G * P.pitch;
+    Cplx<T>* B1 = B0 + bsize;
+    Cplx<T>* B2 = B1 + bsize;
+    for (int j = threadIdx.x; j < (P.n >> 1); j += blockDim.x) tws[j] = P.tw[j];
+    const T inv_n = T(1) / T(P.n);
+    __syncthreads();
+
+    for (long long grp = blockIdx.x; grp < P.groups; grp += gridDim.x) {
+        if (MODE == PM_FWD_REAL) {
+            for_elems(P, grp, [&](int o, long long i, int) { B0[o] = {P.x[i], T(0)}; });
+            __syncthreads();
+            Cplx<T>* R = fft_lines(P, tws, B0, B1, false);
+            for_elems(P, grp, [&](int o, long long i, int) { P.C[0][i] = R[o]; });
+        } else if (MODE == PM_PLAIN) {
+            const T sc = P.inverse ? inv_n : T(1);
+            for (int a = 0; a < P.na; ++a) {
+                Cplx<T>* A = P.C[a];
+                for_elems(P, grp, [&](int o, long long i, int) { B0[o] = A[i]; });
+                __syncthreads();
+                Cplx<T>* R = fft_lines(P, tws, B0, B1, P.inverse != 0);
+                for_elems(P, grp, [&](int o, long long i, int) { A[i] = {R[o].x * sc, R[o].y * sc}; });
+                __syncthreads();
+            }
+        } else if (MODE == PM_PIVOT_MULT) {
+            for_elems(P, grp, [&](int o, long long i, int) { B0[o] = P.C[0][i]; });
+            __syncthreads();
+            Cplx<T>* R = fft_lines(P, tws, B0, B1, false);
+            for_elems(P, grp, [&](int o, long long i, int) { R[o] = cmul(R[o], P.M[i]); });
+            __syncthreads();
+            Cplx<T>* R2 = fft_lines(P, tws, R, R == B0 ? B1 : B0, true);
+            for_elems(P, grp, [&](int o, long long i, int) { P.C[0][i] = {R2[o].x * inv_n, R2[o].y * inv_n}; });
+        } else if (MODE == PM_FINAL_AXPY) {
+            for_elems(P, grp, [&](int o, long long i, int) { B0[o] = P.C[0][i]; });
+            __syncthreads();
+            Cplx<T>* R = fft_lines(P, tws, B0, B1, true);
+            for_elems(P, grp, [&](int o, long long i, int) {
+                const T v = R[o].x * inv_n;
+                P.y[i] = P.base ? P.base[i] + P.alpha * v : v;
+            });
+        } else if (MODE == PM_PIVOT_DERIV) {
+            for_elems(P, grp, [&](int o, long long i, int) { B0[o] = P.Cu[i]; });
+            __syncthreads();
+            Cplx<T>* U = fft_lines(P, tws, B0, B1, false);   // u^ (kept for every mu)
+            Cplx<T>* Fr = (U == B0) ? B1 : B0;
+            for_elems(P, grp, [&](int o, long long i, int) { P.Cu[i] = U[o]; });
+            for (int mu = 0; mu < P.dim; ++mu) {
+                for_elems(P, grp, [&](int o, long long i, int j) {
+                    const T km = wavenumber(P, mu, i, j);
+                    B2[o] = {-km * U[o].y, km * U[o].x};
+                });
+                __syncthreads();
+                Cplx<T>* R = fft_lines(P, tws, B2, Fr, true);
+                Cplx<T>* D = P.C[mu];
+                for_elems(P, grp, [&](int o, long long i, int) { D[i] = {R[o].x * inv_n, R[o].y * inv_n}; });
+                __syncthreads();
+            }
+        } else if (MODE == PM_FLUX) {
+            for (int mu = 0; mu < P.dim; ++mu) {
+                Cplx<T>* D = P.C[mu];
+                const T* am = P.a[mu];
+                const T* bm = P.b[mu];
+                for_elems(P, grp, [&](int o, long long i, int) { B0[o] = D[i]; });
+                __syncthreads();
+                Cplx<T>* R = fft_lines(P, tws, B0, B1, true);
+                for_elems(P, grp, [&](int o, long long i, int) {
+                    R[o] = {am[i] * (R[o].x * inv_n) + bm[i] * P.x[i], T(0)};
+                });
+                __syncthreads();
+                Cplx<T>* R2 = fft_lines(P, tws, R, R == B0 ? B1 : B0, false);
+                for_elems(P, grp, [&](int o, long long i, int) { D[i] = R2[o]; });
+                __syncthreads();
+            }
+        } else if (MODE == PM_PIVOT_DIV) {
+            for (int mu = 0; mu < P.dim; ++mu) {       // S (in B2) = sum_mu i k_mu f_mu^
+                for_elems(P, grp, [&](int o, long long i, int) { B0[o] = P.C[mu][i]; });
+                __syncthreads();
+                Cplx<T>* R = fft_lines(P, tws, B0, B1, false);
+                for_elems(P, grp, [&](int o, long long i, int j) {
+                    const T km = wavenumber(P, mu, i, j);
+                    const Cplx<T> d = {-km * R[o].y, km * R[o].x};
+                    B2[o] = mu == 0 ? d : Cplx<T>{B2[o].x + d.x, B2[o].y + d.y};
+                });
+                __syncthreads();
+            }
+            for (int jo = 0; jo < P.nout; ++jo) {
+                const T cgF = P.cgF[jo], cg = P.cg[jo];
+                for_elems(P, grp, [&](int o, long long i, int) {
+                    const Cplx<T> au = cmul(P.M[i], P.Cu[i]);
+                    B0[o] = {cgF * B2[o].x - cg * au.x, cgF * B2[o].y - cg * au.y};
+                });
+                __syncthreads();
+                Cplx<T>* R = fft_lines(P, tws, B0, B1, true);
+                Cplx<T>* D = P.C[jo];
+                for_elems(P, grp, [&](int o, long long i, int) { D[i] = {R[o].x * inv_n, R[o].y * inv_n}; });
+                __syncthreads();
+            }
+        } else if (MODE == PM_FINAL_OUT) {
+            for (int jo = 0; jo < P.nout; ++jo) {
+                for_elems(P, grp, [&](int o, long long i, int) { B0[o] = P.C[jo][i]; });
+                __syncthreads();
+                Cplx<T>* R = fft_lines(P, tws, B0, B1, true);
+                T* out = P.out[jo];
+                for_elems(P, grp, [&](int o, long long i, int) {
+                    const T u = P.x[i];
+                    T v = P.cu[jo] * u + R[o].x * inv_n +
+                          P.cgF[jo] * (P.r[0] + u * (P.r[1] + u * (P.r[2] + u * P.r[3])));
+                    for (int e = 0; e < P.nx; ++e) v += P.cx[jo][e] * P.X[e][i];
+                    out[i] = v;
+                });
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+    }
+}
+
+int ilog2(long long v) {
+    int l = 0;
+    while ((1LL << l) < v) ++l;
+    return l;
 }
 
 int g_sms = 0;
@@ -154,82 +273,184 @@ int sms() {
     return g_sms;
 }
 
-unsigned pw_grid(long long N) { return unsigned(std::min<long long>((N + 255) / 256, 8LL * sms())); }
+// Buffers of shared memory a mode needs besides the twiddles.
+int mode_buffers(int mode) { return (mode == PM_PIVOT_DERIV || mode == PM_PIVOT_DIV) ? 3 : 2; }
 
-// forward (inverse = 0) or inverse (1, scaled by 1/N) transform over every axis, in place
+size_t pass_smem(int n, int G, int pitch, int nb, size_t cs) { return (size_t(n / 2) + size_t(nb) * G * pitch) * cs; }
+
+// Geometry of a pass along `axis`: G lines per block, as many as keep at least two blocks per
+// SM busy and fit the shared memory, and along strided axes at least one full 32-byte sector.
 template <typename T>
-cudaError_t fft_all(const PeriodicArgs<T>& P, Cplx<T>* c, int inverse, cudaStream_t st) {
+Pass<T> make_pass(const PeriodicArgs<T>& A, int axis, int mode) {
+    Pass<T> P{};
+    P.axis = axis;
+    P.dim = A.dim;
     long long Q = 1;
-    for (int mu = 0; mu < P.dim; ++mu) {
-        const int n = P.n[mu];
-        int logn = 0;
-        while ((1 << logn) < n) ++logn;
-        const long long lines = P.N / n;
-        const unsigned grid = unsigned(std::min<long long>(lines, 4LL * sms()));
-        const int threads = std::min(256, std::max(32, n / 2));
-        fft_axis_kernel<T><<<grid, threads, 2 * n * sizeof(Cplx<T>), st>>>(c, n, logn, Q, lines, P.tw[mu], inverse);
-        const cudaError_t e = cudaGetLastError();
+    for (int m = 0; m < A.dim; ++m) {
+        P.nn[m] = A.n[m];
+        P.logQs[m] = ilog2(Q);
+        P.k[m] = A.k[m];
+        P.a[m] = A.a[m];
+        P.b[m] = A.b[m];
+        P.C[m] = A.C[m];
+        Q *= A.n[m];
+    }
+    P.n = A.n[axis];
+    P.logn = ilog2(P.n);
+    P.logQ = P.logQs[axis];
+    const long long Qa = 1LL << P.logQ;
+    const long long lines = A.N / P.n;
+    const long long limit = P.logQ == 0 ? lines : Qa;     // a group stays inside one outer index
+    const size_t cs = sizeof(Cplx<T>);
+    const int nb = mode_buffers(mode);
+    auto pitch_of = [&](int) { return P.logQ == 0 ? P.n : P.n + 1; };
+    int G = 1;
+    auto fits = [&](int g2) { return g2 <= limit && pass_smem(P.n, g2, pitch_of(g2), nb, cs) <= kPassSmemMax; };
+    while (fits(2 * G) && lines / (2 * G) >= 2LL * sms()) G *= 2;
+    while (P.logQ > 0 && size_t(G) * cs < 32 && fits(2 * G)) G *= 2;
+    P.G = G;
+    P.logG = ilog2(G);
+    P.pitch = pitch_of(G);
+    P.log_gpp = P.logQ > P.logG ? P.logQ - P.logG : 0;
+    P.groups = lines / G;
+    P.tw = A.tw[axis];
+    P.Cu = A.Cu;
+    for (int i = 0; i < 4; ++i) P.r[i] = T(A.r[i]);
+    return P;
+}
+
+template <typename T, int MODE>
+cudaError_t launch_pass_on(const Pass<T>& P, cudaStream_t st) {
+    const size_t smem = pass_smem(P.n, P.G, P.pitch, mode_buffers(MODE), sizeof(Cplx<T>));
+    const int work = std::max(P.G * (P.n >> 1), 1);
+    const int threads = std::min(kPassThreads, (work + 31) / 32 * 32);
+    const long long grid = std::min<long long>(P.groups, 64LL * sms());
+    fourier_pass_kernel<T, MODE><<<unsigned(grid), threads, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t prepare_impl() {
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void* f) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kPassSmemMax));
+    };
+    set(reinterpret_cast<const void*>(fourier_pass_kernel<T, PM_FWD_REAL>));
+    set(reinterpret_cast<const void*>(fourier_pass_kernel<T, PM_PLAIN>));
+    set(reinterpret_cast<const void*>(fourier_pass_kernel<T, PM_PIVOT_MULT>));
+    set(reinterpret_cast<const void*>(fourier_pass_kernel<T, PM_FINAL_AXPY>));
+    set(reinterpret_cast<const void*>(fourier_pass_kernel<T, PM_PIVOT_DERIV>));
+    set(reinterpret_cast<const void*>(fourier_pass_kernel<T, PM_FLUX>));
+    set(reinterpret_cast<const void*>(fourier_pass_kernel<T, PM_PIVOT_DIV>));
+    set(reinterpret_cast<const void*>(fourier_pass_kernel<T, PM_FINAL_OUT>));
+    sms();
+    return e;
+}
+
+// The passes along the middle axes (x2 of a 3-D grid), forward or inverse, on na arrays.
+template <typename T>
+cudaError_t middle_passes(const PeriodicArgs<T>& A, Cplx<T>* const* arrays, int na, int inverse, cudaStream_t st) {
+    for (int ax = 1; ax + 1 < A.dim; ++ax) {
+        const int axis = inverse ? A.dim - 1 - ax : ax;
+        Pass<T> P = make_pass(A, axis, PM_PLAIN);
+        for (int a = 0; a < na; ++a) P.C[a] = arrays[a];
+        P.na = na;
+        P.inverse = inverse;
+        const cudaError_t e = launch_pass_on<T, PM_PLAIN>(P, st);
         if (e != cudaSuccess) return e;
-        Q *= n;
     }
     return cudaSuccess;
 }
 
 template <typename T>
-cudaError_t rhs_impl(const PeriodicArgs<T>& P, const StencilArgs<T>& s, cudaStream_t st) {
-    if (s.nout < 1 || s.nout > kMaxOut || s.nx < 0 || s.nx > kMaxExtra || !s.u) return cudaErrorInvalidValue;
-    const long long N = P.N;
-    const unsigned g = pw_grid(N);
+cudaError_t rhs_impl(const PeriodicArgs<T>& A, const StencilArgs<T>& s, cudaStream_t st) {
+    if (s.nout < 1 || s.nout > kMaxOut || s.nout > A.dim || s.nx < 0 || s.nx > kMaxExtra || !s.u)
+        return cudaErrorInvalidValue;
+    const int d = A.dim, last = d - 1;
     cudaError_t e;
-    to_cplx_kernel<T><<<g, 256, 0, st>>>(s.u, P.Cu, N);
-    if ((e = fft_all(P, P.Cu, 0, st)) != cudaSuccess) return e;
-    long long Q = 1;
-    for (int mu = 0; mu < P.dim; ++mu) {
-        deriv_kernel<T><<<g, 256, 0, st>>>(P.Cu, P.Ct, P.k[mu], P.n[mu], Q, N);
-        if ((e = fft_all(P, P.Ct, 1, st)) != cudaSuccess) return e;
-        flux_kernel<T><<<g, 256, 0, st>>>(P.Ct, P.a[mu], P.b[mu], s.u, N);
-        if ((e = fft_all(P, P.Ct, 0, st)) != cudaSuccess) return e;
-        divacc_kernel<T><<<g, 256, 0, st>>>(P.Ct, P.Cs, P.k[mu], P.n[mu], Q, N, mu == 0 ? 1 : 0);
-        Q *= P.n[mu];
+    {   // Cu = F_1 u
+        Pass<T> P = make_pass(A, 0, PM_FWD_REAL);
+        P.x = s.u;
+        P.C[0] = A.Cu;
+        if ((e = launch_pass_on<T, PM_FWD_REAL>(P, st)) != cudaSuccess) return e;
     }
-    for (int j = 0; j < s.nout; ++j) {
-        const T cgF = T(s.cg[j] + s.cF[j]);
-        spec_out_kernel<T><<<g, 256, 0, st>>>(P.Cs, P.Cu, P.sym, P.Ct, cgF, T(s.cg[j]), N);
-        if ((e = fft_all(P, P.Ct, 1, st)) != cudaSuccess) return e;
-        RealOut<T> ro;
-        ro.u = s.u;
-        ro.nx = s.nx;
-        ro.cu = T(s.cu[j]);
-        ro.cgF = cgF;
-        for (int q = 0; q < 4; ++q) ro.r[q] = T(P.r[q]);
-        for (int x = 0; x < kMaxExtra; ++x) {
-            ro.X[x] = s.X[x];
-            ro.cx[x] = T(s.cx[j][x]);
+    Cplx<T>* cu_only[1] = {A.Cu};
+    if ((e = middle_passes(A, cu_only, 1, 0, st)) != cudaSuccess) return e;
+    {   // u^ and i k_mu u^, back along the pivot axis
+        Pass<T> P = make_pass(A, last, PM_PIVOT_DERIV);
+        if ((e = launch_pass_on<T, PM_PIVOT_DERIV>(P, st)) != cudaSuccess) return e;
+    }
+    Cplx<T>* const* Cs = A.C;
+    if ((e = middle_passes(A, Cs, d, 1, st)) != cudaSuccess) return e;
+    {   // fluxes, forward along x1
+        Pass<T> P = make_pass(A, 0, PM_FLUX);
+        P.x = s.u;
+        if ((e = launch_pass_on<T, PM_FLUX>(P, st)) != cudaSuccess) return e;
+    }
+    if ((e = middle_passes(A, Cs, d, 0, st)) != cudaSuccess) return e;
+    {   // divergence and the stage outputs in Fourier space, back along the pivot axis
+        Pass<T> P = make_pass(A, last, PM_PIVOT_DIV);
+        P.M = A.sym;
+        P.nout = s.nout;
+        for (int j = 0; j < s.nout; ++j) {
+            P.cgF[j] = T(s.cg[j] + s.cF[j]);
+            P.cg[j] = T(s.cg[j]);
         }
-        real_out_kernel<T><<<g, 256, 0, st>>>(ro, P.Ct, s.out[j], N);
+        if ((e = launch_pass_on<T, PM_PIVOT_DIV>(P, st)) != cudaSuccess) return e;
     }
-    return cudaGetLastError();
+    if ((e = middle_passes(A, Cs, s.nout, 1, st)) != cudaSuccess) return e;
+    {   // stage outputs in real space
+        Pass<T> P = make_pass(A, 0, PM_FINAL_OUT);
+        P.x = s.u;
+        P.nout = s.nout;
+        P.nx = s.nx;
+        for (int x = 0; x < kMaxExtra; ++x) P.X[x] = s.X[x];
+        for (int j = 0; j < s.nout; ++j) {
+            P.out[j] = s.out[j];
+            P.cu[j] = T(s.cu[j]);
+            P.cgF[j] = T(s.cg[j] + s.cF[j]);
+            for (int x = 0; x < kMaxExtra; ++x) P.cx[j][x] = T(s.cx[j][x]);
+        }
+        if ((e = launch_pass_on<T, PM_FINAL_OUT>(P, st)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <typename T>
-cudaError_t multiplier_impl(const PeriodicArgs<T>& P, const Cplx<T>* M, const T* x, T* y, const T* base, double alpha,
+cudaError_t multiplier_impl(const PeriodicArgs<T>& A, const Cplx<T>* M, const T* x, T* y, const T* base, double alpha,
                             cudaStream_t st) {
     if (!M || !x || !y) return cudaErrorInvalidValue;
-    const long long N = P.N;
-    const unsigned g = pw_grid(N);
+    const int last = A.dim - 1;
     cudaError_t e;
-    to_cplx_kernel<T><<<g, 256, 0, st>>>(x, P.Ct, N);
-    if ((e = fft_all(P, P.Ct, 0, st)) != cudaSuccess) return e;
-    mul_kernel<T><<<g, 256, 0, st>>>(P.Ct, M, N);
-    if ((e = fft_all(P, P.Ct, 1, st)) != cudaSuccess) return e;
-    axpy_out_kernel<T><<<g, 256, 0, st>>>(P.Ct, base, y, T(alpha), N);
-    return cudaGetLastError();
+    {
+        Pass<T> P = make_pass(A, 0, PM_FWD_REAL);
+        P.x = x;
+        if ((e = launch_pass_on<T, PM_FWD_REAL>(P, st)) != cudaSuccess) return e;
+    }
+    Cplx<T>* c0[1] = {A.C[0]};
+    if ((e = middle_passes(A, c0, 1, 0, st)) != cudaSuccess) return e;
+    {
+        Pass<T> P = make_pass(A, last, PM_PIVOT_MULT);
+        P.M = M;
+        if ((e = launch_pass_on<T, PM_PIVOT_MULT>(P, st)) != cudaSuccess) return e;
+    }
+    if ((e = middle_passes(A, c0, 1, 1, st)) != cudaSuccess) return e;
+    {
+        Pass<T> P = make_pass(A, 0, PM_FINAL_AXPY);
+        P.y = y;
+        P.base = base;
+        P.alpha = T(alpha);
+        if ((e = launch_pass_on<T, PM_FINAL_AXPY>(P, st)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace
 
-int periodic_rhs_launches(int dim, int nout) { return 1 + dim + dim * (2 * dim + 3) + nout * (dim + 2); }
-int periodic_multiplier_launches(int dim) { return 2 * dim + 3; }
+cudaError_t periodic_prepare(bool fp64) { return fp64 ? prepare_impl<double>() : prepare_impl<float>(); }
+
+int periodic_rhs_launches(int dim, int nout) { (void)nout; return 5 + 4 * (dim - 2); }
+int periodic_multiplier_launches(int dim) { return 3 + 2 * (dim - 2); }
 
 cudaError_t launch_periodic_rhs(const PeriodicArgs<double>& P, const StencilArgs<double>& s, cudaStream_t st) {
     return rhs_impl(P, s, st);

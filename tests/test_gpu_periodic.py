@@ -6,8 +6,12 @@ Tolerances (relative l2):
     the FFT's rounding (about 1e-16 log2 N relative to the coefficients) by up to k_max^2,
     k_max = (n/2)(2 pi / L), which is 1e2 to 1e3 on these grids.
   * FP64 time integration 1e-11 (the same amplification, once per step, damped by e^{tau A}).
-  * FP32: 2e-5 on the full E3 horizon (256 steps at n = 256): single precision rounding of
-    the FFTs (about 6e-8 log2 N) amplified the same way.
+  * FP32: 1e-4 on the full E3 horizon (256 steps at n = 256). Each FP32 transform leaves a
+    rounding error of about eps32 log2(N) = 6e-8 x 16 = 1e-6 of the state spread over all modes;
+    the flux divergence multiplies it by up to a^max k_max^2 (0.67 x 42.7^2 = 1.2e3) and the step
+    by tau = 1/64, so each step adds about 2e-5 in the highest modes, which e^{tau A} then damps;
+    random-walk accumulation over sqrt(256) = 16 steps' worth of surviving modes gives an
+    estimate of 7e-5.
 Grids include the largest line (n = 1024), the degenerate n = 2 direction (modes 0 and
 Nyquist only), non-square 2-D and 3-D shapes.
 """
@@ -121,7 +125,7 @@ def test_e3_workload_fp32_full_horizon(scheme):
     ref = O.solve_periodic(w.dims, L, a, b, w.r_poly, w.u0, w.tau, w.m, scheme)
     err = O.rel_l2(host(u), ref)
     print(f"E3 n=256 {scheme} fp32: rel l2 {err:.3e}")
-    assert err < 2e-5
+    assert err < 1e-4
 
 
 def test_graph_replay_equals_direct_steps():
@@ -152,15 +156,16 @@ def test_integrate_host_equals_device():
 def test_context_facts_and_launch_count():
     w, L, a, b = W.periodic_instance((32, 16), scheme="etd2rk")
     ctx = context(w, L, a, b)
-    assert ctx.phi_route() == 3
+    assert ctx.phi_route()[0] == "fourier"
     info = ctx.info()
     assert info["kappa"][:2] == [1.0, 1.0]
     assert info["abar"] == pytest.approx(max(x.max() for x in a))
     assert info["beta"][0] == pytest.approx(b[0].mean()) and info["beta"][1] == pytest.approx(b[1].mean())
-    d = 2
-    rhs = lambda nout: 1 + d + d * (2 * d + 3) + nout * (d + 2)   # noqa: E731
-    mult = 2 * d + 3
-    assert ctx.kernels_per_step() == rhs(2) + mult + rhs(1) + mult   # ETD2RK: 2 stages, 2 phi actions
+    # 2-D: a right-hand side is 5 fused passes, a Fourier multiplier 3; ETD2RK has 2 of each
+    assert ctx.kernels_per_step() == 2 * 5 + 2 * 3
+    w3, L3, a3, b3 = W.periodic_instance((8, 16, 8), scheme="lawson2a")
+    ctx3 = context(w3, L3, a3, b3)
+    assert ctx3.kernels_per_step() == 2 * 9 + 3 * 5   # 3-D: 9 and 5 passes
     ops = ctx.profile_step(dev(w.u0))
     assert [k for k, _ in ops] == [6, 7, 6, 7]
 
