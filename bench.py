@@ -384,7 +384,17 @@ GRID_WORKLOADS = {
     "e3-etd2rk": (lambda W: W.config_e3(n=256, scheme="etd2rk"), "fp64"),
     "e3-lawson4": (lambda W: W.config_e3(n=256, scheme="lawson4"), "fp64"),
 }
-FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (nominal; no measured figure on this machine)
+FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64, nominal (context only; rooflines use the measured rate)
+
+
+def alu_peak(prec):
+    """Measured FMA peak (TFLOP/s) for an ALU-bound roofline, with its description: an FMA-chain
+    kernel of the library on every SM (adr_measure_peak), timed with CUDA events."""
+    from paper_2303_15861_gb300 import adr
+    kind = "fp64_fma" if prec == "fp64" else "fp32_fma"
+    iters = 256 if prec == "fp64" else 4096
+    peak = max(adr.adr_measure_peak(kind, iters) for _ in range(3))
+    return peak, f"measured: {kind} loop on every SM (adr_measure_peak), best of 3; nominal FP64 {FP64_NOMINAL_TFLOPS}"
 
 
 def ours_grid(args):
@@ -506,12 +516,10 @@ def ours_grid(args):
         c_ms = statistics.mean(kinds.get(7, [float("nan")]))
         flops = 10.0 * N * math.log2(N) + 8.0 * N
         ach = flops / (c_ms * 1e-3) / 1e12
-        peak = FP64_NOMINAL_TFLOPS if prec == "fp64" else SMS * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
+        peak, src = alu_peak(prec)
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": None, "kernel": "Fourier multiplier (three fourier_pass_kernel launches)",
-                "launch_ms": c_ms, "algorithmic_flops_per_launch": flops,
-                "peak_source": "nominal FP64 (not measured on this pool)" if prec == "fp64"
-                else "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+                "launch_ms": c_ms, "algorithmic_flops_per_launch": flops, "peak_source": src}
     elif prec == "bf16x3":
         c_ms = statistics.mean(kinds.get(4, [float("nan")]))
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -523,11 +531,10 @@ def ours_grid(args):
     else:
         c_ms = statistics.mean(kinds.get(3, [float("nan")]))
         ach = 2.0 * n * N / (c_ms * 1e-3) / 1e12
-        peak = FP64_NOMINAL_TFLOPS if prec == "fp64" else SMS * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
+        peak, src = alu_peak(prec)
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": None, "kernel": "contract_kernel (SIMT mu-mode pass)", "launch_ms": c_ms,
-                "peak_source": "nominal FP64 (not measured on this pool)" if prec == "fp64"
-                else "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+                "peak_source": src}
     line = dict(base, value=value, ms_per_step=ms / args.steps, us_per_time_step=per_step_us,
                 e2e={"value": N * w.m * e2e_n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * dt.itemsize,
                      "d2h_bytes_per_step": N * dt.itemsize},
@@ -540,6 +547,7 @@ def ours_grid(args):
 
 # ----------------------------------------------------------------------------- batched 2-D
 BATCH_METRIC = "DOF*steps/s, 512 batched 2-D ETD2RK instances (FP32, tol 1e-5 vs FP64 oracle)"
+BATCH_PER_RANK = 512           # instances per rank (weak scaling: the rank's block of one global draw)
 FP32_LANES_PER_SM = 128        # FP32 FMA lanes per SM (4 SMSPs x 32)
 SMS = 152
 
@@ -589,11 +597,9 @@ def reference_batch(args):
 def ours_batch(args):
     import numpy as np
     import torch
-    from paper_2303_15861_gb300 import adr, build_lib, workloads as W
+    from paper_2303_15861_gb300 import adr, build_lib, ranks, workloads as W
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = ranks.rank_env()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -605,7 +611,9 @@ def ours_batch(args):
     adr.load_library()
     prec = "fp64" if args.precision == "fp64" else "fp32"
     dt = torch.float64 if prec == "fp64" else torch.float32
-    ws = W.config4()
+    # weak scaling: a draw of 512 instances per rank; rank r advances its own block of them
+    lo, hi = ranks.shard(BATCH_PER_RANK * world, rank, world)
+    ws = W.config4(count=BATCH_PER_RANK * world, select=range(lo, hi))
     N = sum(w.dof for w in ws)
     m = ws[0].m
     stream = torch.cuda.Stream()
@@ -646,11 +654,9 @@ def ours_batch(args):
         sampler.stop()
         ms = ev0.elapsed_time(ev1)
         ctx.synchronize()
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-        value = world * N * m * args.steps / (ms_max * 1e-3)
+        ms_max = ranks.reduce_scalar(ms, "max", dist, "cuda")
+        N_all = ranks.reduce_scalar(N, "sum", dist, "cuda")      # DOF of all ranks' instances
+        value = N_all * m * args.steps / (ms_max * 1e-3)
 
         # per-op durations of one step: contractions (kind 3) and stencils (kind 2)
         kinds = {}
@@ -666,8 +672,8 @@ def ours_batch(args):
         e2e_steps = max(1, args.steps // 2)
         for _ in range(e2e_steps):
             ctx.integrate_host(host, 0.0, m * ws[0].tau, m)
-        e2e_s = time.perf_counter() - te
-        e2e_value = world * N * m * e2e_steps / e2e_s
+        e2e_s = ranks.reduce_scalar(time.perf_counter() - te, "max", dist, "cuda")
+        e2e_value = N_all * m * e2e_steps / e2e_s
 
         acc = {}
         if rank == 0 and not args.no_fp64:
@@ -694,14 +700,13 @@ def ours_batch(args):
     flops_pass = sum(2.0 * w.dims[0] * w.dims[1] * (w.dims[0] + w.dims[1]) / 2.0 for w in ws)
     c_ms = statistics.mean(kinds.get(3, [float("nan")]))
     clk = sampler.summary()
-    mhz = clk["sm_mhz"] or 2070.0
-    peak = SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12 if prec == "fp32" else None
+    peak, src = alu_peak(prec)
     achieved = flops_pass / (c_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak if peak else None, "traffic": None,
-            "kernel": "batch_contract_kernel (mu-mode pass over all instances, FP32 FMA)",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "batch_contract_kernel (mu-mode pass over all instances, FMA)",
             "launch_ms": c_ms, "stencil_launch_ms": statistics.mean(kinds.get(2, [float("nan")])),
-            "peak_source": f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flops x {mhz:.0f} MHz"}
+            "peak_source": src}
     cpu = None
     if not args.no_cpu:
         t_cpu, d_cpu = batch_oracle_sample(ws, stride=1)
@@ -713,7 +718,8 @@ def ours_batch(args):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": "2d_batch512_etd2rk_T0.1_m30", "instances": len(ws), "dof": N, "precision": prec,
-                   "time_steps_per_bench_step": m, "parallelism": f"replicas{world}",
+                   "time_steps_per_bench_step": m, "parallelism": f"instances sharded over {world} rank(s)",
+                   "instances_all_ranks": BATCH_PER_RANK * world,
                    "l2": "working set > L2 (factors and six packed state arrays)",
                    "autotuned_tiles": edges, "grid": {f"mode{k}": plan[k][1] for k in (1, 2)}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * (8 if prec == "fp64" else 4),

@@ -277,6 +277,14 @@ adr_status adr_lambda_scan(const adr_params* p, const double* a_nodes, const dou
                            const double* lambdas, int ref_substeps, void* cuda_stream,
                            double* errors, double* best_lambda);
 
+/* Measured arithmetic peak of the current device, for rooflines: independent FMA chains in
+ * registers on every SM (8 blocks of 256 threads per SM), `iters` x 128 FMAs per thread, timed
+ * with CUDA events on a private stream after one shorter warm-up launch. Writes 2 x FMAs / time
+ * in TFLOP/s. kind: ADR_PEAK_FP64_FMA or ADR_PEAK_FP32_FMA. Synchronous; allocates 8 bytes.
+ * ADR_ERR_ARG for an unknown kind, iters outside [1, 2^20] or a NULL pointer. */
+typedef enum { ADR_PEAK_FP64_FMA = 0, ADR_PEAK_FP32_FMA = 1 } adr_peak_kind;
+adr_status adr_measure_peak(int kind, int iters, double* tflops);
+
 /* Number of kernels one adr_step launches (for launch accounting; memsets not counted). */
 int adr_kernels_per_step(const adr_ctx* ctx);
 

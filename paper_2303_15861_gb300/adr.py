@@ -74,6 +74,7 @@ def load_library(path: str = LIB_PATH):
         "adr_kernels_per_step": (ip, [vp]),
         "adr_phi_route_used": (ip, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "adr_stability_bound": (ip, [ip, dp]),
+        "adr_measure_peak": (ip, [ip, ip, dp]),
         "adr_lambda_scan": (ip, [C.POINTER(adr_params), dp, dp, dp, dp, ip, ip, dp, ip, vp, dp, dp]),
         "adr_last_error": (C.c_char_p, [vp]),
         "adr_destroy": (None, [vp]),
@@ -168,6 +169,17 @@ def adr_set_coeffs_periodic(ctx, a_diag, b_field, r_poly):
         raise ValueError("a_diag and b_field must hold the same number of nodal arrays")
     rr, rp = _dbl(r_poly, 4)
     _check(_lib.adr_set_coeffs_periodic(ctx, ap, bp, rp), ctx)
+
+
+PEAK_KIND = {"fp64_fma": 0, "fp32_fma": 1}
+
+
+def adr_measure_peak(kind="fp64_fma", iters=2048):
+    """Measured FMA peak of the current device in TFLOP/s (see adr.h)."""
+    out = C.c_double()
+    _check(load_library().adr_measure_peak(PEAK_KIND[kind] if isinstance(kind, str) else int(kind), int(iters),
+                                           C.byref(out)))
+    return out.value
 
 
 def adr_step(ctx, u, t=0.0):

@@ -137,10 +137,14 @@ def config4_draws(count=512, seed=2303):
             for i in range(count)]
 
 
-def config4(count=512, m=30, T=0.1, seed=2303):
-    """Batched 2-D: independent instances of uneven size, ETD2RK, FP32 state."""
+def config4(count=512, m=30, T=0.1, seed=2303, select=None):
+    """Batched 2-D: independent instances of uneven size, ETD2RK, FP32 state. `select` (a range
+    of instance indices) builds only those instances of the count-instance draw; instance i is
+    the same whichever others are built."""
     out = []
-    for i, d in enumerate(config4_draws(count, seed)):
+    draws = config4_draws(count, seed)
+    for i in (range(count) if select is None else select):
+        d = draws[i]
         dims = (d["n"], d["n"])
         out.append(Workload(
             name=f"batch{i}_{d['n']}", dims=dims,

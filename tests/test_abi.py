@@ -145,3 +145,11 @@ def test_create_rejects_invalid_periodic_params_on_host(lib, kw, status):
 def test_periodic_entry_points_reject_null_contexts(lib):
     dp = C.POINTER(C.c_double)
     assert lib.adr_set_coeffs_periodic(None, dp(), dp(), dp()) == 1
+
+
+def test_measure_peak_validates_arguments_on_host(lib):
+    out = C.c_double()
+    assert lib.adr_measure_peak(0, 16, None) == 1
+    assert lib.adr_measure_peak(7, 16, C.byref(out)) == 1
+    assert lib.adr_measure_peak(0, 0, C.byref(out)) == 1
+    assert lib.adr_measure_peak(1, (1 << 20) + 1, C.byref(out)) == 1
