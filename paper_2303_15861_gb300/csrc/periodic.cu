@@ -2,9 +2,10 @@
 // experiment (Section 5.1, Eq. (ad2d)), where A of Eq. (linop) is diagonal in Fourier space and
 // its matrix functions are multipliers on the Fourier coefficients (Section 5.1).
 //
-// FFT: complex radix-2 transforms along one axis at a time in the Stockham autosort form (each
-// stage reads one shared-memory buffer and writes the other in natural order, so no bit
-// reversal is needed), twiddles e^{-2 pi i j / n}, j < n/2, from a host FP64 table. A block
+// FFT: complex radix-4 transforms (one radix-2 stage first when log2 n is odd) along one axis at
+// a time in the Stockham autosort form (each stage reads one shared-memory buffer and writes the
+// other in natural order, so no bit reversal is needed), twiddles e^{-2 pi i j / n}, j < n/2,
+// from a host FP64 table. A block
 // takes G lines of one axis into shared memory: along x1 the lines are contiguous; along the
 // other axes it takes G neighbouring lines, so that every global access moves G consecutive
 // elements. The inverse transform is unscaled inside the stages; its 1/n is applied once per
@@ -107,25 +108,57 @@ __device__ __forceinline__ T wavenumber(const Pass<T>& P, int mu, long long i, i
     return P.k[mu][(i >> P.logQs[mu]) & (P.nn[mu] - 1)];
 }
 
-// Stockham radix-2 transform of the G lines in src (destroys src and dst); returns the buffer
-// that holds the result (unscaled).
+// Stockham transform of the G lines in src (destroys src and dst); returns the buffer that holds
+// the result (unscaled). Radix-4 stages, after one radix-2 stage when log2 n is odd: a stage over
+// sub-transforms of length Ns takes the four points j + q n/4 (q = 0..3) of butterfly j,
+// r = j mod Ns, scales point q by e^{-2 pi i q r / (4 Ns)} (conjugated for the inverse), forms
+// their 4-point DFT V_k and writes V_k to 4 (j - r) + r + k Ns.
 template <typename T>
 __device__ Cplx<T>* fft_lines(const Pass<T>& P, const Cplx<T>* tws, Cplx<T>* src, Cplx<T>* dst, bool inverse) {
-    const int half = P.n >> 1;
-    const int total = P.G * half;
-    for (int s = 0, Ns = 1; s < P.logn; ++s, Ns <<= 1) {
-        for (int bf = threadIdx.x; bf < total; bf += blockDim.x) {
+    const int half = P.n >> 1, quarter = P.n >> 2;
+    int s = 0, Ns = 1;
+    if (P.logn & 1) {                                     // radix 2 with Ns = 1: all twiddles are 1
+        for (int bf = threadIdx.x; bf < P.G * half; bf += blockDim.x) {
             const int g = bf >> (P.logn - 1), jj = bf & (half - 1);
-            const int r = jj & (Ns - 1);                  // position inside the current sub-transforms
-            Cplx<T> w = tws[r << (P.logn - 1 - s)];       // e^{-2 pi i r / (2 Ns)}
-            if (inverse) w.y = -w.y;
             const Cplx<T>* sl = src + g * P.pitch;
             Cplx<T>* dl = dst + g * P.pitch;
-            const Cplx<T> v0 = sl[jj];
-            const Cplx<T> v1 = cmul(sl[jj + half], w);
-            const int o = ((jj - r) << 1) + r;            // (jj / Ns) 2 Ns + r
-            dl[o] = {v0.x + v1.x, v0.y + v1.y};
-            dl[o + Ns] = {v0.x - v1.x, v0.y - v1.y};
+            const Cplx<T> v0 = sl[jj], v1 = sl[jj + half];
+            dl[2 * jj] = {v0.x + v1.x, v0.y + v1.y};
+            dl[2 * jj + 1] = {v0.x - v1.x, v0.y - v1.y};
+        }
+        __syncthreads();
+        Cplx<T>* t = src;
+        src = dst;
+        dst = t;
+        s = 1;
+        Ns = 2;
+    }
+    for (; s < P.logn; s += 2, Ns <<= 2) {
+        const int lstep = P.logn - 2 - s;                 // n / (4 Ns) = 2^lstep
+        for (int bf = threadIdx.x; bf < P.G * quarter; bf += blockDim.x) {
+            const int g = bf >> (P.logn - 2), jj = bf & (quarter - 1);
+            const int r = jj & (Ns - 1);
+            const Cplx<T>* sl = src + g * P.pitch;
+            Cplx<T>* dl = dst + g * P.pitch;
+            Cplx<T> v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = sl[jj + q * quarter];
+#pragma unroll
+            for (int q = 1; q < 4; ++q) {                 // e^{-2 pi i m / n}, m = q r n / (4 Ns) < 3n/4
+                const int m = (q * r) << lstep;
+                Cplx<T> w = m < half ? tws[m] : Cplx<T>{-tws[m - half].x, -tws[m - half].y};
+                if (inverse) w.y = -w.y;
+                v[q] = cmul(v[q], w);
+            }
+            const Cplx<T> a0 = {v[0].x + v[2].x, v[0].y + v[2].y}, a1 = {v[0].x - v[2].x, v[0].y - v[2].y};
+            const Cplx<T> a2 = {v[1].x + v[3].x, v[1].y + v[3].y}, a3 = {v[1].x - v[3].x, v[1].y - v[3].y};
+            // -i a3 = (a3.y, -a3.x) for the forward transform, +i a3 for the inverse
+            const Cplx<T> ia3 = inverse ? Cplx<T>{-a3.y, a3.x} : Cplx<T>{a3.y, -a3.x};
+            const int o = ((jj - r) << 2) + r;
+            dl[o] = {a0.x + a2.x, a0.y + a2.y};
+            dl[o + Ns] = {a1.x + ia3.x, a1.y + ia3.y};
+            dl[o + 2 * Ns] = {a0.x - a2.x, a0.y - a2.y};
+            dl[o + 3 * Ns] = {a1.x - ia3.x, a1.y - ia3.y};
         }
         __syncthreads();
         Cplx<T>* t = src;
