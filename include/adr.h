@@ -53,7 +53,7 @@ typedef enum {
     ADR_ERR_COMPLEX_SPECTRUM = 5, /* s*p <= 0 (cell Peclet >= 1): no real eigenbasis     */
     ADR_ERR_TIMEOUT = 6,          /* a bounded device wait gave up                      */
     ADR_ERR_STATE = 7,            /* call out of order (e.g. step before set_coeffs)    */
-    ADR_ERR_UNSUPPORTED = 8       /* valid request this build does not implement        */
+    ADR_ERR_UNSUPPORTED = 8       /* valid request the library does not implement       */
 } adr_status;
 
 typedef enum {

@@ -25,7 +25,7 @@ What it follows, function by function:
     exponential), plus Lawson4: Lawson's construction (Section 1) applied to the
     classical fourth-order Runge--Kutta method.
 
-Readings where the paper is silent (also listed in the design doc):
+Readings where the paper is silent:
   * face coefficient a_{i+1/2} = (a_i + a_{i+1}) / 2 of the nodal a (incl. boundary);
   * a_max is the maximum over the nodal samples unless an override is given;
   * beta_mu = b_mu + mean over the two boundary faces x_mu = 0, 1 of the jump of a
