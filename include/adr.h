@@ -267,15 +267,25 @@ adr_status adr_stability_bound(int scheme, double* lambda_min);
  * coefficients and host initial state u0_host of N doubles as in adr_set_coeffs) for m
  * steps with each candidate lambda (lambdas[0..n_lambdas-1], or, when lambdas is NULL,
  * n_lambdas values evenly spaced from adr_stability_bound(p->scheme) to 1), and measure the
- * relative l2 error against a reference: the same semidiscrete problem integrated by
+ * relative error against a reference (norm 0: l2; norm 1: the maximum norm, as the paper's
+ * Section 5 measures errors): the same semidiscrete problem integrated by
  * Lawson4 in FP64 with step tau / ref_substeps (<= 0 selects 8). Writes the errors
  * (INFINITY where a lambda is refused) and the lambda with the smallest error. Runs on
  * cuda_stream and synchronises it; allocates its own device buffers. Finite-difference
- * single grids only (ADR_ERR_ARG for batched or periodic params). */
+ * single grids only (ADR_ERR_ARG for batched or periodic params; see adr_lambda_scan_periodic)
+ * and for a norm other than 0 or 1. */
 adr_status adr_lambda_scan(const adr_params* p, const double* a_nodes, const double b[3],
                            const double r_poly[4], const double* u0_host, int m, int n_lambdas,
-                           const double* lambdas, int ref_substeps, void* cuda_stream,
+                           const double* lambdas, int ref_substeps, int norm, void* cuda_stream,
                            double* errors, double* best_lambda);
+
+/* The same scan for a periodic Fourier problem (p->periodic = 1; coefficients as in
+ * adr_set_coeffs_periodic). With the paper's two-dimensional experiment on 2^6 modes and
+ * 2^8 steps this is the scan behind the lambda values of Section 5.1. */
+adr_status adr_lambda_scan_periodic(const adr_params* p, const double* a_diag, const double* b_field,
+                                    const double r_poly[4], const double* u0_host, int m, int n_lambdas,
+                                    const double* lambdas, int ref_substeps, int norm, void* cuda_stream,
+                                    double* errors, double* best_lambda);
 
 /* Measured arithmetic peak of the current device, for rooflines: independent FMA chains in
  * registers on every SM (8 blocks of 256 threads per SM), `iters` x 128 FMAs per thread, timed

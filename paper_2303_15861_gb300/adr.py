@@ -75,7 +75,8 @@ def load_library(path: str = LIB_PATH):
         "adr_phi_route_used": (ip, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "adr_stability_bound": (ip, [ip, dp]),
         "adr_measure_peak": (ip, [ip, ip, dp]),
-        "adr_lambda_scan": (ip, [C.POINTER(adr_params), dp, dp, dp, dp, ip, ip, dp, ip, vp, dp, dp]),
+        "adr_lambda_scan": (ip, [C.POINTER(adr_params), dp, dp, dp, dp, ip, ip, dp, ip, ip, vp, dp, dp]),
+        "adr_lambda_scan_periodic": (ip, [C.POINTER(adr_params), dp, dp, dp, dp, ip, ip, dp, ip, ip, vp, dp, dp]),
         "adr_last_error": (C.c_char_p, [vp]),
         "adr_destroy": (None, [vp]),
     }
@@ -281,9 +282,29 @@ def adr_stability_bound(scheme):
     return out.value
 
 
+NORM = {"l2": 0, "max": 1}
+
+
 def adr_lambda_scan(dims, tau, scheme, precision, a_nodes, b, r_poly, u0, m, lambdas=None, n_lambdas=8,
-                    ref_substeps=8, abar_override=0.0, stream=None):
+                    ref_substeps=8, abar_override=0.0, stream=None, norm="l2"):
     """Section 3's lambda scan on a small problem: returns (best lambda, [(lambda, error)])."""
+    bb, bp = _dbl(list(b) + [0.0] * (3 - len(b)), 3)
+    a, ap = _dbl(a_nodes)
+    return _scan("adr_lambda_scan", dims, tau, scheme, precision, (ap, bp), r_poly, u0, m, lambdas, n_lambdas,
+                 ref_substeps, abar_override, stream, norm, {}, (a, bb))
+
+
+def adr_lambda_scan_periodic(dims, length, tau, scheme, precision, a_diag, b_field, r_poly, u0, m, lambdas=None,
+                             n_lambdas=8, ref_substeps=8, stream=None, norm="l2"):
+    """The lambda scan of a periodic Fourier problem: returns (best lambda, [(lambda, error)])."""
+    a, ap = _dbl(np.stack([np.ravel(np.asarray(x, dtype=np.float64)) for x in a_diag]))
+    b, bp = _dbl(np.stack([np.ravel(np.asarray(x, dtype=np.float64)) for x in b_field]))
+    return _scan("adr_lambda_scan_periodic", dims, tau, scheme, precision, (ap, bp), r_poly, u0, m, lambdas,
+                 n_lambdas, ref_substeps, 0.0, stream, norm, {"periodic": 1, "length": float(length)}, (a, b))
+
+
+def _scan(name, dims, tau, scheme, precision, coef_ptrs, r_poly, u0, m, lambdas, n_lambdas, ref_substeps,
+          abar_override, stream, norm, extra, keep):
     lib = load_library()
     p = adr_params()
     p.dim = len(dims)
@@ -293,8 +314,9 @@ def adr_lambda_scan(dims, tau, scheme, precision, a_nodes, b, r_poly, u0, m, lam
     p.tau = float(tau)
     p.scheme = SCHEME[scheme] if isinstance(scheme, str) else int(scheme)
     p.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
-    a, ap = _dbl(a_nodes)
-    bb, bp = _dbl(list(b) + [0.0] * (3 - len(b)), 3)
+    for k, v in extra.items():
+        setattr(p, k, v)
+    ap, bp = coef_ptrs
     rr, rp = _dbl(r_poly, 4)
     uu, up = _dbl(u0)
     if lambdas is not None:
@@ -307,8 +329,10 @@ def adr_lambda_scan(dims, tau, scheme, precision, a_nodes, b, r_poly, u0, m, lam
         lam_list = [1.0] if n_lambdas == 1 else [lo + (1.0 - lo) * i / (n_lambdas - 1) for i in range(n_lambdas)]
     errs = (C.c_double * int(n_lambdas))()
     best = C.c_double()
-    _check(lib.adr_lambda_scan(C.byref(p), ap, bp, rp, up, int(m), int(n_lambdas), lamp, int(ref_substeps),
-                               _stream_handle(stream), errs, C.byref(best)))
+    _check(getattr(lib, name)(C.byref(p), ap, bp, rp, up, int(m), int(n_lambdas), lamp, int(ref_substeps),
+                              NORM[norm] if isinstance(norm, str) else int(norm), _stream_handle(stream), errs,
+                              C.byref(best)))
+    del keep
     return best.value, list(zip(lam_list, list(errs)))
 
 

@@ -6,6 +6,7 @@
 // u' = lambda z u + (1 - lambda) z u, split as A = lambda z and g(u) = (1 - lambda) z u
 // (Section 2; z = tau times an eigenvalue of the diffusion operator, z <= 0). The scheme
 // is unconditionally stable for lambda when |Phi(z, lambda)| <= 1 for all z <= 0.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -97,12 +98,14 @@ extern "C" adr_status adr_stability_bound(int scheme, double* lambda_min) {
     return ADR_OK;
 }
 
-extern "C" adr_status adr_lambda_scan(const adr_params* p, const double* a_nodes, const double b[3],
-                                      const double r_poly[4], const double* u0_host, int m, int n_lambdas,
-                                      const double* lambdas, int ref_substeps, void* cuda_stream,
-                                      double* errors, double* best_lambda) {
-    if (!p || !a_nodes || !b || !r_poly || !u0_host || !errors || !best_lambda) return ADR_ERR_ARG;
-    if (m < 1 || n_lambdas < 1 || p->batch != 0 || p->periodic || (p->dim != 2 && p->dim != 3)) return ADR_ERR_ARG;
+namespace {
+
+// The scan itself: `setup` gives a context its coefficients (grid or periodic form).
+template <typename Setup>
+adr_status scan(const adr_params* p, Setup setup, const double* u0_host, int m, int n_lambdas, const double* lambdas,
+                int ref_substeps, int norm, void* cuda_stream, double* errors, double* best_lambda) {
+    if (!u0_host || !errors || !best_lambda || (norm != 0 && norm != 1)) return ADR_ERR_ARG;
+    if (m < 1 || n_lambdas < 1 || p->batch != 0 || (p->dim != 2 && p->dim != 3)) return ADR_ERR_ARG;
     if (ref_substeps <= 0) ref_substeps = 8;
     size_t N = 1;
     for (int d = 0; d < p->dim; ++d) {
@@ -142,7 +145,7 @@ extern "C" adr_status adr_lambda_scan(const adr_params* p, const double* a_nodes
         q.tau = p->tau / ref_substeps;
         adr_ctx* c = nullptr;
         adr_status st = adr_create(&q, cuda_stream, &c);
-        if (st == ADR_OK) st = adr_set_coeffs(c, 0, a_nodes, b, r_poly);
+        if (st == ADR_OK) st = setup(c);
         if (st == ADR_OK && cudaMemcpyAsync(d_ref, u0_host, N * 8, cudaMemcpyHostToDevice, s) != cudaSuccess)
             st = ADR_ERR_CUDA;
         if (st == ADR_OK) st = adr_integrate(c, d_ref, 0.0, 0.0, m * ref_substeps);
@@ -152,9 +155,9 @@ extern "C" adr_status adr_lambda_scan(const adr_params* p, const double* a_nodes
         adr_destroy(c);
         if (st != ADR_OK) { cleanup(); return st; }
     }
-    double rnorm = 0.0;
-    for (double v : ref) rnorm += v * v;
-    rnorm = std::sqrt(rnorm);
+    double rnorm = 0.0;   // norm 0: l2, norm 1: max
+    for (double v : ref) rnorm = norm ? std::max(rnorm, std::fabs(v)) : rnorm + v * v;
+    if (!norm) rnorm = std::sqrt(rnorm);
 
     std::vector<float> f32(N);
     int best = -1;
@@ -163,7 +166,7 @@ extern "C" adr_status adr_lambda_scan(const adr_params* p, const double* a_nodes
         q.lambda = cand[static_cast<size_t>(i)];
         adr_ctx* c = nullptr;
         adr_status st = adr_create(&q, cuda_stream, &c);
-        if (st == ADR_OK) st = adr_set_coeffs(c, 0, a_nodes, b, r_poly);
+        if (st == ADR_OK) st = setup(c);
         if (st == ADR_OK) {
             if (fp64) {
                 if (cudaMemcpyAsync(d_u, u0_host, N * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) st = ADR_ERR_CUDA;
@@ -187,8 +190,10 @@ extern "C" adr_status adr_lambda_scan(const adr_params* p, const double* a_nodes
         if (!fp64)
             for (size_t k = 0; k < N; ++k) got[k] = f32[k];
         double d = 0.0;
-        for (size_t k = 0; k < N; ++k) d += (got[k] - ref[k]) * (got[k] - ref[k]);
-        errors[i] = rnorm > 0 ? std::sqrt(d) / rnorm : std::sqrt(d);
+        for (size_t k = 0; k < N; ++k)
+            d = norm ? std::max(d, std::fabs(got[k] - ref[k])) : d + (got[k] - ref[k]) * (got[k] - ref[k]);
+        if (!norm) d = std::sqrt(d);
+        errors[i] = rnorm > 0 ? d / rnorm : d;
         if (!std::isfinite(errors[i])) errors[i] = INFINITY;
         if (best < 0 || errors[i] < errors[best]) best = i;
     }
@@ -196,4 +201,24 @@ extern "C" adr_status adr_lambda_scan(const adr_params* p, const double* a_nodes
     if (best < 0 || !std::isfinite(errors[best])) return ADR_ERR_STATE;
     *best_lambda = cand[static_cast<size_t>(best)];
     return ADR_OK;
+}
+
+}  // namespace
+
+extern "C" adr_status adr_lambda_scan(const adr_params* p, const double* a_nodes, const double b[3],
+                                      const double r_poly[4], const double* u0_host, int m, int n_lambdas,
+                                      const double* lambdas, int ref_substeps, int norm, void* cuda_stream,
+                                      double* errors, double* best_lambda) {
+    if (!p || !a_nodes || !b || !r_poly || p->periodic) return ADR_ERR_ARG;
+    return scan(p, [&](adr_ctx* c) { return adr_set_coeffs(c, 0, a_nodes, b, r_poly); }, u0_host, m, n_lambdas,
+                lambdas, ref_substeps, norm, cuda_stream, errors, best_lambda);
+}
+
+extern "C" adr_status adr_lambda_scan_periodic(const adr_params* p, const double* a_diag, const double* b_field,
+                                               const double r_poly[4], const double* u0_host, int m, int n_lambdas,
+                                               const double* lambdas, int ref_substeps, int norm, void* cuda_stream,
+                                               double* errors, double* best_lambda) {
+    if (!p || !a_diag || !b_field || !r_poly || p->periodic != 1) return ADR_ERR_ARG;
+    return scan(p, [&](adr_ctx* c) { return adr_set_coeffs_periodic(c, a_diag, b_field, r_poly); }, u0_host, m,
+                n_lambdas, lambdas, ref_substeps, norm, cuda_stream, errors, best_lambda);
 }

@@ -188,3 +188,23 @@ def test_periodic_context_refuses_grid_coefficients_and_unset_steps():
     ctx.set_coeffs_periodic(a, b, w.r_poly)
     ctx.step(u)
     ctx.synchronize()
+
+
+def test_periodic_lambda_scan_reproduces_the_papers_choice():
+    """Section 3's scan on the paper's 2-D experiment as Section 5.1 runs it (2^6 modes, 2^8
+    steps to T = 4, relative maximum-norm errors), over the lambda values the paper printed for
+    Lawson-Euler: the library's errors equal the oracle's (the same scheme against Lawson4 at
+    tau/8), and the chosen lambda is the paper's (0.218; the table of lambda values gives 0.22)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "e3_lambda_scan_paper.json")))
+    lams = [lam for lam, _ in g["points"]["lawson_euler"]]
+    w, L, a, b = W.config_e3(n=64, scheme="lawson_euler", m=256, T=4.0)
+    best, errs = adr.adr_lambda_scan_periodic(w.dims, L, w.tau, "lawson_euler", "fp64", a, b, w.r_poly, w.u0, w.m,
+                                              lambdas=lams, norm="max")
+    assert best == 0.218
+    ref = O.solve_periodic(w.dims, L, a, b, w.r_poly, w.u0, w.tau / 8, 8 * w.m, "lawson4")
+    for lam, err in (errs[0], errs[7], errs[-1]):
+        got = O.solve_periodic(w.dims, L, a, b, w.r_poly, w.u0, w.tau, w.m, "lawson_euler", lam=lam)
+        want = np.abs(got - ref).max() / np.abs(ref).max()
+        assert abs(err - want) <= 1e-6 * want, (lam, err, want)
