@@ -243,3 +243,25 @@ def periodic_instance(dims, L=2.0 * np.pi, scheme="lawson2a", m=8, T=0.05, seed=
                  b=(0.0, 0.0, 0.0), r_poly=(0.0, 0.25, -0.25, 0.0), u0=np.ascontiguousarray(u0), tau=T / m,
                  m=int(m), scheme=scheme, extra=dict(periodic=True, L=L))
     return w, L, a_diag, b_field
+
+
+def config_e2(n=1024, scheme="lawson_euler", m=4096, T=0.1, embed=False):
+    """The paper's one-dimensional nonlinear diffusion-reaction problem (Section 4, Eq.
+    (adnonlinear)): u_t = (a u_x)_x + u (1 - u) on (-pi, pi), periodic, a = 1 + 10 sin^2 x,
+    u0 = sin x, on n Fourier nodes x_j = -pi + j 2 pi / n. With embed=True the problem is given
+    on n x 2 nodes, constant along x2 (a_22 = a_11, b = 0): the x2 direction then has only the
+    mean and the Nyquist mode, whose first derivative is 0, so the solution stays the 1-D one.
+    Returns (workload, L, a_diag, b_field)."""
+    L = 2.0 * np.pi
+    x = -np.pi + np.arange(n, dtype=np.float64) * (L / n)
+    a = 1.0 + 10.0 * np.sin(x) ** 2
+    u0 = np.sin(x)
+    dims, a_diag, b_field = (n,), [a], [np.zeros(n)]
+    if embed:
+        dims = (n, 2)
+        a2 = np.stack([a, a])
+        a_diag, b_field, u0 = [a2, a2], [np.zeros((2, n)), np.zeros((2, n))], np.stack([u0, u0])
+    w = Workload(name=f"e2_{n}_{scheme}", dims=dims, a_nodes=None, b=(0.0, 0.0, 0.0),
+                 r_poly=(0.0, 1.0, -1.0, 0.0), u0=np.ascontiguousarray(u0), tau=T / m, m=int(m), scheme=scheme,
+                 extra=dict(periodic=True, L=L))
+    return w, L, a_diag, b_field

@@ -208,3 +208,24 @@ def test_periodic_lambda_scan_reproduces_the_papers_choice():
         got = O.solve_periodic(w.dims, L, a, b, w.r_poly, w.u0, w.tau, w.m, "lawson_euler", lam=lam)
         want = np.abs(got - ref).max() / np.abs(ref).max()
         assert abs(err - want) <= 1e-6 * want, (lam, err, want)
+
+
+def test_e2_on_an_embedded_grid_matches_the_1d_oracle_and_the_paper():
+    """The paper's one-dimensional problem (Section 4, Eq. (adnonlinear)) on n x 2 Fourier nodes,
+    constant along x2: Lawson-Euler at lambda = 0.218 with the paper's 2^12 steps to T = 1/10 in
+    FP64. The two rows stay equal, the x1 line equals the 1-D oracle, and its error against a
+    converged reference is the paper's printed 2.574e-4 (the figure of errors against lambda)
+    within 1%."""
+    w, L, a, b = W.config_e2(embed=True, scheme="lawson_euler")
+    ctx = context(w, L, a, b, lam=0.218)
+    u = dev(w.u0)
+    ctx.integrate(u, 0.0, w.m * w.tau, w.m)
+    ctx.synchronize()
+    h = host(u)
+    assert np.allclose(h[0], h[1], rtol=0, atol=1e-15)
+    w1, L1, a1, b1 = W.config_e2(scheme="lawson_euler")
+    ref1 = O.solve_periodic(w1.dims, L1, a1, b1, w1.r_poly, w1.u0, w1.tau, w1.m, "lawson_euler", lam=0.218)
+    assert O.rel_l2(h[0], ref1) < 1e-11
+    conv = O.solve_periodic(w1.dims, L1, a1, b1, w1.r_poly, w1.u0, w1.tau / 4, 4 * w1.m, "lawson4")
+    err = np.abs(h[0] - conv).max() / np.abs(conv).max()
+    assert abs(err / 2.57438011667187e-04 - 1.0) < 0.01, err
