@@ -388,7 +388,10 @@ class PeriodicProblem:
     s(k) = -lambda sum_mu a^max_mu k_mu^2 + i beta . k.
     a_diag, b_field: d nodal arrays each, numpy shape (n_d, ..., n_1)."""
 
-    def __init__(self, dims, L, a_diag, b_field, r_poly, lam=1.0):
+    def __init__(self, dims, L, a_diag, b_field, r_poly, lam=1.0, form="flux"):
+        if form not in ("flux", "adelta"):
+            raise ValueError("form must be 'flux' or 'adelta'")
+        self.form = form
         self.dims = tuple(int(n) for n in dims)
         self.d = len(self.dims)
         self.L = float(L)
@@ -420,18 +423,45 @@ class PeriodicProblem:
         return r0 + u * (r1 + u * (r2 + u * r3))
 
     def F(self, u):
-        """sum_mu D_mu (a_mumu D_mu u + b_mu u) + r(u)."""
+        """sum_mu D_mu (a_mumu D_mu u + b_mu u) + r(u); for form "adelta" (the one-dimensional
+        linear experiment of Section 4, Eq. (adlinearzero)) sum_mu (a_mumu D_mu D_mu u + D_mu (b_mu u)) + r(u)."""
+        if self.form == "adelta":
+            return sum(self.a[mu - 1] * self.D(self.D(u, mu), mu) + self.D(self.bf[mu - 1] * u, mu)
+                       for mu in range(1, self.d + 1)) + self.reaction(u)
         return sum(self.D(self.a[mu - 1] * self.D(u, mu) + self.bf[mu - 1] * u, mu)
                    for mu in range(1, self.d + 1)) + self.reaction(u)
 
     def g(self, u):
-        """Eq. (nonlin): sum_mu D_mu ((a_mumu - lambda a^max) D_mu u + (b_mu - beta_mu) u) + r(u)."""
+        """Eq. (nonlin): sum_mu D_mu ((a_mumu - lambda a^max) D_mu u + (b_mu - beta_mu) u) + r(u);
+        for form "adelta" (Eq. (ex0stab)) (a_mumu - lambda a^max) D_mu D_mu u in place of the flux."""
+        if self.form == "adelta":
+            return sum((self.a[mu - 1] - self.amax[mu - 1]) * self.D(self.D(u, mu), mu)
+                       + self.D((self.bf[mu - 1] - self.beta[mu - 1]) * u, mu)
+                       for mu in range(1, self.d + 1)) + self.reaction(u)
         return sum(self.D((self.a[mu - 1] - self.amax[mu - 1]) * self.D(u, mu)
                           + (self.bf[mu - 1] - self.beta[mu - 1]) * u, mu)
                    for mu in range(1, self.d + 1)) + self.reaction(u)
 
     def A_apply(self, u):
         return np.real(np.fft.ifftn(self.symbol * np.fft.fftn(u)))
+
+
+def periodic_linear_exact(prob: PeriodicProblem, u0, T):
+    """The exact solution exp(T M) u0 of the semidiscrete problem u' = M u = F(u) for a
+    one-dimensional "adelta" problem without advection and reaction (the linear experiment of
+    Section 4, Eq. (adlinearzero)): M = diag(a) D D with D the pseudospectral derivative, which is
+    similar to the symmetric diag(a)^{1/2} D D diag(a)^{1/2}; its eigendecomposition gives the
+    exponential. Dense, so for n up to a few thousand."""
+    if prob.d != 1 or prob.form != "adelta" or any(c != 0.0 for c in prob.r) or np.any(prob.bf[0] != 0.0):
+        raise ValueError("only the 1-D a u_xx problem without advection or reaction")
+    n = prob.dims[0]
+    eye = np.eye(n)
+    D2 = np.real(np.fft.ifft((1j * prob.k[0].reshape(-1, 1)) ** 2 * np.fft.fft(eye, axis=0), axis=0))
+    D2 = 0.5 * (D2 + D2.T)                       # symmetric up to rounding
+    sa = np.sqrt(prob.a[0])
+    w, V = np.linalg.eigh(sa[:, None] * D2 * sa[None, :])
+    u0 = np.asarray(u0, dtype=np.float64)
+    return sa * (V @ (np.exp(T * w) * (V.T @ (u0 / sa))))
 
 
 class PeriodicOps:
@@ -455,9 +485,9 @@ class PeriodicOps:
         return np.real(np.fft.ifftn(phi_complex(k, c * self.tau * self.prob.symbol) * np.fft.fftn(v)))
 
 
-def solve_periodic(dims, L, a_diag, b_field, r_poly, u0, tau, m, scheme, lam=1.0):
+def solve_periodic(dims, L, a_diag, b_field, r_poly, u0, tau, m, scheme, lam=1.0, form="flux"):
     """FP64 oracle solution of the periodic problem after m steps of `scheme`."""
-    prob = PeriodicProblem(dims, L, a_diag, b_field, r_poly, lam=lam)
+    prob = PeriodicProblem(dims, L, a_diag, b_field, r_poly, lam=lam, form=form)
     return integrate(PeriodicOps(prob, tau), u0, m, scheme)
 
 

@@ -265,3 +265,15 @@ def config_e2(n=1024, scheme="lawson_euler", m=4096, T=0.1, embed=False):
                  r_poly=(0.0, 1.0, -1.0, 0.0), u0=np.ascontiguousarray(u0), tau=T / m, m=int(m), scheme=scheme,
                  extra=dict(periodic=True, L=L))
     return w, L, a_diag, b_field
+
+
+def config_e1(n=4096, scheme="lawson_euler", m=64, T=1.0 / 40.0, embed=False):
+    """The paper's one-dimensional linear diffusion problem (Section 4, Eq. (adlinearzero)):
+    u_t = a(x) u_xx on (-pi, pi), periodic, a = 1 + 10 sin^2 x, u0 = sin x, on n Fourier nodes
+    x_j = -pi + j 2 pi / n (the a Lap u form, no advection, no reaction). embed=True gives it on
+    n x 2 nodes, constant along x2, as config_e2 does. Returns (workload, L, a_diag, b_field)."""
+    w, L, a_diag, b_field = config_e2(n=n, scheme=scheme, m=m, T=T, embed=embed)
+    w.name = f"e1_{n}_{scheme}"
+    w.r_poly = (0.0, 0.0, 0.0, 0.0)
+    w.extra = dict(periodic=True, L=L, form="adelta")
+    return w, L, a_diag, b_field

@@ -1,5 +1,14 @@
 """The oracle against numbers the paper prints for its periodic Fourier experiments.
 
+The one-dimensional linear diffusion problem a(x) u_xx (Section 4, Eq. (adlinearzero); the
+figures of errors against the number of steps, one panel per lambda; tests/golden/
+e1_errors_paper.json), against the exact semidiscrete solution, for the printed points with
+m <= 256 (the figures also hold short segments that run off the plotted range above 1e-1; they
+are not data points). Where lambda is at or above the scheme's Table 1 bound (unconditionally
+stable) every point matches: to seven digits at lambda = 1 and within 0.2% at the bound;
+asserted within 3e-3. Below the bound the errors come from growing modes and amplify rounding
+differences: the points agree within 30%, asserted within [0.7, 1.4].
+
 The one-dimensional nonlinear diffusion-reaction problem (Section 4, Eq. (adnonlinear); the
 figure of errors against lambda; tests/golden/e2_lambda_errors_paper.json): every printed point
 of the eight schemes the paper plots and this project implements matches to 0.1%, against a
@@ -83,3 +92,41 @@ def test_e2_errors_match_the_paper(e2, scheme):
         u = O.solve_periodic(w.dims, L, a, b, w.r_poly, w.u0, g["T"] / g["m"], g["m"], scheme, lam=lam)
         ours = np.abs(u - ref).max() / np.abs(ref).max()
         assert abs(ours / paper - 1.0) <= 0.01, (scheme, lam, ours, paper)
+
+
+GOLDEN_E1 = os.path.join(os.path.dirname(__file__), "golden", "e1_errors_paper.json")
+
+
+@pytest.fixture(scope="module")
+def e1():
+    g = json.load(open(GOLDEN_E1))
+    w, L, a, b = W.config_e1(n=g["N"], T=g["T"])
+    prob = O.PeriodicProblem(w.dims, L, a, b, w.r_poly, form="adelta")
+    exact = O.periodic_linear_exact(prob, w.u0, g["T"])
+    return g, w, L, a, b, exact
+
+
+# Table 1 bounds on lambda for unconditional stability (tests/golden/table1_stability_bounds.json)
+TABLE1 = {"lawson_euler": 0.2178, "etd2rk": 0.5, "exponential_euler": 0.5, "erk2p1": 1.0 / 3.0,
+          "stabilized_lawson_euler": 0.18394, "lawson2a": 0.30056, "lawson2b": 0.30056, "stabilized_lawson2": 0.18203}
+
+
+@pytest.mark.parametrize("panel", ["1", "1/2", "1/3", "0.301", "0.218", "1/(2e)", "0.183", "0.17"])
+def test_e1_errors_match_the_paper(e1, panel):
+    g, w, L, a, b, exact = e1
+    p = g["panels"][panel]
+    checked = 0
+    for scheme, pts in p["curves"].items():
+        stable = p["lambda"] >= TABLE1[scheme] - 1e-4
+        for m, paper in pts:
+            if m not in (16, 64, 256) or paper > 0.1:
+                continue
+            u = O.solve_periodic(w.dims, L, a, b, w.r_poly, w.u0, g["T"] / m, m, scheme, lam=p["lambda"],
+                                 form="adelta")
+            ours = np.abs(u - exact).max() / np.abs(exact).max()
+            if stable:
+                assert abs(ours / paper - 1.0) <= 3e-3, (panel, scheme, m, ours, paper)
+            else:
+                assert 0.7 <= ours / paper <= 1.4, (panel, scheme, m, ours, paper)
+            checked += 1
+    assert checked > 0
