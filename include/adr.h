@@ -107,13 +107,16 @@ typedef struct {
 /* Periodic Fourier pseudospectral contexts (periodic = 1; the discretisation of the paper's
  * two-dimensional experiment, Section 5.1, Eq. (ad2d)):
  *     u_t = div(a grad u) + div(b u) + r(u)
+ * or, with form = ADR_FORM_ADELTA (the one-dimensional linear experiment of Section 4, Eq.
+ * (adlinearzero)), u_t = sum_mu a_mumu d_mumu u + div(b u) + r(u)
  * on a periodic box of side `length` with a diagonal diffusion tensor a = diag(a_11, ..., a_dd)
  * and a velocity field b(x), both given at the nodes x_j = x0 + j length / n_mu. Derivatives
  * are spectral (Nyquist wavenumber 0); A = lambda sum_mu a_mumu^max D_mu^2 + beta . D with
  * a^max the nodal maxima and beta_mu the mean of b_mu (Eqs. (linop), (amaxbeta)). A is
  * diagonal in Fourier space, so e^{c tau A} and phi_k(tau A) are multipliers on the Fourier
- * coefficients (ADR_PHI_FOURIER). n_mu must be powers of two in [2, 1024]; ADR_FP64 or
- * ADR_FP32; single grids; bc_hi and form at their defaults. The coefficients are set with
+ * coefficients (ADR_PHI_FOURIER). n_mu must be powers of two in [2, 4096] along x1 and
+ * [2, 1024] along the other axes (a one-dimensional problem runs on n x 2 nodes, constant along
+ * x2); ADR_FP64 or ADR_FP32; single grids; bc_hi at its default. The coefficients are set with
  * adr_set_coeffs_periodic; all other entry points work as for finite-difference contexts. */
 adr_status adr_set_coeffs_periodic(adr_ctx* ctx, const double* a_diag, const double* b_field,
                                    const double r_poly[4]);

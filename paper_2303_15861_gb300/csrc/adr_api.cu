@@ -136,6 +136,7 @@ struct adr_ctx {
     void* d_pb[3] = {nullptr, nullptr, nullptr};   // b_mu at the nodes
     void* d_psym = nullptr;                        // symbol of A
     void* d_pm[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // E(1/2), E(1), E(alpha), phi_1, phi_2
+    void* d_pdif = nullptr;                        // a Lap u form: sum_mu a_mumu D_mu D_mu u
 
     // phi_k route; for the doubling route: X = tau A / 2^s, Taylor terms, level factors
     int phi_route = 0;                     // adr_phi_route in use (0: no phi_k needed)
@@ -424,6 +425,8 @@ adr::PeriodicArgs<T> periodic_args(const adr_ctx* c) {
     }
     P.sym = static_cast<const adr::Cplx<T>*>(c->d_psym);
     for (int i = 0; i < 4; ++i) P.r[i] = c->r[i];
+    P.adelta = c->p.form == ADR_FORM_ADELTA;
+    P.dif = static_cast<T*>(c->d_pdif);
     return P;
 }
 
@@ -1322,8 +1325,10 @@ adr_status create_periodic(const adr_params* p, void* cuda_stream, adr_ctx** out
     if (p->batch != 0) return fail(nullptr, ADR_ERR_UNSUPPORTED, "periodic contexts are single grids");
     if (p->dim != 2 && p->dim != 3) return fail(nullptr, ADR_ERR_ARG, "dim must be 2 or 3");
     for (int m = 0; m < p->dim; ++m)
-        if (!power_of_two(p->n[m]) || p->n[m] > 1024)
-            return fail(nullptr, ADR_ERR_ARG, "periodic contexts need n a power of two in [2, 1024]");
+        if (!power_of_two(p->n[m]) || p->n[m] > (m == 0 ? 4096 : 1024) ||
+            !adr::periodic_line_fits(p->n[m], m, p->dim, p->precision == ADR_FP64))
+            return fail(nullptr, ADR_ERR_ARG,
+                        "periodic contexts need n a power of two in [2, 4096] along x1 and [2, 1024] along the other axes");
     if (!(p->tau > 0.0) || !std::isfinite(p->tau)) return fail(nullptr, ADR_ERR_ARG, "tau must be positive");
     if (!(p->length > 0.0) || !std::isfinite(p->length)) return fail(nullptr, ADR_ERR_ARG, "length must be positive");
     if (p->scheme < ADR_LAWSON_EULER || p->scheme > ADR_STABILIZED_LAWSON2) return fail(nullptr, ADR_ERR_ARG, "unknown scheme");
@@ -1331,8 +1336,8 @@ adr_status create_periodic(const adr_params* p, void* cuda_stream, adr_ctx** out
         return fail(nullptr, ADR_ERR_UNSUPPORTED, "periodic contexts run in ADR_FP64 or ADR_FP32");
     if (p->phi_route != ADR_PHI_AUTO && p->phi_route != ADR_PHI_FOURIER)
         return fail(nullptr, ADR_ERR_ARG, "periodic contexts apply phi_k as Fourier multipliers");
-    if (p->bc_hi != ADR_BC_DIRICHLET || p->form != ADR_FORM_FLUX)
-        return fail(nullptr, ADR_ERR_ARG, "bc_hi and form do not apply to periodic contexts");
+    if (p->bc_hi != ADR_BC_DIRICHLET) return fail(nullptr, ADR_ERR_ARG, "bc_hi does not apply to periodic contexts");
+    if (p->form != ADR_FORM_FLUX && p->form != ADR_FORM_ADELTA) return fail(nullptr, ADR_ERR_ARG, "unknown form");
     size_t N = 1;
     for (int m = 0; m < p->dim; ++m) N *= size_t(p->n[m]);
     if (N > (size_t(1) << 31) - 1) return fail(nullptr, ADR_ERR_ARG, "grid too large");
@@ -1352,6 +1357,7 @@ adr_status create_periodic(const adr_params* p, void* cuda_stream, adr_ctx** out
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
     for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaMalloc(&c->ws[i], N * c->esize);
     for (int i = 0; i <= c->dim && e == cudaSuccess; ++i) e = cudaMalloc(&c->d_pc[i], 2 * N * c->esize);
+    if (e == cudaSuccess && p->form == ADR_FORM_ADELTA) e = cudaMalloc(&c->d_pdif, N * c->esize);
     if (e == cudaSuccess) e = adr::periodic_prepare(c->fp64);
     if (e != cudaSuccess) {
         adr_destroy(c.release());
@@ -1891,6 +1897,7 @@ void adr_destroy(adr_ctx* c) {
     for (auto& q : c->d_pb) free_dev(q);
     free_dev(c->d_psym);
     for (auto& q : c->d_pm) free_dev(q);
+    free_dev(c->d_pdif);
     for (auto& row : c->d_img) for (auto& p : row) { void* q = p; free_dev(q); p = nullptr; }  // 5 kinds
     for (auto& row : c->d_fsc) for (auto& p : row) { void* q = p; free_dev(q); p = nullptr; }
     for (auto& row : c->d_img2) for (auto& p : row) { void* q = p; free_dev(q); p = nullptr; }

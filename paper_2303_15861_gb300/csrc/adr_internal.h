@@ -261,11 +261,16 @@ struct PeriodicArgs {
     const T* b[3] = {nullptr, nullptr, nullptr};          // b_mu at the nodes
     const Cplx<T>* sym = nullptr;          // symbol of A at every Fourier point
     double r[4] = {0, 0, 0, 0};
+    bool adelta = false;                   // a Lap u form: sum_mu a_mumu D_mu D_mu u + D_mu (b_mu u)
+    T* dif = nullptr;                      // adelta: sum_mu a_mumu D_mu D_mu u at the nodes (work)
 };
 
 // Sets the shared-memory limits of the Fourier kernels of one precision (once, before any
 // launch or stream capture).
 cudaError_t periodic_prepare(bool fp64);
+// Whether the lines of an axis (n points; axis 0 = x1, dim - 1 the pivot) fit the shared memory
+// of the Fourier passes.
+bool periodic_line_fits(int n, int axis, int dim, bool fp64);
 // One stage: out_j = cu u + sum_e cx X_e + cg g(u) + cF F(u), F(u) = sum_mu D_mu(a_mumu D_mu u +
 // b_mu u) + r(u), g = F - A u (the grid fields of s are not used; out_j must not alias u).
 // Number of kernel launches:

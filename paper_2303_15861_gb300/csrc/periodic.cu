@@ -77,6 +77,8 @@ struct Pass {
     const T* X[kMaxExtra];
     T* out[kMaxOut];
     T cu[kMaxOut], cx[kMaxOut][kMaxExtra], cgF[kMaxOut], cg[kMaxOut], r[4];
+    int adelta;               // a Lap u form (see PeriodicArgs)
+    T* dif;                   // adelta: sum_mu a_mumu D_mu D_mu u
 };
 
 // Global index of element j of line g of line group grp.
@@ -221,7 +223,8 @@ __global__ void __launch_bounds__(kPassThreads) fourier_pass_kernel(const __grid
             for (int mu = 0; mu < P.dim; ++mu) {
                 for_elems(P, grp, [&](int o, long long i, int j) {
                     const T km = wavenumber(P, mu, i, j);
-                    B2[o] = {-km * U[o].y, km * U[o].x};
+                    if (P.adelta) B2[o] = {-km * km * U[o].x, -km * km * U[o].y};   // (i k)^2 u^
+                    else          B2[o] = {-km * U[o].y, km * U[o].x};              // i k u^
                 });
                 __syncthreads();
                 Cplx<T>* R = fft_lines(P, tws, B2, Fr, true);
@@ -237,9 +240,17 @@ __global__ void __launch_bounds__(kPassThreads) fourier_pass_kernel(const __grid
                 for_elems(P, grp, [&](int o, long long i, int) { B0[o] = D[i]; });
                 __syncthreads();
                 Cplx<T>* R = fft_lines(P, tws, B0, B1, true);
-                for_elems(P, grp, [&](int o, long long i, int) {
-                    R[o] = {am[i] * (R[o].x * inv_n) + bm[i] * P.x[i], T(0)};
-                });
+                if (P.adelta) {      // D_mu D_mu u is complete here: a_mumu times it goes to dif; the flux is b_mu u
+                    for_elems(P, grp, [&](int o, long long i, int) {
+                        const T d2 = am[i] * (R[o].x * inv_n);
+                        P.dif[i] = mu == 0 ? d2 : P.dif[i] + d2;
+                        R[o] = {bm[i] * P.x[i], T(0)};
+                    });
+                } else {
+                    for_elems(P, grp, [&](int o, long long i, int) {
+                        R[o] = {am[i] * (R[o].x * inv_n) + bm[i] * P.x[i], T(0)};
+                    });
+                }
                 __syncthreads();
                 Cplx<T>* R2 = fft_lines(P, tws, R, R == B0 ? B1 : B0, false);
                 for_elems(P, grp, [&](int o, long long i, int) { D[i] = R2[o]; });
@@ -279,6 +290,7 @@ __global__ void __launch_bounds__(kPassThreads) fourier_pass_kernel(const __grid
                     const T u = P.x[i];
                     T v = P.cu[jo] * u + R[o].x * inv_n +
                           P.cgF[jo] * (P.r[0] + u * (P.r[1] + u * (P.r[2] + u * P.r[3])));
+                    if (P.adelta) v += P.cgF[jo] * P.dif[i];
                     for (int e = 0; e < P.nx; ++e) v += P.cx[jo][e] * P.X[e][i];
                     out[i] = v;
                 });
@@ -349,6 +361,8 @@ Pass<T> make_pass(const PeriodicArgs<T>& A, int axis, int mode) {
     P.tw = A.tw[axis];
     P.Cu = A.Cu;
     for (int i = 0; i < 4; ++i) P.r[i] = T(A.r[i]);
+    P.adelta = A.adelta ? 1 : 0;
+    P.dif = A.dif;
     return P;
 }
 
@@ -481,6 +495,13 @@ cudaError_t multiplier_impl(const PeriodicArgs<T>& A, const Cplx<T>* M, const T*
 }  // namespace
 
 cudaError_t periodic_prepare(bool fp64) { return fp64 ? prepare_impl<double>() : prepare_impl<float>(); }
+
+bool periodic_line_fits(int n, int axis, int dim, bool fp64) {
+    const int mode = axis == dim - 1 ? PM_PIVOT_DIV : PM_PLAIN;   // the most buffers a pass on that axis uses
+    const int pitch = axis == 0 ? n : n + 1;
+    return pass_smem(n, 1, pitch, mode_buffers(mode), fp64 ? sizeof(Cplx<double>) : sizeof(Cplx<float>)) <=
+           kPassSmemMax;
+}
 
 int periodic_rhs_launches(int dim, int nout) { (void)nout; return 5 + 4 * (dim - 2); }
 int periodic_multiplier_launches(int dim) { return 3 + 2 * (dim - 2); }

@@ -123,7 +123,9 @@ def _periodic_params(**kw):
 
 @pytest.mark.parametrize("kw,status", [
     (dict(n=(12, 16, 1)), 1),          # not a power of two
-    (dict(n=(2048, 16, 1)), 1),        # beyond one shared-memory line
+    (dict(n=(8192, 16, 1)), 1),        # x1 lines beyond 4096 points
+    (dict(n=(16, 2048, 1)), 1),        # other lines beyond 1024 points
+    (dict(form=2), 1),
     (dict(n=(1, 16, 1)), 1),
     (dict(length=0.0), 1),
     (dict(length=float("inf")), 1),

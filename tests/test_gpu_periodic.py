@@ -229,3 +229,44 @@ def test_e2_on_an_embedded_grid_matches_the_1d_oracle_and_the_paper():
     conv = O.solve_periodic(w1.dims, L1, a1, b1, w1.r_poly, w1.u0, w1.tau / 4, 4 * w1.m, "lawson4")
     err = np.abs(h[0] - conv).max() / np.abs(conv).max()
     assert abs(err / 2.57438011667187e-04 - 1.0) < 0.01, err
+
+
+@pytest.mark.parametrize("dims", [(32, 64), (64, 2), (16, 8, 32)])
+def test_adelta_building_blocks_match_oracle(dims):
+    """The a Lap u form (Section 4, Eq. (adlinearzero), with advection and reaction added):
+    F and g against the oracle."""
+    w, L, a, b = W.periodic_instance(dims, T=0.05, m=4)
+    ctx = adr.Context(w.dims, w.tau, "etd2rk", "fp64", periodic=True, length=L, form="adelta")
+    ctx.set_coeffs_periodic(a, b, w.r_poly)
+    prob = O.PeriodicProblem(dims, L, a, b, w.r_poly, form="adelta")
+    u = dev(w.u0)
+    F = torch.empty_like(u)
+    g = torch.empty_like(u)
+    ctx.eval_rhs(u, F, g)
+    ctx.synchronize()
+    assert O.rel_l2(host(F), prob.F(w.u0)) < 1e-11
+    assert O.rel_l2(host(g), prob.g(w.u0)) < 1e-11
+
+
+@pytest.mark.parametrize("scheme,lam,m,paper", [("lawson_euler", 1.0, 64, 0.00288149591423319),
+                                                ("stabilized_lawson_euler", 1.0, 16, 0.00423707305496343),
+                                                ("exponential_euler", 1.0, 16, 0.00192512919614741)])
+def test_e1_on_an_embedded_grid_matches_the_paper(scheme, lam, m, paper):
+    """The paper's linear experiment (Section 4, Eq. (adlinearzero)) at its 2^12 modes on
+    4096 x 2 nodes in FP64: the error against the exact semidiscrete solution is the printed one
+    (the figure of errors against m, panel lambda = 1) within 0.1%, and the x1 line equals the
+    1-D oracle."""
+    w, L, a, b = W.config_e1(scheme=scheme, m=m, embed=True)
+    ctx = adr.Context(w.dims, w.tau, scheme, "fp64", periodic=True, length=L, form="adelta", lam=lam)
+    ctx.set_coeffs_periodic(a, b, w.r_poly)
+    u = dev(w.u0)
+    ctx.integrate(u, 0.0, w.m * w.tau, w.m)
+    ctx.synchronize()
+    h = host(u)
+    w1, L1, a1, b1 = W.config_e1(scheme=scheme, m=m)
+    ref1 = O.solve_periodic(w1.dims, L1, a1, b1, w1.r_poly, w1.u0, w1.tau, w1.m, scheme, lam=lam, form="adelta")
+    assert O.rel_l2(h[0], ref1) < 1e-11
+    exact = O.periodic_linear_exact(O.PeriodicProblem(w1.dims, L1, a1, b1, w1.r_poly, form="adelta"), w1.u0,
+                                    w1.m * w1.tau)
+    err = np.abs(h[0] - exact).max() / np.abs(exact).max()
+    assert abs(err / paper - 1.0) < 1e-3, err
