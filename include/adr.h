@@ -213,6 +213,13 @@ adr_status adr_apply_phi(adr_ctx* ctx, int k, const void* v_dev, void* y_dev);
  * kernel gave up since the last call. */
 adr_status adr_synchronize(adr_ctx* ctx);
 
+/* The failure path of the bounded device waits, exercised on purpose: enqueues on the context's
+ * stream a kernel that waits on an mbarrier nothing arrives on, gives up after limit_ms
+ * (in (0, 1000]; cycles at the maximum SM clock) and records a code in the context's error
+ * word. The next adr_synchronize returns ADR_ERR_TIMEOUT and clears the word; the context stays
+ * usable. The kernels' own waits take the same path with a limit of about 2 s. */
+adr_status adr_test_bounded_wait(adr_ctx* ctx, double limit_ms);
+
 /* Host-side facts of the current operator: kappa(V_mu) per direction (0 when the
  * spectrum is complex), lambda*a_max, and beta. Any pointer may be NULL. Periodic
  * contexts: kappa = 1 (the Fourier basis is unitary), the largest lambda*a_mumu^max. */

@@ -66,6 +66,7 @@ def load_library(path: str = LIB_PATH):
         "adr_apply_exp": (ip, [vp, C.c_double, vp, vp]),
         "adr_apply_phi": (ip, [vp, ip, vp, vp]),
         "adr_synchronize": (ip, [vp]),
+        "adr_test_bounded_wait": (ip, [vp, C.c_double]),
         "adr_profile_step": (ip, [vp, vp, ip, C.POINTER(C.c_float), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "adr_get_info": (ip, [vp, dp, dp, dp]),
         "adr_get_instance_info": (ip, [vp, ip, dp, dp, dp]),
@@ -214,6 +215,12 @@ def adr_apply_exp(ctx, c, v, y):
 
 def adr_apply_phi(ctx, k, v, y):
     _check(_lib.adr_apply_phi(ctx, int(k), _ptr(v), _ptr(y)), ctx)
+
+
+def adr_test_bounded_wait(ctx, limit_ms=1.0):
+    """Enqueue a wait that runs out after limit_ms (see adr.h); the next synchronize raises
+    AdrError(ADR_ERR_TIMEOUT)."""
+    _check(_lib.adr_test_bounded_wait(ctx, float(limit_ms)), ctx)
 
 
 def adr_synchronize(ctx):

@@ -1787,6 +1787,13 @@ adr_status adr_synchronize(adr_ctx* c) {
     return ADR_OK;
 }
 
+adr_status adr_test_bounded_wait(adr_ctx* c, double limit_ms) {
+    if (!c) return ADR_ERR_ARG;
+    if (!(limit_ms > 0.0) || limit_ms > 1000.0) return fail(c, ADR_ERR_ARG, "limit_ms must be in (0, 1000]");
+    const cudaError_t e = adr::launch_wait_probe(c->d_err, limit_ms, c->stream);
+    return e == cudaSuccess ? ADR_OK : cuda_fail(c, e, "adr_test_bounded_wait");
+}
+
 adr_status adr_get_info(const adr_ctx* c, double kappa[3], double* abar, double beta[3]) {
     if (!c) return ADR_ERR_ARG;
     if (c->bs) {

@@ -239,6 +239,10 @@ cudaError_t launch_batch_stencil(const BatchStencilArgs<float>& a, cudaStream_t 
 cudaError_t launch_batch_contract(const BatchContractArgs<double>& a, cudaStream_t s);
 cudaError_t launch_batch_contract(const BatchContractArgs<float>& a, cudaStream_t s);
 
+// A kernel that waits on an mbarrier nothing arrives on, gives up after limit_ms and sets a code
+// in err (wait_check.cu).
+cudaError_t launch_wait_probe(int* err, double limit_ms, cudaStream_t s);
+
 // ---------------------------------------------------------------- periodic Fourier contexts
 // The pseudospectral form of the paper's two-dimensional experiment (Section 5.1): the state
 // lives on n_1 x ... x n_d Fourier nodes (n_mu a power of two, <= 1024); derivatives and the

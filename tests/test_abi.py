@@ -155,3 +155,7 @@ def test_measure_peak_validates_arguments_on_host(lib):
     assert lib.adr_measure_peak(7, 16, C.byref(out)) == 1
     assert lib.adr_measure_peak(0, 0, C.byref(out)) == 1
     assert lib.adr_measure_peak(1, (1 << 20) + 1, C.byref(out)) == 1
+
+
+def test_bounded_wait_probe_validates_arguments_on_host(lib):
+    assert lib.adr_test_bounded_wait(None, 1.0) == 1
