@@ -383,6 +383,8 @@ GRID_WORKLOADS = {
     "e3-lawson2a": (lambda W: W.config_e3(n=256, scheme="lawson2a"), "fp64"),
     "e3-etd2rk": (lambda W: W.config_e3(n=256, scheme="etd2rk"), "fp64"),
     "e3-lawson4": (lambda W: W.config_e3(n=256, scheme="lawson4"), "fp64"),
+    # the same problem on 1024 x 1024 nodes (16 times the paper's resolution), 64 steps to T = 1
+    "e3-lawson2a-1024": (lambda W: W.config_e3(n=1024, scheme="lawson2a", m=64, T=1.0), "fp64"),
 }
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64, nominal (context only; rooflines use the measured rate)
 
