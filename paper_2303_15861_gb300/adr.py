@@ -293,12 +293,13 @@ NORM = {"l2": 0, "max": 1}
 
 
 def adr_lambda_scan(dims, tau, scheme, precision, a_nodes, b, r_poly, u0, m, lambdas=None, n_lambdas=8,
-                    ref_substeps=8, abar_override=0.0, stream=None, norm="l2"):
+                    ref_substeps=8, abar_override=0.0, stream=None, norm="l2", bc="dirichlet", form="flux"):
     """Section 3's lambda scan on a small problem: returns (best lambda, [(lambda, error)])."""
     bb, bp = _dbl(list(b) + [0.0] * (3 - len(b)), 3)
     a, ap = _dbl(a_nodes)
+    extra = {"bc_hi": BC[bc] if isinstance(bc, str) else int(bc), "form": FORM[form] if isinstance(form, str) else int(form)}
     return _scan("adr_lambda_scan", dims, tau, scheme, precision, (ap, bp), r_poly, u0, m, lambdas, n_lambdas,
-                 ref_substeps, abar_override, stream, norm, {}, (a, bb))
+                 ref_substeps, abar_override, stream, norm, extra, (a, bb))
 
 
 def adr_lambda_scan_periodic(dims, length, tau, scheme, precision, a_diag, b_field, r_poly, u0, m, lambdas=None,

@@ -407,3 +407,22 @@ def test_neumann_faces_need_the_adelta_form():
     with pytest.raises(adr.AdrError) as e:
         adr.Context((16, 16), 1e-3, "lawson4", "fp64", bc="mixed", form="flux")
     assert e.value.status == 8
+
+
+def test_e4_lambda_scan_on_the_gpu_chooses_the_papers_lambda():
+    """Section 3's scan on the paper's 3-D experiment as Section 5.2 runs it (N = 2^4, m = 2^8,
+    T = 1/4, b = -0.01, maximum norm), over the lambda values the paper printed for
+    Lawson-Euler: the library chooses the printed argmin (0.356; the table of lambda values of
+    Section 5.2 gives 0.36), and its errors are the printed ones within 1e-3 (its reference is
+    Lawson4 at tau/16, the paper's Lawson2b at a small step)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "e4_lambda_scan_paper.json")))
+    pts = g["points"]["-0.01"]["lawson_euler"]
+    w = W.config_e4(n=16, b=-0.01, scheme="lawson_euler", m=256, T=0.25)
+    best, errs = adr.adr_lambda_scan(w.dims, w.tau, "lawson_euler", "fp64", w.a_nodes, w.b, w.r_poly, w.u0, w.m,
+                                     lambdas=[lam for lam, _ in pts], norm="max", ref_substeps=16,
+                                     bc="mixed", form="adelta")
+    assert best == min(pts, key=lambda t: t[1])[0]
+    for (lam, err), (_, paper) in zip(errs, pts):
+        assert abs(err / paper - 1.0) <= 1e-3, (lam, err, paper)

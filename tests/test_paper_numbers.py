@@ -1,4 +1,10 @@
-"""The oracle against numbers the paper prints for its periodic Fourier experiments.
+"""The oracle against numbers the paper prints for its experiments.
+
+The three-dimensional experiment (Section 5.2, Eq. (adr3d): a Lap u, Dirichlet faces at
+x_mu = 0, Neumann faces at x_mu = 1; the figure of errors against lambda, N = 2^4, m = 2^8,
+T = 1/4, b = -0.01 and -1; tests/golden/e4_lambda_scan_paper.json): every printed point of the
+four schemes matches to 1e-4 relative against a Lawson2b reference with 2^13 steps; asserted
+within 1e-3, with the printed argmin.
 
 The one-dimensional linear diffusion problem a(x) u_xx (Section 4, Eq. (adlinearzero); the
 figures of errors against the number of steps, one panel per lambda; tests/golden/
@@ -130,3 +136,22 @@ def test_e1_errors_match_the_paper(e1, panel):
                 assert 0.7 <= ours / paper <= 1.4, (panel, scheme, m, ours, paper)
             checked += 1
     assert checked > 0
+
+
+GOLDEN_E4 = os.path.join(os.path.dirname(__file__), "golden", "e4_lambda_scan_paper.json")
+
+
+@pytest.mark.parametrize("b", ["-0.01", "-1"])
+def test_e4_lambda_scan_errors_and_argmin_match_the_paper(b):
+    g = json.load(open(GOLDEN_E4))
+    w = W.config_e4(n=g["N"], b=float(b), scheme="lawson_euler", m=g["m"], T=g["T"])
+    kw = dict(bc="mixed", form="adelta")
+    ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, g["T"] / 8192, 8192, "lawson2b", **kw)
+    for scheme, pts in g["points"][b].items():
+        errs = []
+        for lam, paper in pts:
+            u = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, g["T"] / g["m"], g["m"], scheme, lam=lam, **kw)
+            ours = np.abs(u - ref).max() / np.abs(ref).max()
+            assert abs(ours / paper - 1.0) <= 1e-3, (b, scheme, lam, ours, paper)
+            errs.append(ours)
+        assert pts[int(np.argmin(errs))][0] == min(pts, key=lambda t: t[1])[0]
