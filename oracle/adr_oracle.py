@@ -471,6 +471,7 @@ class PeriodicOps:
     def __init__(self, prob: PeriodicProblem, tau: float):
         self.prob = prob
         self.tau = float(tau)
+        self._mult = {}                       # the multipliers already formed, by (k, c)
 
     def g(self, u):
         return self.prob.g(u)
@@ -478,11 +479,18 @@ class PeriodicOps:
     def F(self, u):
         return self.prob.F(u)
 
+    def _multiplier(self, k, c):
+        key = (k, float(c))
+        if key not in self._mult:
+            z = c * self.tau * self.prob.symbol
+            self._mult[key] = np.exp(z) if k == 0 else phi_complex(k, z)
+        return self._mult[key]
+
     def expA(self, c, v):
-        return np.real(np.fft.ifftn(np.exp(c * self.tau * self.prob.symbol) * np.fft.fftn(v)))
+        return np.real(np.fft.ifftn(self._multiplier(0, c) * np.fft.fftn(v)))
 
     def phi(self, k, c, v):
-        return np.real(np.fft.ifftn(phi_complex(k, c * self.tau * self.prob.symbol) * np.fft.fftn(v)))
+        return np.real(np.fft.ifftn(self._multiplier(k, c) * np.fft.fftn(v)))
 
 
 def solve_periodic(dims, L, a_diag, b_field, r_poly, u0, tau, m, scheme, lam=1.0, form="flux"):
