@@ -46,7 +46,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--workload", choices=["3d", "batch2d"] + sorted(GRID_WORKLOADS), default="3d",
                    help="3d: the 256^3 Lawson4 workload (default); batch2d: 512 uneven 2-D ETD2RK instances; "
-                        "c1-*, c2, c5-*, e4-*, e3-*: the other single-grid workloads")
+                        "c1-*, c2, c5-*, e1-*, e2-*, e3-*, e4-*: the other single-grid workloads")
     p.add_argument("--check", action="store_true",
                    help="single-grid workloads: also measure the error (oracle for c1/c2, FP64 GPU at tau/4 for c5)")
     p.add_argument("--ncu-steps", type=int, default=0,
@@ -383,6 +383,10 @@ GRID_WORKLOADS = {
     "e3-lawson2a": (lambda W: W.config_e3(n=256, scheme="lawson2a"), "fp64"),
     "e3-etd2rk": (lambda W: W.config_e3(n=256, scheme="etd2rk"), "fp64"),
     "e3-lawson4": (lambda W: W.config_e3(n=256, scheme="lawson4"), "fp64"),
+    # the paper's 1-D experiments (Section 4) on n x 2 nodes, constant along x2: the linear a u_xx
+    # problem (2^12 modes, T = 1/40, 2^10 steps) and the nonlinear one (2^10 modes, T = 1/10, 2^12 steps)
+    "e1-lawson-euler": (lambda W: W.config_e1(n=4096, scheme="lawson_euler", m=1024, embed=True), "fp64"),
+    "e2-lawson2a": (lambda W: W.config_e2(n=1024, scheme="lawson2a", m=4096, embed=True), "fp64"),
     # the same problem on 1024 x 1024 nodes (16 times the paper's resolution), 64 steps to T = 1
     "e3-lawson2a-1024": (lambda W: W.config_e3(n=1024, scheme="lawson2a", m=64, T=1.0), "fp64"),
 }
@@ -431,7 +435,8 @@ def ours_grid(args):
     if args.ncu_steps > 0:   # profiling mode: untimed adr_step calls only
         with torch.cuda.stream(stream):
             if periodic:
-                ctx = adr.Context(w.dims, w.tau, w.scheme, prec, stream=stream, periodic=True, length=L)
+                ctx = adr.Context(w.dims, w.tau, w.scheme, prec, stream=stream, periodic=True, length=L,
+                                  form=w.extra.get("form", "flux"))
                 ctx.set_coeffs_periodic(a_diag, b_field, w.r_poly)
             else:
                 ctx = adr.Context(w.dims, w.tau, w.scheme, prec, stream=stream, **form_kw)
@@ -444,7 +449,8 @@ def ours_grid(args):
     with torch.cuda.stream(stream):
         try:
             if periodic:
-                ctx = adr.Context(w.dims, w.tau, w.scheme, prec, stream=stream, periodic=True, length=L)
+                ctx = adr.Context(w.dims, w.tau, w.scheme, prec, stream=stream, periodic=True, length=L,
+                                  form=w.extra.get("form", "flux"))
                 ctx.set_coeffs_periodic(a_diag, b_field, w.r_poly)
             else:
                 ctx = adr.Context(w.dims, w.tau, w.scheme, prec, stream=stream, **form_kw)
@@ -499,7 +505,8 @@ def ours_grid(args):
                 rc.close()
                 acc = {"reference": "FP64 GPU path at tau/4"}
             elif periodic:
-                ref = O.solve_periodic(w.dims, L, a_diag, b_field, w.r_poly, w.u0, w.tau, w.m, w.scheme)
+                ref = O.solve_periodic(w.dims, L, a_diag, b_field, w.r_poly, w.u0, w.tau, w.m, w.scheme,
+                                       form=w.extra.get("form", "flux"))
                 acc = {"reference": "FP64 oracle"}
             else:
                 ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, w.m, w.scheme, **form_kw)
