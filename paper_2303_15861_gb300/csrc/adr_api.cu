@@ -146,8 +146,10 @@ struct adr_ctx {
     void* wsd[3] = {nullptr, nullptr, nullptr};   // doubling-route workspace
 
     // graph cache for adr_integrate
-    cudaGraph_t graph = nullptr;
+    cudaGraph_t graph = nullptr;           // one step
     cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph_k = nullptr;         // kGraphSteps steps in one graph (fewer replays)
+    cudaGraphExec_t gexec_k = nullptr;
     void* graph_u = nullptr;
 
     std::string err;
@@ -170,6 +172,10 @@ void free_dev(void*& p) {
 }
 
 void drop_graph(adr_ctx* c) {
+    if (c->gexec_k) cudaGraphExecDestroy(c->gexec_k);
+    if (c->graph_k) cudaGraphDestroy(c->graph_k);
+    c->gexec_k = nullptr;
+    c->graph_k = nullptr;
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     c->gexec = nullptr;
@@ -214,6 +220,7 @@ cudaError_t upload_tc(adr_ctx* c, int kind, int m, const std::vector<double>& M)
 
 // ------------------------------------------------------------------ schedule builders
 constexpr int kSlots = 4096;
+constexpr int kGraphSteps = 8;             // steps per replay of the multi-step graph
 
 // The ops of one call, plus the max-abs bookkeeping of the mixed path: every array a
 // step produces gets a fresh slot (zeroed at the start of the step) that its producer
@@ -1657,25 +1664,36 @@ adr_status adr_integrate(adr_ctx* c, void* u, double t0, double T, int m) {
         return ADR_OK;
     }
     if (c->graph_u != u) {
+        // two graphs of the same step: one step, and kGraphSteps steps back to back (one replay
+        // then covers several steps, which matters where a step is a few microseconds)
         drop_graph(c);
         const auto ops = step_ops(c, u);
-        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
-        cudaError_t le = cudaSuccess;
-        for (const auto& op : ops) {
-            le = op(c->stream);
-            if (le != cudaSuccess) break;
-        }
-        e = cudaStreamEndCapture(c->stream, &c->graph);
-        if (le != cudaSuccess) { drop_graph(c); return cuda_fail(c, le, "capture launch"); }
-        if (e != cudaSuccess) { drop_graph(c); return cuda_fail(c, e, "end capture"); }
-        e = cudaGraphInstantiate(&c->gexec, c->graph, 0);
-        if (e != cudaSuccess) { drop_graph(c); return cuda_fail(c, e, "instantiate graph"); }
+        auto capture = [&](int steps, cudaGraph_t* g, cudaGraphExec_t* x) -> adr_status {
+            cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
+            cudaError_t le = cudaSuccess;
+            for (int k = 0; k < steps && le == cudaSuccess; ++k)
+                for (const auto& op : ops) {
+                    le = op(c->stream);
+                    if (le != cudaSuccess) break;
+                }
+            e = cudaStreamEndCapture(c->stream, g);
+            if (le != cudaSuccess) { drop_graph(c); return cuda_fail(c, le, "capture launch"); }
+            if (e != cudaSuccess) { drop_graph(c); return cuda_fail(c, e, "end capture"); }
+            e = cudaGraphInstantiate(x, *g, 0);
+            if (e != cudaSuccess) { drop_graph(c); return cuda_fail(c, e, "instantiate graph"); }
+            return ADR_OK;
+        };
+        st = capture(1, &c->graph, &c->gexec);
+        if (st == ADR_OK) st = capture(kGraphSteps, &c->graph_k, &c->gexec_k);
+        if (st != ADR_OK) return st;
         c->graph_u = u;
     }
-    for (int i = 0; i < m; ++i) {
-        cudaError_t e = cudaGraphLaunch(c->gexec, c->stream);
+    for (int left = m; left > 0;) {
+        const bool many = left >= kGraphSteps;
+        cudaError_t e = cudaGraphLaunch(many ? c->gexec_k : c->gexec, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+        left -= many ? kGraphSteps : 1;
     }
     return ADR_OK;
 }

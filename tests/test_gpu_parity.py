@@ -155,25 +155,28 @@ def test_integrate_matches_oracle(dims, b, scheme, T, m, prec, tol):
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 @pytest.mark.parametrize("scheme", ["lawson_euler", "etd2rk", "lawson4"])
 def test_graph_replay_equals_direct_steps_bitwise(scheme, prec):
-    """adr_integrate (a captured CUDA graph on a non-default stream) and m calls of adr_step
-    give identical bits, and two runs are bitwise deterministic."""
+    """adr_integrate (captured CUDA graphs on a non-default stream: an 8-step graph and a
+    1-step graph for the rest) and m calls of adr_step give identical bits, for m below and
+    above 8, and two runs are bitwise deterministic."""
     dims = (29, 23, 21) if prec == "fp64" else (64, 48, 40)
     a, b, r, u0 = make_case(dims)
     tau = 2e-3
     dt = torch.float64 if prec == "fp64" else torch.float32
     stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        ctx = adr.Context(dims, tau, scheme, prec, stream=stream)
-        ctx.set_coeffs(a, b, r)
-        u1 = torch.tensor(u0, dtype=dt, device="cuda")
-        u2 = u1.clone()
-        u3 = u1.clone()
-        ctx.integrate(u1, 0.0, 5 * tau, 5)
-        for i in range(5):
-            ctx.step(u2, i * tau)
-        ctx.integrate(u3, 0.0, 5 * tau, 5)
-        ctx.synchronize()
-    assert torch.equal(u1, u2) and torch.equal(u1, u3)
+    for m in (5, 19):
+        with torch.cuda.stream(stream):
+            ctx = adr.Context(dims, tau, scheme, prec, stream=stream)
+            ctx.set_coeffs(a, b, r)
+            u1 = torch.tensor(u0, dtype=dt, device="cuda")
+            u2 = u1.clone()
+            u3 = u1.clone()
+            ctx.integrate(u1, 0.0, m * tau, m)
+            for i in range(m):
+                ctx.step(u2, i * tau)
+            ctx.integrate(u3, 0.0, m * tau, m)
+            ctx.synchronize()
+        assert torch.equal(u1, u2) and torch.equal(u1, u3), m
+        ctx.close()
 
 
 def test_integrate_host_matches_device():
