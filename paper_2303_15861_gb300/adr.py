@@ -73,6 +73,7 @@ def load_library(path: str = LIB_PATH):
         "adr_get_batch_plan": (ip, [vp, ip, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "adr_mumode_apply_static": (ip, [ip, C.POINTER(C.c_int), C.POINTER(vp), vp, vp, vp]),
         "adr_kernels_per_step": (ip, [vp]),
+        "adr_tc_factor_slices": (ip, [vp, C.POINTER(C.c_int)]),
         "adr_phi_route_used": (ip, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "adr_stability_bound": (ip, [ip, dp]),
         "adr_measure_peak": (ip, [ip, ip, dp]),
@@ -348,6 +349,12 @@ def adr_kernels_per_step(ctx):
     return int(_lib.adr_kernels_per_step(ctx))
 
 
+def adr_tc_factor_slices(ctx):
+    n = C.c_int()
+    _check(_lib.adr_tc_factor_slices(ctx, C.byref(n)), ctx)
+    return n.value
+
+
 def adr_last_error(ctx=None):
     return _lib.adr_last_error(ctx).decode()
 
@@ -417,6 +424,9 @@ class Context:
 
     def kernels_per_step(self):
         return adr_kernels_per_step(self.ctx)
+
+    def tc_factor_slices(self):
+        return adr_tc_factor_slices(self.ctx)
 
     def phi_route(self):
         return adr_phi_route_used(self.ctx)

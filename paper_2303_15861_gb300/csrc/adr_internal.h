@@ -137,18 +137,24 @@ struct TmaArgs : TcArgs {
     alignas(64) CUtensorMap map_xlo;
     long long nqt = 1;          // position tiles per p: ceil(Q / 128) (modes >= 2)
     bool has_lo = false;
+    bool f4 = false;            // standard configuration: the factor image has four slices
 };
 bool tma_supported(int n, long long Q, const void* x, const void* xlo);
 cudaError_t launch_contract_tma(TmaArgs a, long long P, cudaStream_t s);
 
 // Host: slice an FP64 factor into the tensor-core image, with output tiles of `rows` rows
 // and K chunks of `chunk` (64: 128-byte swizzle, contract_tc.cu; 32: 64-byte swizzle,
-// contract_tma.cu); standard slices F0, F1, 2^-8 F1, 2^-8 F2 or precise F0..F3.
+// contract_tma.cu); standard slices F0, F1, 2^-8 F1, 2^-8 F2 (chunk 64), F0, F1, 2^-8 F2
+// (chunk 32; with `four` also 2^-16 F3) or precise F0..F3.
 struct TcFactor {
     std::vector<uint8_t> img;
     std::vector<float> fscale;
 };
-TcFactor make_tc_factor(const std::vector<double>& M, int n, int rows, bool precise, int chunk = 64);
+TcFactor make_tc_factor(const std::vector<double>& M, int n, int rows, bool precise, int chunk = 64,
+                        bool four = false);
+// Largest relative change of a row sum, max_i |sum_k (R - M)[i][k]| / sum_k |M[i][k]|, when the
+// rows of M are written with three slices (R: the 24-bit representation of the standard image).
+double tc_rowsum_error3(const std::vector<double>& M, int n);
 int tc_out_rows(bool state_is_a, bool precise);   // rows of an output tile of a kernel variant
 int tc_pos_rows(bool state_is_a, bool precise);   // rows of a position / fibre tile
 

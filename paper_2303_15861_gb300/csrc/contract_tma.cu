@@ -39,18 +39,23 @@ constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kN >>
 
 // Standard: state slices S0, S1, 2^-8 S2, 2^-8 S1 and factor slices F0, F1, 2^-8 F2 (the
 // product S1 (2^-8 F1) of the split is formed as (2^-8 S1) F1, the same exact value, so
-// each K chunk moves three factor tiles from L2 instead of four). Precise: four of each.
-template <bool PR>
+// each K chunk moves three factor tiles from L2 instead of four). F4: a fourth factor slice
+// 2^-16 F3 and a seventh product S0 (2^-16 F3) carry the factor to 32 bits. The factor is
+// the same in every time step, so its representation error is a fixed matrix whose action
+// on a slowly varying state adds up step after step; where e^{c tau A_mu} is close to the
+// identity (tau a / h^2 of order 1) the 24-bit form moves row sums by a few 1e-7, and the
+// host then builds the four-slice image (see upload_tc). Precise: four of each.
+template <bool PR, bool F4 = false>
 struct Cfg {
     static constexpr int SS = 4;                       // state slices
-    static constexpr int FS = PR ? 4 : 3;              // factor slices
+    static constexpr int FS = (PR || F4) ? 4 : 3;      // factor slices
     static constexpr int NACC = PR ? 4 : 2;            // accumulators (128 columns each)
     static constexpr int NSETS = PR ? 1 : 2;           // TMEM accumulator sets
     static constexpr int TILE = kM * kKc * 2;          // one bf16 slice tile: 8 KB
     static constexpr int SBYTES = SS * TILE;           // one state-slice stage
     static constexpr int FBYTES = FS * TILE;           // one factor stage (24 or 32 KB)
     static constexpr int NSLICE = PR ? 2 : 3;          // state-slice ring
-    static constexpr int NF = PR ? 3 : 4;              // factor ring (the loader runs it ahead)
+    static constexpr int NF = (PR || F4) ? 3 : 4;      // factor ring (the loader runs it ahead)
     static constexpr int XTILE = kM * kKc * 4;         // one FP32 staging tile: 16 KB
     static constexpr int XSTAGE = PR ? 2 * XTILE : XTILE;   // hi (+ lo)
     static constexpr int NX = 2;
@@ -171,7 +176,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
-template <bool SA, bool PR>
+template <bool SA, bool PR, bool F4>
 __device__ __forceinline__ void mma_kstep(uint32_t d, const uint64_t (&S)[4], const uint64_t (&F)[4], uint64_t adv,
                                           uint32_t first) {
     auto mma = [&](int acc, int si, int fi, uint32_t accumulate) {
@@ -180,13 +185,14 @@ __device__ __forceinline__ void mma_kstep(uint32_t d, const uint64_t (&S)[4], co
         else    tc_mma(dd, F[fi] + adv, S[si] + adv, kIdesc, accumulate);
     };
     const uint32_t acc = first ? 0u : 1u;
-    if (!PR) {                       // S = {S0, S1, 2^-8 S2, 2^-8 S1}, F = {F0, F1, 2^-8 F2}
+    if (!PR) {                       // S = {S0, S1, 2^-8 S2, 2^-8 S1}, F = {F0, F1, 2^-8 F2 (, 2^-16 F3)}
         mma(0, 0, 0, acc);
         mma(1, 0, 1, acc);
         mma(1, 1, 0, 1u);
         mma(1, 0, 2, 1u);
         mma(1, 2, 0, 1u);
         mma(1, 3, 1, 1u);
+        if (F4) mma(1, 0, 3, 1u);
     } else {
         mma(0, 0, 0, acc);
         mma(1, 0, 1, acc);
@@ -201,9 +207,9 @@ __device__ __forceinline__ void mma_kstep(uint32_t d, const uint64_t (&S)[4], co
     }
 }
 
-template <bool SA, bool PR, int EPI>
+template <bool SA, bool PR, int EPI, bool F4>
 __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_constant__ TmaArgs p) {
-    using C = Cfg<PR>;
+    using C = Cfg<PR, F4>;
     extern __shared__ uint8_t smem_raw[];
     // barriers: xfull[NX] xempty[NX] sfull[NSLICE] sempty[NSLICE] ffull[NF] fempty[NF] accf[2] acce[2] drain
     constexpr uint32_t kXF = 0, kXE = kXF + 8 * C::NX, kSF = kXE + 8 * C::NX, kSE = kSF + 8 * C::NSLICE;
@@ -506,7 +512,7 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
                 }
 #pragma unroll
                 for (int kk = 0; kk < kKc / 16; ++kk)
-                    mma_kstep<SA, PR>(d, S, F, uint64_t(kk * 32) >> 4, (c == 0 && kk == 0) ? 1u : 0u);
+                    mma_kstep<SA, PR, F4>(d, S, F, uint64_t(kk * 32) >> 4, (c == 0 && kk == 0) ? 1u : 0u);
                 tc_commit(sempty(s));
                 tc_commit(fempty(fs));
             }
@@ -529,17 +535,24 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
 
 int g_sms = 0;
 
-template <bool SA, bool PR, int EPI>
+template <bool SA, bool PR, int EPI, bool F4 = false>
 cudaError_t launch_variant(const TmaArgs& a, unsigned grid, cudaStream_t s) {
+    using C = Cfg<PR, F4>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(tma_contract_kernel<SA, PR, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             Cfg<PR>::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(tma_contract_kernel<SA, PR, EPI, F4>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    tma_contract_kernel<SA, PR, EPI><<<grid, kThreads, Cfg<PR>::SMEM, s>>>(a);
+    tma_contract_kernel<SA, PR, EPI, F4><<<grid, kThreads, C::SMEM, s>>>(a);
     return cudaGetLastError();
+}
+
+// Standard configuration, three or four factor slices (the image the host built).
+template <bool SA, int EPI>
+cudaError_t launch_standard(const TmaArgs& a, unsigned grid, cudaStream_t s) {
+    return a.f4 ? launch_variant<SA, false, EPI, true>(a, grid, s) : launch_variant<SA, false, EPI, false>(a, grid, s);
 }
 
 // FP32 tensor map over the state seen as [P][n][Q] (modes >= 2; box 128 q x 32 k x 1 p) or
@@ -620,14 +633,14 @@ cudaError_t launch_contract_tma(TmaArgs a, long long P, cudaStream_t s) {
                                    : launch_variant<false, true, EPI_STORE>(a, g, s);
     }
     if (a.state_is_a) {
-        if (a.epi == EPI_PHI) return launch_variant<true, false, EPI_PHI>(a, g, s);
-        if (a.epi == EPI_AXPY) return launch_variant<true, false, EPI_AXPY>(a, g, s);
-        if (a.epi == EPI_STORE2) return launch_variant<true, false, EPI_STORE2>(a, g, s);
-        return launch_variant<true, false, EPI_STORE>(a, g, s);
+        if (a.epi == EPI_PHI) return launch_standard<true, EPI_PHI>(a, g, s);
+        if (a.epi == EPI_AXPY) return launch_standard<true, EPI_AXPY>(a, g, s);
+        if (a.epi == EPI_STORE2) return launch_standard<true, EPI_STORE2>(a, g, s);
+        return launch_standard<true, EPI_STORE>(a, g, s);
     }
     if (a.epi == EPI_PHI || a.epi == EPI_STORE2) return cudaErrorInvalidValue;
-    if (a.epi == EPI_AXPY) return launch_variant<false, false, EPI_AXPY>(a, g, s);
-    return launch_variant<false, false, EPI_STORE>(a, g, s);
+    if (a.epi == EPI_AXPY) return launch_standard<false, EPI_AXPY>(a, g, s);
+    return launch_standard<false, EPI_STORE>(a, g, s);
 }
 
 }  // namespace adr

@@ -159,3 +159,9 @@ def test_measure_peak_validates_arguments_on_host(lib):
 
 def test_bounded_wait_probe_validates_arguments_on_host(lib):
     assert lib.adr_test_bounded_wait(None, 1.0) == 1
+
+
+def test_factor_slice_query_validates_arguments_on_host(lib):
+    n = C.c_int(-1)
+    assert lib.adr_tc_factor_slices(None, C.byref(n)) == 1
+    assert lib.adr_tc_factor_slices(None, None) == 1
