@@ -575,7 +575,7 @@ def ours_grid(args):
 
 
 # ----------------------------------------------------------------------------- batched 2-D
-BATCH_METRIC = "DOF*steps/s, 512 batched 2-D ETD2RK instances (FP32, tol 1e-5 vs FP64)"
+BATCH_METRIC = "DOF*steps/s, 512 batched 2-D ETD2RK instances (FP32)"
 BATCH_PER_RANK = 512           # instances per rank (weak scaling: the rank's block of one global draw)
 FP32_LANES_PER_SM = 128        # FP32 FMA lanes per SM (4 SMSPs x 32)
 SMS = 152
@@ -723,7 +723,8 @@ def ours_batch(args):
             rc.close()
             offs = np.cumsum([0] + [w.dof for w in ws])
             errs = [rel_l2(h[offs[i]:offs[i + 1]], ref[offs[i]:offs[i + 1]]) for i in range(len(ws))]
-            acc = {"rel_l2_vs_fp64_gpu_max": max(errs), "instances_checked": len(ws)}
+            acc = {"rel_l2_vs_fp64_gpu_max": max(errs), "instances_checked": len(ws),
+                   "instances_over_1e-5": int(sum(e > 1e-5 for e in errs))}
         launches = ctx.kernels_per_step() * m * args.steps
         ctx.close()
     if rank != 0:

@@ -224,3 +224,30 @@ def test_batched_workload_512_instances_sampled_against_oracle():
         w = ws[i]
         ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, w.m, "etd2rk")
         assert O.rel_l2(res[i], ref) < 1e-5, (i, w.dims)
+
+
+def test_batched_workload_every_instance_against_the_fp64_batch():
+    """All 512 instances of the batched workload, FP32 against the same batch in FP64 (whose
+    parity with the oracle the tests above check). 500 of them stay within 1e-5. The other 12
+    have c >= 0.77 (a down to 0.1 against a_max = 1.9) and b near 20. There ETD2RK at lambda = 1
+    amplifies any perturbation about a hundredfold over the 30 steps: in the FP64 oracle a
+    relative 1e-7 change of u0 grows to 9.4e-6 on instance 314, and rounding the state to FP32
+    after every step leaves 1.2e-5. The FP32 eigenbasis route (prod kappa up to 3e4 on those
+    instances) adds its kappa-amplified rounding before the amplification, so the worst
+    instance ends at 3.4e-4. Bound: at most 16 instances above 1e-5, every instance below 1e-3."""
+    ws = W.config4()
+    m = ws[0].m
+    out = {}
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for prec in ("fp32", "fp64"):
+            ctx = batch_context(ws, prec, "etd2rk", stream=s, kappa_tol=1.0)
+            _, u = packed(ws, prec)
+            ctx.integrate(u, 0.0, m * ws[0].tau, m)
+            ctx.synchronize()
+            out[prec] = unpack(ws, u)
+    errs = np.array([O.rel_l2(a, b) for a, b in zip(out["fp32"], out["fp64"])])
+    over = np.flatnonzero(errs > 1e-5)
+    print(f"instances over 1e-5: {over.tolist()}, max {errs.max():.3e}")
+    assert len(over) <= 16 and errs.max() < 1e-3
+    assert all(ws[i].extra["c"] > 0.7 for i in over), [(int(i), ws[i].extra) for i in over]
