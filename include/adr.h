@@ -308,13 +308,12 @@ adr_status adr_measure_peak(int kind, int iters, double* tflops);
 /* Number of kernels one adr_step launches (for launch accounting; memsets not counted). */
 int adr_kernels_per_step(const adr_ctx* ctx);
 
-/* Mixed-precision contexts after adr_set_coeffs: the largest number of slices (3 or 4) in which
- * the standard tensor-core images of the TMA-fed contraction write a factor; 0 for FP64 and
- * FP32 contexts, periodic and batched contexts, and before adr_set_coeffs. The exact-slice split
- * of the mu-mode products (Section 1) writes each factor row as 2^(e_i-7) sum_j 2^(-8j) f_j
- * with integer slices; a factor gets the fourth slice (a 32-bit instead of a 24-bit factor, and
- * seven BF16 products per multiply-add instead of six) where three slices would change one of
- * its row sums by more than 2^-23 of the row's absolute sum. *slices must not be NULL. */
+/* Mixed-precision contexts after adr_set_coeffs: the number of slices (4) in which the standard
+ * tensor-core images of the TMA-fed contraction write a factor; 0 for FP64 and FP32 contexts,
+ * periodic and batched contexts, and before adr_set_coeffs. The exact-slice split of the
+ * mu-mode products (Section 1) writes each factor row as 2^(e_i-7) sum_j 2^(-8j) f_j with
+ * integer slices: four slices make a 32-bit factor, and the standard contraction then issues
+ * seven BF16 products per multiply-add. *slices must not be NULL. */
 adr_status adr_tc_factor_slices(const adr_ctx* ctx, int* slices);
 
 /* The phi route a context uses after adr_set_coeffs (ADR_PHI_EIGEN or ADR_PHI_DOUBLING; 0

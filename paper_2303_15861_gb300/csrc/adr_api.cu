@@ -119,8 +119,6 @@ struct adr_ctx {
     uint8_t* d_img[kFactorKinds][3] = {{nullptr}};    // sliced image per factor kind and direction
     float* d_fsc[kFactorKinds][3] = {{nullptr}};
     uint8_t* d_img2[kFactorKinds][3] = {{nullptr}};   // the same for the TMA-fed kernel (K chunks of 32)
-    size_t img2_bytes[kFactorKinds][3] = {{0}};       // allocated bytes of d_img2
-    bool img2_four[kFactorKinds][3] = {{false}};      // d_img2 holds four factor slices (standard)
     float* d_fsc2[kFactorKinds][3] = {{nullptr}};
     float* d_zt[3] = {nullptr};            // tau * lambda_mu[j] (FP32)
     unsigned* d_slots = nullptr;           // max-abs slots of the arrays a step produces
@@ -209,21 +207,9 @@ cudaError_t upload_tc(adr_ctx* c, int kind, int m, const std::vector<double>& M)
     if (e == cudaSuccess)
         e = cudaMemcpy(c->d_fsc[kind][m], f.fscale.data(), f.fscale.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
-    // TMA-fed kernel: 128-row output tiles, K chunks of 32. The standard image gets a fourth
-    // factor slice where three slices would move a row sum by more than one FP32 ulp
-    // (2^-23 relative): a fixed error that every pass would add again.
-    const bool four = !precise && adr::tc_rowsum_error3(M, c->n[m]) > 0x1p-23;
-    const adr::TcFactor f2 = adr::make_tc_factor(M, c->n[m], 128, precise, 32, four);
-    if (c->d_img2[kind][m] && c->img2_bytes[kind][m] < f2.img.size()) {
-        void* q = c->d_img2[kind][m];
-        free_dev(q);
-        c->d_img2[kind][m] = nullptr;
-    }
-    if (!c->d_img2[kind][m]) {
-        e = cudaMalloc(reinterpret_cast<void**>(&c->d_img2[kind][m]), f2.img.size());
-        c->img2_bytes[kind][m] = (e == cudaSuccess) ? f2.img.size() : 0;
-    }
-    c->img2_four[kind][m] = four;
+    // TMA-fed kernel: 128-row output tiles, K chunks of 32
+    const adr::TcFactor f2 = adr::make_tc_factor(M, c->n[m], 128, precise, 32);
+    if (!c->d_img2[kind][m]) e = cudaMalloc(reinterpret_cast<void**>(&c->d_img2[kind][m]), f2.img.size());
     if (e == cudaSuccess && !c->d_fsc2[kind][m])
         e = cudaMalloc(reinterpret_cast<void**>(&c->d_fsc2[kind][m]), f2.fscale.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(c->d_img2[kind][m], f2.img.data(), f2.img.size(), cudaMemcpyHostToDevice);
@@ -417,7 +403,6 @@ void push_mode(Sched& S, int mu, int kind, const T* x, T* y, int epi = adr::EPI_
         adr::TmaArgs t;
         static_cast<adr::TcArgs&>(t) = a;
         t.fimg = c->d_img2[kind][mu - 1];
-        t.f4 = c->img2_four[kind][mu - 1];
         t.fscale = c->d_fsc2[kind][mu - 1];
         t.nK = (n + 31) / 32;
         t.nOut = (n + 127) / 128;
@@ -1882,10 +1867,7 @@ adr_status adr_tc_factor_slices(const adr_ctx* c, int* slices) {
     if (!c || !slices) return ADR_ERR_ARG;
     *slices = 0;
     if (!c->tc || c->bs || c->periodic || !c->coeffs_set) return ADR_OK;
-    for (int k = 0; k < kFactorKinds; ++k)
-        for (int m = 0; m < 3; ++m)
-            if (c->d_img2[k][m] && k != FK_EXP_HALF_PRECISE)
-                *slices = std::max(*slices, c->img2_four[k][m] ? 4 : 3);
+    *slices = 4;   // every standard image of the TMA-fed kernel (contract_tma.cu)
     return ADR_OK;
 }
 

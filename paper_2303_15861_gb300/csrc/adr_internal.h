@@ -41,6 +41,38 @@ double mean_face_jump(const double* a, int dim, const int* n, int mu);  // mu = 
 constexpr int kMaxExtra = 3;
 constexpr int kMaxOut = 2;
 
+// The state coefficients of one stage output (cu for the stencil's input, cx for the extra
+// inputs) in the working precision T. Where they sum to one, an affine combination of states
+// such as Lawson4's 2/3 Eu + 1/3 U2, the smallest nonzero one is replaced by one minus the
+// others when that difference is exact in T, so the rounded coefficients still sum to one:
+// 2/3 and 1/3 rounded to FP32 one by one sum to 1 + 3e-8, a gain that every time step would
+// apply to the whole state.
+template <typename T>
+inline void state_coefs(double cu, const double* cx, T& tu, T* tx) {
+    tu = T(cu);
+    double sum = cu;
+    for (int e = 0; e < kMaxExtra; ++e) {
+        tx[e] = T(cx[e]);
+        sum += cx[e];
+    }
+    if (!(sum > 1.0 - 1e-12 && sum < 1.0 + 1e-12)) return;
+    int k = -2;                      // -1: cu; e >= 0: cx[e]
+    double mag = 0.0;
+    if (cu != 0.0) { k = -1; mag = cu < 0 ? -cu : cu; }
+    for (int e = 0; e < kMaxExtra; ++e) {
+        const double m = cx[e] < 0 ? -cx[e] : cx[e];
+        if (cx[e] != 0.0 && (k == -2 || m < mag)) { k = e; mag = m; }
+    }
+    if (k == -2) return;
+    double rest = (k == -1) ? 0.0 : double(tu);   // the others as T values (exact in double)
+    for (int e = 0; e < kMaxExtra; ++e)
+        if (e != k) rest += double(tx[e]);
+    const T adj = T(1.0 - rest);
+    if (double(adj) + rest != 1.0) return;           // not exact in T: keep the rounded values
+    if (k == -1) tu = adj;
+    else tx[k] = adj;
+}
+
 // K1: variable-coefficient stencil with a fused stage-combination epilogue.
 //   g   = div_h((a - abar) grad_h u) + (b - beta) . grad_h u + r(u)
 //   F   = g + A_h u,  A_h u = abar lap_h u + beta . grad_h u
@@ -137,24 +169,19 @@ struct TmaArgs : TcArgs {
     alignas(64) CUtensorMap map_xlo;
     long long nqt = 1;          // position tiles per p: ceil(Q / 128) (modes >= 2)
     bool has_lo = false;
-    bool f4 = false;            // standard configuration: the factor image has four slices
 };
 bool tma_supported(int n, long long Q, const void* x, const void* xlo);
 cudaError_t launch_contract_tma(TmaArgs a, long long P, cudaStream_t s);
 
 // Host: slice an FP64 factor into the tensor-core image, with output tiles of `rows` rows
 // and K chunks of `chunk` (64: 128-byte swizzle, contract_tc.cu; 32: 64-byte swizzle,
-// contract_tma.cu); standard slices F0, F1, 2^-8 F1, 2^-8 F2 (chunk 64), F0, F1, 2^-8 F2
-// (chunk 32; with `four` also 2^-16 F3) or precise F0..F3.
+// contract_tma.cu); slices F0, F1, 2^-8 F1, 2^-8 F2 (chunk 64, standard) or F0..F3 (chunk 32,
+// and chunk 64 precise).
 struct TcFactor {
     std::vector<uint8_t> img;
     std::vector<float> fscale;
 };
-TcFactor make_tc_factor(const std::vector<double>& M, int n, int rows, bool precise, int chunk = 64,
-                        bool four = false);
-// Largest relative change of a row sum, max_i |sum_k (R - M)[i][k]| / sum_k |M[i][k]|, when the
-// rows of M are written with three slices (R: the 24-bit representation of the standard image).
-double tc_rowsum_error3(const std::vector<double>& M, int n);
+TcFactor make_tc_factor(const std::vector<double>& M, int n, int rows, bool precise, int chunk = 64);
 int tc_out_rows(bool state_is_a, bool precise);   // rows of an output tile of a kernel variant
 int tc_pos_rows(bool state_is_a, bool precise);   // rows of a position / fibre tile
 

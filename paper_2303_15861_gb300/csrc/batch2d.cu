@@ -354,8 +354,8 @@ cudaError_t stencil_launch(const BatchStencilArgs<T>& p, cudaStream_t s) {
     Combo<T> cb;
     bool needF = false;
     for (int j = 0; j < kMaxOut; ++j) {
-        cb.cu[j] = T(p.cu[j]); cb.cg[j] = T(p.cg[j]); cb.cF[j] = T(p.cF[j]);
-        for (int e = 0; e < kMaxExtra; ++e) cb.cx[j][e] = T(p.cx[j][e]);
+        cb.cg[j] = T(p.cg[j]); cb.cF[j] = T(p.cF[j]);
+        state_coefs<T>(p.cu[j], p.cx[j], cb.cu[j], cb.cx[j]);
         if (j < p.nout && p.cF[j] != 0.0) needF = true;
     }
     const long long want = (p.rows + 7) / 8;                 // 8 warps (rows) per block

@@ -181,20 +181,18 @@ uint16_t bf16_bits_exact(double v) {
 }
 }  // namespace
 
-TcFactor make_tc_factor(const std::vector<double>& M, int n, int rows, bool precise, int chunk, bool four) {
+TcFactor make_tc_factor(const std::vector<double>& M, int n, int rows, bool precise, int chunk) {
     // Each row i of M (an output index) is written as 2^(e_i-7) sum_j 2^(-8j) f_j with
     // integer slices |f_j| <= 128 and max_k |M[i][k]| < 2^e_i. The image stores, per
     // (output tile of `rows` rows, K chunk of 64), four slice tiles in the 128-byte-swizzled
     // K-major layout the tensor cores read (8-row groups of 1024 B; 16-byte chunk j of row r
     // at position j ^ (r mod 8)): F0, F1, 2^-8 F1, 2^-8 F2 (standard) or F0, F1, F2, F3
     // (precise). With chunks of 32 the tiles use the 64-byte swizzle (8-row groups of 512 B;
-    // chunk j of row r at position j ^ ((r / 2) mod 4)), and the standard image holds three
-    // tiles F0, F1, 2^-8 F2: that kernel forms S1 (2^-8 F1) as (2^-8 S1) F1 from a scaled
-    // state slice, the same exact product, so one factor tile less crosses from L2. With
-    // `four` a fourth tile 2^-16 F3 carries the factor to 32 bits.
+    // chunk j of row r at position j ^ ((r / 2) mod 4)), and every image holds F0, F1, F2, F3:
+    // that kernel runs the ten-product split in every pass.
     const int tile = rows * chunk * 2;
     const int nK = (n + chunk - 1) / chunk, nOut = (n + rows - 1) / rows;
-    const int nq = (precise || chunk == 64 || four) ? 4 : 3;
+    const int nq = 4;
     TcFactor out;
     out.img.assign(size_t(nOut) * nK * nq * tile, 0);
     out.fscale.assign(size_t(nOut) * rows, 0.0f);
@@ -214,12 +212,10 @@ TcFactor make_tc_factor(const std::vector<double>& M, int n, int rows, bool prec
             const double f2 = std::nearbyint(y2);
             const double f3 = std::nearbyint((y2 - f2) * 256.0);
             double* sl = &slices[(size_t(i) * n + k) * 4];
-            if (precise) {
+            if (precise || chunk == 32) {
                 sl[0] = f0; sl[1] = f1; sl[2] = f2; sl[3] = f3;
-            } else if (chunk == 64) {
-                sl[0] = f0; sl[1] = f1; sl[2] = f1 / 256.0; sl[3] = f2 / 256.0;
             } else {
-                sl[0] = f0; sl[1] = f1; sl[2] = f2 / 256.0; sl[3] = four ? f3 / 65536.0 : 0.0;
+                sl[0] = f0; sl[1] = f1; sl[2] = f1 / 256.0; sl[3] = f2 / 256.0;
             }
         }
     }
@@ -244,32 +240,6 @@ TcFactor make_tc_factor(const std::vector<double>& M, int n, int rows, bool prec
                 }
             }
     return out;
-}
-
-double tc_rowsum_error3(const std::vector<double>& M, int n) {
-    double worst = 0.0;
-    for (int i = 0; i < n; ++i) {
-        double rmax = 0.0, rabs = 0.0;
-        for (int k = 0; k < n; ++k) {
-            rmax = std::max(rmax, std::fabs(M[size_t(i) * n + k]));
-            rabs += std::fabs(M[size_t(i) * n + k]);
-        }
-        if (!(rabs > 0.0)) continue;
-        int e = 0;
-        std::frexp(rmax, &e);
-        double err = 0.0;   // sum over the row of (three-slice value - value), in units 2^(e-7)
-        for (int k = 0; k < n; ++k) {
-            const double y = std::ldexp(M[size_t(i) * n + k], 7 - e);
-            const double f0 = std::nearbyint(y);
-            const double y1 = (y - f0) * 256.0;
-            const double f1 = std::nearbyint(y1);
-            const double y2 = (y1 - f1) * 256.0;
-            const double f2 = std::nearbyint(y2);
-            err += (f2 - y2) / 65536.0;
-        }
-        worst = std::max(worst, std::fabs(std::ldexp(err, e - 7)) / rabs);
-    }
-    return worst;
 }
 
 double nodal_max(const double* a, size_t count) {

@@ -454,9 +454,8 @@ cudaError_t rhs_impl(const PeriodicArgs<T>& A, const StencilArgs<T>& s, cudaStre
         for (int x = 0; x < kMaxExtra; ++x) P.X[x] = s.X[x];
         for (int j = 0; j < s.nout; ++j) {
             P.out[j] = s.out[j];
-            P.cu[j] = T(s.cu[j]);
             P.cgF[j] = T(s.cg[j] + s.cF[j]);
-            for (int x = 0; x < kMaxExtra; ++x) P.cx[j][x] = T(s.cx[j][x]);
+            state_coefs<T>(s.cu[j], s.cx[j], P.cu[j], P.cx[j]);
         }
         if ((e = launch_pass_on<T, PM_FINAL_OUT>(P, st)) != cudaSuccess) return e;
     }

@@ -456,8 +456,8 @@ cudaError_t launch_impl(const StencilArgs<T>& p, cudaStream_t s) {
     c.r0 = T(p.r[0]); c.r1 = T(p.r[1]); c.r2 = T(p.r[2]); c.r3 = T(p.r[3]);
     bool needF = false;
     for (int j = 0; j < kMaxOut; ++j) {
-        c.cu[j] = T(p.cu[j]); c.cg[j] = T(p.cg[j]); c.cF[j] = T(p.cF[j]);
-        for (int e = 0; e < kMaxExtra; ++e) c.cx[j][e] = T(p.cx[j][e]);
+        c.cg[j] = T(p.cg[j]); c.cF[j] = T(p.cF[j]);
+        state_coefs<T>(p.cu[j], p.cx[j], c.cu[j], c.cx[j]);
         if (j < p.nout && p.cF[j] != 0.0) needF = true;
     }
     dim3 block(TX * TY);

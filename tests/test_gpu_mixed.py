@@ -181,7 +181,11 @@ def test_config3_full_size_two_steps_vs_oracle():
 
 def test_config3_full_run_vs_fp64_gpu():
     """All 40 steps of the 256^3 Lawson4 workload: mixed precision against the FP64 GPU
-    path (itself matched to the oracle at 1e-12), relative l2 <= 1e-6."""
+    path (itself matched to the oracle at 1e-12), relative l2 <= 1e-6 with a margin, and no
+    drift: the mean error sum(u - u64) / sum|u64| stays below 1e-7. Measured 2.6e-7 and +1e-9.
+    A biased contraction or stage combination shows up in the drift first: the six-product
+    split drifted by -1.0e-6 over these 40 steps, and Lawson4's 2/3 and 1/3 rounded to FP32
+    one by one by +1.2e-6."""
     w = W.config3()
     mixed = ctx_for(w.dims, w.tau, w.scheme, w.a_nodes, w.b, w.r_poly)
     u = torch.tensor(w.u0, dtype=torch.float32, device="cuda")
@@ -192,9 +196,11 @@ def test_config3_full_run_vs_fp64_gpu():
     ud = torch.tensor(w.u0, dtype=torch.float64, device="cuda")
     f64.integrate(ud, 0.0, w.m * w.tau, w.m)
     torch.cuda.synchronize()
-    err = O.rel_l2(u.cpu().numpy(), ud.cpu().numpy())
-    print(f"256^3 lawson4 40 steps: bf16x3 vs fp64 GPU rel l2 {err:.3e}")
-    assert err < 1e-6
+    got, ref = u.double().cpu().numpy(), ud.cpu().numpy()
+    err = O.rel_l2(got, ref)
+    drift = float((got - ref).sum() / np.abs(ref).sum())
+    print(f"256^3 lawson4 40 steps: bf16x3 vs fp64 GPU rel l2 {err:.3e}, mean drift {drift:+.2e}")
+    assert err < 5e-7 and abs(drift) < 1e-7, (err, drift)
 
 
 @pytest.mark.parametrize("scheme", ["etd2rk", "exponential_euler"])
