@@ -198,7 +198,8 @@ cudaError_t upload(adr_ctx* c, void** dst, const std::vector<double>& src) {
 // uses the factor as the A operand (128-row tiles), modes >= 2 as the B operand.
 cudaError_t upload_tc(adr_ctx* c, int kind, int m, const std::vector<double>& M) {
     const bool precise = (kind == 4);   // FK_EXP_HALF_PRECISE
-    const adr::TcFactor f = adr::make_tc_factor(M, c->n[m], adr::tc_out_rows(m >= 1, precise), precise);
+    // register-fed kernel: every image in the four-slice layout of its precise variant
+    const adr::TcFactor f = adr::make_tc_factor(M, c->n[m], adr::tc_out_rows(m >= 1, true), true);
     cudaError_t e = cudaSuccess;
     if (!c->d_img[kind][m]) e = cudaMalloc(reinterpret_cast<void**>(&c->d_img[kind][m]), f.img.size());
     if (e == cudaSuccess && !c->d_fsc[kind][m])
@@ -378,9 +379,6 @@ void push_mode(Sched& S, int mu, int kind, const T* x, T* y, int epi = adr::EPI_
     a.vec4 = (mu == 1) && (n % 4 == 0) && (reinterpret_cast<uintptr_t>(x) % 16 == 0);
     a.npos = (mu >= 2) ? P * Q : P;
     a.nK = (n + 63) / 64;
-    const int orows = adr::tc_out_rows(a.state_is_a, a.precise), prows = adr::tc_pos_rows(a.state_is_a, a.precise);
-    a.nOut = (n + orows - 1) / orows;
-    a.ntiles = ((a.npos + prows - 1) / prows) * a.nOut;
     if (epi == adr::EPI_PHI) {
         // the phi scaling is fused into a mode >= 2 pass: decode (q, p) into the other directions
         a.zmu = c->d_zt[mu - 1];
@@ -412,7 +410,15 @@ void push_mode(Sched& S, int mu, int kind, const T* x, T* y, int epi = adr::EPI_
         S.ops.push_back({[t, PP](cudaStream_t s) { return adr::launch_contract_tma(t, PP, s); }, tc_kind});
         return;
     }
-    S.ops.push_back({[a](cudaStream_t s) { return adr::launch_contract_tc(a, s); }, tc_kind});
+    // Register-fed kernel (shapes the TMA rules exclude): every pass in its precise variant, the
+    // ten-product split into exact accumulators (its images are built in that layout); the low
+    // part stays optional.
+    adr::TcArgs r = a;
+    r.precise = true;
+    const int orows = adr::tc_out_rows(r.state_is_a, true), prows = adr::tc_pos_rows(r.state_is_a, true);
+    r.nOut = (n + orows - 1) / orows;
+    r.ntiles = ((r.npos + prows - 1) / prows) * r.nOut;
+    S.ops.push_back({[r](cudaStream_t s) { return adr::launch_contract_tc(r, s); }, tc_kind});
 }
 
 // The device arrays of a periodic context as the Fourier kernels take them.

@@ -16,9 +16,10 @@
 // of a heat-kernel product carries no accumulation bias. D1 is weighted 2^-8 and its
 // terms have random signs. Representation errors are 2^-24 of the scales (as FP32).
 //
-// Precise configuration (the exponential whose result feeds the one stencil that no later
-// exponential smooths): four slices per operand, x = 2^(es-7) sum_j 2^(-8j) s_j (j < 4),
-// the input itself a double-float pair hi + lo, and ten MMAs per K step
+// Precise configuration, which the library uses for every pass of this kernel (the
+// two-accumulator standard configuration above rounds D1, and that biased every pass of a time
+// integration): four slices per operand, x = 2^(es-7) sum_j 2^(-8j) s_j (j < 4), the input
+// optionally a double-float pair hi + lo, and ten MMAs per K step
 //     D0 = S0.F0, D1 = S0.F1 + S1.F0, D2 = S0.F2 + S1.F1 + S2.F0 (all three exact),
 //     D3 = S0.F3 + S1.F2 + S2.F1 + S3.F0,
 // combined in double-float arithmetic into a hi + lo result (about 2^-31 of the scales).
@@ -584,22 +585,20 @@ cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
     const long long grid = a.ntiles < g_num_sms ? a.ntiles : g_num_sms;
     if (grid <= 0) return cudaSuccess;
     const unsigned g = unsigned(grid);
-    if (a.precise) {
-        if (a.epi != EPI_STORE2 && a.epi != EPI_STORE) return cudaErrorInvalidValue;
-        if (a.state_is_a) return a.epi == EPI_STORE2 ? launch_variant<true, true, EPI_STORE2>(a, g, s)
-                                                     : launch_variant<true, true, EPI_STORE>(a, g, s);
-        return a.epi == EPI_STORE2 ? launch_variant<false, true, EPI_STORE2>(a, g, s)
-                                   : launch_variant<false, true, EPI_STORE>(a, g, s);
-    }
+    // The library runs every pass in the precise configuration (ten products into exact
+    // accumulators); the standard configuration's two accumulators round, and that rounding
+    // biased every pass.
+    if (!a.precise) return cudaErrorInvalidValue;
     if (a.state_is_a) {
-        if (a.epi == EPI_PHI) return launch_variant<true, false, EPI_PHI>(a, g, s);
-        if (a.epi == EPI_AXPY) return launch_variant<true, false, EPI_AXPY>(a, g, s);
-        if (a.epi == EPI_STORE2) return launch_variant<true, false, EPI_STORE2>(a, g, s);
-        return launch_variant<true, false, EPI_STORE>(a, g, s);
+        if (a.epi == EPI_PHI) return launch_variant<true, true, EPI_PHI>(a, g, s);
+        if (a.epi == EPI_AXPY) return launch_variant<true, true, EPI_AXPY>(a, g, s);
+        if (a.epi == EPI_STORE2) return launch_variant<true, true, EPI_STORE2>(a, g, s);
+        return launch_variant<true, true, EPI_STORE>(a, g, s);
     }
-    if (a.epi == EPI_PHI || a.epi == EPI_STORE2) return cudaErrorInvalidValue;   // fused into modes >= 2 only
-    if (a.epi == EPI_AXPY) return launch_variant<false, false, EPI_AXPY>(a, g, s);
-    return launch_variant<false, false, EPI_STORE>(a, g, s);
+    if (a.epi == EPI_PHI) return cudaErrorInvalidValue;   // fused into modes >= 2 only
+    if (a.epi == EPI_AXPY) return launch_variant<false, true, EPI_AXPY>(a, g, s);
+    if (a.epi == EPI_STORE2) return launch_variant<false, true, EPI_STORE2>(a, g, s);
+    return launch_variant<false, true, EPI_STORE>(a, g, s);
 }
 
 }  // namespace adr

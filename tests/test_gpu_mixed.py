@@ -222,3 +222,26 @@ def test_phi_doubling_route_on_the_tensor_cores(scheme):
     err = O.rel_l2(u.cpu().numpy(), ref)
     print(f"{scheme} doubling route, bf16x3: {err:.3e}")
     assert err < 1e-5
+
+
+def test_register_fed_kernel_runs_unbiased():
+    """x1 = 129 is not a multiple of 4, so every contraction goes through the register-fed kernel
+    (the TMA rules exclude it): 40 Lawson4 steps of the 129 x 128 x 64 problem (b = 10) against
+    the FP64 GPU path. The ten-product split keeps the run unbiased: relative l2 below 5e-7 and
+    a mean drift below 1e-7 (the six-product split drifted by several 1e-6 on such runs)."""
+    dims = (129, 128, 64)
+    a, b, r = make(dims)
+    u0 = W.smooth_initial_state(dims, noise=1e-3, seed=4)
+    tau, m = 0.1 / 40, 40
+    out = {}
+    for prec, dt in (("bf16x3", torch.float32), ("fp64", torch.float64)):
+        c = ctx_for(dims, tau, "lawson4", a, b, r, prec=prec)
+        u = torch.tensor(u0, dtype=dt, device="cuda")
+        c.integrate(u, 0.0, m * tau, m)
+        c.synchronize()
+        out[prec] = u.double().cpu().numpy()
+        c.close()
+    err = O.rel_l2(out["bf16x3"], out["fp64"])
+    drift = float((out["bf16x3"] - out["fp64"]).sum() / np.abs(out["fp64"]).sum())
+    print(f"129 x 128 x 64 lawson4 40 steps (register-fed): rel l2 {err:.3e}, drift {drift:+.2e}")
+    assert err < 5e-7 and abs(drift) < 1e-7, (err, drift)
