@@ -345,7 +345,7 @@ def ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"bf16x3": "bf16x3+f32", "fp32": "f32", "fp64": "f64"}[args.precision],
+        "dtype": {"bf16x3": "bf16x4+f32", "fp32": "f32", "fp64": "f64"}[args.precision],
         "data": "synthetic",
         "config": {"workload": f"3d_{n}^3_lawson4_T0.1_m{w.m}", "grid": list(w.dims), "scheme": "lawson4",
                    "precision": args.precision, "tau": w.tau, "time_steps_per_bench_step": w.m,
@@ -446,7 +446,7 @@ def ours_grid(args):
     stream = torch.cuda.Stream()
     base = {"metric": f"DOF*steps/s, {args.workload}", "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3+f32"}[prec], "data": "synthetic",
+            "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x4+f32"}[prec], "data": "synthetic",
             "config": {"workload": w.name, "grid": list(w.dims), "scheme": w.scheme, "precision": prec,
                        "tau": w.tau, "time_steps_per_bench_step": w.m, "b": list(w.b[:len(w.dims)])}}
     if periodic:
