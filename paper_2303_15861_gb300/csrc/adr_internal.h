@@ -46,7 +46,8 @@ constexpr int kMaxOut = 2;
 // such as Lawson4's 2/3 Eu + 1/3 U2, the smallest nonzero one is replaced by one minus the
 // others when that difference is exact in T, so the rounded coefficients still sum to one:
 // 2/3 and 1/3 rounded to FP32 one by one sum to 1 + 3e-8, a gain that every time step would
-// apply to the whole state.
+// apply to the whole state. Only below double precision: the sum of the others is then exact
+// in double, and in FP64 the rounding of the coefficients (1e-16) does not matter.
 template <typename T>
 inline void state_coefs(double cu, const double* cx, T& tu, T* tx) {
     tu = T(cu);
@@ -55,6 +56,7 @@ inline void state_coefs(double cu, const double* cx, T& tu, T* tx) {
         tx[e] = T(cx[e]);
         sum += cx[e];
     }
+    if (sizeof(T) >= sizeof(double)) return;
     if (!(sum > 1.0 - 1e-12 && sum < 1.0 + 1e-12)) return;
     int k = -2;                      // -1: cu; e >= 0: cx[e]
     double mag = 0.0;
