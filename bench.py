@@ -4,8 +4,9 @@
 Workload: 3-D unit cube, 256^3 interior nodes, Dirichlet, u_t = div(a grad u) + b.grad u
 + u^2(1-u) with a = 1 + 0.5 sin(2 pi x) sin(2 pi y) sin(2 pi z), b = (10,10,10); Lawson4
 with 40 steps to T = 0.1; FP32 state and stencil, mu-mode contractions on the tensor
-cores (three BF16 slices per operand). One benchmark step = one integration of the 40
-time steps; the metric is DOF*steps/s (interior nodes times time steps per second).
+cores (four BF16 slices per operand, ten products into exact accumulators). One
+benchmark step = one integration of the 40 time steps; the metric is DOF*steps/s
+(interior nodes times time steps per second).
 
 Prints one JSON line (rank 0). --impl reference times the FP64 numpy oracle on the host
 cores on a bounded sample (one time step of the same workload per benchmark step).

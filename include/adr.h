@@ -61,8 +61,8 @@ typedef enum {
     ADR_FP32 = 1,          /* FP32 state, stencil and contractions (FP32 FMA)            */
     ADR_MIXED_TF32X3 = 2,  /* reserved: not implemented (returns ADR_ERR_UNSUPPORTED)    */
     ADR_MIXED_BF16X3 = 3   /* FP32 state and stencil; mu-mode contractions on the tensor
-                              cores from three BF16 slices per operand (six products) with
-                              exact FP32 accumulation; factors and phi near 0 in FP64    */
+                              cores from four BF16 slices per operand (ten products) into
+                              exact FP32 accumulators; factors and phi near 0 in FP64    */
 } adr_precision;
 
 typedef enum {

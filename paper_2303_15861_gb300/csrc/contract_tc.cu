@@ -9,7 +9,8 @@
 // its own scale 2^e_i. With integer slices |s_j|, |f_j| <= 128 (exact in BF16):
 //     x = 2^(es-7) (s0 + 2^-8 s1 + 2^-16 s2),   f = 2^(e_i-7) (f0 + 2^-8 f1 + 2^-16 f2),
 //     sum_k x f = 2^(es+e_i-14) (D0 + 2^-8 D1),
-//     D0 = S0.F0,  D1 = S0.F1 + S1.F0 + S0.F2' + S2'.F0 + S1.F1'    (six MMAs per K step)
+//     D0 = S0.F0,  D1 = S0.F1 + S1.F0 + S0.F2' + S2'.F0 + S1.F1'    (six MMAs per K step;
+//     the library runs the precise configuration below instead)
 // with F1' = 2^-8 F1, F2' = 2^-8 F2, S2' = 2^-8 S2 (exact scalings). Every term of D0 is
 // an integer of magnitude < 2^14 and |D0| < 2^24 for K <= 512, so D0 is exact in the FP32
 // accumulator whatever rounding the tensor core applies: the dominant, same-signed part

@@ -1,5 +1,6 @@
 """Parity of the mixed-precision path (FP32 state and stencil, mu-mode contractions on the
-tensor cores from three BF16 slices per operand) with the FP64 oracle.
+tensor cores from four BF16 slices per operand, ten products into exact accumulators)
+with the FP64 oracle.
 
 Tolerance: 1e-6 relative l2 for the 256^3 Lawson4 workload (the mixed-precision
 requirement); per-kernel checks use the same bound. The phi route through the eigenbasis
