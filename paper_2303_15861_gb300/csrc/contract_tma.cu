@@ -40,9 +40,12 @@ constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kN >>
 // Every pass: four slices of the state and of the factor, ten products into four accumulators,
 //     D0 = S0.F0,  D1 = S0.F1 + S1.F0,  D2 = S0.F2 + S1.F1 + S2.F0,
 //     D3 = S0.F3 + S1.F2 + S2.F1 + S3.F0,
-// integer terms below 2^14 and sums below 2^24 for K <= 512, so all four are exact whatever
-// rounding the tensor cores apply; x.f = D0 + 2^-8 D1 + 2^-16 D2 + 2^-24 D3 up to the products
-// below 2^-32, combined once in the epilogue. A time integration applies the same factor to a
+// integer terms of magnitude at most 2^14. For K <= 256 all four stay within 2^24 even in the
+// worst case (D0 and D1 for K <= 512), so they are exact whatever rounding the tensor cores
+// apply; beyond that D2 and D3 could pass 2^24 only if hundreds of residual-slice products
+// shared the largest magnitude and one sign, and their rounding would weigh 2^-16 and 2^-24 of
+// a unit of D0. x.f = D0 + 2^-8 D1 + 2^-16 D2 + 2^-24 D3 up to the products below 2^-32,
+// combined once in the epilogue. A time integration applies the same factor to a
 // slowly varying state in every step, so any bias of a pass adds up. Measured on the 40-step
 // 256^3 Lawson4 run (relative error and mean drift against the FP64 path): six products into
 // two accumulators 1.5e-6 / -1.0e-6; seven into three exact accumulators with a 32-bit factor
