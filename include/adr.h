@@ -313,7 +313,9 @@ int adr_kernels_per_step(const adr_ctx* ctx);
  * periodic and batched contexts, and before adr_set_coeffs. The exact-slice split of the
  * mu-mode products (Section 1) writes each factor row as 2^(e_i-7) sum_j 2^(-8j) f_j with
  * integer slices: four slices make a 32-bit factor, and the standard contraction then issues
- * seven BF16 products per multiply-add. *slices must not be NULL. */
+ * ten BF16 products per multiply-add (every pair of state slice i and factor slice j with
+ * i + j <= 3) into four TMEM accumulators D0..D3, one per weight 2^(-8(i+j)), each exact in
+ * FP32. *slices must not be NULL. */
 adr_status adr_tc_factor_slices(const adr_ctx* ctx, int* slices);
 
 /* The phi route a context uses after adr_set_coeffs (ADR_PHI_EIGEN or ADR_PHI_DOUBLING; 0

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 from oracle import adr_oracle as O
+from parity import assert_parity
 from paper_2303_15861_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -73,7 +74,7 @@ def test_batch_fp64_schemes_match_oracle(scheme):
     check_guards(full)
     for w, got in zip(ws, unpack(ws, u)):
         ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, m, scheme)
-        assert O.rel_l2(got, ref) < 1e-12, w.name
+        assert_parity(got, ref, 1e-12, what=w.name)
 
 
 def test_batch_fp32_etd2rk_full_horizon_matches_oracle():
@@ -85,7 +86,7 @@ def test_batch_fp32_etd2rk_full_horizon_matches_oracle():
     check_guards(full)
     for w, got in zip(ws, unpack(ws, u)):
         ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, w.m, "etd2rk")
-        assert O.rel_l2(got, ref) < 1e-5, w.name
+        assert_parity(got, ref, 1e-5, what=w.name)
 
 
 def test_batch_building_blocks_match_oracle():
@@ -110,12 +111,12 @@ def test_batch_building_blocks_match_oracle():
     Fs, gs = unpack(ws, F), unpack(ws, g)
     for i, w in enumerate(ws):
         prob = O.ADRProblem(w.dims, w.a_nodes, w.b, w.r_poly)
-        assert O.rel_l2(Fs[i], prob.F(w.u0)) < 1e-12, w.name
-        assert O.rel_l2(gs[i], prob.g(w.u0)) < 1e-12, w.name
+        assert_parity(Fs[i], prob.F(w.u0), 1e-12, what=w.name)
+        assert_parity(gs[i], prob.g(w.u0), 1e-12, what=w.name)
         mf = O.MatrixFunctions(prob, w.tau)
         for k, (_, y) in ys.items():
             ref = mf.exp_action(1.0, vs[i]) if k == 0 else mf.phi_action(k, 1.0, vs[i])
-            assert O.rel_l2(unpack(ws, y)[i], ref) < 1e-12, (w.name, k)
+            assert_parity(unpack(ws, y)[i], ref, 1e-12, what=(w.name, k))
 
 
 def test_batch_result_does_not_depend_on_tile_shapes():
@@ -204,7 +205,7 @@ def test_batch_coefficient_update_of_one_instance():
     ctx.synchronize()
     for w, got in zip(ws2, unpack(ws2, u)):
         ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, 2, "etd2rk")
-        assert O.rel_l2(got, ref) < 1e-12, w.name
+        assert_parity(got, ref, 1e-12, what=w.name)
 
 
 def test_batched_workload_512_instances_sampled_against_oracle():
@@ -223,7 +224,7 @@ def test_batched_workload_512_instances_sampled_against_oracle():
     for i in (0, 1, 31, 146, 255, 349, 448, 511):
         w = ws[i]
         ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, w.m, "etd2rk")
-        assert O.rel_l2(res[i], ref) < 1e-5, (i, w.dims)
+        assert_parity(res[i], ref, 1e-5, what=(i, w.dims))
 
 
 def test_batched_workload_every_instance_against_the_fp64_batch():

@@ -26,6 +26,7 @@ import numpy as np
 import pytest
 
 from oracle import adr_oracle as O
+from parity import assert_parity
 import bench
 
 pytestmark = pytest.mark.gpu
@@ -100,10 +101,8 @@ def test_every_single_grid_workload_but_the_384_cube_is_covered():
 def test_bench_workload_matches_oracle(name, prec):
     got = gpu_solution(name, prec)
     ref = oracle_solution(name)
-    assert np.all(np.isfinite(got))
-    err = O.rel_l2(got, ref)
-    print(f"{name} {prec}: rel l2 vs oracle {err:.3e}, rel inf {O.rel_inf(got, ref):.3e}")
-    assert err < TOL[prec], (name, prec, err)
+    err, err_inf, _ = assert_parity(got, ref, TOL[prec], what=f"{name} {prec}")
+    print(f"{name} {prec}: rel l2 vs oracle {err:.3e}, rel max {err_inf:.3e}")
 
 
 def test_the_standard_tensor_core_factors_have_four_slices():

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from oracle import adr_oracle as O
+from parity import assert_parity
 from paper_2303_15861_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -39,4 +40,4 @@ def test_bounded_wait_timeout_is_reported_and_the_context_recovers(prec):
         ctx.integrate(u, 0.0, 2 * w.tau, 2)
         ctx.synchronize()
     ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, 2, w.scheme)
-    assert O.rel_l2(u.double().cpu().numpy(), ref) < (1e-12 if prec == "fp64" else 2e-6)
+    assert_parity(u.double().cpu().numpy(), ref, (1e-12 if prec == "fp64" else 2e-6))

@@ -5,12 +5,15 @@ with the FP64 oracle.
 Tolerance: 1e-6 relative l2 for the 256^3 Lawson4 workload (the mixed-precision
 requirement); per-kernel checks use the same bound. The phi route through the eigenbasis
 loses up to prod_mu kappa(V_mu) times the slicing error, so its bound scales with kappa.
+Every comparison is also element by element (tests/parity.py): the relative maximum norm and
+each boundary-adjacent plane on its own scale.
 """
 import numpy as np
 import pytest
 
 from oracle import adr_oracle as O
 from paper_2303_15861_gb300 import workloads as W
+from parity import assert_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -70,8 +73,7 @@ def test_exp_action(dims, c):
     vin = v.double().cpu().numpy()
     prob = O.ADRProblem(dims, a, b, r)
     ref = O.MatrixFunctions(prob, tau).exp_action(c, vin)
-    err = O.rel_l2(y.cpu().numpy(), ref)
-    assert err < 1e-6, err
+    assert_parity(y.cpu().numpy(), ref, 1e-6, what=f"mixed exp {dims} c={c}")
 
 
 @pytest.mark.parametrize("dims", [(128, 128), (64, 64, 64), (31, 17, 22)])
@@ -90,8 +92,7 @@ def test_phi_action(dims, k):
     vin = v.double().cpu().numpy()
     mf = O.MatrixFunctions(O.ADRProblem(dims, a, b, r), tau)
     ref = mf.exp_action(1.0, vin) if k == 0 else mf.phi_action(k, 1.0, vin)
-    err = O.rel_l2(y.cpu().numpy(), ref)
-    assert err < 2e-7 * max(1.0, kappa), (err, kappa)
+    assert_parity(y.cpu().numpy(), ref, 2e-7 * max(1.0, kappa), what=f"mixed phi{k} {dims} kappa {kappa:.1e}")
 
 
 def test_no_accumulation_bias():
@@ -112,9 +113,9 @@ def test_no_accumulation_bias():
         ref = mf.exp_action(0.5, mf.exp_action(0.5, ref))
     torch.cuda.synchronize()
     got = x.double().cpu().numpy()
-    err = O.rel_l2(got, ref)
+    assert_parity(got, ref, 1e-6, what="200 E actions")
     drift = abs(got.sum() / ref.sum() - 1.0)
-    assert err < 1e-6 and drift < 1e-6, (err, drift)
+    assert drift < 1e-6, drift
 
 
 # (dims, b, scheme, T, m, tol). The relative error of a run grows as |u(T)| decays while the
@@ -154,39 +155,27 @@ def test_integrate_matches_oracle(dims, b, scheme, T, m, tol):
     ctx.synchronize()
     check_guards(fu)
     ref = O.solve(dims, a, bb, r, u0, tau, m, scheme)
-    err = O.rel_l2(u.cpu().numpy(), ref)
+    err, err_inf, _ = assert_parity(u.cpu().numpy(), ref, tol, what=f"mixed {scheme} {dims}")
     f32 = ctx_for(dims, tau, scheme, a, bb, r, prec="fp32")
     v = torch.tensor(u0, dtype=torch.float32, device="cuda")
     f32.integrate(v, 0.0, T, m)
     torch.cuda.synchronize()
     err32 = O.rel_l2(v.cpu().numpy(), ref)
-    assert err < tol, (err, err32)
-    print(f"{scheme} {dims}: mixed {err:.3e}, plain FP32 {err32:.3e}")
+    print(f"{scheme} {dims}: mixed {err:.3e} (max norm {err_inf:.3e}), plain FP32 {err32:.3e}")
     if scheme not in ("etd2rk", "exponential_euler", "erk2p1"):
         assert err < 2.5 * err32 + 2e-7, (err, err32)
 
 
-def test_config3_full_size_two_steps_vs_oracle():
-    """256^3 Lawson4 in the launch configuration the benchmark times: two steps against the
-    FP64 oracle (the full 40 are compared against the FP64 GPU path below)."""
-    w = W.config3()
-    ctx = ctx_for(w.dims, w.tau, w.scheme, w.a_nodes, w.b, w.r_poly)
-    u = torch.tensor(w.u0, dtype=torch.float32, device="cuda")
-    ctx.integrate(u, 0.0, 2 * w.tau, 2)
-    ctx.synchronize()
-    ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, 2, w.scheme)
-    err = O.rel_l2(u.cpu().numpy(), ref)
-    print(f"256^3 lawson4 bf16x3, 2 steps: rel l2 vs oracle {err:.3e}")
-    assert err < 1e-6
-
-
-def test_config3_full_run_vs_fp64_gpu():
-    """All 40 steps of the 256^3 Lawson4 workload: mixed precision against the FP64 GPU
-    path (itself matched to the oracle at 1e-12), relative l2 <= 1e-6 with a margin, and no
-    drift: the mean error sum(u - u64) / sum|u64| stays below 1e-7. Measured 2.6e-7 and +1e-9.
-    A biased contraction or stage combination shows up in the drift first: the six-product
-    split drifted by -1.0e-6 over these 40 steps, and Lawson4's 2/3 and 1/3 rounded to FP32
-    one by one by +1.2e-6."""
+def test_config3_full_run_vs_oracle_and_fp64_gpu():
+    """All 40 steps of the 256^3 Lawson4 workload, in the launch configuration the benchmark
+    times, against the FP64 oracle run for the same 40 steps (about 3 minutes on the host):
+      * the mixed path within 1e-6 relative l2 (the workload's tolerance), element by element;
+      * the plain FP64 GPU path within 1e-12 of the oracle;
+      * mixed against the FP64 GPU path within 5e-7 and without drift: the mean error
+        sum(u - u64) / sum|u64| stays below 1e-7. A biased contraction or stage combination
+        shows up in the drift first: the six-product split drifted by -1.0e-6 over these 40
+        steps, and Lawson4's 2/3 and 1/3 rounded to FP32 one by one by +1.2e-6.
+    Measured 2.6e-7 and +1e-9 for the last item."""
     w = W.config3()
     mixed = ctx_for(w.dims, w.tau, w.scheme, w.a_nodes, w.b, w.r_poly)
     u = torch.tensor(w.u0, dtype=torch.float32, device="cuda")
@@ -197,11 +186,18 @@ def test_config3_full_run_vs_fp64_gpu():
     ud = torch.tensor(w.u0, dtype=torch.float64, device="cuda")
     f64.integrate(ud, 0.0, w.m * w.tau, w.m)
     torch.cuda.synchronize()
-    got, ref = u.double().cpu().numpy(), ud.cpu().numpy()
-    err = O.rel_l2(got, ref)
-    drift = float((got - ref).sum() / np.abs(ref).sum())
-    print(f"256^3 lawson4 40 steps: bf16x3 vs fp64 GPU rel l2 {err:.3e}, mean drift {drift:+.2e}")
-    assert err < 5e-7 and abs(drift) < 1e-7, (err, drift)
+    f64.close()
+    got, g64 = u.double().cpu().numpy(), ud.cpu().numpy()
+    del u, ud
+    ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, w.m, w.scheme)
+    e_mixed = assert_parity(got, ref, 1e-6, what="256^3 lawson4 40 steps mixed vs oracle")
+    e_f64 = assert_parity(g64, ref, 1e-12, what="256^3 lawson4 40 steps FP64 GPU vs oracle")
+    err, err_inf, _ = assert_parity(got, g64, 5e-7, inf=2e-6, what="256^3 lawson4 40 steps mixed vs FP64 GPU")
+    drift = float((got - g64).sum() / np.abs(g64).sum())
+    print(f"256^3 lawson4 40 steps: mixed vs oracle l2 {e_mixed[0]:.3e} max {e_mixed[1]:.3e}; "
+          f"FP64 GPU vs oracle l2 {e_f64[0]:.3e} max {e_f64[1]:.3e}; "
+          f"mixed vs FP64 GPU l2 {err:.3e} max {err_inf:.3e} drift {drift:+.2e}")
+    assert abs(drift) < 1e-7, drift
 
 
 @pytest.mark.parametrize("scheme", ["etd2rk", "exponential_euler"])
@@ -220,9 +216,8 @@ def test_phi_doubling_route_on_the_tensor_cores(scheme):
     ctx.synchronize()
     check_guards(fu)
     ref = O.solve(dims, a, bb, r, u0, tau, m, scheme)
-    err = O.rel_l2(u.cpu().numpy(), ref)
-    print(f"{scheme} doubling route, bf16x3: {err:.3e}")
-    assert err < 1e-5
+    err, err_inf, _ = assert_parity(u.cpu().numpy(), ref, 1e-5, what=f"mixed doubling {scheme}")
+    print(f"{scheme} doubling route, bf16x3: {err:.3e}, max norm {err_inf:.3e}")
 
 
 def test_register_fed_kernel_runs_unbiased():
@@ -242,7 +237,8 @@ def test_register_fed_kernel_runs_unbiased():
         c.synchronize()
         out[prec] = u.double().cpu().numpy()
         c.close()
-    err = O.rel_l2(out["bf16x3"], out["fp64"])
+    err, err_inf, _ = assert_parity(out["bf16x3"], out["fp64"], 5e-7, inf=2e-6,
+                                    what="129 x 128 x 64 lawson4 40 steps (register-fed)")
     drift = float((out["bf16x3"] - out["fp64"]).sum() / np.abs(out["fp64"]).sum())
-    print(f"129 x 128 x 64 lawson4 40 steps (register-fed): rel l2 {err:.3e}, drift {drift:+.2e}")
-    assert err < 5e-7 and abs(drift) < 1e-7, (err, drift)
+    print(f"129 x 128 x 64 lawson4 40 steps (register-fed): rel l2 {err:.3e}, max {err_inf:.3e}, drift {drift:+.2e}")
+    assert abs(drift) < 1e-7, drift

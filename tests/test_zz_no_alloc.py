@@ -5,8 +5,10 @@ their device memory up front in their own pool, or pipelines in which an allocat
 synchronise the device. For them the library offers one entry point that allocates
 nothing and keeps its intermediates in a fixed static device array. This test checks,
 through the C ABI, that two calls in a row give the same result as the context-based
-entry point adr_apply_exp (the one that uses library workspace), within the FP64
-tolerance of the other parity tests, and that grids beyond the static array are refused.
+entry point adr_apply_exp (the one that uses library workspace) and as the FP64 oracle's
+mu-mode exponential action (Section 1), element by element within the FP64 tolerance of
+the other parity tests; that a grid of exactly the static array's 1,048,576 points is
+accepted; and that larger grids are refused.
 """
 import numpy as np
 import pytest
@@ -25,7 +27,7 @@ from paper_2303_15861_gb300 import adr, build_lib  # noqa: E402
 build_lib.build()
 adr.load_library()
 
-TOL = 1e-13   # FP64 exp-action tolerance of tests/test_gpu_parity.py
+TOL = 1e-13   # FP64 exp-action tolerance of tests/test_gpu_parity.py (relative l2 and max norm)
 
 
 def _case(dims, c, tau, seed):
@@ -38,24 +40,38 @@ def _case(dims, c, tau, seed):
     prob = O.ADRProblem(dims, a, b, r)
     factors = [torch.tensor(O.expm(c * tau * prob.factor(mu)), device="cuda")
                for mu in range(1, len(dims) + 1)]
-    v = torch.tensor(np.random.default_rng(seed).standard_normal(tuple(dims[::-1])), device="cuda")
-    return ctx, factors, v
+    v_host = np.random.default_rng(seed).standard_normal(tuple(dims[::-1]))
+    v = torch.tensor(v_host, device="cuda")
+    oracle = O.MatrixFunctions(prob, tau).exp_action(c, v_host)
+    return ctx, factors, v, oracle
 
 
-def test_static_chain_matches_context_entry_point_twice_in_a_row():
-    cases = [((45, 19, 23), 0.5, 2.5e-3, 1), ((70, 45), 1.0, 2e-3, 2)]
+def _check(y, ref):
+    got = y.cpu().numpy()
+    assert np.isfinite(got).all()
+    assert O.rel_l2(got, ref) < TOL
+    assert O.rel_inf(got, ref) < TOL
+
+
+@pytest.mark.parametrize("cases", [
+    [((45, 19, 23), 0.5, 2.5e-3, 1), ((70, 45), 1.0, 2e-3, 2)],
+    [((128, 128, 64), 0.5, 2.5e-3, 3)],          # exactly the static array: 1,048,576 points
+], ids=["small", "at_the_limit"])
+def test_static_chain_matches_context_entry_point_and_oracle_twice_in_a_row(cases):
     results = []
     for dims, c, tau, seed in cases:
-        ctx, factors, v = _case(dims, c, tau, seed)
-        y_ref = torch.empty_like(v)
-        ctx.apply_exp(c, v, y_ref)
-        y = torch.full_like(v, float("nan"))
-        adr.adr_mumode_apply_static(factors, v, y)
-        torch.cuda.synchronize()
-        results.append((y, y_ref))
-    for y, y_ref in results:
-        err = O.rel_l2(y.cpu().numpy(), y_ref.cpu().numpy())
-        assert err < TOL, err
+        for _ in range(2):                       # two calls in a row share the static array
+            ctx, factors, v, oracle = _case(dims, c, tau, seed)
+            y_ref = torch.empty_like(v)
+            ctx.apply_exp(c, v, y_ref)
+            y = torch.full_like(v, float("nan"))
+            adr.adr_mumode_apply_static(factors, v, y)
+            torch.cuda.synchronize()
+            results.append((y, y_ref, oracle))
+            ctx.close()
+    for y, y_ref, oracle in results:
+        _check(y, y_ref.cpu().numpy())          # the context-based entry point
+        _check(y, oracle)                        # the FP64 oracle
 
 
 def test_static_chain_refuses_grids_beyond_the_static_array():
