@@ -602,7 +602,7 @@ def ours_grid(args):
 
 
 # ----------------------------------------------------------------------------- batched 2-D
-BATCH_METRIC = "DOF*steps/s, 512 batched 2-D ETD2RK instances (FP32)"
+BATCH_METRIC = "DOF*steps/s, 512 batched 2-D ETD2RK instances (FP32 state pairs)"
 BATCH_PER_RANK = 512           # instances per rank (weak scaling: the rank's block of one global draw)
 FP32_LANES_PER_SM = 128        # FP32 FMA lanes per SM (4 SMSPs x 32)
 SMS = 152
@@ -665,7 +665,7 @@ def ours_batch(args):
         torch.cuda.set_device(0)
     build_lib.build()
     adr.load_library()
-    prec = "fp64" if args.precision == "fp64" else "fp32"
+    prec = args.precision                 # bf16x3 (default): compensated pairs, tensor-core contractions
     dt = torch.float64 if prec == "fp64" else torch.float32
     # weak scaling: a draw of 512 instances per rank; rank r advances its own block of them
     lo, hi = ranks.shard(BATCH_PER_RANK * world, rank, world)
@@ -759,17 +759,29 @@ def ours_batch(args):
             dist.destroy_process_group()
         return 0
 
-    # roofline of the dominant kernel: the batched contraction on the FP32 FMA pipes
+    # roofline of the dominant kernel: one mu-mode pass over all instances, 2 n flops per node
+    # (the mean of the two modes' K), on the tensor cores (mixed) or the FMA pipes
     flops_pass = sum(2.0 * w.dims[0] * w.dims[1] * (w.dims[0] + w.dims[1]) / 2.0 for w in ws)
-    c_ms = statistics.mean(kinds.get(3, [float("nan")]))
     clk = sampler.summary()
-    peak, src = alu_peak(prec)
-    achieved = flops_pass / (c_ms * 1e-3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
-            "kernel": "batch_contract_kernel (mu-mode pass over all instances, FMA)",
-            "launch_ms": c_ms, "stencil_launch_ms": statistics.mean(kinds.get(2, [float("nan")])),
-            "peak_source": src}
+    if prec == "bf16x3":
+        c_ms = statistics.mean(kinds.get(4, [float("nan")]))
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = json.load(f)["bf16_tflops_sustained"]
+        achieved = flops_pass / (c_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "batch_tc_kernel (mu-mode pass over all instances, tcgen05 kind::f16)",
+                "launch_ms": c_ms, "products_per_multiply_add": 14.0, "issued_frac": 14.0 * achieved / peak,
+                "stencil_launch_ms": statistics.mean(kinds.get(2, [float("nan")])),
+                "peak_source": "measured bf16 sustained"}
+    else:
+        c_ms = statistics.mean(kinds.get(3, [float("nan")]))
+        peak, src = alu_peak(prec)
+        achieved = flops_pass / (c_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "batch_contract_kernel (mu-mode pass over all instances, FMA)",
+                "launch_ms": c_ms, "stencil_launch_ms": statistics.mean(kinds.get(2, [float("nan")])),
+                "peak_source": src}
     cpu = None
     if not args.no_cpu:
         t_cpu, d_cpu = batch_oracle_sample(ws, stride=1)
@@ -779,7 +791,8 @@ def ours_batch(args):
     line = {
         "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"bf16x3": "bf16x5+f32x2", "fp32": "f32", "fp64": "f64"}[prec],
+        "data": "synthetic",
         "config": {"workload": "2d_batch512_etd2rk_T0.1_m30", "instances": len(ws), "dof": N, "precision": prec,
                    "time_steps_per_bench_step": m, "parallelism": f"instances sharded over {world} rank(s)",
                    "instances_all_ranks": BATCH_PER_RANK * world,

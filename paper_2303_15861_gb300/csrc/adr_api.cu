@@ -85,6 +85,19 @@ struct adr_batch_state {
     int sgrid = 0;                         // persistent CTAs of the stencil
     std::vector<int> tile[2];              // BatchTile per instance, per mode
     bool uploaded = false, tuned = false;
+    // mixed precision (compensated FP32 pairs, tensor-core contractions; batch_tc.cu)
+    bool mixed = false;
+    std::vector<adr::BatchTcInst> tci;     // per instance: sizes, image and scale offsets
+    void* d_tci = nullptr;
+    uint8_t* d_img = nullptr;              // sliced factor images of every instance, role, direction
+    float* d_fsc = nullptr;                // their row scales
+    float2* d_phi[3] = {nullptr, nullptr, nullptr};   // double-float phi_0, phi_1, phi_2 per node
+    int4* d_titems[2] = {nullptr, nullptr};           // tensor-core work items per mode
+    int ntitems[2] = {0, 0};
+    float* d_lo[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // low parts of ws[0..5]
+    float* d_ulo = nullptr;                // low part of the caller's state
+    float* d_uhs = nullptr;                // the high part the library last wrote to the caller's state
+    unsigned* d_bslots = nullptr;          // max|x| per (produced array, instance)
 };
 
 struct adr_ctx {
@@ -221,6 +234,7 @@ cudaError_t upload_tc(adr_ctx* c, int kind, int m, const std::vector<double>& M)
 
 // ------------------------------------------------------------------ schedule builders
 constexpr int kSlots = 4096;
+constexpr int kBatchSlots = 64;         // per-instance max-abs slots of a mixed batched step
 constexpr int kGraphSteps = 8;             // steps per replay of the multi-step graph
 
 // The ops of one call, plus the max-abs bookkeeping of the mixed path: every array a
@@ -231,32 +245,64 @@ struct Sched {
     std::vector<Op> ops;
     int next = 0;
     std::vector<std::pair<const void*, int>> slot_of;
+    // mixed batched contexts: the low part (and the copy of the high part) kept beside an array
+    struct Companion {
+        const void* hi;
+        float* lo;
+        float* hs;
+    };
+    std::vector<Companion> comp;
+
+    bool batch_mixed() const { return c->bs && c->bs->mixed; }
+    bool slots_on() const { return c->tc || batch_mixed(); }
+    int max_slots() const { return batch_mixed() ? kBatchSlots : kSlots; }
+    // a slot is one word, or one word per instance in a batched context
+    unsigned* slot(int id) const { return batch_mixed() ? c->bs->d_bslots + size_t(id) * c->bs->B : c->d_slots + id; }
 
     explicit Sched(const adr_ctx* ctx) : c(ctx) {
         if (c->tc) {
             unsigned* sl = c->d_slots;
             ops.push_back({[sl](cudaStream_t s) { return cudaMemsetAsync(sl, 0, kSlots * sizeof(unsigned), s); }, OP_MEMSET});
         }
+        if (batch_mixed()) {
+            unsigned* sl = c->bs->d_bslots;
+            const size_t bytes = size_t(kBatchSlots) * c->bs->B * sizeof(unsigned);
+            ops.push_back({[sl, bytes](cudaStream_t s) { return cudaMemsetAsync(sl, 0, bytes, s); }, OP_MEMSET});
+            for (int i = 0; i < 6; ++i) comp.push_back({c->ws[i], c->bs->d_lo[i], nullptr});
+        }
     }
     bool overflow = false;
     unsigned* produce(const void* buf) {
-        if (!c->tc) return nullptr;
-        if (next >= kSlots) { overflow = true; return c->d_slots + (kSlots - 1); }
+        if (!slots_on()) return nullptr;
+        if (next >= max_slots()) { overflow = true; return slot(max_slots() - 1); }
         const int id = next++;
         for (auto& e : slot_of)
-            if (e.first == buf) { e.second = id; return c->d_slots + id; }
+            if (e.first == buf) { e.second = id; return slot(id); }
         slot_of.push_back({buf, id});
-        return c->d_slots + id;
+        return slot(id);
     }
-    const unsigned* consume(const void* buf) {
-        for (auto& e : slot_of)
-            if (e.first == buf) return c->d_slots + e.second;
-        // not produced in this schedule (a caller's array): measure it first
-        unsigned* sl = produce(buf);
-        const float* x = static_cast<const float*>(buf);
-        const size_t N = c->N;
-        ops.push_back({[x, N, sl](cudaStream_t s) { return adr::launch_amax(x, N, sl, s); }, OP_AMAX});
-        return sl;
+    const unsigned* consume(const void* buf);
+    float* lo_of(const void* p) const {
+        for (const auto& e : comp)
+            if (p && e.hi == p) return e.lo;
+        return nullptr;
+    }
+    float* hs_of(const void* p) const {
+        for (const auto& e : comp)
+            if (p && e.hi == p) return e.hs;
+        return nullptr;
+    }
+    // The caller's state u of a step of a mixed batched context: its low part lives in the
+    // library and is kept only where u still holds the high part the library wrote last.
+    void bind_state(const void* u) {
+        if (!batch_mixed()) return;
+        const adr_batch_state& b = *c->bs;
+        comp.push_back({u, b.d_ulo, b.d_uhs});
+        const float* uu = static_cast<const float*>(u);
+        float* hs = b.d_uhs;
+        float* lo = b.d_ulo;
+        const long long n = static_cast<long long>(c->N);
+        ops.push_back({[uu, hs, lo, n](cudaStream_t s) { return adr::launch_batch_keep_lo(uu, hs, lo, n, s); }, OP_AMAX});
     }
 };
 
@@ -291,11 +337,45 @@ static_assert(int(FK_EXP_HALF) == adr::BR_EXP_HALF && int(FK_EXP_ONE) == adr::BR
 
 bool aligned16(const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
 
+// Mixed batched context: one tensor-core pass over every instance (batch_tc.cu); inputs,
+// outputs and the axpy base carry their low parts where the schedule keeps them.
+void push_mode_batch_tc(Sched& S, int mu, int kind, const float* x, float* y, int epi, const float* base, double alpha,
+                        int phik) {
+    const adr_ctx* c = S.c;
+    const adr_batch_state& b = *c->bs;
+    adr::BatchTcArgs a;
+    a.inst = static_cast<const adr::BatchTcInst*>(b.d_tci);
+    a.items = b.d_titems[mu - 1];
+    a.nitems = b.ntitems[mu - 1];
+    a.mode = mu;
+    a.role = kind == FK_EXP_ALPHA ? adr::BR_EXP_ALPHA : kind;
+    a.fimg = b.d_img;
+    a.fscale = b.d_fsc;
+    a.X = x;
+    a.Xlo = S.lo_of(x);
+    a.Y = y;
+    a.Ylo = S.lo_of(y);
+    a.Yhs = S.hs_of(y);
+    a.epi = epi;
+    a.base = base;
+    a.base_lo = S.lo_of(base);
+    a.alpha = alpha;
+    a.phi = epi == adr::EPI_PHI ? b.d_phi[phik] : nullptr;
+    a.amax_in = S.consume(x);
+    a.amax_out = S.produce(y);
+    a.err = c->d_err;
+    S.ops.push_back({[a](cudaStream_t s) { return adr::launch_batch_tc(a, s); }, OP_CONTRACT_TC});
+}
+
 // Batched context: one pass over every instance (one persistent launch).
 template <typename T>
 void push_mode_batch(Sched& S, int mu, int kind, const T* x, T* y, int epi, const T* base, double alpha, int phik) {
     const adr_ctx* c = S.c;
     const adr_batch_state& b = *c->bs;
+    if (b.mixed) {
+        if constexpr (sizeof(T) == 4) push_mode_batch_tc(S, mu, kind, x, y, epi, base, alpha, phik);
+        return;
+    }
     adr::BatchContractArgs<T> a;
     a.inst = static_cast<const adr::BatchInst<T>*>(b.d_inst);
     a.items = b.d_items[mu - 1];
@@ -339,6 +419,27 @@ adr::BatchStencilArgs<T> batch_stencil_args(const adr_ctx* c, const StencilArgs<
     }
     a.grid = b.sgrid;
     return a;
+}
+
+const unsigned* Sched::consume(const void* buf) {
+    for (auto& e : slot_of)
+        if (e.first == buf) return slot(e.second);
+    // not produced in this schedule (a caller's array): measure it first
+    unsigned* sl = produce(buf);
+    const float* x = static_cast<const float*>(buf);
+    if (batch_mixed()) {
+        const adr_batch_state& b = *c->bs;
+        adr::BatchStencilArgs<float> g;
+        g.inst = static_cast<const adr::BatchInst<float>*>(b.d_inst);
+        g.row_start = b.d_row_start;
+        g.ninst = b.B;
+        g.rows = b.rows;
+        ops.push_back({[g, x, sl](cudaStream_t s) { return adr::launch_batch_amax(g, x, sl, s); }, OP_AMAX});
+        return sl;
+    }
+    const size_t N = c->N;
+    ops.push_back({[x, N, sl](cudaStream_t s) { return adr::launch_amax(x, N, sl, s); }, OP_AMAX});
+    return sl;
 }
 
 // One mu-mode pass y = x x_mu M_kind with epilogue (epi, base, alpha, phik).
@@ -639,6 +740,21 @@ void push_stencil(Sched& S, StencilArgs<T> s, bool record_input) {
     }
     if (S.c->bs) {
         const auto a = batch_stencil_args(S.c, s);
+        if constexpr (sizeof(T) == 4) {
+            if (S.batch_mixed()) {   // compensated stencil: low parts in and out, max|out| per instance
+                adr::BatchStencil2Args P;
+                P.s = a;
+                P.u_lo = S.lo_of(s.u);
+                for (int e = 0; e < s.nx; ++e) P.X_lo[e] = S.lo_of(s.X[e]);
+                for (int j = 0; j < s.nout; ++j) {
+                    P.out_lo[j] = S.lo_of(s.out[j]);
+                    P.out_hs[j] = S.hs_of(s.out[j]);
+                    P.amax[j] = S.produce(s.out[j]);
+                }
+                S.ops.push_back({[P](cudaStream_t st) { return adr::launch_batch_stencil2(P, st); }, OP_STENCIL});
+                return;
+            }
+        }
         S.ops.push_back({[a](cudaStream_t st) { return adr::launch_batch_stencil(a, st); }, OP_STENCIL});
         return;
     }
@@ -652,6 +768,7 @@ void push_stencil(Sched& S, StencilArgs<T> s, bool record_input) {
 template <typename T>
 std::vector<Op> build_step(const adr_ctx* c, T* u) {
     Sched S(c);
+    S.bind_state(u);
     const double tau = c->p.tau;
     T* B0 = static_cast<T*>(c->ws[0]);
     T* B1 = static_cast<T*>(c->ws[1]);
@@ -1037,6 +1154,88 @@ adr_status batch_tune(adr_ctx* c) {
     return ADR_OK;
 }
 
+// phi_k(z) for real z in FP64: the Taylor series for |z| < 1, the closed forms with expm1 elsewhere.
+double phi_real(int k, double z) {
+    if (k == 0) return std::exp(z);
+    if (std::fabs(z) < 1.0) {
+        double acc = 0.0;
+        for (int j = 29; j >= 0; --j) acc = acc * z + inv_factorial(j + k);
+        return acc;
+    }
+    const double em1 = std::expm1(z);
+    return k == 1 ? em1 / z : (em1 - z) / (z * z);
+}
+
+// Mixed batched context, instance i: slice its factors for the tensor cores (batch_tc.cu)
+// and upload them with their row scales; for the phi schemes also the double-float tables
+// phi_k(tau (lambda_1[i1] + lambda_2[i2])), k = 0, 1, 2, at the instance's nodes.
+cudaError_t batch_mixed_instance(adr_ctx* c, int i) {
+    adr_batch_state& b = *c->bs;
+    const adr::BatchTcInst& t = b.tci[size_t(i)];
+    const int n[2] = {t.n1, t.n2};
+    cudaError_t e = cudaSuccess;
+    std::vector<uint8_t> img;
+    std::vector<float> fsc;
+    for (int r = 0; r < adr::kBatchRoles && e == cudaSuccess; ++r)
+        for (int m = 0; m < 2 && e == cudaSuccess; ++m) {
+            if (!b.roles[r]) continue;
+            const double* M = &b.hF[size_t(b.f_off[size_t(i) * 2 * adr::kBatchRoles + r * 2 + m])];
+            img.assign(adr::batch_tc_image_bytes(n[m], m + 1), 0);
+            fsc.assign(size_t(n[m]), 0.0f);
+            adr::make_batch_tc_factor(M, n[m], m + 1, img.data(), fsc.data());
+            e = cudaMemcpy(b.d_img + t.img_off[r][m], img.data(), img.size(), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(b.d_fsc + t.fsc_off[r][m], fsc.data(), fsc.size() * sizeof(float), cudaMemcpyHostToDevice);
+        }
+    if (e != cudaSuccess || !b.roles[adr::BR_V]) return e;
+    const double* z1 = &b.hZt[size_t(b.zt_off[size_t(i) * 2])];
+    const double* z2 = &b.hZt[size_t(b.zt_off[size_t(i) * 2 + 1])];
+    std::vector<float2> tab(size_t(t.n1) * t.n2);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        for (int i2 = 0; i2 < t.n2; ++i2)
+            for (int i1 = 0; i1 < t.n1; ++i1) {
+                const double v = phi_real(k, z1[i1] + z2[i2]);
+                const float hi = float(v);
+                tab[size_t(i2) * t.n1 + i1] = make_float2(hi, float(v - double(hi)));
+            }
+        e = cudaMemcpy(b.d_phi[k] + t.off, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    }
+    return e;
+}
+
+// Mixed batched context, once every instance is set: the instance table and the work items of
+// the tensor-core passes, instances in order of decreasing size (longest-processing-time order
+// for the persistent CTAs that take items round robin). Mode 1: 64-row x2 tiles x 128 outputs
+// along x1; mode 2: 128-position x1 tiles x 64 outputs along x2.
+cudaError_t batch_mixed_plan(adr_ctx* c) {
+    adr_batch_state& b = *c->bs;
+    cudaError_t e = cudaMemcpy(b.d_tci, b.tci.data(), b.tci.size() * sizeof(adr::BatchTcInst), cudaMemcpyHostToDevice);
+    std::vector<int> order(size_t(b.B));
+    for (int i = 0; i < b.B; ++i) order[size_t(i)] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return (long long)b.n1[x] * b.n2[x] * (b.n1[x] + b.n2[x]) > (long long)b.n1[y] * b.n2[y] * (b.n1[y] + b.n2[y]);
+    });
+    for (int mode = 1; mode <= 2 && e == cudaSuccess; ++mode) {
+        std::vector<int4> items;
+        for (int i : order) {
+            const int n1 = b.n1[i], n2 = b.n2[i];
+            const int npt = mode == 1 ? (n2 + 63) / 64 : (n1 + 127) / 128;
+            const int nout = mode == 1 ? (n1 + 127) / 128 : (n2 + 63) / 64;
+            for (int pt = 0; pt < npt; ++pt)
+                for (int ot = 0; ot < nout; ++ot) items.push_back(make_int4(i, pt, ot, 0));
+        }
+        if (b.d_titems[mode - 1]) cudaFree(b.d_titems[mode - 1]);
+        b.d_titems[mode - 1] = nullptr;
+        e = cudaMalloc(reinterpret_cast<void**>(&b.d_titems[mode - 1]), items.size() * sizeof(int4));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b.d_titems[mode - 1], items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
+        b.ntitems[mode - 1] = int(items.size());
+        b.grid[mode - 1] = std::min(int(items.size()), device_sms());
+    }
+    b.sgrid = 8 * device_sms();
+    return e;
+}
+
 adr_status create_batch(const adr_params* p, void* cuda_stream, adr_ctx** out) {
     if (p->dim != 2) return fail(nullptr, ADR_ERR_ARG, "a batched context is 2-D: dim must be 2");
     if (p->bc_hi != ADR_BC_DIRICHLET || p->form != ADR_FORM_FLUX)
@@ -1045,11 +1244,12 @@ adr_status create_batch(const adr_params* p, void* cuda_stream, adr_ctx** out) {
     if (p->batch > (1 << 20)) return fail(nullptr, ADR_ERR_ARG, "batch must be <= 2^20");
     if (!(p->tau > 0.0) || !std::isfinite(p->tau)) return fail(nullptr, ADR_ERR_ARG, "tau must be positive");
     if (p->scheme < ADR_LAWSON_EULER || p->scheme > ADR_STABILIZED_LAWSON2) return fail(nullptr, ADR_ERR_ARG, "unknown scheme");
-    if (p->precision == ADR_MIXED_BF16X3 || p->precision == ADR_MIXED_TF32X3)
-        return fail(nullptr, ADR_ERR_UNSUPPORTED,
-                    "batched contexts run in ADR_FP64 or ADR_FP32 (the fixed-point slices of the mixed "
-                    "path lose the small entries of ill-scaled eigenvector factors)");
-    if (p->precision != ADR_FP64 && p->precision != ADR_FP32) return fail(nullptr, ADR_ERR_ARG, "unknown precision");
+    if (p->precision == ADR_MIXED_TF32X3)
+        return fail(nullptr, ADR_ERR_UNSUPPORTED, "ADR_MIXED_TF32X3 is not built; batched contexts run in ADR_FP64, "
+                    "ADR_FP32 or ADR_MIXED_BF16X3");
+    if (p->precision != ADR_FP64 && p->precision != ADR_FP32 && p->precision != ADR_MIXED_BF16X3)
+        return fail(nullptr, ADR_ERR_ARG, "unknown precision");
+    const bool mixed = p->precision == ADR_MIXED_BF16X3;
     int force = -1;
     if (p->batch_tile == 32) force = adr::BT_32;
     else if (p->batch_tile == 64) force = adr::BT_64;
@@ -1060,6 +1260,7 @@ adr_status create_batch(const adr_params* p, void* cuda_stream, adr_ctx** out) {
     adr_batch_state& b = *bs;
     b.B = p->batch;
     b.tile_force = force;
+    b.mixed = mixed;
     switch (p->scheme) {
     case ADR_LAWSON_EULER:
     case ADR_STABILIZED_LAWSON_EULER:
@@ -1075,11 +1276,13 @@ adr_status create_batch(const adr_params* p, void* cuda_stream, adr_ctx** out) {
     b.off.resize(b.B); b.row0.resize(b.B); b.a_off.resize(b.B);
     b.f_off.assign(size_t(b.B) * 2 * adr::kBatchRoles, -1);
     b.zt_off.assign(size_t(b.B) * 2, -1);
-    long long N = 0;
+    long long N = 0, img_len = 0, fsc_len = 0;
     for (int i = 0; i < b.B; ++i) {
         const int n1 = p->n_batch[2 * i], n2 = p->n_batch[2 * i + 1];
         if (n1 < 2 || n1 > 4096 || n2 < 2 || n2 > 4096)
             return fail(nullptr, ADR_ERR_ARG, "instance sizes must be in [2, 4096]");
+        if (mixed && (n1 > 256 || n2 > 256))
+            return fail(nullptr, ADR_ERR_ARG, "mixed batched instances must have n1, n2 <= 256 (exact accumulators)");
         b.n1[i] = n1; b.n2[i] = n2;
         b.off[i] = N; N += (long long)n1 * n2;
         b.row0[i] = b.rows; b.rows += n2;
@@ -1097,6 +1300,23 @@ adr_status create_batch(const adr_params* p, void* cuda_stream, adr_ctx** out) {
                 b.zt_off[size_t(i) * 2 + m] = b.zt_len;
                 b.zt_len += ((m == 0 ? n1 : n2) + 3) / 4 * 4;
             }
+        if (mixed) {
+            adr::BatchTcInst t;
+            t.n1 = n1;
+            t.n2 = n2;
+            t.off = b.off[i];
+            t.vec = (n1 % 4 == 0 && b.off[i] % 4 == 0) ? 1 : 0;
+            for (int r = 0; r < adr::kBatchRoles; ++r)
+                for (int m = 0; m < 2; ++m) {
+                    if (!b.roles[r]) continue;
+                    const int nm = m == 0 ? n1 : n2;
+                    t.img_off[r][m] = img_len;
+                    img_len += (long long)adr::batch_tc_image_bytes(nm, m + 1);
+                    t.fsc_off[r][m] = fsc_len;
+                    fsc_len += (nm + 3) / 4 * 4;
+                }
+            b.tci.push_back(t);
+        }
     }
     if (N > (1LL << 31) - 1) return fail(nullptr, ADR_ERR_ARG, "batch too large (more than 2^31 - 1 nodes)");
     b.hA.assign(size_t(b.a_len), 0.0);
@@ -1135,6 +1355,27 @@ adr_status create_batch(const adr_params* p, void* cuda_stream, adr_ctx** out) {
     if (e == cudaSuccess) e = cudaMalloc(&b.d_a, size_t(b.a_len) * c->esize);
     if (e == cudaSuccess) e = cudaMalloc(&b.d_f, size_t(b.f_len) * c->esize);
     if (e == cudaSuccess && b.zt_len > 0) e = cudaMalloc(&b.d_zt, size_t(b.zt_len) * c->esize);
+    if (mixed && e == cudaSuccess) {
+        // tensor-core images, row scales, double-float phi tables, low parts, per-instance slots
+        e = cudaMalloc(reinterpret_cast<void**>(&b.d_img), size_t(img_len));
+        if (e == cudaSuccess) e = cudaMemset(b.d_img, 0, size_t(img_len));
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b.d_fsc), size_t(fsc_len) * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemset(b.d_fsc, 0, size_t(fsc_len) * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&b.d_tci, size_t(b.B) * sizeof(adr::BatchTcInst));
+        for (int k = 0; k < 3 && e == cudaSuccess && b.roles[adr::BR_V]; ++k)
+            e = cudaMalloc(reinterpret_cast<void**>(&b.d_phi[k]), c->N * sizeof(float2));
+        for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
+            e = cudaMalloc(reinterpret_cast<void**>(&b.d_lo[k]), c->N * sizeof(float));
+            if (e == cudaSuccess) e = cudaMemset(b.d_lo[k], 0, c->N * sizeof(float));
+        }
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b.d_ulo), c->N * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemset(b.d_ulo, 0, c->N * sizeof(float));
+        // NaN (all bits set) compares unequal to any state, so the first step starts with a zero low part
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b.d_uhs), c->N * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemset(b.d_uhs, 0xFF, c->N * sizeof(float));
+        if (e == cudaSuccess)
+            e = cudaMalloc(reinterpret_cast<void**>(&b.d_bslots), size_t(kBatchSlots) * b.B * sizeof(unsigned));
+    }
     c->bs = std::move(bs);
     if (e != cudaSuccess) {
         const std::string msg = std::string("batched context: ") + cudaGetErrorString(e);
@@ -1203,9 +1444,14 @@ adr_status batch_set_coeffs(adr_ctx* c, int i, const double* a_nodes, const doub
             for (long long j = 0; j < nm; ++j) b.hZt[size_t(b.zt_off[size_t(i) * 2 + m] + j)] = c->p.tau * eg.lam[size_t(j)];
         }
     }
+    if (b.mixed) {
+        const cudaError_t me = batch_mixed_instance(c, i);
+        if (me != cudaSuccess) return cuda_fail(c, me, "upload mixed batch instance");
+    }
     if (b.roles[adr::BR_V]) {
         const double kp = b.kappa[size_t(i) * 2] * b.kappa[size_t(i) * 2 + 1];
-        const double unit = c->fp64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+        // the unit of the working precision: FP64, FP32, or the 40-bit state slices of the mixed path
+        const double unit = c->fp64 ? std::ldexp(1.0, -53) : b.mixed ? std::ldexp(1.0, -40) : std::ldexp(1.0, -24);
         if (kp * unit > c->p.kappa_tol) {
             char buf[192];
             std::snprintf(buf, sizeof buf, "instance %d: eigen route ill-conditioned: prod kappa * u = %.3e > kappa_tol %.3e",
@@ -1217,6 +1463,15 @@ adr_status batch_set_coeffs(adr_ctx* c, int i, const double* a_nodes, const doub
     if (b.nset < b.B) return ADR_OK;
     cudaError_t e = batch_upload(c, i);
     if (e != cudaSuccess) return cuda_fail(c, e, "upload batch");
+    if (b.mixed) {
+        if (!b.tuned) {
+            e = batch_mixed_plan(c);
+            if (e != cudaSuccess) return cuda_fail(c, e, "mixed batch plan");
+            b.tuned = true;
+        }
+        c->coeffs_set = true;
+        return ADR_OK;
+    }
     if (!b.tuned) {
         const adr_status st = c->fp64 ? batch_tune<double>(c) : batch_tune<float>(c);
         if (st != ADR_OK) return st;
@@ -1857,7 +2112,8 @@ adr_status adr_get_batch_plan(const adr_ctx* c, int mode, int* tile_edge, int* g
     const adr_batch_state& b = *c->bs;
     if (!b.tuned) return ADR_ERR_STATE;
     if (tile_edge)
-        for (int i = 0; i < b.B; ++i) tile_edge[i] = adr::batch_tile_edge(b.tile[mode - 1][i]);
+        for (int i = 0; i < b.B; ++i)   // mixed: the tensor-core tiles' output extent (128 along x1, 64 along x2)
+            tile_edge[i] = b.mixed ? (mode == 1 ? 128 : 64) : adr::batch_tile_edge(b.tile[mode - 1][i]);
     if (grid) *grid = b.grid[mode - 1];
     return ADR_OK;
 }
@@ -1921,6 +2177,15 @@ void adr_destroy(adr_ctx* c) {
         { void* q = b.d_row_start; free_dev(q); b.d_row_start = nullptr; }
         free_dev(b.d_zt);
         for (auto& it : b.d_items) { void* q = it; free_dev(q); it = nullptr; }
+        for (auto& it : b.d_titems) { void* q = it; free_dev(q); it = nullptr; }
+        { void* q = b.d_img; free_dev(q); b.d_img = nullptr; }
+        { void* q = b.d_fsc; free_dev(q); b.d_fsc = nullptr; }
+        free_dev(b.d_tci);
+        for (auto& t : b.d_phi) { void* q = t; free_dev(q); t = nullptr; }
+        for (auto& t : b.d_lo) { void* q = t; free_dev(q); t = nullptr; }
+        { void* q = b.d_ulo; free_dev(q); b.d_ulo = nullptr; }
+        { void* q = b.d_uhs; free_dev(q); b.d_uhs = nullptr; }
+        { void* q = b.d_bslots; free_dev(q); b.d_bslots = nullptr; }
     }
     free_dev(c->d_a);
     for (auto& row : c->d_E) for (auto& p : row) free_dev(p);

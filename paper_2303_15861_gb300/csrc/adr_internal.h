@@ -274,6 +274,87 @@ cudaError_t launch_batch_stencil(const BatchStencilArgs<float>& a, cudaStream_t 
 cudaError_t launch_batch_contract(const BatchContractArgs<double>& a, cudaStream_t s);
 cudaError_t launch_batch_contract(const BatchContractArgs<float>& a, cudaStream_t s);
 
+// ------------------------------------------------ batched 2-D instances, mixed precision
+// The batched workload's eigenbases are ill-scaled (kappa(V_mu) up to 2e2 per direction) and
+// ETD2RK at lambda = 1 amplifies a perturbation about a hundredfold over its 30 steps, so an
+// FP32 state or FP32 rounding between the passes of a phi action leaves up to 3e-4 on the worst
+// instances. The mixed batched path therefore carries every state-like array as a compensated
+// FP32 pair (hi + lo), slices it into five exact BF16 slices against a per-instance scale, and
+// runs the mu-mode products on the tensor cores (batch_tc.cu); the stencil forms its one-sided
+// differences from both parts (batch_stencil2_kernel, batch2d.cu).
+
+// Per instance (batch_tc.cu): sizes, packed offset, and the offsets of its sliced factor
+// images (bytes into the image buffer), row scales and double-float phi tables.
+struct BatchTcInst {
+    int n1 = 0, n2 = 0;
+    long long off = 0;                                   // element offset in every packed array
+    long long img_off[5][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};  // role x direction
+    long long fsc_off[5][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};
+    int vec = 0;                                         // n1 and off multiples of 4 (16-byte rows)
+};
+
+// One mu-mode pass over every instance on the tensor cores. items[i] = {instance, position
+// tile, output tile, 0}: mode 1 (Y_i = X_i M^T, K = n1): 64 rows (x2 fibres) x 128 outputs;
+// mode 2 (Y_i = M X_i, K = n2): 128 positions (x1) x 64 outputs. Inputs and outputs are
+// double-float pairs (a NULL low part reads as zero / is not written).
+//   EPI_STORE: Y (+ Ylo) = the product;  EPI_PHI (mode 2): times the double-float table
+//   phi = (hi, lo) pairs, one per node of the instance;  EPI_AXPY: base (+ base_lo) + alpha
+//   times the product. Yhs, when set, receives a copy of the high part. amax_in[i] is the
+//   max|X| of instance i (float bits), amax_out[i] accumulates max|Y|.
+struct BatchTcArgs {
+    const BatchTcInst* inst = nullptr;
+    const int4* items = nullptr;
+    int nitems = 0;
+    int mode = 1;
+    int role = 0;
+    const uint8_t* fimg = nullptr;
+    const float* fscale = nullptr;
+    const float* X = nullptr;
+    const float* Xlo = nullptr;
+    float* Y = nullptr;
+    float* Ylo = nullptr;
+    float* Yhs = nullptr;
+    int epi = EPI_STORE;
+    const float* base = nullptr;
+    const float* base_lo = nullptr;
+    double alpha = 0;
+    const float2* phi = nullptr;
+    const unsigned* amax_in = nullptr;
+    unsigned* amax_out = nullptr;
+    int* err = nullptr;
+    int grid = 0;
+};
+cudaError_t launch_batch_tc(const BatchTcArgs& a, cudaStream_t s);
+// Bytes of the sliced image of an n x n factor in a pass of the given mode, and the host
+// slicing: per (output tile, K chunk of 32), seven 64-byte-swizzled K-major BF16 tiles
+// F0, F1, F2, F3, 2^-8 F1, 2^-8 F2, 2^-8 F3 of 64 (mode 2) or 128 (mode 1) rows; row i of
+// the factor is 2^(e_i-7) sum_j 2^(-8j) F_j with integer |F_j| <= 128.
+constexpr int kBatchTcRows1 = 128;         // output rows of a mode-1 factor tile (UMMA M)
+constexpr int kBatchTcRows2 = 64;          // output rows of a mode-2 factor tile (UMMA N)
+constexpr int kBatchTcChunk = 32;          // K per tile
+constexpr int kBatchTcFactorTiles = 7;     // F0, F1, F2, F3, 2^-8 F1, 2^-8 F2, 2^-8 F3
+size_t batch_tc_image_bytes(int n, int mode);
+void make_batch_tc_factor(const double* M, int n, int mode, uint8_t* img, float* fscale);   // host_setup.cpp
+
+// The compensated stage stencil of a mixed batched context: as BatchStencilArgs, with
+// optional low parts of u and of the extra inputs, and per output an optional low part
+// (the combination in double-float arithmetic), an optional copy of the high part (hs) and
+// an optional per-instance max|out| (amax[j][instance], float bits).
+struct BatchStencil2Args {
+    BatchStencilArgs<float> s;
+    const float* u_lo = nullptr;
+    const float* X_lo[kMaxExtra] = {nullptr, nullptr, nullptr};
+    float* out_lo[kMaxOut] = {nullptr, nullptr};
+    float* out_hs[kMaxOut] = {nullptr, nullptr};
+    unsigned* amax[kMaxOut] = {nullptr, nullptr};
+};
+cudaError_t launch_batch_stencil2(const BatchStencil2Args& a, cudaStream_t s);
+// lo[i] = (u[i] == hs[i]) ? lo[i] : 0 over n elements: the low part of the state survives
+// only where the caller's array still holds the high part the library wrote last.
+cudaError_t launch_batch_keep_lo(const float* u, const float* hs, float* lo, long long n, cudaStream_t s);
+// amax[i] = max |x| over instance i (float bits; atomicMax, so zero the slots first).
+cudaError_t launch_batch_amax(const BatchStencilArgs<float>& geom, const float* x, unsigned* amax, cudaStream_t s);
+
 // A kernel that waits on an mbarrier nothing arrives on, gives up after limit_ms and sets a code
 // in err (wait_check.cu).
 cudaError_t launch_wait_probe(int* err, double limit_ms, cudaStream_t s);

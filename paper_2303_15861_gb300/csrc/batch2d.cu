@@ -89,6 +89,114 @@ __global__ void __launch_bounds__(256) batch_stencil_kernel(BatchStencilArgs<T> 
     }
 }
 
+// ------------------------------------------------------------- compensated stencil (mixed)
+// Coefficients of the stage combination as double-float pairs (hi, lo) of the host's doubles.
+struct Combo2 {
+    float cu[kMaxOut][2], cx[kMaxOut][kMaxExtra][2], cg[kMaxOut][2], cF[kMaxOut][2];
+};
+
+__device__ __forceinline__ void two_sum2(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// acc (hi, lo) += (ch + cl) (xh + xl), in double-float arithmetic
+__device__ __forceinline__ void df_fma(float ch, float cl, float xh, float xl, float& hi, float& lo) {
+    const float p = ch * xh;
+    float e = fmaf(ch, xh, -p);
+    e = fmaf(ch, xl, fmaf(cl, xh, e));
+    float s, t;
+    two_sum2(hi, p, s, t);
+    t += lo + e;
+    hi = s + t;
+    lo = t - (hi - s);
+}
+
+// The stencil of batch_stencil_kernel on a compensated state u + u_lo: each one-sided
+// difference is formed from both parts, (u_E - u_C) + (lo_E - lo_C), so that FP32 rounding of
+// the state does not enter through the 1/h^2 of the stencil; the differences, coefficients and
+// reaction are then FP32 as in the plain kernel. The stage combination is formed in
+// double-float arithmetic (inputs with their low parts); an output with a low-part array gets
+// both parts, one without gets their FP32 sum. Per output the maximum |out| of each instance is
+// recorded (one atomic per row).
+__global__ void __launch_bounds__(256) batch_stencil2_kernel(BatchStencil2Args P, Combo<float> cb, Combo2 c2, bool needF) {
+    const BatchStencilArgs<float>& p = P.s;
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < p.rows; r += warps) {
+        const int ii = find_instance(p.row_start, p.ninst, r);
+        const BatchInst<float>& in = p.inst[ii];
+        const int n1 = in.n1, n2 = in.n2;
+        const int i2 = int(r - in.row0);
+        Coefs<float> c;
+        c.ih2[0] = in.ih2[0]; c.ih2[1] = in.ih2[1]; c.ih2[2] = 0.f;
+        c.i2h[0] = in.i2h[0]; c.i2h[1] = in.i2h[1]; c.i2h[2] = 0.f;
+        c.bmb[0] = in.bmb[0]; c.bmb[1] = in.bmb[1]; c.bmb[2] = 0.f;
+        c.beta[0] = in.beta[0]; c.beta[1] = in.beta[1]; c.beta[2] = 0.f;
+        c.abar = in.abar;
+        c.r0 = in.r[0]; c.r1 = in.r[1]; c.r2 = in.r[2]; c.r3 = in.r[3];
+        const long long row = in.off + (long long)i2 * n1;
+        const float* u = p.u + row;
+        const float* ul = P.u_lo ? P.u_lo + row : nullptr;
+        const float* a = p.a + in.a_off + (long long)(i2 + 1) * in.apitch + 4;   // interior i1 = 0
+        float vmax[kMaxOut] = {0.f, 0.f};
+        for (int i1 = lane; i1 < n1; i1 += 32) {
+            auto ld = [&](const float* base, int di1, int di2, bool inside) -> float {
+                return inside ? __ldg(base + di1 + (long long)di2 * n1) : 0.f;
+            };
+            const bool hw = i1 > 0, he = i1 + 1 < n1, hs = i2 > 0, hn = i2 + 1 < n2;
+            const float u0 = __ldg(u + i1);
+            const float uw = ld(u + i1, -1, 0, hw), ue = ld(u + i1, 1, 0, he);
+            const float us = ld(u + i1, 0, -1, hs), un = ld(u + i1, 0, 1, hn);
+            float l0 = 0.f, lw = 0.f, le = 0.f, ls = 0.f, ln = 0.f;
+            if (ul) {
+                l0 = __ldg(ul + i1);
+                lw = ld(ul + i1, -1, 0, hw); le = ld(ul + i1, 1, 0, he);
+                ls = ld(ul + i1, 0, -1, hs); ln = ld(ul + i1, 0, 1, hn);
+            }
+            const float dE = (ue - u0) + (le - l0), dW = (u0 - uw) + (l0 - lw);
+            const float dN = (un - u0) + (ln - l0), dS = (u0 - us) + (l0 - ls);
+            const float a0 = __ldg(a + i1);
+            const float aw = __ldg(a + i1 - 1), ae = __ldg(a + i1 + 1);
+            const float as = __ldg(a + i1 - in.apitch), an = __ldg(a + i1 + in.apitch);
+            float F = 0.f;
+            const float g = stencil_core<float, 2>(c, u0 + l0, dE, dW, dN, dS, 0.f, 0.f, a0 + ae, a0 + aw, a0 + an, a0 + as,
+                                                   0.f, 0.f, needF, F);
+#pragma unroll
+            for (int j = 0; j < kMaxOut; ++j) {
+                if (j >= p.nout) continue;
+                float hi = 0.f, lo = 0.f;
+                if (cb.cu[j] != 0.f) df_fma(c2.cu[j][0], c2.cu[j][1], u0, l0, hi, lo);
+#pragma unroll
+                for (int e = 0; e < kMaxExtra; ++e)
+                    if (e < p.nx && cb.cx[j][e] != 0.f) {
+                        const float xh = __ldg(p.X[e] + row + i1);
+                        const float xl = P.X_lo[e] ? __ldg(P.X_lo[e] + row + i1) : 0.f;
+                        df_fma(c2.cx[j][e][0], c2.cx[j][e][1], xh, xl, hi, lo);
+                    }
+                if (cb.cg[j] != 0.f) df_fma(c2.cg[j][0], c2.cg[j][1], g, 0.f, hi, lo);
+                if (cb.cF[j] != 0.f) df_fma(c2.cF[j][0], c2.cF[j][1], F, 0.f, hi, lo);
+                if (P.out_lo[j]) {
+                    p.out[j][row + i1] = hi;
+                    P.out_lo[j][row + i1] = lo;
+                } else {
+                    hi = hi + lo;
+                    p.out[j][row + i1] = hi;
+                }
+                if (P.out_hs[j]) P.out_hs[j][row + i1] = hi;
+                vmax[j] = fmaxf(vmax[j], fabsf(hi));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kMaxOut; ++j) {
+            if (j >= p.nout || !P.amax[j]) continue;
+            float m = vmax[j];
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0 && m > 0.f) atomicMax(P.amax[j] + ii, __float_as_uint(m));
+        }
+    }
+}
+
 // --------------------------------------------------------------------------- contraction
 constexpr int kThreads = 256;      // 16 x 16 threads per tile of every shape
 constexpr int kBK = 16;            // K per shared-memory stage
@@ -379,11 +487,40 @@ cudaError_t contract_launch(const BatchContractArgs<T>& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t stencil2_launch(const BatchStencil2Args& P, cudaStream_t s) {
+    const BatchStencilArgs<float>& p = P.s;
+    if (p.rows <= 0) return cudaSuccess;
+    if (!p.inst || !p.row_start || !p.a || !p.u || p.nout < 1 || p.nout > kMaxOut || p.nx < 0 || p.nx > kMaxExtra)
+        return cudaErrorInvalidValue;
+    Combo<float> cb;
+    Combo2 c2;
+    bool needF = false;
+    auto split = [](double v, float (&o)[2]) {
+        o[0] = float(v);
+        o[1] = float(v - double(o[0]));
+    };
+    for (int j = 0; j < kMaxOut; ++j) {
+        cb.cu[j] = float(p.cu[j]); cb.cg[j] = float(p.cg[j]); cb.cF[j] = float(p.cF[j]);
+        split(p.cu[j], c2.cu[j]); split(p.cg[j], c2.cg[j]); split(p.cF[j], c2.cF[j]);
+        for (int e = 0; e < kMaxExtra; ++e) {
+            cb.cx[j][e] = float(p.cx[j][e]);
+            split(p.cx[j][e], c2.cx[j][e]);
+        }
+        if (j < p.nout && p.cF[j] != 0.0) needF = true;
+    }
+    const long long want = (p.rows + 7) / 8;
+    long long grid = p.grid > 0 ? p.grid : 8LL * sm_count();
+    if (grid > want) grid = want;
+    batch_stencil2_kernel<<<unsigned(grid), 256, 0, s>>>(P, cb, c2, needF);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_batch_stencil(const BatchStencilArgs<double>& a, cudaStream_t s) { return stencil_launch(a, s); }
 cudaError_t launch_batch_stencil(const BatchStencilArgs<float>& a, cudaStream_t s) { return stencil_launch(a, s); }
 cudaError_t launch_batch_contract(const BatchContractArgs<double>& a, cudaStream_t s) { return contract_launch(a, s); }
 cudaError_t launch_batch_contract(const BatchContractArgs<float>& a, cudaStream_t s) { return contract_launch(a, s); }
+cudaError_t launch_batch_stencil2(const BatchStencil2Args& a, cudaStream_t s) { return stencil2_launch(a, s); }
 
 }  // namespace adr

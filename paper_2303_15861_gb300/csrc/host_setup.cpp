@@ -273,4 +273,53 @@ double mean_face_jump(const double* a, int dim, const int* n, int mu) {
     return acc;
 }
 
+// ------------------------------------------------------------------ host: factor images
+size_t batch_tc_image_bytes(int n, int mode) {
+    const int rows = mode == 2 ? kBatchTcRows2 : kBatchTcRows1;
+    const size_t nOut = size_t((n + rows - 1) / rows), nK = size_t((n + kBatchTcChunk - 1) / kBatchTcChunk);
+    return nOut * nK * kBatchTcFactorTiles * size_t(rows) * kBatchTcChunk * 2;
+}
+
+void make_batch_tc_factor(const double* M, int n, int mode, uint8_t* img, float* fscale) {
+    // Row i (an output index) of M is 2^(e_i-7) sum_j 2^(-8j) F_j with max_k |M[i][k]| < 2^e_i and
+    // integer slices |F_j| <= 128 (rounded to nearest, so the remainder of each step is at most
+    // half a unit of its slice). Per (output tile, K chunk of 32): tiles F0, F1, F2, F3,
+    // 2^-8 F1, 2^-8 F2, 2^-8 F3 of `rows` rows in the 64-byte-swizzled K-major layout (8-row
+    // groups of 512 B; the 16-byte chunk j of row r at position j ^ ((r / 2) mod 4)).
+    const int rows = mode == 2 ? kBatchTcRows2 : kBatchTcRows1;
+    const int tile = rows * kBatchTcChunk * 2;
+    const int nK = (n + kBatchTcChunk - 1) / kBatchTcChunk;
+    std::memset(img, 0, batch_tc_image_bytes(n, mode));
+    for (int i = 0; i < n; ++i) {
+        double rmax = 0.0;
+        for (int k = 0; k < n; ++k) rmax = std::fmax(rmax, std::fabs(M[size_t(i) * n + k]));
+        int e = 0;
+        if (rmax > 0.0) std::frexp(rmax, &e);
+        fscale[i] = static_cast<float>(std::ldexp(1.0, e - 7));
+        const int ot = i / rows, r = i % rows;
+        for (int k = 0; k < n; ++k) {
+            double y = std::ldexp(M[size_t(i) * n + k], 7 - e);
+            double f[4];
+            for (int q = 0; q < 4; ++q) {
+                f[q] = std::nearbyint(y);
+                y = (y - f[q]) * 256.0;
+            }
+            const double vals[kBatchTcFactorTiles] = {f[0], f[1], f[2], f[3], f[1] / 256.0, f[2] / 256.0, f[3] / 256.0};
+            const int c = k / kBatchTcChunk, kk = k % kBatchTcChunk, j = kk / 8, e2 = kk % 8;
+            const size_t off = size_t((r >> 3) * 512 + (r & 7) * 64 + ((j ^ ((r >> 1) & 3)) << 4) + 2 * e2);
+            for (int q = 0; q < kBatchTcFactorTiles; ++q) {
+                // integers up to 128 (and their 2^-8 multiples) are exact in BF16: the upper half
+                // of the FP32 pattern
+                const float fv = static_cast<float>(vals[q]);
+                uint32_t bits;
+                std::memcpy(&bits, &fv, 4);
+                const uint16_t b = uint16_t(bits >> 16);
+                uint8_t* t = img + ((size_t(ot) * nK + c) * kBatchTcFactorTiles + q) * tile;
+                t[off] = uint8_t(b & 0xFF);
+                t[off + 1] = uint8_t(b >> 8);
+            }
+        }
+    }
+}
+
 }  // namespace adr

@@ -208,47 +208,153 @@ def test_batch_coefficient_update_of_one_instance():
         assert_parity(got, ref, 1e-12, what=w.name)
 
 
-def test_batched_workload_512_instances_sampled_against_oracle():
-    """The full batched workload (512 instances, n in {48, ..., 256}, ETD2RK, 30 steps, FP32):
-    one graph-replayed integration, then the oracle on sampled instances, including the
-    most ill-conditioned eigenbases of the draw (prod kappa up to 1e7, hence kappa_tol = 1)."""
-    ws = W.config4()
+# ------------------------------------------------ mixed precision (tensor cores, compensated state)
+# The mixed batched path carries every state-like array as an FP32 pair (hi + lo), slices it
+# into five exact BF16 slices per instance and runs the mu-mode products on the tensor cores
+# (csrc/batch_tc.cu); the stencil forms its differences from both parts. Tolerance 1e-5
+# against the FP64 oracle for whole runs (the batched workload's), element by element.
+
+@pytest.mark.parametrize("scheme", ["etd2rk", "lawson4", "lawson_euler", "exponential_euler", "erk2p1",
+                                    "stabilized_lawson_euler", "lawson2a", "lawson2b", "stabilized_lawson2"])
+def test_batch_mixed_schemes_match_oracle(scheme):
+    ws = W.batch_instances(SIZES, scheme=scheme)
+    m = 8
+    ctx = batch_context(ws, "bf16x3", scheme)
+    full, u = packed(ws, "fp32")
+    ctx.integrate(u, 0.0, m * ws[0].tau, m)
+    ctx.synchronize()
+    check_guards(full)
+    for w, got in zip(ws, unpack(ws, u)):
+        ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, m, scheme)
+        assert_parity(got, ref, 1e-5, what=(scheme, w.name))
+
+
+def test_batch_mixed_building_blocks_match_oracle():
+    """F, g and the actions of e^{tau A/2}-free schemes' phi_0, phi_1, phi_2 for every instance in
+    one call each, on caller arrays (FP32 in, FP32 out: no low parts)."""
+    ws = W.batch_instances(SIZES, scheme="etd2rk")
+    ctx = batch_context(ws, "bf16x3", "etd2rk")
+    rng = np.random.default_rng(11)
+    vs = [rng.standard_normal(w.dims[::-1]) for w in ws]
+    _, u = packed(ws, "fp32")
+    fF, F = packed(ws, "fp32", [np.zeros(w.dims[::-1]) for w in ws])
+    fg, g = packed(ws, "fp32", [np.zeros(w.dims[::-1]) for w in ws])
+    ctx.eval_rhs(u, F, g)
+    _, v = packed(ws, "fp32", vs)
+    ys = {}
+    for k in (0, 1, 2):
+        fy, y = packed(ws, "fp32", [np.zeros(w.dims[::-1]) for w in ws])
+        ctx.apply_phi(k, v, y)
+        ys[k] = (fy, y)
+    ctx.synchronize()
+    for full in (fF, fg) + tuple(f for f, _ in ys.values()):
+        check_guards(full)
+    Fs, gs, us, vin = unpack(ws, F), unpack(ws, g), unpack(ws, u), unpack(ws, v)
+    for i, w in enumerate(ws):
+        prob = O.ADRProblem(w.dims, w.a_nodes, w.b, w.r_poly)
+        assert_parity(Fs[i], prob.F(us[i]), 2e-6, what=("F", w.name))
+        assert_parity(gs[i], prob.g(us[i]), 2e-6, what=("g", w.name))
+        mf = O.MatrixFunctions(prob, w.tau)
+        for k, (_, y) in ys.items():
+            ref = mf.exp_action(1.0, vin[i]) if k == 0 else mf.phi_action(k, 1.0, vin[i])
+            assert_parity(unpack(ws, y)[i], ref, 1e-6, what=(w.name, k))
+
+
+def test_batch_mixed_graph_replay_equals_direct_steps():
+    """adr_integrate (graph replay) and single adr_step calls give identical bits; the low part of
+    the state is carried from step to step in both."""
+    ws = W.batch_instances(SIZES, scheme="etd2rk")
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
-        ctx = batch_context(ws, "fp32", "etd2rk", stream=s, kappa_tol=1.0)
+        ctx = batch_context(ws, "bf16x3", "etd2rk", stream=s)
+        _, u1 = packed(ws, "fp32")
+        _, u2 = packed(ws, "fp32")
+        ctx.integrate(u1, 0.0, 5 * ws[0].tau, 5)
+        for i in range(5):
+            ctx.step(u2, i * ws[0].tau)
+        ctx.synchronize()
+    assert torch.equal(u1, u2)
+
+
+def test_batch_mixed_low_part_follows_the_callers_array():
+    """The library keeps the state's low part only where the caller's array still holds the high
+    part the library wrote last: integrating 3 + 3 steps equals 6 steps at once (the low part is
+    carried across the calls), and after the caller overwrites the state, the next run equals a
+    run from a fresh context (the stale low part is dropped)."""
+    ws = W.batch_instances(SIZES[:4], scheme="etd2rk")
+    tau = ws[0].tau
+    ctx = batch_context(ws, "bf16x3", "etd2rk")
+    _, u = packed(ws, "fp32")
+    ctx.integrate(u, 0.0, 3 * tau, 3)
+    ctx.integrate(u, 3 * tau, 6 * tau, 3)
+    ctx.synchronize()
+    fresh = batch_context(ws, "bf16x3", "etd2rk")
+    _, v = packed(ws, "fp32")
+    fresh.integrate(v, 0.0, 6 * tau, 6)
+    fresh.synchronize()
+    assert torch.equal(u, v)
+    _, w0 = packed(ws, "fp32")
+    u.copy_(w0)                                  # the caller restarts from the initial state
+    ctx.integrate(u, 0.0, 2 * tau, 2)
+    fresh2 = batch_context(ws, "bf16x3", "etd2rk")
+    _, v2 = packed(ws, "fp32")
+    fresh2.integrate(v2, 0.0, 2 * tau, 2)
+    ctx.synchronize()
+    fresh2.synchronize()
+    assert torch.equal(u, v2)
+
+
+def test_batch_mixed_integrate_host_equals_device():
+    ws = W.batch_instances(SIZES[:3], scheme="etd2rk")
+    ctx = batch_context(ws, "bf16x3", "etd2rk")
+    _, u = packed(ws, "fp32")
+    host = u.cpu().pin_memory()
+    ctx.integrate(u, 0.0, 2 * ws[0].tau, 2)
+    ctx.integrate_host(host, 0.0, 2 * ws[0].tau, 2)
+    ctx.synchronize()
+    assert torch.equal(u.cpu(), host)
+
+
+def test_batch_mixed_refuses_instances_beyond_256():
+    with pytest.raises(adr.AdrError) as e:
+        adr.Context(None, 1e-3, "etd2rk", "bf16x3", batch_dims=[(64, 64), (257, 64)])
+    assert e.value.status == 1
+
+
+_WORKLOAD = {}
+
+
+def workload_oracle():
+    """The FP64 oracle's solution of every instance of the batched workload (about 100 s on
+    the host), computed once per session."""
+    if not _WORKLOAD:
+        ws = W.config4()
+        _WORKLOAD["ws"] = ws
+        _WORKLOAD["ref"] = [O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, w.m, "etd2rk") for w in ws]
+    return _WORKLOAD["ws"], _WORKLOAD["ref"]
+
+
+def test_batched_workload_every_instance_against_the_oracle():
+    """The full batched workload (512 instances, n in {48, ..., 256}, ETD2RK, 30 steps) in the
+    launch configuration the benchmark times (mixed precision, graph-replayed), every instance
+    against the FP64 oracle at the workload's 1e-5, element by element. The draw holds the
+    most ill-conditioned eigenbases of the workload (prod kappa up to 1e7, hence kappa_tol = 1),
+    and 12 instances (c >= 0.77, b near 20) on which ETD2RK at lambda = 1 amplifies any
+    perturbation about a hundredfold over the 30 steps: there a plain FP32 state ends at up to
+    3.4e-4, which is why this path carries the state and the phi intermediates as pairs."""
+    ws, refs = workload_oracle()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx = batch_context(ws, "bf16x3", "etd2rk", stream=s, kappa_tol=1.0)
         full, u = packed(ws, "fp32")
         ctx.integrate(u, 0.0, ws[0].m * ws[0].tau, ws[0].m)
         ctx.synchronize()
     check_guards(full)
     res = unpack(ws, u)
-    for i in (0, 1, 31, 146, 255, 349, 448, 511):
-        w = ws[i]
-        ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, w.m, "etd2rk")
-        assert_parity(res[i], ref, 1e-5, what=(i, w.dims))
-
-
-def test_batched_workload_every_instance_against_the_fp64_batch():
-    """All 512 instances of the batched workload, FP32 against the same batch in FP64 (whose
-    parity with the oracle the tests above check). 500 of them stay within 1e-5. The other 12
-    have c >= 0.77 (a down to 0.1 against a_max = 1.9) and b near 20. There ETD2RK at lambda = 1
-    amplifies any perturbation about a hundredfold over the 30 steps: in the FP64 oracle a
-    relative 1e-7 change of u0 grows to 9.4e-6 on instance 314, and rounding the state to FP32
-    after every step leaves 1.2e-5. The FP32 eigenbasis route (prod kappa up to 3e4 on those
-    instances) adds its kappa-amplified rounding before the amplification, so the worst
-    instance ends at 3.4e-4. Bound: at most 16 instances above 1e-5, every instance below 1e-3."""
-    ws = W.config4()
-    m = ws[0].m
-    out = {}
-    s = torch.cuda.Stream()
-    with torch.cuda.stream(s):
-        for prec in ("fp32", "fp64"):
-            ctx = batch_context(ws, prec, "etd2rk", stream=s, kappa_tol=1.0)
-            _, u = packed(ws, prec)
-            ctx.integrate(u, 0.0, m * ws[0].tau, m)
-            ctx.synchronize()
-            out[prec] = unpack(ws, u)
-    errs = np.array([O.rel_l2(a, b) for a, b in zip(out["fp32"], out["fp64"])])
-    over = np.flatnonzero(errs > 1e-5)
-    print(f"instances over 1e-5: {over.tolist()}, max {errs.max():.3e}")
-    assert len(over) <= 16 and errs.max() < 1e-3
-    assert all(ws[i].extra["c"] > 0.7 for i in over), [(int(i), ws[i].extra) for i in over]
+    errs = []
+    for i, (w, got, ref) in enumerate(zip(ws, res, refs)):
+        errs.append(assert_parity(got, ref, 1e-5, what=(i, w.dims, w.extra["c"]))[0])
+    errs = np.array(errs)
+    worst = int(np.argmax(errs))
+    print(f"batched workload, mixed: max rel l2 vs oracle {errs.max():.3e} (instance {worst}), "
+          f"median {np.median(errs):.3e}")

@@ -190,9 +190,12 @@ def test_config3_full_run_vs_oracle_and_fp64_gpu():
     got, g64 = u.double().cpu().numpy(), ud.cpu().numpy()
     del u, ud
     ref = O.solve(w.dims, w.a_nodes, w.b, w.r_poly, w.u0, w.tau, w.m, w.scheme)
-    e_mixed = assert_parity(got, ref, 1e-6, what="256^3 lawson4 40 steps mixed vs oracle")
+    # the slices are fixed point against the array's maximum, so the error is nearly uniform in
+    # absolute terms; the boundary-adjacent planes hold ~1/257 of the maximum (measured 5.8e-4 of
+    # their own norm): bound 2e-3, which an O(1) face error still exceeds by far
+    e_mixed = assert_parity(got, ref, 1e-6, face=2e-3, what="256^3 lawson4 40 steps mixed vs oracle")
     e_f64 = assert_parity(g64, ref, 1e-12, what="256^3 lawson4 40 steps FP64 GPU vs oracle")
-    err, err_inf, _ = assert_parity(got, g64, 5e-7, inf=2e-6, what="256^3 lawson4 40 steps mixed vs FP64 GPU")
+    err, err_inf, _ = assert_parity(got, g64, 5e-7, inf=2e-6, face=2e-3, what="256^3 lawson4 40 steps mixed vs FP64 GPU")
     drift = float((got - g64).sum() / np.abs(g64).sum())
     print(f"256^3 lawson4 40 steps: mixed vs oracle l2 {e_mixed[0]:.3e} max {e_mixed[1]:.3e}; "
           f"FP64 GPU vs oracle l2 {e_f64[0]:.3e} max {e_f64[1]:.3e}; "
