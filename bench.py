@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--m", type=int, default=40)
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison run")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--no-batch", action="store_true", help="default workload: skip the batched workload's summary")
     p.add_argument("--workload", choices=["3d", "batch2d"] + sorted(GRID_WORKLOADS), default="3d",
                    help="3d: the 256^3 Lawson4 workload (default); batch2d: 512 uneven 2-D ETD2RK instances; "
                         "c1-*, c2, c5-*, e1-*, e2-*, e3-*, e4-*: the other single-grid workloads")
@@ -388,6 +389,20 @@ def ours(args):
         "kernel_ms_per_time_step": {str(k): v for k, v in step_kernel_ms.items()},
     }
     line.update(acc)
+    if world == 1 and not args.no_batch:
+        # the batched workload (512 uneven 2-D ETD2RK instances, mixed precision) on the same GPU,
+        # so that every default run records it: throughput, its roofline and its error count
+        bargs = argparse.Namespace(**vars(args))
+        bargs.precision, bargs.steps, bargs.warmup, bargs.ncu_steps = "bf16x3", 5, 3, 0
+        b = ours_batch(bargs, embedded=True)
+        line["batch2d"] = {k: b.get(k) for k in ("metric", "value", "unit", "ms_per_step", "dtype", "e2e",
+                                                 "gpu_launches", "rel_l2_vs_fp64_gpu_max", "instances_checked",
+                                                 "instances_over_1e-5", "setup_s")}
+        line["batch2d"]["config"] = {"workload": b["config"]["workload"], "instances": b["config"]["instances"],
+                                     "dof": b["config"]["dof"], "steps": 5, "warmup": 3}
+        line["batch2d"]["roofline"] = {k: b["roofline"].get(k) for k in ("bound", "achieved", "peak", "unit", "frac",
+                                                                          "issued_frac", "kernel", "launch_ms")}
+        line["batch2d"]["clocks"] = b["clocks"]
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -650,21 +665,26 @@ def reference_batch(args):
     return 0
 
 
-def ours_batch(args):
+def ours_batch(args, embedded=False):
+    """The batched workload. embedded: one GPU, library already loaded, no CPU baseline; the
+    JSON line is returned instead of printed (the default benchmark line carries it)."""
     import numpy as np
     import torch
     from paper_2303_15861_gb300 import adr, build_lib, ranks, workloads as W
 
     rank, world, local = ranks.rank_env()
+    if embedded:
+        rank, world, local = 0, 1, torch.cuda.current_device()
     dist = None
     if world > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
+    elif not embedded:
         torch.cuda.set_device(0)
-    build_lib.build()
-    adr.load_library()
+    if not embedded:
+        build_lib.build()
+        adr.load_library()
     prec = args.precision                 # bf16x3 (default): compensated pairs, tensor-core contractions
     dt = torch.float64 if prec == "fp64" else torch.float32
     # weak scaling: a draw of 512 instances per rank; rank r advances its own block of them
@@ -783,7 +803,7 @@ def ours_batch(args):
                 "launch_ms": c_ms, "stencil_launch_ms": statistics.mean(kinds.get(2, [float("nan")])),
                 "peak_source": src}
     cpu = None
-    if not args.no_cpu:
+    if not args.no_cpu and not embedded:
         t_cpu, d_cpu = batch_oracle_sample(ws, stride=1)
         cpu = {"value": d_cpu / t_cpu, "unit": UNIT, "cores": _CORES, "kind": "oracle",
                "sample": f"one ETD2RK step of all 512 instances ({t_cpu:.1f} s)"}
@@ -804,6 +824,8 @@ def ours_batch(args):
         "kernel_ms_per_time_step": {str(k): sum(v) / 3.0 for k, v in kinds.items()},
     }
     line.update(acc)
+    if embedded:
+        return line
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -28,6 +28,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/adr.h"
 #include "adr_internal.h"
 
@@ -908,11 +910,34 @@ std::vector<Op> step_ops(const adr_ctx* c, void* u) {
     return c->fp64 ? build_step<double>(c, static_cast<double*>(u)) : build_step<float>(c, static_cast<float*>(u));
 }
 
-adr_status run_ops(adr_ctx* c, const std::vector<Op>& ops, const char* where) {
-    for (const auto& op : ops) {
-        cudaError_t e = op(c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, where);
+// NVTX range names of the op kinds (a profiler attributes the kernels an op launches to its range).
+const char* op_name(int kind) {
+    switch (kind) {
+    case OP_MEMSET: return "max-abs slots: clear";
+    case OP_AMAX: return "max-abs / low-part check";
+    case OP_STENCIL: return "K1 stencil + stage combination";
+    case OP_CONTRACT_SIMT: return "K2 mu-mode pass (FMA)";
+    case OP_CONTRACT_TC: return "K2 mu-mode pass (tensor cores)";
+    case OP_CONTRACT_TC_PRECISE: return "K2 mu-mode pass (tensor cores, double-float)";
+    case OP_PERIODIC_RHS: return "periodic right-hand side (Fourier passes)";
+    case OP_FOURIER_MULT: return "Fourier multiplier";
+    default: return "op";
     }
+}
+
+// Enqueue ops directly (not under capture), each inside an NVTX range, the whole in one.
+adr_status run_ops(adr_ctx* c, const std::vector<Op>& ops, const char* where) {
+    nvtxRangePushA(where);
+    for (const auto& op : ops) {
+        nvtxRangePushA(op_name(op.kind));
+        cudaError_t e = op(c->stream);
+        nvtxRangePop();
+        if (e != cudaSuccess) {
+            nvtxRangePop();
+            return cuda_fail(c, e, where);
+        }
+    }
+    nvtxRangePop();
     return ADR_OK;
 }
 
@@ -1950,12 +1975,17 @@ adr_status adr_integrate(adr_ctx* c, void* u, double t0, double T, int m) {
         if (st != ADR_OK) return st;
         c->graph_u = u;
     }
+    nvtxRangePushA("adr_integrate: graph replays");
     for (int left = m; left > 0;) {
         const bool many = left >= kGraphSteps;
         cudaError_t e = cudaGraphLaunch(many ? c->gexec_k : c->gexec, c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+        if (e != cudaSuccess) {
+            nvtxRangePop();
+            return cuda_fail(c, e, "graph launch");
+        }
         left -= many ? kGraphSteps : 1;
     }
+    nvtxRangePop();
     return ADR_OK;
 }
 
