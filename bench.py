@@ -57,6 +57,8 @@ def parse():
                         "c1-*, c2, c5-*, e1-*, e2-*, e3-*, e4-*: the other single-grid workloads")
     p.add_argument("--check", action="store_true",
                    help="single-grid workloads: also measure the error (oracle for c1/c2, FP64 GPU at tau/4 for c5)")
+    p.add_argument("--window", action="store_true",
+                   help="c5-*: step-by-step errors (mixed vs FP64 at tau/4 and at tau) while max|u| >= 1e-2")
     p.add_argument("--ncu-steps", type=int, default=0,
                    help="profiling mode: run this many untimed time steps (adr_step) and exit")
     return p.parse_args()
@@ -832,8 +834,68 @@ def ours_batch(args, embedded=False):
     return 0
 
 
+def c5_window(args):
+    """The 384^3, b = 50 workloads while the solution is still in the box: with advection 50
+    across the unit cube and Dirichlet faces, max|u| drops below 1e-2 within a few steps of
+    tau = 5e-3, after which a relative error divides by a vanishing norm. Step by step, the
+    mixed path (tau), the FP64 GPU path (tau) and the FP64 GPU path at tau/4 (four steps per
+    step) advance the same initial state; printed per step: max|u| and the relative l2 and
+    maximum-norm errors of mixed vs FP64 at tau/4 (the workload's reference), of mixed vs FP64
+    at tau (the precision's own error) and of FP64 at tau vs tau/4 (the time discretisation)."""
+    import torch
+    from paper_2303_15861_gb300 import adr, build_lib, workloads as W
+
+    torch.cuda.set_device(0)
+    build_lib.build()
+    adr.load_library()
+    make, _ = GRID_WORKLOADS[args.workload]
+    w = make(W)
+    stream = torch.cuda.Stream()
+    rows = []
+    with torch.cuda.stream(stream):
+        ctxs = {}
+        for name, prec, tau in (("mixed", "bf16x3", w.tau), ("fp64", "fp64", w.tau), ("fp64_q", "fp64", w.tau / 4)):
+            ctxs[name] = adr.Context(w.dims, tau, w.scheme, prec, stream=stream)
+            ctxs[name].set_coeffs(w.a_nodes, w.b, w.r_poly)
+        u = {"mixed": torch.tensor(w.u0, dtype=torch.float32, device="cuda"),
+             "fp64": torch.tensor(w.u0, dtype=torch.float64, device="cuda"),
+             "fp64_q": torch.tensor(w.u0, dtype=torch.float64, device="cuda")}
+
+        def err(x, ref):
+            d = x.double() - ref
+            return float(d.norm() / ref.norm()), float(d.abs().max() / ref.abs().max())
+
+        for k in range(1, w.m + 1):
+            ctxs["mixed"].step(u["mixed"], (k - 1) * w.tau)
+            ctxs["fp64"].step(u["fp64"], (k - 1) * w.tau)
+            for q in range(4):
+                ctxs["fp64_q"].step(u["fp64_q"], (k - 1) * w.tau + q * w.tau / 4)
+            for c in ctxs.values():
+                c.synchronize()
+            umax = float(u["fp64_q"].abs().max())
+            e_ref, e_prec, e_time = err(u["mixed"], u["fp64_q"]), err(u["mixed"], u["fp64"]), err(u["fp64"], u["fp64_q"])
+            rows.append({"step": k, "t": k * w.tau, "max_abs_u": umax,
+                         "mixed_vs_fp64_tau4": {"rel_l2": e_ref[0], "rel_inf": e_ref[1]},
+                         "mixed_vs_fp64_tau": {"rel_l2": e_prec[0], "rel_inf": e_prec[1]},
+                         "fp64_tau_vs_tau4": {"rel_l2": e_time[0], "rel_inf": e_time[1]}})
+            if umax < 1e-2:
+                break
+        for c in ctxs.values():
+            c.close()
+    in_window = [r for r in rows if r["max_abs_u"] >= 1e-2]
+    line = {"metric": f"error window, {args.workload}", "workload": w.name, "grid": list(w.dims), "scheme": w.scheme,
+            "tau": w.tau, "window": "steps with max|u| >= 1e-2 (FP64 at tau/4)", "steps_in_window": len(in_window),
+            "max_mixed_vs_fp64_tau4_rel_l2": max((r["mixed_vs_fp64_tau4"]["rel_l2"] for r in in_window), default=None),
+            "max_mixed_vs_fp64_tau_rel_l2": max((r["mixed_vs_fp64_tau"]["rel_l2"] for r in in_window), default=None),
+            "steps": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.window:
+        return c5_window(args)
     if args.workload == "batch2d":
         return reference_batch(args) if args.impl == "reference" else ours_batch(args)
     if args.workload in GRID_WORKLOADS:

@@ -50,7 +50,6 @@ constexpr int kFS = 7;                  // factor slice tiles: F0..F3, 2^-8 F1..
 static_assert(kM == kBatchTcRows1 && kN == kBatchTcRows2 && kKc == kBatchTcChunk && kFS == kBatchTcFactorTiles,
               "the host slicing (host_setup.cpp) writes the tiles this kernel reads");
 constexpr int kNacc = 4;
-constexpr int kStages = 2;
 constexpr int kProducerWarps = 8;
 constexpr int kEpiWarp0 = 8;
 constexpr int kMmaWarp = 12;
@@ -68,7 +67,8 @@ struct BCfg {
     static constexpr int SBYTES = kSS * STILE;
     static constexpr int FBYTES = kFS * FTILE;
     static constexpr int STAGE = SBYTES + FBYTES;
-    static constexpr int SMEM = kStages * STAGE + 1024;
+    static constexpr int NST = SA ? 3 : 2;         // pipeline stages (as many as shared memory holds)
+    static constexpr int SMEM = NST * STAGE + 1024;
     static constexpr int NV = SROWS * kKc / (kProducerWarps * 32);   // values per producer thread
     static_assert(SMEM <= 227 * 1024, "shared memory budget");
 };
@@ -245,6 +245,7 @@ template <bool SA, int EPI>
 __global__ void __launch_bounds__(kThreads, 1) batch_tc_kernel(const __grid_constant__ BatchTcArgs p) {
     using C = BCfg<SA>;
     extern __shared__ uint8_t smem_raw[];
+    constexpr int kStages = C::NST;
     __shared__ __align__(8) uint64_t bars[2 * kStages + 4 + 1];
     __shared__ uint32_t tmem_base_s;
     __shared__ volatile int abort_s;
@@ -285,40 +286,66 @@ __global__ void __launch_bounds__(kThreads, 1) batch_tc_kernel(const __grid_cons
 
     if (warp < kProducerWarps) {
         // ------------------------------------------------------------ producers
+        // The chunks of this CTA's tiles in order; the global loads of the next chunk are issued
+        // before the current one is sliced, so their latency overlaps the slicing.
         const int t = threadIdx.x;
-        long long g = 0;
-        bool ok = true;
-        for (int tile = blockIdx.x; tile < p.nitems && ok; tile += gridDim.x) {
-            const int4 item = __ldg(p.items + tile);
-            const BatchTcInst& in = p.inst[item.x];
-            const int K = SA ? in.n2 : in.n1;
-            const int nK = (K + kKc - 1) / kKc;
-            const float sc = ldexpf(1.f, 7 - input_exponent(p.amax_in, item.x));
-            const uint8_t* img = p.fimg + in.img_off[p.role][dir] + size_t(item.z) * nK * C::FBYTES;
-            for (int c = 0; c < nK; ++c, ++g) {
-                const int s = int(g % kStages);
-                const uint32_t ph = uint32_t(g / kStages) & 1u;
-                if (!mbar_wait(empty_bar(s), ph ^ 1u, p.err, 1, &abort_s, 64)) { ok = false; break; }
-                const uint32_t sA = sbase + s * C::STAGE;
-                if (t == 0) {
-                    mbar_arrive_expect_tx(full_bar(s), C::FBYTES);
-                    const uint8_t* src = img + size_t(c) * C::FBYTES;
+        struct Job {
+            int tile = 0, c = 0, nK = 0;
+            int4 item;
+            const BatchTcInst* in = nullptr;
+            float sc = 0.f;
+            const uint8_t* img = nullptr;
+        };
+        auto start = [&](int tile, Job& j) {
+            j.tile = tile;
+            j.c = 0;
+            if (tile >= p.nitems) return;
+            j.item = __ldg(p.items + tile);
+            j.in = p.inst + j.item.x;
+            j.nK = ((SA ? j.in->n2 : j.in->n1) + kKc - 1) / kKc;
+            j.sc = ldexpf(1.f, 7 - input_exponent(p.amax_in, j.item.x));
+            j.img = p.fimg + j.in->img_off[p.role][dir] + size_t(j.item.z) * j.nK * C::FBYTES;
+        };
+        auto next = [&](const Job& j, Job& n) {
+            if (j.c + 1 < j.nK) { n = j; n.c = j.c + 1; }
+            else start(j.tile + int(gridDim.x), n);
+        };
+        // one chunk: wait for its stage, start its factor copy, prefetch the next chunk, slice
+        auto step = [&](const Job& j, long long g, const float (&v)[C::NV], const float (&vl)[C::NV], const Job& nj,
+                        float (&nv)[C::NV], float (&nvl)[C::NV]) -> bool {
+            const int s = int(g % kStages);
+            const uint32_t ph = uint32_t(g / kStages) & 1u;
+            if (!mbar_wait(empty_bar(s), ph ^ 1u, p.err, 1, &abort_s, 64)) return false;
+            const uint32_t sA = sbase + s * C::STAGE;
+            if (t == 0) {
+                mbar_arrive_expect_tx(full_bar(s), C::FBYTES);
+                const uint8_t* src = j.img + size_t(j.c) * C::FBYTES;
 #pragma unroll
-                    for (int q = 0; q < kFS; ++q)
-                        bulk_g2s(sA + C::SBYTES + q * C::FTILE, src + q * C::FTILE, C::FTILE, full_bar(s));
-                }
-                float v[C::NV], vl[C::NV];
-                load_chunk<SA>(p, in, item.y, c, t, v, vl);
-                if (SA) {
-                    const int row = t & (kM - 1), part = t >> 7;
-                    slice_store8(v, vl, sc, sA, C::STILE, row, 2 * part);
-                    slice_store8(v + 8, vl + 8, sc, sA, C::STILE, row, 2 * part + 1);
-                } else {
-                    slice_store8(v, vl, sc, sA, C::STILE, t >> 2, t & 3);
-                }
-                fence_proxy_async();
-                mbar_arrive(full_bar(s));
+                for (int q = 0; q < kFS; ++q)
+                    bulk_g2s(sA + C::SBYTES + q * C::FTILE, src + q * C::FTILE, C::FTILE, full_bar(s));
             }
+            if (nj.tile < p.nitems) load_chunk<SA>(p, *nj.in, nj.item.y, nj.c, t, nv, nvl);
+            if (SA) {
+                const int row = t & (kM - 1), part = t >> 7;
+                slice_store8(v, vl, j.sc, sA, C::STILE, row, 2 * part);
+                slice_store8(v + 8, vl + 8, j.sc, sA, C::STILE, row, 2 * part + 1);
+            } else {
+                slice_store8(v, vl, j.sc, sA, C::STILE, t >> 2, t & 3);
+            }
+            fence_proxy_async();
+            mbar_arrive(full_bar(s));
+            return true;
+        };
+        Job a, b;
+        start(blockIdx.x, a);
+        float va[C::NV], vla[C::NV], vb[C::NV], vlb[C::NV];
+        if (a.tile < p.nitems) load_chunk<SA>(p, *a.in, a.item.y, a.c, t, va, vla);
+        for (long long g = 0; a.tile < p.nitems; g += 2) {
+            next(a, b);
+            if (!step(a, g, va, vla, b, vb, vlb)) break;
+            if (b.tile >= p.nitems) break;
+            next(b, a);
+            if (!step(b, g + 1, vb, vlb, a, va, vla)) break;
         }
     } else if (warp < kEpiWarp0 + 4) {
         // ------------------------------------------------------------ epilogue
