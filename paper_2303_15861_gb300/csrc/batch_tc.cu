@@ -387,43 +387,63 @@ __global__ void __launch_bounds__(kThreads, 1) batch_tc_kernel(const __grid_cons
             }
             float vmax = 0.f;
             const uint32_t tbase = tmem + (uint32_t(ew * 32) << 16) + uint32_t(a) * uint32_t(kNacc * kN);
+            // the global operands of the next 8 columns (column scales, the phi table or the axpy
+            // base) are loaded while the current ones are combined
+            auto load_ops = [&](int j0, float (&sc)[8], float2 (&op)[8]) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const bool ok = rvalid && j0 + j < ncol;
+                    const long long o = off0 + (long long)(j0 + j) * cstep;
+                    sc[j] = SA ? (ok ? sback * __ldg(fsc + col0 + j0 + j) : 0.f) : rscale;
+                    if (EPI == EPI_PHI) op[j] = ok ? __ldg(p.phi + o) : make_float2(0.f, 0.f);
+                    else if (EPI == EPI_AXPY)
+                        op[j] = make_float2(ok ? __ldg(p.base + o) : 0.f, (ok && p.base_lo) ? __ldg(p.base_lo + o) : 0.f);
+                    else op[j] = make_float2(0.f, 0.f);
+                }
+            };
+            float sc_c[8], sc_n[8];
+            float2 op_c[8], op_n[8];
+            load_ops(0, sc_c, op_c);
 #pragma unroll 1
             for (int j0 = 0; j0 < kN; j0 += 8) {
                 float d[4][8];
+                if (j0 + 8 < kN) load_ops(j0 + 8, sc_n, op_n);
                 __syncwarp();
                 tmem_ld8x4(tbase + j0, d);
-                if (!rvalid || j0 >= ncol) continue;
+                if (rvalid && j0 < ncol) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (j0 + j >= ncol) break;
+                        // D0 + 2^-8 D1 + 2^-16 D2 + 2^-24 D3 in double-float arithmetic
+                        float hi, lo;
+                        two_sum(d[0][j], d[1][j] * 0.00390625f, hi, lo);
+                        lo += fmaf(d[3][j], 5.9604644775390625e-08f, d[2][j] * 1.52587890625e-05f);
+                        quick_two_sum(hi, lo, hi, lo);
+                        hi *= sc_c[j];                 // a power of two: exact
+                        lo *= sc_c[j];
+                        const long long o = off0 + (long long)(j0 + j) * cstep;
+                        if (EPI == EPI_PHI) {
+                            df_mul(hi, lo, op_c[j].x, op_c[j].y, hi, lo);
+                        } else if (EPI == EPI_AXPY) {
+                            float th, tl2;
+                            df_mul(ah, al, hi, lo, th, tl2);
+                            df_add(op_c[j].x, op_c[j].y, th, tl2, hi, lo);
+                        }
+                        if (p.Ylo) {
+                            p.Y[o] = hi;
+                            p.Ylo[o] = lo;
+                        } else {
+                            hi = hi + lo;
+                            p.Y[o] = hi;
+                        }
+                        if (p.Yhs) p.Yhs[o] = hi;
+                        vmax = fmaxf(vmax, fabsf(hi));
+                    }
+                }
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    if (j0 + j >= ncol) break;
-                    // D0 + 2^-8 D1 + 2^-16 D2 + 2^-24 D3 in double-float arithmetic
-                    float hi, lo;
-                    two_sum(d[0][j], d[1][j] * 0.00390625f, hi, lo);
-                    lo += fmaf(d[3][j], 5.9604644775390625e-08f, d[2][j] * 1.52587890625e-05f);
-                    quick_two_sum(hi, lo, hi, lo);
-                    const float scale = SA ? sback * __ldg(fsc + col0 + j0 + j) : rscale;   // a power of two
-                    hi *= scale;
-                    lo *= scale;
-                    const long long o = off0 + (long long)(j0 + j) * cstep;
-                    if (EPI == EPI_PHI) {
-                        const float2 f = __ldg(p.phi + o);
-                        df_mul(hi, lo, f.x, f.y, hi, lo);
-                    } else if (EPI == EPI_AXPY) {
-                        float th, tl2;
-                        df_mul(ah, al, hi, lo, th, tl2);
-                        const float bh = __ldg(p.base + o);
-                        const float bl = p.base_lo ? __ldg(p.base_lo + o) : 0.f;
-                        df_add(bh, bl, th, tl2, hi, lo);
-                    }
-                    if (p.Ylo) {
-                        p.Y[o] = hi;
-                        p.Ylo[o] = lo;
-                    } else {
-                        hi = hi + lo;
-                        p.Y[o] = hi;
-                    }
-                    if (p.Yhs) p.Yhs[o] = hi;
-                    vmax = fmaxf(vmax, fabsf(hi));
+                    sc_c[j] = sc_n[j];
+                    op_c[j] = op_n[j];
                 }
             }
             tc_fence_before();

@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
             float* ylo = (EPI == EPI_STORE2) ? p.Ylo + off0 : nullptr;
             const float* brow = (EPI == EPI_AXPY) ? p.base + off0 : nullptr;
             const uint32_t tbase = tmem + (uint32_t(ew * 32) << 16) + uint32_t(a) * 256u;
-            auto emit = [&](int col, float hi, float lo) {
+            auto emit = [&](int col, float hi, float lo, float bval) {
                 const float scale = SA ? sback * __ldg(fsc + col) : rscale;
                 const long long o = (long long)col * cstep;
                 if (EPI == EPI_STORE2) {
@@ -405,27 +405,40 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
                 }
                 float v = (hi + lo) * scale;
                 if (EPI == EPI_PHI) v *= phi_eval(p.phik, zrow + __ldg(zc + col));
-                if (EPI == EPI_AXPY) v = fmaf(p.alpha, v, __ldg(brow + o));
+                if (EPI == EPI_AXPY) v = fmaf(p.alpha, v, bval);
                 yrow[o] = v;
                 vmax = fmaxf(vmax, fabsf(v));
             };
+            // the axpy's base values of the next 8 columns are loaded while the current ones are
+            // combined, so their latency does not add to every group
+            auto load_base = [&](int j0, float (&b)[8]) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    b[j] = (EPI == EPI_AXPY && rvalid && j0 + j < ncol) ? __ldg(brow + (long long)(j0 + j) * cstep) : 0.f;
+            };
             const int jlo = half * (kN / 2), jhi = jlo + kN / 2;
+            float bcur[8], bnxt[8];
+            load_base(jlo, bcur);
 #pragma unroll 1
             for (int j0 = jlo; j0 < jhi; j0 += 8) {
                 float d[4][8];
+                if (j0 + 8 < jhi) load_base(j0 + 8, bnxt);
                 __syncwarp();
                 tmem_ld8x4(tbase + j0, uint32_t(kN), d);
-                if (!rvalid || j0 >= ncol) continue;
+                if (rvalid && j0 < ncol) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    if (j0 + j >= ncol) break;
-                    float hi, lo;
-                    two_sum(d[0][j], d[1][j] * 0.00390625f, hi, lo);
-                    lo += fmaf(d[3][j], 5.9604644775390625e-08f, d[2][j] * 1.52587890625e-05f);
-                    const float s = hi + lo;
-                    lo = lo - (s - hi);
-                    emit(j0 + j, s, lo);
+                    for (int j = 0; j < 8; ++j) {
+                        if (j0 + j >= ncol) break;
+                        float hi, lo;
+                        two_sum(d[0][j], d[1][j] * 0.00390625f, hi, lo);
+                        lo += fmaf(d[3][j], 5.9604644775390625e-08f, d[2][j] * 1.52587890625e-05f);
+                        const float s = hi + lo;
+                        lo = lo - (s - hi);
+                        emit(j0 + j, s, lo, bcur[j]);
+                    }
                 }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) bcur[j] = bnxt[j];
             }
             tc_fence_before();
             __syncwarp();
