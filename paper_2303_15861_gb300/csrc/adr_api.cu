@@ -96,6 +96,8 @@ struct adr_batch_state {
     float2* d_phi[3] = {nullptr, nullptr, nullptr};   // double-float phi_0, phi_1, phi_2 per node
     int4* d_titems[2] = {nullptr, nullptr};           // tensor-core work items per mode
     int ntitems[2] = {0, 0};
+    int4* d_sunits = nullptr;              // marching stencil units {instance, x1 start, first row, rows}
+    int nsunits = 0;
     float* d_lo[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // low parts of ws[0..5]
     float* d_ulo = nullptr;                // low part of the caller's state
     float* d_uhs = nullptr;                // the high part the library last wrote to the caller's state
@@ -746,6 +748,8 @@ void push_stencil(Sched& S, StencilArgs<T> s, bool record_input) {
             if (S.batch_mixed()) {   // compensated stencil: low parts in and out, max|out| per instance
                 adr::BatchStencil2Args P;
                 P.s = a;
+                P.units = S.c->bs->d_sunits;
+                P.nunits = S.c->bs->nsunits;
                 P.u_lo = S.lo_of(s.u);
                 for (int e = 0; e < s.nx; ++e) P.X_lo[e] = S.lo_of(s.X[e]);
                 for (int j = 0; j < s.nout; ++j) {
@@ -1256,6 +1260,18 @@ cudaError_t batch_mixed_plan(adr_ctx* c) {
             e = cudaMemcpy(b.d_titems[mode - 1], items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
         b.ntitems[mode - 1] = int(items.size());
         b.grid[mode - 1] = std::min(int(items.size()), device_sms());
+    }
+    // the compensated stencil marches down 16 rows of 32 x1 nodes per warp
+    std::vector<int4> units;
+    for (int i : order)
+        for (int x0 = 0; x0 < b.n1[i]; x0 += 32)
+            for (int r0 = 0; r0 < b.n2[i]; r0 += 16) units.push_back(make_int4(i, x0, r0, std::min(16, b.n2[i] - r0)));
+    if (e == cudaSuccess) {
+        if (b.d_sunits) cudaFree(b.d_sunits);
+        b.d_sunits = nullptr;
+        e = cudaMalloc(reinterpret_cast<void**>(&b.d_sunits), units.size() * sizeof(int4));
+        if (e == cudaSuccess) e = cudaMemcpy(b.d_sunits, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice);
+        b.nsunits = int(units.size());
     }
     b.sgrid = 8 * device_sms();
     return e;
@@ -2208,6 +2224,7 @@ void adr_destroy(adr_ctx* c) {
         free_dev(b.d_zt);
         for (auto& it : b.d_items) { void* q = it; free_dev(q); it = nullptr; }
         for (auto& it : b.d_titems) { void* q = it; free_dev(q); it = nullptr; }
+        { void* q = b.d_sunits; free_dev(q); b.d_sunits = nullptr; }
         { void* q = b.d_img; free_dev(q); b.d_img = nullptr; }
         { void* q = b.d_fsc; free_dev(q); b.d_fsc = nullptr; }
         free_dev(b.d_tci);

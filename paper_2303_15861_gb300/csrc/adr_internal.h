@@ -347,6 +347,10 @@ struct BatchStencil2Args {
     float* out_lo[kMaxOut] = {nullptr, nullptr};
     float* out_hs[kMaxOut] = {nullptr, nullptr};
     unsigned* amax[kMaxOut] = {nullptr, nullptr};
+    // optional marching form: units {instance, first x1 node, first row, rows}, one warp each
+    // (32 x1 nodes); without them one warp per row of an instance
+    const int4* units = nullptr;
+    int nunits = 0;
 };
 cudaError_t launch_batch_stencil2(const BatchStencil2Args& a, cudaStream_t s);
 // lo[i] = (u[i] == hs[i]) ? lo[i] : 0 over n elements: the low part of the state survives

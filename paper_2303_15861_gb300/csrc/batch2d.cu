@@ -197,6 +197,108 @@ __global__ void __launch_bounds__(256) batch_stencil2_kernel(BatchStencil2Args P
     }
 }
 
+// The same node arithmetic as batch_stencil2_kernel, marching: a warp takes 32 consecutive x1
+// nodes of one instance (a unit {instance, x1 start, first row, rows}) and walks down its rows,
+// keeping the rows above, at and below the current one of u, its low part and (a - abar) in
+// registers; the x1 neighbours come from the adjacent lanes, the two at the ends of the strip
+// from memory. Each input element is read once per strip instead of five times.
+__global__ void __launch_bounds__(256) batch_stencil2_march_kernel(BatchStencil2Args P, const int4* __restrict__ units,
+                                                                   int nunits, Combo<float> cb, Combo2 c2, bool needF) {
+    const BatchStencilArgs<float>& p = P.s;
+    const int lane = threadIdx.x & 31;
+    const int warps = int(gridDim.x) * int(blockDim.x >> 5);
+    for (int w = int(blockIdx.x) * int(blockDim.x >> 5) + int(threadIdx.x >> 5); w < nunits; w += warps) {
+        const int4 un = __ldg(units + w);
+        const BatchInst<float>& in = p.inst[un.x];
+        const int n1 = in.n1, n2 = in.n2, ap = in.apitch;
+        const int i1 = un.y + lane;
+        const bool valid = i1 < n1;
+        Coefs<float> c;
+        c.ih2[0] = in.ih2[0]; c.ih2[1] = in.ih2[1]; c.ih2[2] = 0.f;
+        c.i2h[0] = in.i2h[0]; c.i2h[1] = in.i2h[1]; c.i2h[2] = 0.f;
+        c.bmb[0] = in.bmb[0]; c.bmb[1] = in.bmb[1]; c.bmb[2] = 0.f;
+        c.beta[0] = in.beta[0]; c.beta[1] = in.beta[1]; c.beta[2] = 0.f;
+        c.abar = in.abar;
+        c.r0 = in.r[0]; c.r1 = in.r[1]; c.r2 = in.r[2]; c.r3 = in.r[3];
+        const float* ub = p.u + in.off;
+        const float* lb = P.u_lo ? P.u_lo + in.off : nullptr;
+        const float* ab = p.a + in.a_off + 4;          // (a - abar) at interior i1 = 0 of ring row 0
+        // value of row r (-1..n2) at this lane's node: zero outside the grid (Dirichlet ghosts)
+        auto ldu = [&](const float* base, int r) -> float {
+            return (base && valid && r >= 0 && r < n2) ? __ldg(base + (long long)r * n1 + i1) : 0.f;
+        };
+        auto lda = [&](int r) -> float {            // ring rows -1..n2 exist for every node i1 in 0..n1-1
+            return valid ? __ldg(ab + (long long)(r + 1) * ap + i1) : 0.f;
+        };
+        const int r0 = un.z, r1 = un.z + un.w;
+        float um = ldu(ub, r0 - 1), uc = ldu(ub, r0);
+        float lm = ldu(lb, r0 - 1), lc = ldu(lb, r0);
+        float am = lda(r0 - 1), ac = lda(r0);
+        float vmax[kMaxOut] = {0.f, 0.f};
+        for (int r = r0; r < r1; ++r) {
+            const float up = ldu(ub, r + 1), lp = ldu(lb, r + 1), apl = lda(r + 1);
+            // x1 neighbours: adjacent lanes, and memory at the two ends of the strip
+            float uw = __shfl_up_sync(0xffffffffu, uc, 1), ue = __shfl_down_sync(0xffffffffu, uc, 1);
+            float lw = __shfl_up_sync(0xffffffffu, lc, 1), le = __shfl_down_sync(0xffffffffu, lc, 1);
+            float aw = __shfl_up_sync(0xffffffffu, ac, 1), ae = __shfl_down_sync(0xffffffffu, ac, 1);
+            const long long rowoff = (long long)r * n1;
+            const float* arow = ab + (long long)(r + 1) * ap;
+            if (lane == 0 && valid) {
+                uw = i1 > 0 ? __ldg(ub + rowoff + i1 - 1) : 0.f;
+                lw = (lb && i1 > 0) ? __ldg(lb + rowoff + i1 - 1) : 0.f;
+                aw = __ldg(arow + i1 - 1);           // the ring column at i1 = -1 exists
+            }
+            if (valid && (lane == 31 || i1 + 1 >= n1)) {
+                ue = i1 + 1 < n1 ? __ldg(ub + rowoff + i1 + 1) : 0.f;
+                le = (lb && i1 + 1 < n1) ? __ldg(lb + rowoff + i1 + 1) : 0.f;
+                ae = __ldg(arow + i1 + 1);           // the ring column at i1 = n1 exists
+            }
+            if (valid) {
+                const float dE = (ue - uc) + (le - lc), dW = (uc - uw) + (lc - lw);
+                const float dN = (up - uc) + (lp - lc), dS = (uc - um) + (lc - lm);
+                float F = 0.f;
+                const float g = stencil_core<float, 2>(c, uc + lc, dE, dW, dN, dS, 0.f, 0.f, ac + ae, ac + aw, ac + apl,
+                                                       ac + am, 0.f, 0.f, needF, F);
+                const long long o = in.off + rowoff + i1;
+#pragma unroll
+                for (int j = 0; j < kMaxOut; ++j) {
+                    if (j >= p.nout) continue;
+                    float hi = 0.f, lo = 0.f;
+                    if (cb.cu[j] != 0.f) df_fma(c2.cu[j][0], c2.cu[j][1], uc, lc, hi, lo);
+#pragma unroll
+                    for (int e = 0; e < kMaxExtra; ++e)
+                        if (e < p.nx && cb.cx[j][e] != 0.f) {
+                            const float xh = __ldg(p.X[e] + o);
+                            const float xl = P.X_lo[e] ? __ldg(P.X_lo[e] + o) : 0.f;
+                            df_fma(c2.cx[j][e][0], c2.cx[j][e][1], xh, xl, hi, lo);
+                        }
+                    if (cb.cg[j] != 0.f) df_fma(c2.cg[j][0], c2.cg[j][1], g, 0.f, hi, lo);
+                    if (cb.cF[j] != 0.f) df_fma(c2.cF[j][0], c2.cF[j][1], F, 0.f, hi, lo);
+                    if (P.out_lo[j]) {
+                        p.out[j][o] = hi;
+                        P.out_lo[j][o] = lo;
+                    } else {
+                        hi = hi + lo;
+                        p.out[j][o] = hi;
+                    }
+                    if (P.out_hs[j]) P.out_hs[j][o] = hi;
+                    vmax[j] = fmaxf(vmax[j], fabsf(hi));
+                }
+            }
+            um = uc; uc = up;
+            lm = lc; lc = lp;
+            am = ac; ac = apl;
+        }
+#pragma unroll
+        for (int j = 0; j < kMaxOut; ++j) {
+            if (j >= p.nout || !P.amax[j]) continue;
+            float m = vmax[j];
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0 && m > 0.f) atomicMax(P.amax[j] + un.x, __float_as_uint(m));
+        }
+    }
+}
+
 // --------------------------------------------------------------------------- contraction
 constexpr int kThreads = 256;      // 16 x 16 threads per tile of every shape
 constexpr int kBK = 16;            // K per shared-memory stage
@@ -507,6 +609,13 @@ cudaError_t stencil2_launch(const BatchStencil2Args& P, cudaStream_t s) {
             split(p.cx[j][e], c2.cx[j][e]);
         }
         if (j < p.nout && p.cF[j] != 0.0) needF = true;
+    }
+    if (P.units && P.nunits > 0) {   // the marching form over {instance, x1 start, first row, rows} units
+        long long grid = (P.nunits + 7) / 8;
+        const long long cap = 16LL * sm_count();
+        if (grid > cap) grid = cap;
+        batch_stencil2_march_kernel<<<unsigned(grid), 256, 0, s>>>(P, P.units, P.nunits, cb, c2, needF);
+        return cudaGetLastError();
     }
     const long long want = (p.rows + 7) / 8;
     long long grid = p.grid > 0 ? p.grid : 8LL * sm_count();
