@@ -88,8 +88,8 @@ def _batch_params(sizes, **kw):
     (dict(dim=3), 1),                       # batched contexts are 2-D
     (dict(with_sizes=False), 1),            # n_batch missing
     (dict(batch=-1), 1),
-    (dict(precision=3), 8),                 # the mixed path is not offered for batches
-    (dict(precision=2), 8),
+    (dict(precision=3, sizes=[(48, 48), (257, 64)]), 1),   # mixed batches: instances up to 256 per direction
+    (dict(precision=2), 8),                 # TF32x3 is not built
     (dict(batch_tile=48), 1),
     (dict(sizes=[(48, 48), (1, 64)]), 1),   # an instance below the minimum size
 ])
