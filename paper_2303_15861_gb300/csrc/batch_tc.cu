@@ -53,7 +53,8 @@ constexpr int kNacc = 4;
 constexpr int kProducerWarps = 8;
 constexpr int kEpiWarp0 = 8;
 constexpr int kMmaWarp = 12;
-constexpr int kThreads = (kMmaWarp + 1) * 32;
+constexpr int kLoadWarp = 13;           // factor tiles: bulk copies, its own ring, running ahead
+constexpr int kThreads = (kLoadWarp + 1) * 32;
 constexpr uint32_t kTmemCols = 512;     // two sets of kNacc x kN columns
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kN >> 3) << 17) | (uint32_t(kM >> 4) << 24);
 static_assert(2 * kNacc * kN <= int(kTmemCols), "TMEM");
@@ -66,9 +67,9 @@ struct BCfg {
     static constexpr int FTILE = FROWS * kKc * 2;
     static constexpr int SBYTES = kSS * STILE;
     static constexpr int FBYTES = kFS * FTILE;
-    static constexpr int STAGE = SBYTES + FBYTES;
-    static constexpr int NST = SA ? 3 : 2;         // pipeline stages (as many as shared memory holds)
-    static constexpr int SMEM = NST * STAGE + 1024;
+    static constexpr int SST = SA ? 3 : 2;         // state-slice ring stages
+    static constexpr int FST = 3;                  // factor ring stages
+    static constexpr int SMEM = SST * SBYTES + FST * FBYTES + 1024;
     static constexpr int NV = SROWS * kKc / (kProducerWarps * 32);   // values per producer thread
     static_assert(SMEM <= 227 * 1024, "shared memory budget");
 };
@@ -150,6 +151,23 @@ __device__ __forceinline__ int input_exponent(const unsigned* amax, int inst) {
     int es = 0;
     if (m > 0.f) frexpf(m, &es);
     return es;
+}
+
+// Prefetch into L2 the lines that K chunk c of a tile will load: one 128-byte line per producer
+// thread (mode 2: 32 rows x 4 lines of hi and of lo; mode 1: 64 rows x 1 line of hi and of lo).
+template <bool SA>
+__device__ __forceinline__ void prefetch_chunk(const BatchTcArgs& p, const BatchTcInst& in, int pt, int c, int t) {
+    const int n1 = in.n1, n2 = in.n2;
+    const float* base = nullptr;
+    long long e = 0;
+    if (SA) {
+        const int k = c * kKc + ((t >> 2) & 31), q = pt * kM + 32 * (t & 3);
+        if (k < n2 && q < n1) { base = (t >> 7) ? p.Xlo : p.X; e = in.off + (long long)k * n1 + q; }
+    } else if (t < 128) {
+        const int f = pt * kN + (t & 63), k = c * kKc;
+        if (f < n2 && k < n1) { base = (t >> 6) ? p.Xlo : p.X; e = in.off + (long long)f * n1 + k; }
+    }
+    if (base) asm volatile("prefetch.global.L2 [%0];" ::"l"(base + e));
 }
 
 // Load the NV state values (and low parts) of producer thread t for K chunk c of a tile.
@@ -245,24 +263,33 @@ template <bool SA, int EPI>
 __global__ void __launch_bounds__(kThreads, 1) batch_tc_kernel(const __grid_constant__ BatchTcArgs p) {
     using C = BCfg<SA>;
     extern __shared__ uint8_t smem_raw[];
-    constexpr int kStages = C::NST;
-    __shared__ __align__(8) uint64_t bars[2 * kStages + 4 + 1];
+    constexpr int kStages = C::SST, kFStages = C::FST;
+    // barriers: sfull[SST] sempty[SST] ffull[FST] fempty[FST] accf[2] acce[2] drain
+    __shared__ __align__(8) uint64_t bars[2 * kStages + 2 * kFStages + 4 + 1];
     __shared__ uint32_t tmem_base_s;
     __shared__ volatile int abort_s;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;   // state-slice ring
+    const uint32_t fbase = sbase + kStages * C::SBYTES;               // factor ring
     const uint32_t bar0 = smem_u32(&bars[0]);
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
     auto empty_bar = [&](int s) { return bar0 + 8u * (kStages + s); };
-    auto accf_bar = [&](int a) { return bar0 + 8u * (2 * kStages + a); };
-    auto acce_bar = [&](int a) { return bar0 + 8u * (2 * kStages + 2 + a); };
-    const uint32_t drain_bar = bar0 + 8u * (2 * kStages + 4);
+    auto ffull_bar = [&](int s) { return bar0 + 8u * (2 * kStages + s); };
+    auto fempty_bar = [&](int s) { return bar0 + 8u * (2 * kStages + kFStages + s); };
+    const uint32_t acc0 = bar0 + 8u * (2 * kStages + 2 * kFStages);
+    auto accf_bar = [&](int a) { return acc0 + 8u * a; };
+    auto acce_bar = [&](int a) { return acc0 + 8u * (2 + a); };
+    const uint32_t drain_bar = acc0 + 8u * 4;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(full_bar(s), kProducerWarps * 32 + 1);   // producers + the expect_tx arrival
+            mbar_init(full_bar(s), kProducerWarps * 32);        // one arrival per producer thread
             mbar_init(empty_bar(s), 1);                         // tcgen05.commit
+        }
+        for (int s = 0; s < kFStages; ++s) {
+            mbar_init(ffull_bar(s), 1);                         // the loader's expect_tx arrival
+            mbar_init(fempty_bar(s), 1);                        // tcgen05.commit
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(accf_bar(a), 1);                          // tcgen05.commit
@@ -310,20 +337,13 @@ __global__ void __launch_bounds__(kThreads, 1) batch_tc_kernel(const __grid_cons
             if (j.c + 1 < j.nK) { n = j; n.c = j.c + 1; }
             else start(j.tile + int(gridDim.x), n);
         };
-        // one chunk: wait for its stage, start its factor copy, prefetch the next chunk, slice
+        // one chunk: wait for its stage, prefetch the next chunk, slice
         auto step = [&](const Job& j, long long g, const float (&v)[C::NV], const float (&vl)[C::NV], const Job& nj,
                         float (&nv)[C::NV], float (&nvl)[C::NV]) -> bool {
             const int s = int(g % kStages);
             const uint32_t ph = uint32_t(g / kStages) & 1u;
             if (!mbar_wait(empty_bar(s), ph ^ 1u, p.err, 1, &abort_s, 64)) return false;
-            const uint32_t sA = sbase + s * C::STAGE;
-            if (t == 0) {
-                mbar_arrive_expect_tx(full_bar(s), C::FBYTES);
-                const uint8_t* src = j.img + size_t(j.c) * C::FBYTES;
-#pragma unroll
-                for (int q = 0; q < kFS; ++q)
-                    bulk_g2s(sA + C::SBYTES + q * C::FTILE, src + q * C::FTILE, C::FTILE, full_bar(s));
-            }
+            const uint32_t sA = sbase + s * C::SBYTES;
             if (nj.tile < p.nitems) load_chunk<SA>(p, *nj.in, nj.item.y, nj.c, t, nv, nvl);
             if (SA) {
                 const int row = t & (kM - 1), part = t >> 7;
@@ -336,15 +356,33 @@ __global__ void __launch_bounds__(kThreads, 1) batch_tc_kernel(const __grid_cons
             mbar_arrive(full_bar(s));
             return true;
         };
-        Job a, b;
+        Job a, b, pf;
         start(blockIdx.x, a);
         float va[C::NV], vla[C::NV], vb[C::NV], vlb[C::NV];
         if (a.tile < p.nitems) load_chunk<SA>(p, *a.in, a.item.y, a.c, t, va, vla);
+        // an L2 prefetch cursor kPrefetch chunks ahead of the chunk being sliced
+        constexpr int kPrefetch = 3;
+        pf = a;
+        for (int i = 0; i < kPrefetch && pf.tile < p.nitems; ++i) {
+            prefetch_chunk<SA>(p, *pf.in, pf.item.y, pf.c, t);
+            Job nx;
+            next(pf, nx);
+            pf = nx;
+        }
+        auto advance_prefetch = [&]() {
+            if (pf.tile >= p.nitems) return;
+            prefetch_chunk<SA>(p, *pf.in, pf.item.y, pf.c, t);
+            Job nx;
+            next(pf, nx);
+            pf = nx;
+        };
         for (long long g = 0; a.tile < p.nitems; g += 2) {
             next(a, b);
+            advance_prefetch();
             if (!step(a, g, va, vla, b, vb, vlb)) break;
             if (b.tile >= p.nitems) break;
             next(b, a);
+            advance_prefetch();
             if (!step(b, g + 1, vb, vlb, a, va, vla)) break;
         }
     } else if (warp < kEpiWarp0 + 4) {
@@ -451,6 +489,30 @@ __global__ void __launch_bounds__(kThreads, 1) batch_tc_kernel(const __grid_cons
             for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
             if (lane == 0 && p.amax_out && vmax > 0.f) atomicMax(p.amax_out + item.x, __float_as_uint(vmax));
         }
+    } else if (warp == kLoadWarp) {
+        // ------------------------------------------------------------ factor loader
+        // The CTA's chunks in the same order as the MMA issuer; a ring slot frees when the MMAs
+        // of the chunk kFStages earlier retire, so each copy has kFStages - 1 chunks of lead.
+        if (lane == 0) {
+            long long g = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < p.nitems && ok && !abort_s; tile += gridDim.x) {
+                const int4 item = __ldg(p.items + tile);
+                const BatchTcInst& in = p.inst[item.x];
+                const int nK = ((SA ? in.n2 : in.n1) + kKc - 1) / kKc;
+                const uint8_t* img = p.fimg + in.img_off[p.role][dir] + size_t(item.z) * nK * C::FBYTES;
+                for (int c = 0; c < nK; ++c, ++g) {
+                    const int fs = int(g % kFStages);
+                    const uint32_t fph = uint32_t(g / kFStages) & 1u;
+                    if (!mbar_wait(fempty_bar(fs), fph ^ 1u, p.err, 32, &abort_s, 32)) { ok = false; break; }
+                    mbar_arrive_expect_tx(ffull_bar(fs), C::FBYTES);
+                    const uint8_t* src = img + size_t(c) * C::FBYTES;
+                    const uint32_t dst = fbase + fs * C::FBYTES;
+#pragma unroll
+                    for (int q = 0; q < kFS; ++q) bulk_g2s(dst + q * C::FTILE, src + q * C::FTILE, C::FTILE, ffull_bar(fs));
+                }
+            }
+        }
     } else if (lane == 0) {
         // ------------------------------------------------------------ MMA issuer
         long long g = 0, tl = 0;
@@ -467,10 +529,13 @@ __global__ void __launch_bounds__(kThreads, 1) batch_tc_kernel(const __grid_cons
             for (int c = 0; c < nK; ++c, ++g) {
                 const int s = int(g % kStages);
                 const uint32_t ph = uint32_t(g / kStages) & 1u;
+                const int fs = int(g % kFStages);
+                const uint32_t fph = uint32_t(g / kFStages) & 1u;
+                if (!mbar_wait(ffull_bar(fs), fph, p.err, 16, &abort_s)) { ok = false; break; }
                 if (!mbar_wait(full_bar(s), ph, p.err, 8, &abort_s)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t sS = sbase + s * C::STAGE;
-                const uint32_t sF = sS + C::SBYTES;
+                const uint32_t sS = sbase + s * C::SBYTES;
+                const uint32_t sF = fbase + fs * C::FBYTES;
                 uint64_t S[kSS], F[kFS];
 #pragma unroll
                 for (int q = 0; q < kSS; ++q) S[q] = sdesc64(sS + q * C::STILE);
@@ -480,6 +545,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_tc_kernel(const __grid_cons
                 for (int kk = 0; kk < kKc / 16; ++kk)
                     mma_kstep<SA>(d, S, F, uint64_t(kk * 32) >> 4, (c == 0 && kk == 0) ? 1u : 0u);
                 tc_commit(empty_bar(s));
+                tc_commit(fempty_bar(fs));
             }
             if (!ok) break;
             tc_commit(accf_bar(a));
