@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_tc_kernel(const __grid_cons
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(full_bar(s), kProducerWarps * 32);        // one arrival per producer thread
+            mbar_init(full_bar(s), kProducerWarps);             // one arrival per producer warp
             mbar_init(empty_bar(s), 1);                         // tcgen05.commit
         }
         for (int s = 0; s < kFStages; ++s) {
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_tc_kernel(const __grid_cons
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(accf_bar(a), 1);                          // tcgen05.commit
-            mbar_init(acce_bar(a), 128);                        // epilogue threads
+            mbar_init(acce_bar(a), 4);                          // one arrival per epilogue warp
         }
         mbar_init(drain_bar, 1);
         abort_s = 0;
@@ -342,7 +342,8 @@ __global__ void __launch_bounds__(kThreads, 1) batch_tc_kernel(const __grid_cons
                         float (&nv)[C::NV], float (&nvl)[C::NV]) -> bool {
             const int s = int(g % kStages);
             const uint32_t ph = uint32_t(g / kStages) & 1u;
-            if (!mbar_wait(empty_bar(s), ph ^ 1u, p.err, 1, &abort_s, 64)) return false;
+            // warp-uniform decision: the per-warp arrival below needs every lane
+            if (!__all_sync(0xffffffffu, mbar_wait(empty_bar(s), ph ^ 1u, p.err, 1, &abort_s, 64))) return false;
             const uint32_t sA = sbase + s * C::SBYTES;
             if (nj.tile < p.nitems) load_chunk<SA>(p, *nj.in, nj.item.y, nj.c, t, nv, nvl);
             if (SA) {
@@ -352,8 +353,11 @@ __global__ void __launch_bounds__(kThreads, 1) batch_tc_kernel(const __grid_cons
             } else {
                 slice_store8(v, vl, j.sc, sA, C::STILE, t >> 2, t & 3);
             }
+            // one arrival per warp once every lane's slices are visible to the tensor cores
+            // (256 single-thread arrivals on one barrier word serialise)
             fence_proxy_async();
-            mbar_arrive(full_bar(s));
+            __syncwarp();
+            if (lane == 0) mbar_arrive(full_bar(s));
             return true;
         };
         Job a, b, pf;
@@ -485,7 +489,8 @@ __global__ void __launch_bounds__(kThreads, 1) batch_tc_kernel(const __grid_cons
                 }
             }
             tc_fence_before();
-            mbar_arrive(acce_bar(a));
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce_bar(a));
             for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
             if (lane == 0 && p.amax_out && vmax > 0.f) atomicMax(p.amax_out + item.x, __float_as_uint(vmax));
         }
