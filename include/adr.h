@@ -62,7 +62,10 @@ typedef enum {
     ADR_MIXED_TF32X3 = 2,  /* reserved: not implemented (returns ADR_ERR_UNSUPPORTED)    */
     ADR_MIXED_BF16X3 = 3   /* FP32 state and stencil; mu-mode contractions on the tensor
                               cores from four BF16 slices per operand (ten products) into
-                              exact FP32 accumulators; factors and phi near 0 in FP64    */
+                              exact FP32 accumulators; factors and phi near 0 in FP64.
+                              Batched contexts: the state is a compensated FP32 pair (the
+                              caller's array holds the high part), five state slices and
+                              fourteen products per multiply-add (see adr_create)        */
 } adr_precision;
 
 typedef enum {
@@ -92,11 +95,13 @@ typedef struct {
                               ADR_EXPONENTIAL_EULER, ADR_ERK2P1) check it.               */
     int batch;             /* 0: one grid (dim, n). > 0: that many independent 2-D
                               instances of uneven size in one context (dim must be 2;
-                              ADR_FP64 or ADR_FP32)                                       */
+                              ADR_FP64, ADR_FP32 or ADR_MIXED_BF16X3, the last with
+                              n1, n2 <= 256 per instance)                                 */
     const int* n_batch;    /* batch > 0: host, 2*batch ints (n1, n2) of instance i at
                               [2i], [2i+1]; copied by adr_create                          */
-    int batch_tile;        /* batch > 0: 0 = tile shapes and grid chosen by the autotuner;
-                              32, 64 or 128 = that square tile for every instance          */
+    int batch_tile;        /* batch > 0, FP64 / FP32: 0 = tile shapes and grid chosen by
+                              the autotuner; 32, 64 or 128 = that square tile for every
+                              instance (mixed batched contexts have one tiling)           */
     int phi_route;         /* adr_phi_route: how phi_k(tau A) is applied (single grids)     */
     int bc_hi;             /* adr_bc: the boundary condition on the faces x_mu = 1          */
     int form;              /* adr_form: the diffusion term                                  */
@@ -162,7 +167,18 @@ typedef enum { ADR_PHI_AUTO = 0, ADR_PHI_EIGEN = 1, ADR_PHI_DOUBLING = 2,
  * the inputs and outputs of the building blocks) packs the instances one after another:
  * instance i occupies n1_i*n2_i elements (x1 fastest) starting at element
  * sum_{j<i} n1_j*n2_j. Every stage of a step is one persistent kernel launch over all
- * instances. All instances share tau and the scheme. */
+ * instances. All instances share tau and the scheme.
+ *
+ * Mixed batched contexts (ADR_MIXED_BF16X3) carry the state as a compensated FP32 pair: the
+ * caller's FP32 array is the high part, and the library keeps the low part and a copy of the
+ * high part it last wrote. Every step first keeps the low part only where the caller's array
+ * still equals that copy: consecutive adr_step / adr_integrate calls on the same array continue
+ * the compensated state, and elements the caller has overwritten start from a zero low part.
+ * The contractions run on the tensor cores with five integer BF16 slices of the pair against
+ * four of each factor row (fourteen products, exact accumulators for n <= 256); intermediates
+ * between the passes of a phi action are pairs; phi_k comes from a double-float table; the
+ * stencil forms its differences from both parts. This holds the batched ETD2RK workload to
+ * 1e-5 of the FP64 oracle on instances where an FP32 state does not. */
 adr_status adr_create(const adr_params* p, void* cuda_stream, adr_ctx** out);
 
 /* Set the coefficients of Eq. (adr) of one instance (0 for a single-grid context,
@@ -233,7 +249,8 @@ adr_status adr_get_instance_info(const adr_ctx* ctx, int instance, double kappa[
 /* The contraction schedule of a batched context, as chosen by the autotuner (or forced
  * by batch_tile), for mode 1 (contraction along x1) or mode 2: the tile edge (32, 64 or
  * 128) of every instance in tile_edge[0..batch-1] (may be NULL) and the number of
- * persistent CTAs of the launch in *grid (may be NULL). ADR_ERR_STATE before every
+ * persistent CTAs of the launch in *grid (may be NULL). Mixed batched contexts report their
+ * tensor-core tiles' output extent: 128 in mode 1, 64 in mode 2. ADR_ERR_STATE before every
  * instance is set; ADR_ERR_ARG for a single-grid context. */
 adr_status adr_get_batch_plan(const adr_ctx* ctx, int mode, int* tile_edge, int* grid);
 
