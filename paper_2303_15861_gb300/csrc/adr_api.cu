@@ -154,6 +154,8 @@ struct adr_ctx {
     void* d_psym = nullptr;                        // symbol of A
     void* d_pm[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // E(1/2), E(1), E(alpha), phi_1, phi_2
     void* d_pdif = nullptr;                        // a Lap u form: sum_mu a_mumu D_mu D_mu u
+    void* d_pcn = nullptr;                         // fused 2-D stages: the pointwise part of F, transformed
+    void* d_pz = nullptr;                          // fused 2-D stages: a Fourier-space array kept between stages
 
     // phi_k route; for the doubling route: X = tau A / 2^s, Taylor terms, level factors
     int phi_route = 0;                     // adr_phi_route in use (0: no phi_k needed)
@@ -545,6 +547,7 @@ adr::PeriodicArgs<T> periodic_args(const adr_ctx* c) {
     for (int i = 0; i < 4; ++i) P.r[i] = c->r[i];
     P.adelta = c->p.form == ADR_FORM_ADELTA;
     P.dif = static_cast<T*>(c->d_pdif);
+    P.CN = static_cast<adr::Cplx<T>*>(c->d_pcn);
     return P;
 }
 
@@ -558,6 +561,33 @@ void push_fourier(Sched& S, int mi, const T* x, T* y, const T* base, double alph
     Op op{[P, M, x, y, base, alpha](cudaStream_t st) { return adr::launch_periodic_multiplier(P, M, x, y, base, alpha, st); },
           OP_FOURIER_MULT};
     op.launches = adr::periodic_multiplier_launches(c->dim);
+    S.ops.push_back(op);
+}
+
+// A fused stage of a 2-D periodic context (see PeriodicStage): multipliers by index into d_pm
+// (-1: none); the Fourier-space array d_pz is read (cz != 0) or written (save_mi >= 0).
+template <typename T>
+void push_periodic_stage(Sched& S, const T* x, T* y, int mu_mi, double cu, int mg_mi, double cgF, double cg, double cz,
+                         int save_mi) {
+    const adr_ctx* c = S.c;
+    const auto P = periodic_args<T>(c);
+    auto pm = [&](int i) { return i < 0 ? nullptr : static_cast<const adr::Cplx<T>*>(c->d_pm[i]); };
+    adr::PeriodicStage<T> st;
+    st.x = x;
+    st.y = y;
+    st.Mu = pm(mu_mi);
+    st.Mg = pm(mg_mi);
+    st.cu = cu;
+    st.cgF = cgF;
+    st.cg = cg;
+    st.cz = cz;
+    if (cz != 0.0) st.Z = static_cast<const adr::Cplx<T>*>(c->d_pz);
+    if (save_mi >= 0) {
+        st.Zs = static_cast<adr::Cplx<T>*>(c->d_pz);
+        st.Ms = pm(save_mi);
+    }
+    Op op{[P, st](cudaStream_t s) { return adr::launch_periodic_stage(P, st, s); }, OP_PERIODIC_RHS};
+    op.launches = adr::periodic_stage_launches(c->dim);
     S.ops.push_back(op);
 }
 
@@ -776,6 +806,19 @@ std::vector<Op> build_step(const adr_ctx* c, T* u) {
     Sched S(c);
     S.bind_state(u);
     const double tau = c->p.tau;
+    if (c->periodic && c->dim == 2 && (c->p.scheme == ADR_LAWSON2A || c->p.scheme == ADR_LAWSON_EULER)) {
+        // Stages kept in Fourier space from the state's transform to the stage result (d_pm: 0
+        // e^{tau A/2}, 1 e^{tau A}): Lawson2a U = e^{tau A/2}(u + tau/2 g(u)), saving e^{tau A} u^,
+        // then u+ = e^{tau A} u + tau e^{tau A/2} g(U); Lawson-Euler u+ = e^{tau A}(u + tau g(u)).
+        T* B0 = static_cast<T*>(c->ws[0]);
+        if (c->p.scheme == ADR_LAWSON2A) {
+            push_periodic_stage<T>(S, u, B0, 0, 1.0, 0, 0.5 * tau, 0.5 * tau, 0.0, 1);
+            push_periodic_stage<T>(S, B0, u, -1, 0.0, 0, tau, tau, 1.0, -1);
+        } else {
+            push_periodic_stage<T>(S, u, u, 1, 1.0, 1, tau, tau, 0.0, -1);
+        }
+        return std::move(S.ops);
+    }
     T* B0 = static_cast<T*>(c->ws[0]);
     T* B1 = static_cast<T*>(c->ws[1]);
     T* B2 = static_cast<T*>(c->ws[2]);
@@ -1667,6 +1710,8 @@ adr_status create_periodic(const adr_params* p, void* cuda_stream, adr_ctx** out
     for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaMalloc(&c->ws[i], N * c->esize);
     for (int i = 0; i <= c->dim && e == cudaSuccess; ++i) e = cudaMalloc(&c->d_pc[i], 2 * N * c->esize);
     if (e == cudaSuccess && p->form == ADR_FORM_ADELTA) e = cudaMalloc(&c->d_pdif, N * c->esize);
+    if (e == cudaSuccess && p->dim == 2) e = cudaMalloc(&c->d_pcn, 2 * N * c->esize);
+    if (e == cudaSuccess && p->dim == 2) e = cudaMalloc(&c->d_pz, 2 * N * c->esize);
     if (e == cudaSuccess) e = adr::periodic_prepare(c->fp64);
     if (e != cudaSuccess) {
         adr_destroy(c.release());
@@ -2249,6 +2294,8 @@ void adr_destroy(adr_ctx* c) {
     free_dev(c->d_psym);
     for (auto& q : c->d_pm) free_dev(q);
     free_dev(c->d_pdif);
+    free_dev(c->d_pcn);
+    free_dev(c->d_pz);
     for (auto& row : c->d_img) for (auto& p : row) { void* q = p; free_dev(q); p = nullptr; }  // 5 kinds
     for (auto& row : c->d_fsc) for (auto& p : row) { void* q = p; free_dev(q); p = nullptr; }
     for (auto& row : c->d_img2) for (auto& p : row) { void* q = p; free_dev(q); p = nullptr; }

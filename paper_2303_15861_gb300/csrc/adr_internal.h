@@ -387,6 +387,26 @@ struct PeriodicArgs {
     double r[4] = {0, 0, 0, 0};
     bool adelta = false;                   // a Lap u form: sum_mu a_mumu D_mu D_mu u + D_mu (b_mu u)
     T* dif = nullptr;                      // adelta: sum_mu a_mumu D_mu D_mu u at the nodes (work)
+    Cplx<T>* CN = nullptr;                 // fused stages: the pointwise part of F, transformed (work)
+};
+
+// One fused stage of a 2-D periodic context, computed in Fourier space from the transform of x
+// to the result y (real): with H = cgF F^(x) - cg s x^ (s the symbol of A; cgF = cg: the
+// remainder g, cg = 0: F),
+//     y = Re F^-1 ( Mu (cu x^) + Mg H + cz Z ),   and, when Zs is set, Zs = Ms x^,
+// where the multipliers Mu, Mg, Ms (NULL: the identity) are Fourier-space arrays and Z a
+// Fourier-space array saved by an earlier stage. Lawson2a: U = E_h (u + tau/2 g(u)) with
+// Zs = E_1 u^; then u+ = Re F^-1 (Z + tau E_h g(U)^). Lawson-Euler: u+ = E_1 (u + tau g(u)).
+template <typename T>
+struct PeriodicStage {
+    const T* x = nullptr;
+    T* y = nullptr;
+    const Cplx<T>* Mu = nullptr;
+    const Cplx<T>* Mg = nullptr;
+    const Cplx<T>* Ms = nullptr;
+    const Cplx<T>* Z = nullptr;
+    Cplx<T>* Zs = nullptr;
+    double cu = 0, cgF = 0, cg = 0, cz = 0;
 };
 
 // Sets the shared-memory limits of the Fourier kernels of one precision (once, before any
@@ -403,6 +423,10 @@ cudaError_t launch_periodic_rhs(const PeriodicArgs<double>& P, const StencilArgs
 cudaError_t launch_periodic_rhs(const PeriodicArgs<float>& P, const StencilArgs<float>& s, cudaStream_t st);
 // y = base + alpha Re(IFFT(M FFT(x))) (y = Re(...) when base is null). Number of launches:
 int periodic_multiplier_launches(int dim);
+// Fused stages (2-D only; 5 launches). Number of launches (0: not available for dim):
+int periodic_stage_launches(int dim);
+cudaError_t launch_periodic_stage(const PeriodicArgs<double>& P, const PeriodicStage<double>& s, cudaStream_t st);
+cudaError_t launch_periodic_stage(const PeriodicArgs<float>& P, const PeriodicStage<float>& s, cudaStream_t st);
 cudaError_t launch_periodic_multiplier(const PeriodicArgs<double>& P, const Cplx<double>* M, const double* x, double* y,
                                        const double* base, double alpha, cudaStream_t st);
 cudaError_t launch_periodic_multiplier(const PeriodicArgs<float>& P, const Cplx<float>* M, const float* x, float* y,

@@ -46,6 +46,8 @@ enum PassMode {
     PM_FLUX = 5,         // x1: C[mu] = F_1 (a_mu Re F_1^-1 C[mu] + b_mu u)
     PM_PIVOT_DIV = 6,    // S = sum_mu i k_mu F_d C[mu]; C[j] = F_d^-1 (cgF_j S - cg_j M Cu)
     PM_FINAL_OUT = 7,    // x1: out_j = cu_j u + sum cx_je X_e + Re F_1^-1 C[j] + cgF_j r(u)
+    PM_PIVOT_STAGE = 8,  // H = cgF (sum_mu i k_mu F_d C[mu] + F_d CN) - cg s u^;
+                         // C[0] = F_d^-1 (Mu (cu u^) + Mg H + cz Z);  Zs = Ms u^
 };
 
 constexpr int kPassThreads = 256;
@@ -79,6 +81,16 @@ struct Pass {
     T cu[kMaxOut], cx[kMaxOut][kMaxExtra], cgF[kMaxOut], cg[kMaxOut], r[4];
     int adelta;               // a Lap u form (see PeriodicArgs)
     T* dif;                   // adelta: sum_mu a_mumu D_mu D_mu u
+    // fused stages (PM_FLUX with nonflux, PM_PIVOT_STAGE): the pointwise part of F (r(u), and the
+    // a Lap u product) transformed along x1 into CN; the stage's multipliers and saved array
+    int nonflux;
+    Cplx<T>* CN;
+    const Cplx<T>* Mu;
+    const Cplx<T>* Mg;
+    const Cplx<T>* Ms;
+    const Cplx<T>* Z;
+    Cplx<T>* Zs;
+    T scu, scgF, scg, scz;
 };
 
 // Global index of element j of line g of line group grp.
@@ -256,6 +268,49 @@ __global__ void __launch_bounds__(kPassThreads) fourier_pass_kernel(const __grid
                 for_elems(P, grp, [&](int o, long long i, int) { D[i] = R2[o]; });
                 __syncthreads();
             }
+            if (P.nonflux) {   // r(u) (+ the a Lap u product), forward along x1, into CN
+                for_elems(P, grp, [&](int o, long long i, int) {
+                    const T u = P.x[i];
+                    T v = P.r[0] + u * (P.r[1] + u * (P.r[2] + u * P.r[3]));
+                    if (P.adelta) v += P.dif[i];
+                    B0[o] = {v, T(0)};
+                });
+                __syncthreads();
+                Cplx<T>* R = fft_lines(P, tws, B0, B1, false);
+                for_elems(P, grp, [&](int o, long long i, int) { P.CN[i] = R[o]; });
+                __syncthreads();
+            }
+        } else if (MODE == PM_PIVOT_STAGE) {
+            for (int mu = 0; mu <= P.dim; ++mu) {      // B2 = sum_mu i k_mu f_mu^ + (pointwise part)^
+                const Cplx<T>* src = mu < P.dim ? P.C[mu] : P.CN;
+                for_elems(P, grp, [&](int o, long long i, int) { B0[o] = src[i]; });
+                __syncthreads();
+                Cplx<T>* R = fft_lines(P, tws, B0, B1, false);
+                for_elems(P, grp, [&](int o, long long i, int j) {
+                    Cplx<T> d = R[o];
+                    if (mu < P.dim) {
+                        const T km = wavenumber(P, mu, i, j);
+                        d = {-km * R[o].y, km * R[o].x};
+                    }
+                    B2[o] = mu == 0 ? d : Cplx<T>{B2[o].x + d.x, B2[o].y + d.y};
+                });
+                __syncthreads();
+            }
+            for_elems(P, grp, [&](int o, long long i, int) {
+                const Cplx<T> uh = P.Cu[i];
+                if (P.Zs) P.Zs[i] = P.Ms ? cmul(P.Ms[i], uh) : uh;
+                const Cplx<T> au = cmul(P.M[i], uh);
+                Cplx<T> h = {P.scgF * B2[o].x - P.scg * au.x, P.scgF * B2[o].y - P.scg * au.y};
+                if (P.Mg) h = cmul(P.Mg[i], h);
+                Cplx<T> v = {P.scu * uh.x, P.scu * uh.y};
+                if (P.Mu) v = cmul(P.Mu[i], v);
+                v = {v.x + h.x, v.y + h.y};
+                if (P.Z) v = {v.x + P.scz * P.Z[i].x, v.y + P.scz * P.Z[i].y};
+                B0[o] = v;
+            });
+            __syncthreads();
+            Cplx<T>* R = fft_lines(P, tws, B0, B1, true);
+            for_elems(P, grp, [&](int o, long long i, int) { P.C[0][i] = {R[o].x * inv_n, R[o].y * inv_n}; });
         } else if (MODE == PM_PIVOT_DIV) {
             for (int mu = 0; mu < P.dim; ++mu) {       // S (in B2) = sum_mu i k_mu f_mu^
                 for_elems(P, grp, [&](int o, long long i, int) { B0[o] = P.C[mu][i]; });
@@ -319,7 +374,7 @@ int sms() {
 }
 
 // Buffers of shared memory a mode needs besides the twiddles.
-int mode_buffers(int mode) { return (mode == PM_PIVOT_DERIV || mode == PM_PIVOT_DIV) ? 3 : 2; }
+int mode_buffers(int mode) { return (mode == PM_PIVOT_DERIV || mode == PM_PIVOT_DIV || mode == PM_PIVOT_STAGE) ? 3 : 2; }
 
 size_t pass_smem(int n, int G, int pitch, int nb, size_t cs) { return (size_t(n / 2) + size_t(nb) * G * pitch) * cs; }
 
@@ -390,6 +445,7 @@ cudaError_t prepare_impl() {
     set(reinterpret_cast<const void*>(fourier_pass_kernel<T, PM_FLUX>));
     set(reinterpret_cast<const void*>(fourier_pass_kernel<T, PM_PIVOT_DIV>));
     set(reinterpret_cast<const void*>(fourier_pass_kernel<T, PM_FINAL_OUT>));
+    set(reinterpret_cast<const void*>(fourier_pass_kernel<T, PM_PIVOT_STAGE>));
     sms();
     return e;
 }
@@ -491,7 +547,64 @@ cudaError_t multiplier_impl(const PeriodicArgs<T>& A, const Cplx<T>* M, const T*
     return cudaSuccess;
 }
 
+// One fused stage of a 2-D periodic context, kept in Fourier space from the state's transform to
+// the stage's result: y = Re F^-1 (Mu (cu u^) + Mg (cgF (F(u) - pointwise)^ ... ) + cz Z), see
+// PeriodicStage. Five launches: x1 forward of u | pivot: u^ and i k_mu u^ back | x1: fluxes and
+// the pointwise part forward | pivot: the combination and its multipliers, back | x1 inverse.
+template <typename T>
+cudaError_t stage_impl(const PeriodicArgs<T>& A, const PeriodicStage<T>& s, cudaStream_t st) {
+    if (A.dim != 2 || !s.x || !s.y || !A.CN || (s.Zs && !A.Cu)) return cudaErrorInvalidValue;
+    cudaError_t e;
+    {
+        Pass<T> P = make_pass(A, 0, PM_FWD_REAL);
+        P.x = s.x;
+        P.C[0] = A.Cu;
+        if ((e = launch_pass_on<T, PM_FWD_REAL>(P, st)) != cudaSuccess) return e;
+    }
+    {
+        Pass<T> P = make_pass(A, 1, PM_PIVOT_DERIV);
+        if ((e = launch_pass_on<T, PM_PIVOT_DERIV>(P, st)) != cudaSuccess) return e;
+    }
+    {
+        Pass<T> P = make_pass(A, 0, PM_FLUX);
+        P.x = s.x;
+        P.nonflux = 1;
+        P.CN = A.CN;
+        if ((e = launch_pass_on<T, PM_FLUX>(P, st)) != cudaSuccess) return e;
+    }
+    {
+        Pass<T> P = make_pass(A, 1, PM_PIVOT_STAGE);
+        P.M = A.sym;
+        P.CN = A.CN;
+        P.Mu = s.Mu;
+        P.Mg = s.Mg;
+        P.Ms = s.Ms;
+        P.Z = s.Z;
+        P.Zs = s.Zs;
+        P.scu = T(s.cu);
+        P.scgF = T(s.cgF);
+        P.scg = T(s.cg);
+        P.scz = T(s.cz);
+        if ((e = launch_pass_on<T, PM_PIVOT_STAGE>(P, st)) != cudaSuccess) return e;
+    }
+    {
+        Pass<T> P = make_pass(A, 0, PM_FINAL_AXPY);
+        P.y = s.y;
+        P.base = nullptr;
+        if ((e = launch_pass_on<T, PM_FINAL_AXPY>(P, st)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
+
+int periodic_stage_launches(int dim) { return dim == 2 ? 5 : 0; }
+cudaError_t launch_periodic_stage(const PeriodicArgs<double>& P, const PeriodicStage<double>& s, cudaStream_t st) {
+    return stage_impl(P, s, st);
+}
+cudaError_t launch_periodic_stage(const PeriodicArgs<float>& P, const PeriodicStage<float>& s, cudaStream_t st) {
+    return stage_impl(P, s, st);
+}
 
 cudaError_t periodic_prepare(bool fp64) { return fp64 ? prepare_impl<double>() : prepare_impl<float>(); }
 

@@ -166,6 +166,11 @@ def test_context_facts_and_launch_count():
     w3, L3, a3, b3 = W.periodic_instance((8, 16, 8), scheme="lawson2a")
     ctx3 = context(w3, L3, a3, b3)
     assert ctx3.kernels_per_step() == 2 * 9 + 3 * 5   # 3-D: 9 and 5 passes
+    # 2-D Lawson2a and Lawson-Euler keep each stage in Fourier space from the state's transform
+    # to the stage result: five passes per stage (instead of a right-hand side and multipliers)
+    for scheme, launches in (("lawson2a", 2 * 5), ("lawson_euler", 5)):
+        w2, L2, a2, b2 = W.periodic_instance((32, 16), scheme=scheme)
+        assert context(w2, L2, a2, b2).kernels_per_step() == launches, scheme
     ops = ctx.profile_step(dev(w.u0))
     assert [k for k, _ in ops] == [6, 7, 6, 7]
 
