@@ -259,7 +259,8 @@ adr_status adr_get_batch_plan(const adr_ctx* ctx, int mode, int* tile_edge, int*
  * in kind[i] (0 memset, 1 max-abs reduction, 2 stencil, 3 SIMT contraction,
  * 4 tensor-core contraction, 5 tensor-core contraction in the precise four-slice
  * configuration; periodic contexts: 6 pseudospectral right-hand side, 7 Fourier multiplier,
- * each several kernels: FFTs and pointwise passes) and the count in *n_ops. Synchronous. ADR_ERR_ARG if the step
+ * 8 whole stage kept in Fourier space (2-D Lawson2a and Lawson-Euler), each several kernels:
+ * FFTs and pointwise passes) and the count in *n_ops. Synchronous. ADR_ERR_ARG if the step
  * has more than max_ops operations. */
 adr_status adr_profile_step(adr_ctx* ctx, void* u_dev, int max_ops, float* ms, int* kind, int* n_ops);
 

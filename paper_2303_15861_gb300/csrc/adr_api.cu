@@ -40,7 +40,8 @@ namespace {
 
 // One enqueued operation of a schedule and the kind of kernel it launches.
 enum OpKind { OP_MEMSET = 0, OP_AMAX = 1, OP_STENCIL = 2, OP_CONTRACT_SIMT = 3, OP_CONTRACT_TC = 4,
-              OP_CONTRACT_TC_PRECISE = 5, OP_PERIODIC_RHS = 6, OP_FOURIER_MULT = 7 };
+              OP_CONTRACT_TC_PRECISE = 5, OP_PERIODIC_RHS = 6, OP_FOURIER_MULT = 7,
+              OP_PERIODIC_STAGE = 8 };
 struct Op {
     std::function<cudaError_t(cudaStream_t)> fn;
     int kind;
@@ -564,29 +565,42 @@ void push_fourier(Sched& S, int mi, const T* x, T* y, const T* base, double alph
     S.ops.push_back(op);
 }
 
-// A fused stage of a 2-D periodic context (see PeriodicStage): multipliers by index into d_pm
-// (-1: none); the Fourier-space array d_pz is read (cz != 0) or written (save_mi >= 0).
+// A fused stage of a 2-D periodic context (see PeriodicStage). Multipliers by index into d_pm
+// (-1: the identity); the Fourier-space array d_pz is read (cgz or cz nonzero) or written (save).
+struct StageSpec {
+    int mu = -1;                     // Mu
+    double cu = 0;
+    int mg = -1;                     // Mg
+    double cgF = 0, cg = 0, cgz = 0, cz = 0;
+    bool save = false;
+    int ms = -1;                     // Ms
+    double zu = 1, zF = 0, zg = 0;
+};
+
 template <typename T>
-void push_periodic_stage(Sched& S, const T* x, T* y, int mu_mi, double cu, int mg_mi, double cgF, double cg, double cz,
-                         int save_mi) {
+void push_periodic_stage(Sched& S, const T* x, T* y, const StageSpec& q) {
     const adr_ctx* c = S.c;
     const auto P = periodic_args<T>(c);
     auto pm = [&](int i) { return i < 0 ? nullptr : static_cast<const adr::Cplx<T>*>(c->d_pm[i]); };
     adr::PeriodicStage<T> st;
     st.x = x;
     st.y = y;
-    st.Mu = pm(mu_mi);
-    st.Mg = pm(mg_mi);
-    st.cu = cu;
-    st.cgF = cgF;
-    st.cg = cg;
-    st.cz = cz;
-    if (cz != 0.0) st.Z = static_cast<const adr::Cplx<T>*>(c->d_pz);
-    if (save_mi >= 0) {
+    st.Mu = pm(q.mu);
+    st.Mg = pm(q.mg);
+    st.cu = q.cu;
+    st.cgF = q.cgF;
+    st.cg = q.cg;
+    st.cgz = q.cgz;
+    st.cz = q.cz;
+    if (q.cgz != 0.0 || q.cz != 0.0) st.Z = static_cast<const adr::Cplx<T>*>(c->d_pz);
+    if (q.save) {
         st.Zs = static_cast<adr::Cplx<T>*>(c->d_pz);
-        st.Ms = pm(save_mi);
+        st.Ms = pm(q.ms);
+        st.zu = q.zu;
+        st.zF = q.zF;
+        st.zg = q.zg;
     }
-    Op op{[P, st](cudaStream_t s) { return adr::launch_periodic_stage(P, st, s); }, OP_PERIODIC_RHS};
+    Op op{[P, st](cudaStream_t s) { return adr::launch_periodic_stage(P, st, s); }, OP_PERIODIC_STAGE};
     op.launches = adr::periodic_stage_launches(c->dim);
     S.ops.push_back(op);
 }
@@ -801,24 +815,60 @@ void push_stencil(Sched& S, StencilArgs<T> s, bool record_input) {
     S.ops.push_back({[s](cudaStream_t st) { return adr::launch_stencil(s, st); }, OP_STENCIL});
 }
 
+// The step of a 2-D periodic context as stages kept in Fourier space from the state's transform
+// to the stage result (see PeriodicStage); false for a scheme without that form (Lawson4 and
+// stabilized Lawson2 keep more than one array between stages). d_pm: 0 e^{tau s/2}, 1 e^{tau s},
+// 3 phi_1(tau s), 4 phi_2(tau s).
+template <typename T>
+bool push_fused_periodic_step(Sched& S, const adr_ctx* c, T* u) {
+    if (!c->periodic || c->dim != 2) return false;
+    constexpr int kEh = 0, kE1 = 1, kPhi1 = 3, kPhi2 = 4;
+    const double tau = c->p.tau;
+    T* B0 = static_cast<T*>(c->ws[0]);
+    StageSpec a, b;
+    switch (c->p.scheme) {
+    case ADR_LAWSON_EULER:                       // u+ = E_1 (u + tau g(u))
+        a.mu = kE1; a.cu = 1.0; a.mg = kE1; a.cgF = a.cg = tau;
+        push_periodic_stage<T>(S, u, u, a);
+        return true;
+    case ADR_STABILIZED_LAWSON_EULER:            // u+ = u + tau E_1 F(u)
+    case ADR_EXPONENTIAL_EULER:                  // u+ = u + tau phi_1 F(u)
+        a.cu = 1.0; a.mg = c->p.scheme == ADR_EXPONENTIAL_EULER ? kPhi1 : kE1; a.cgF = tau;
+        push_periodic_stage<T>(S, u, u, a);
+        return true;
+    case ADR_ETD2RK:                             // U = u + tau phi_1 F(u), Z = g(u)^;
+    case ADR_ERK2P1: {                           // u+ = U + h phi_k (g(U)^ - Z)
+        a.cu = 1.0; a.mg = kPhi1; a.cgF = tau;
+        a.save = true; a.zu = 0.0; a.zF = 1.0; a.zg = 1.0;
+        const bool etd = c->p.scheme == ADR_ETD2RK;
+        const double h = etd ? tau : 0.5 * tau;  // ETD2RK: tau phi_2; erk2p1: tau/2 phi_1
+        b.cu = 1.0; b.mg = etd ? kPhi2 : kPhi1; b.cgF = b.cg = h; b.cgz = -h;
+        break;
+    }
+    case ADR_LAWSON2A:                           // U = E_h (u + tau/2 g(u)), Z = E_1 u^;
+        a.mu = kEh; a.cu = 1.0; a.mg = kEh; a.cgF = a.cg = 0.5 * tau;
+        a.save = true; a.ms = kE1;
+        b.mg = kEh; b.cgF = b.cg = tau; b.cz = 1.0;   // u+ = Z + tau E_h g(U)^
+        break;
+    case ADR_LAWSON2B:                           // U = E_1 (u + tau g(u)), Z = E_1 (u^ + tau/2 g(u)^);
+        a.mu = kE1; a.cu = 1.0; a.mg = kE1; a.cgF = a.cg = tau;
+        a.save = true; a.ms = kE1; a.zF = a.zg = 0.5 * tau;
+        b.cgF = b.cg = 0.5 * tau; b.cz = 1.0;          // u+ = Z + tau/2 g(U)^
+        break;
+    default:
+        return false;
+    }
+    push_periodic_stage<T>(S, u, B0, a);
+    push_periodic_stage<T>(S, B0, u, b);
+    return true;
+}
+
 template <typename T>
 std::vector<Op> build_step(const adr_ctx* c, T* u) {
     Sched S(c);
     S.bind_state(u);
     const double tau = c->p.tau;
-    if (c->periodic && c->dim == 2 && (c->p.scheme == ADR_LAWSON2A || c->p.scheme == ADR_LAWSON_EULER)) {
-        // Stages kept in Fourier space from the state's transform to the stage result (d_pm: 0
-        // e^{tau A/2}, 1 e^{tau A}): Lawson2a U = e^{tau A/2}(u + tau/2 g(u)), saving e^{tau A} u^,
-        // then u+ = e^{tau A} u + tau e^{tau A/2} g(U); Lawson-Euler u+ = e^{tau A}(u + tau g(u)).
-        T* B0 = static_cast<T*>(c->ws[0]);
-        if (c->p.scheme == ADR_LAWSON2A) {
-            push_periodic_stage<T>(S, u, B0, 0, 1.0, 0, 0.5 * tau, 0.5 * tau, 0.0, 1);
-            push_periodic_stage<T>(S, B0, u, -1, 0.0, 0, tau, tau, 1.0, -1);
-        } else {
-            push_periodic_stage<T>(S, u, u, 1, 1.0, 1, tau, tau, 0.0, -1);
-        }
-        return std::move(S.ops);
-    }
+    if (push_fused_periodic_step<T>(S, c, u)) return std::move(S.ops);
     T* B0 = static_cast<T*>(c->ws[0]);
     T* B1 = static_cast<T*>(c->ws[1]);
     T* B2 = static_cast<T*>(c->ws[2]);
@@ -968,6 +1018,7 @@ const char* op_name(int kind) {
     case OP_CONTRACT_TC_PRECISE: return "K2 mu-mode pass (tensor cores, double-float)";
     case OP_PERIODIC_RHS: return "periodic right-hand side (Fourier passes)";
     case OP_FOURIER_MULT: return "Fourier multiplier";
+    case OP_PERIODIC_STAGE: return "periodic stage in Fourier space";
     default: return "op";
     }
 }

@@ -393,10 +393,17 @@ struct PeriodicArgs {
 // One fused stage of a 2-D periodic context, computed in Fourier space from the transform of x
 // to the result y (real): with H = cgF F^(x) - cg s x^ (s the symbol of A; cgF = cg: the
 // remainder g, cg = 0: F),
-//     y = Re F^-1 ( Mu (cu x^) + Mg H + cz Z ),   and, when Zs is set, Zs = Ms x^,
-// where the multipliers Mu, Mg, Ms (NULL: the identity) are Fourier-space arrays and Z a
-// Fourier-space array saved by an earlier stage. Lawson2a: U = E_h (u + tau/2 g(u)) with
-// Zs = E_1 u^; then u+ = Re F^-1 (Z + tau E_h g(U)^). Lawson-Euler: u+ = E_1 (u + tau g(u)).
+//     y = Re F^-1 ( Mu (cu x^) + Mg (H + cgz Z) + cz Z ),
+// and, when Zs is set, Zs = Ms (zu x^ + zF F^(x) - zg s x^), where the multipliers Mu, Mg, Ms
+// (NULL: the identity) are Fourier-space arrays and Z a Fourier-space array saved by an earlier
+// stage (read before Zs is written, so a stage may read and save the same array). With E_h, E_1
+// the multipliers e^{tau s/2}, e^{tau s}:
+//   Lawson2a: U = E_h (u + tau/2 g(u)), Zs = E_1 u^; u+ = Re F^-1 (Z + tau E_h g(U)^).
+//   Lawson2b: U = E_1 (u + tau g(u)), Zs = E_1 (u^ + tau/2 g(u)^); u+ = Re F^-1 (Z + tau/2 g(U)^).
+//   Lawson-Euler u+ = E_1 (u + tau g(u)); stabilized Lawson-Euler u+ = u + tau E_1 F(u);
+//   exponential Euler u+ = u + tau phi_1 F(u).
+//   ETD2RK: U = u + tau phi_1 F(u), Zs = g(u)^; u+ = U + tau phi_2 (g(U)^ - Z); erk2p1 the
+//   same with tau/2 phi_1 in the second stage.
 template <typename T>
 struct PeriodicStage {
     const T* x = nullptr;
@@ -406,7 +413,8 @@ struct PeriodicStage {
     const Cplx<T>* Ms = nullptr;
     const Cplx<T>* Z = nullptr;
     Cplx<T>* Zs = nullptr;
-    double cu = 0, cgF = 0, cg = 0, cz = 0;
+    double cu = 0, cgF = 0, cg = 0, cgz = 0, cz = 0;
+    double zu = 1, zF = 0, zg = 0;
 };
 
 // Sets the shared-memory limits of the Fourier kernels of one precision (once, before any

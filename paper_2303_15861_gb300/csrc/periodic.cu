@@ -23,6 +23,12 @@
 //     x1: D_mu u -> flux f_mu = a_mumu D_mu u + b_mu u -> forward | (x2 fwd) |
 //     pivot: S = sum_mu i k_mu f_mu^, O_j = (cg_j + cF_j) S - cg_j s u^ | (x2 inv) |
 //     x1 inv + out_j = cu_j u + sum_e cx_je X_e + Re O_j + (cg_j + cF_j) r(u).      2-D: 5 kernels
+//   Stage kept in Fourier space (2-D periodic Lawson-Euler, ETD2RK, exponential Euler, erk2p1,
+//   stabilized Lawson-Euler, Lawson2a/2b): the same first three passes, the x1 flux pass also
+//   transforming the pointwise part r(u) into CN; the pivot then forms F^ = S + F_d CN,
+//   H = cgF F^ - cg s u^ and the whole stage Mu (cu u^) + Mg (H + cgz Z) + cz Z, saves
+//   Ms (zu u^ + zF F^ - zg s u^) for a later stage, and transforms back; the last x1 pass
+//   writes y.                                                                           2-D: 5 kernels
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,8 +52,9 @@ enum PassMode {
     PM_FLUX = 5,         // x1: C[mu] = F_1 (a_mu Re F_1^-1 C[mu] + b_mu u)
     PM_PIVOT_DIV = 6,    // S = sum_mu i k_mu F_d C[mu]; C[j] = F_d^-1 (cgF_j S - cg_j M Cu)
     PM_FINAL_OUT = 7,    // x1: out_j = cu_j u + sum cx_je X_e + Re F_1^-1 C[j] + cgF_j r(u)
-    PM_PIVOT_STAGE = 8,  // H = cgF (sum_mu i k_mu F_d C[mu] + F_d CN) - cg s u^;
-                         // C[0] = F_d^-1 (Mu (cu u^) + Mg H + cz Z);  Zs = Ms u^
+    PM_PIVOT_STAGE = 8,  // F^ = sum_mu i k_mu F_d C[mu] + F_d CN, H = cgF F^ - cg s u^;
+                         // C[0] = F_d^-1 (Mu (cu u^) + Mg (H + cgz Z) + cz Z);
+                         // Zs = Ms (zu u^ + zF F^ - zg s u^)
 };
 
 constexpr int kPassThreads = 256;
@@ -90,7 +97,8 @@ struct Pass {
     const Cplx<T>* Ms;
     const Cplx<T>* Z;
     Cplx<T>* Zs;
-    T scu, scgF, scg, scz;
+    T scu, scgF, scg, scgz, scz;
+    T szu, szF, szg;
 };
 
 // Global index of element j of line g of line group grp.
@@ -298,15 +306,20 @@ __global__ void __launch_bounds__(kPassThreads) fourier_pass_kernel(const __grid
             }
             for_elems(P, grp, [&](int o, long long i, int) {
                 const Cplx<T> uh = P.Cu[i];
-                if (P.Zs) P.Zs[i] = P.Ms ? cmul(P.Ms[i], uh) : uh;
+                const Cplx<T> fh = B2[o];
                 const Cplx<T> au = cmul(P.M[i], uh);
-                Cplx<T> h = {P.scgF * B2[o].x - P.scg * au.x, P.scgF * B2[o].y - P.scg * au.y};
+                const Cplx<T> z = P.Z ? P.Z[i] : Cplx<T>{T(0), T(0)};
+                if (P.Zs) {
+                    const Cplx<T> w = {P.szu * uh.x + P.szF * fh.x - P.szg * au.x,
+                                       P.szu * uh.y + P.szF * fh.y - P.szg * au.y};
+                    P.Zs[i] = P.Ms ? cmul(P.Ms[i], w) : w;
+                }
+                Cplx<T> h = {P.scgF * fh.x - P.scg * au.x + P.scgz * z.x,
+                             P.scgF * fh.y - P.scg * au.y + P.scgz * z.y};
                 if (P.Mg) h = cmul(P.Mg[i], h);
                 Cplx<T> v = {P.scu * uh.x, P.scu * uh.y};
                 if (P.Mu) v = cmul(P.Mu[i], v);
-                v = {v.x + h.x, v.y + h.y};
-                if (P.Z) v = {v.x + P.scz * P.Z[i].x, v.y + P.scz * P.Z[i].y};
-                B0[o] = v;
+                B0[o] = {v.x + h.x + P.scz * z.x, v.y + h.y + P.scz * z.y};
             });
             __syncthreads();
             Cplx<T>* R = fft_lines(P, tws, B0, B1, true);
@@ -584,7 +597,11 @@ cudaError_t stage_impl(const PeriodicArgs<T>& A, const PeriodicStage<T>& s, cuda
         P.scu = T(s.cu);
         P.scgF = T(s.cgF);
         P.scg = T(s.cg);
+        P.scgz = T(s.cgz);
         P.scz = T(s.cz);
+        P.szu = T(s.zu);
+        P.szF = T(s.zF);
+        P.szg = T(s.zg);
         if ((e = launch_pass_on<T, PM_PIVOT_STAGE>(P, st)) != cudaSuccess) return e;
     }
     {

@@ -161,18 +161,23 @@ def test_context_facts_and_launch_count():
     assert info["kappa"][:2] == [1.0, 1.0]
     assert info["abar"] == pytest.approx(max(x.max() for x in a))
     assert info["beta"][0] == pytest.approx(b[0].mean()) and info["beta"][1] == pytest.approx(b[1].mean())
-    # 2-D: a right-hand side is 5 fused passes, a Fourier multiplier 3; ETD2RK has 2 of each
-    assert ctx.kernels_per_step() == 2 * 5 + 2 * 3
+    # 2-D: every stage is kept in Fourier space from the state's transform to the stage result,
+    # five passes (instead of a right-hand side of 5 passes and multipliers of 3); Lawson4 and
+    # stabilized Lawson2 keep the right-hand side and multiplier passes
+    assert ctx.kernels_per_step() == 2 * 5
+    ops = ctx.profile_step(dev(w.u0))
+    assert [k for k, _ in ops] == [8, 8]
     w3, L3, a3, b3 = W.periodic_instance((8, 16, 8), scheme="lawson2a")
     ctx3 = context(w3, L3, a3, b3)
     assert ctx3.kernels_per_step() == 2 * 9 + 3 * 5   # 3-D: 9 and 5 passes
-    # 2-D Lawson2a and Lawson-Euler keep each stage in Fourier space from the state's transform
-    # to the stage result: five passes per stage (instead of a right-hand side and multipliers)
-    for scheme, launches in (("lawson2a", 2 * 5), ("lawson_euler", 5)):
+    fused = {"lawson2a": 2, "lawson_euler": 1, "etd2rk": 2, "erk2p1": 2, "exponential_euler": 1,
+             "stabilized_lawson_euler": 1, "lawson2b": 2}
+    for scheme, stages in fused.items():
         w2, L2, a2, b2 = W.periodic_instance((32, 16), scheme=scheme)
-        assert context(w2, L2, a2, b2).kernels_per_step() == launches, scheme
-    ops = ctx.profile_step(dev(w.u0))
-    assert [k for k, _ in ops] == [6, 7, 6, 7]
+        assert context(w2, L2, a2, b2).kernels_per_step() == 5 * stages, scheme
+    w4, L4, a4, b4 = W.periodic_instance((32, 16), scheme="lawson4")
+    c4 = context(w4, L4, a4, b4)
+    assert 8 not in [k for k, _ in c4.profile_step(dev(w4.u0))]
 
 
 def test_periodic_context_refuses_grid_coefficients_and_unset_steps():
@@ -251,6 +256,33 @@ def test_adelta_building_blocks_match_oracle(dims):
     ctx.synchronize()
     assert_parity(host(F), prob.F(w.u0), 1e-11)
     assert_parity(host(g), prob.g(w.u0), 1e-11)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_fp64_schemes_in_the_adelta_form_match_oracle(scheme):
+    """Every scheme in the a Lap u form (the Fourier-space stages then carry the a Lap u product
+    with r(u) in the transformed pointwise part), on a non-square grid, lambda = 0.8."""
+    w, L, a, b = W.periodic_instance((16, 32), scheme=scheme, T=0.1, m=5)
+    ctx = adr.Context(w.dims, w.tau, scheme, "fp64", periodic=True, length=L, form="adelta", lam=0.8)
+    ctx.set_coeffs_periodic(a, b, w.r_poly)
+    u = dev(w.u0)
+    ctx.integrate(u, 0.0, w.m * w.tau, w.m)
+    ctx.synchronize()
+    ref = O.solve_periodic(w.dims, L, a, b, w.r_poly, w.u0, w.tau, w.m, scheme, lam=0.8, form="adelta")
+    assert_parity(host(u), ref, 1e-11, what=scheme)
+
+
+@pytest.mark.parametrize("scheme", ["erk2p1", "lawson2b", "exponential_euler", "stabilized_lawson_euler"])
+def test_fp32_fused_schemes_match_oracle(scheme):
+    """FP32 Fourier-space stages at n = 128 over 32 steps against the FP64 oracle (the FP32
+    bound of the module docstring, on a shorter horizon)."""
+    w, L, a, b = W.config_e3(n=128, scheme=scheme, m=32, T=0.5)
+    ctx = context(w, L, a, b, prec="fp32")
+    u = dev(w.u0, "fp32")
+    ctx.integrate(u, 0.0, w.m * w.tau, w.m)
+    ctx.synchronize()
+    ref = O.solve_periodic(w.dims, L, a, b, w.r_poly, w.u0, w.tau, w.m, scheme)
+    assert_parity(host(u), ref, 1e-4, what=f"fp32 {scheme}")
 
 
 @pytest.mark.parametrize("scheme,lam,m,paper", [("lawson_euler", 1.0, 64, 0.00288149591423319),
