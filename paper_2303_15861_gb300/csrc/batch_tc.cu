@@ -56,7 +56,6 @@ constexpr int kMmaWarp = 12;
 constexpr int kLoadWarp = 13;           // factor tiles: bulk copies, its own ring, running ahead
 constexpr int kThreads = (kLoadWarp + 1) * 32;
 constexpr uint32_t kTmemCols = 512;     // two sets of kNacc x kN columns
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kN >> 3) << 17) | (uint32_t(kM >> 4) << 24);
 static_assert(2 * kNacc * kN <= int(kTmemCols), "TMEM");
 
 template <bool SA>
@@ -213,29 +212,46 @@ __device__ __forceinline__ void load_chunk(const BatchTcArgs& p, const BatchTcIn
     }
 }
 
+// Instruction descriptor of an M = 128 product of N columns (BF16 inputs, FP32 accumulate).
+constexpr uint32_t idesc_n(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(kM >> 4) << 24);
+}
+
+// One K step of 16 of the fourteen products. The accumulators D0..D3 sit in consecutive kN-column
+// blocks of TMEM and the slice tiles of each operand in consecutive shared-memory tiles, so one
+// A slice against r consecutive B slices is one product of r kN columns that adds each pair to
+// its own accumulator: eight MMAs (N = 256, 192, 128 and five of 64) instead of fourteen of
+// N = 64, the same tensor work with less operand traffic from shared memory.
+//   SA (A = state): S0.[F0..F3] -> D0..D3, S1.[F0..F2] -> D1..D3, S2.[F0 F1] -> D2 D3, and into
+//       D3: S1 (2^-8 F3), S2 (2^-8 F2), S3 F0, S3 (2^-8 F1), (2^-8 S4) F0.
+//   mode 1 (A = factor): F0.[S0..S3] -> D0..D3, F1.[S0..S2] -> D1..D3, F2.[S0 S1] -> D2 D3, and
+//       into D3: F0 (2^-8 S4), F3 S0, (2^-8 F1) S3, (2^-8 F2) S2, (2^-8 F3) S1.
 template <bool SA>
 __device__ __forceinline__ void mma_kstep(uint32_t d, const uint64_t (&S)[kSS], const uint64_t (&F)[kFS], uint64_t adv,
                                           uint32_t first) {
-    auto mma = [&](int acc, int si, int fi, uint32_t accumulate) {
-        const uint32_t dd = d + uint32_t(acc * kN);
-        if (SA) tc_mma(dd, S[si] + adv, F[fi] + adv, kIdesc, accumulate);
-        else    tc_mma(dd, F[fi] + adv, S[si] + adv, kIdesc, accumulate);
+    auto mma = [&](int acc, uint64_t a, uint64_t b, int nacc, uint32_t accumulate) {
+        tc_mma(d + uint32_t(acc * kN), a + adv, b + adv, idesc_n(nacc * kN), accumulate);
     };
     const uint32_t acc = first ? 0u : 1u;
-    mma(0, 0, 0, acc);
-    mma(1, 0, 1, acc);
-    mma(1, 1, 0, 1u);
-    mma(2, 0, 2, acc);
-    mma(2, 1, 1, 1u);
-    mma(2, 2, 0, 1u);
-    mma(3, 0, 3, acc);
-    mma(3, 1, 2, 1u);
-    mma(3, 2, 1, 1u);
-    mma(3, 3, 0, 1u);
-    mma(3, 1, 6, 1u);     // S1 (2^-8 F3)
-    mma(3, 2, 5, 1u);     // S2 (2^-8 F2)
-    mma(3, 3, 4, 1u);     // S3 (2^-8 F1)
-    mma(3, 4, 0, 1u);     // (2^-8 S4) F0
+    if (SA) {
+        mma(0, S[0], F[0], 4, acc);
+        mma(1, S[1], F[0], 3, 1u);
+        mma(2, S[2], F[0], 2, 1u);
+        mma(3, S[1], F[6], 1, 1u);
+        mma(3, S[2], F[5], 1, 1u);
+        mma(3, S[3], F[0], 1, 1u);
+        mma(3, S[3], F[4], 1, 1u);
+        mma(3, S[4], F[0], 1, 1u);
+    } else {
+        mma(0, F[0], S[0], 4, acc);
+        mma(1, F[1], S[0], 3, 1u);
+        mma(2, F[2], S[0], 2, 1u);
+        mma(3, F[0], S[4], 1, 1u);
+        mma(3, F[3], S[0], 1, 1u);
+        mma(3, F[4], S[3], 1, 1u);
+        mma(3, F[5], S[2], 1, 1u);
+        mma(3, F[6], S[1], 1, 1u);
+    }
 }
 
 // Load 8 columns of the four accumulators (kN columns apart) for this warp's 32 lanes.

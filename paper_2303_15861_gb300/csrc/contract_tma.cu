@@ -257,13 +257,14 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
 
     if (warp == kLoadWarp) {
         // ------------------------------------------------------------ TMA loader
-        // Fills the factor ring (pre-sliced factor tiles, consumed directly by the MMA; the
-        // slot of item i frees when the MMA of item i - NF retires, so each copy has NF - 1
-        // chunks of lead time) and the FP32 staging ring (state tiles for the producers).
-        if (lane == 0) {
+        // Lane 0 fills the factor ring (pre-sliced factor tiles, consumed directly by the MMA;
+        // the slot of item i frees when the MMA of item i - NF retires, so each copy has NF - 1
+        // chunks of lead time), lane 1 the FP32 staging ring (state tiles for the producers),
+        // each at its own pace: a wait on one ring does not hold back the other.
+        if (lane < 2) {
             for (long long it = 0; it < items && !abort_s; ++it) {
                 const long long tile = tile_of(it);
-                {
+                if (lane == 0) {
                     const int s = int(it % C::NF);
                     const uint32_t ph = uint32_t(it / C::NF) & 1u;
                     if (!mbar_wait(fempty(s), ph ^ 1u, p.err, 64, &abort_s, 32)) break;
@@ -271,9 +272,9 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
                     const uint8_t* src = p.fimg + (size_t(tile % p.nOut) * p.nK + it % p.nK) * C::FBYTES;
                     const uint32_t dst = fbase + s * C::FBYTES;
 #pragma unroll
-                    for (int q = 0; q < C::FS; ++q) bulk_g2s(dst + q * C::TILE, src + q * C::TILE, C::TILE, ffull(s));
+                    bulk_g2s(dst, src, C::FBYTES, ffull(s));
                 }
-                {
+                if (lane == 1) {
                     const int s = int(it % C::NX);
                     const uint32_t ph = uint32_t(it / C::NX) & 1u;
                     if (!mbar_wait(xempty(s), ph ^ 1u, p.err, 16, &abort_s, 32)) break;
@@ -399,8 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
             float* ylo = (EPI == EPI_STORE2) ? p.Ylo + off0 : nullptr;
             const float* brow = (EPI == EPI_AXPY) ? p.base + off0 : nullptr;
             const uint32_t tbase = tmem + (uint32_t(ew * 32) << 16) + uint32_t(a) * 256u;
-            auto emit = [&](int col, float hi, float lo, float bval) {
-                const float scale = SA ? sback * __ldg(fsc + col) : rscale;
+            auto emit = [&](int col, float hi, float lo, float bval, float scale) {
                 const long long o = (long long)col * cstep;
                 if (EPI == EPI_STORE2) {
                     yrow[o] = hi * scale;
@@ -430,24 +430,38 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
                 if (j0 + 8 < jhi) load_base(j0 + 8, bnxt);
                 __syncwarp();
                 tmem_ld8x4(tbase + j0, uint32_t(kN), d);
+                if (j0 + 8 >= jhi) {       // the last columns are in registers: TMEM is free
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(acce(a));
+                }
+                // the column scales of the group (the factor's row scales, padded to whole tiles)
+                float scl8[8];
+                if (SA) {
+                    const float4 s0 = __ldg(reinterpret_cast<const float4*>(fsc + j0));
+                    const float4 s1 = __ldg(reinterpret_cast<const float4*>(fsc + j0 + 4));
+                    scl8[0] = sback * s0.x; scl8[1] = sback * s0.y; scl8[2] = sback * s0.z; scl8[3] = sback * s0.w;
+                    scl8[4] = sback * s1.x; scl8[5] = sback * s1.y; scl8[6] = sback * s1.z; scl8[7] = sback * s1.w;
+                }
                 if (rvalid && j0 < ncol) {
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         if (j0 + j >= ncol) break;
-                        float hi, lo;
-                        two_sum(d[0][j], d[1][j] * 0.00390625f, hi, lo);
-                        lo += fmaf(d[3][j], 5.9604644775390625e-08f, d[2][j] * 1.52587890625e-05f);
-                        const float s = hi + lo;
-                        lo = lo - (s - hi);
-                        emit(j0 + j, s, lo, bcur[j]);
+                        const float tail = fmaf(d[3][j], 5.9604644775390625e-08f, d[2][j] * 1.52587890625e-05f);
+                        if (EPI == EPI_STORE2) {     // double-float result: D0 + 2^-8 D1 exactly, then the tail
+                            float hi, lo;
+                            two_sum(d[0][j], d[1][j] * 0.00390625f, hi, lo);
+                            lo += tail;
+                            const float s = hi + lo;
+                            emit(j0 + j, s, lo - (s - hi), bcur[j], SA ? scl8[j] : rscale);
+                        } else {                     // one FP32 result: the smaller terms first, D0 last
+                            emit(j0 + j, d[0][j] + fmaf(d[1][j], 0.00390625f, tail), 0.f, bcur[j], SA ? scl8[j] : rscale);
+                        }
                     }
                 }
 #pragma unroll
                 for (int j = 0; j < 8; ++j) bcur[j] = bnxt[j];
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acce(a));
             for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
             if (lane == 0 && p.amax_out && vmax > 0.f) atomicMax(p.amax_out, __float_as_uint(vmax));
         }
