@@ -65,12 +65,12 @@ def parse():
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per standard pass of the
-# tensor-core contraction at 256^3, averaged over the three modes of one exponential, from an
-# ncu --set full capture of `python bench.py --ncu-steps 2`. The figure holds only for the
+# tensor-core contraction at 256^3, averaged over the six standard passes of the second step
+# of `python bench.py --ncu-steps 2` (ncu -k regex:tma_contract -s 12 -c 6). The figure holds only for the
 # kernel source it was taken from, identified by the hash below; after any change to that
 # source the bench reports null until the kernel is captured again.
-_TRAFFIC_CAPTURE = {"n": 256, "bytes_per_launch": 86.0e6,
-                    "source_sha256": "5dce18c05144f5a35a1a367e1edbf105b9fe866dd6d432b9fd64561a356a9bdd"}
+_TRAFFIC_CAPTURE = {"n": 256, "bytes_per_launch": 85.9e6,
+                    "source_sha256": "d1e72ff500f5375f5d6e2e9ddd57db5ff11512eafb921b07a675bd3606b7c37e"}
 _TRAFFIC_SOURCES = ("paper_2303_15861_gb300/csrc/contract_tma.cu", "paper_2303_15861_gb300/csrc/tc_common.cuh",
                     "paper_2303_15861_gb300/csrc/host_setup.cpp")
 

@@ -528,9 +528,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_tc_kernel(const __grid_cons
                     if (!mbar_wait(fempty_bar(fs), fph ^ 1u, p.err, 32, &abort_s, 32)) { ok = false; break; }
                     mbar_arrive_expect_tx(ffull_bar(fs), C::FBYTES);
                     const uint8_t* src = img + size_t(c) * C::FBYTES;
-                    const uint32_t dst = fbase + fs * C::FBYTES;
-#pragma unroll
-                    for (int q = 0; q < kFS; ++q) bulk_g2s(dst + q * C::FTILE, src + q * C::FTILE, C::FTILE, ffull_bar(fs));
+                    bulk_g2s(fbase + fs * C::FBYTES, src, C::FBYTES, ffull_bar(fs));   // the seven tiles are contiguous
                 }
             }
         }
