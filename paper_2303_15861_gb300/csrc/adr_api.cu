@@ -756,6 +756,7 @@ template <typename T>
 StencilArgs<T> stencil_base(const adr_ctx* c, const T* u) {
     StencilArgs<T> s;
     s.u = u;
+    s.err = c->d_err;
     s.a = static_cast<const T*>(c->d_a);
     s.apitch = c->apitch;
     s.dim = c->dim;

@@ -105,6 +105,7 @@ struct StencilArgs {
     double cF[kMaxOut] = {0, 0};
     unsigned* amax[kMaxOut] = {nullptr, nullptr};  // optional max|out_j| (float bits)
     unsigned* amax_u = nullptr;                      // optional max|u| over the interior
+    int* err = nullptr;                              // device error word (bounded waits of the TMA form)
 };
 
 // K2 (SIMT): strided batched contraction C[b] = A[b] * B[b] with a fused epilogue.

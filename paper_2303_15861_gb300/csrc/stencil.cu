@@ -472,6 +472,7 @@ cudaError_t launch_impl(const StencilArgs<T>& p, cudaStream_t s) {
         if (aligned) {
             dim3 g4((p.n1 / 4 + 31) / 32, (p.n2 + 7) / 8, p.dim == 3 ? (p.n3 + ZV - 1) / ZV : 1);
             if (p.dim == 3) {
+                if (stencil_tma_usable(p)) return launch_stencil_tma(p, c, needF, s);
                 const int zb = kMarchPlanes;
                 dim3 gm((p.n1 / 4 + 31) / 32, (p.n2 + 7) / 8, (p.n3 + zb - 1) / zb);
                 return launch_march(p, c, needF, zb, gm, s);

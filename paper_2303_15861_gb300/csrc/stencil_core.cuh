@@ -15,6 +15,12 @@ struct Coefs {
     T cu[kMaxOut], cx[kMaxOut][kMaxExtra], cg[kMaxOut], cF[kMaxOut];
 };
 
+// The TMA-staged 3-D FP32 stencil (stencil_tma.cu): whether it takes these arguments (Dirichlet
+// faces, n1 a multiple of 4 and at least 64, n2 at least 16, 16-byte aligned arrays), and its
+// launch.
+bool stencil_tma_usable(const StencilArgs<float>& p);
+cudaError_t launch_stencil_tma(const StencilArgs<float>& p, const Coefs<float>& c, bool needF, cudaStream_t s);
+
 template <typename T>
 __device__ __forceinline__ T absval(T v) { return v < T(0) ? -v : v; }
 

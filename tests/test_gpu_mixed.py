@@ -128,6 +128,8 @@ def test_no_accumulation_bias():
 INTEGRATE = [
     ((64, 64, 64), (10.0, 10.0, 10.0), "lawson4", 0.05, 20, 6e-6),
     ((45, 19, 23), (3.0, -5.0, 8.0), "lawson4", 0.04, 8, 1e-6),
+    # ragged tiles of the TMA-staged stencil (64 x 16 nodes), its low-part form in the last stage
+    ((132, 36, 20), (3.0, -5.0, 8.0), "lawson4", 0.02, 6, 2e-6),
     ((64, 64, 64), (10.0, 10.0, 10.0), "lawson_euler", 0.05, 20, 2e-6),
     ((128, 128), (10.0, 10.0), "lawson4", 0.1, 40, 2e-6),
     ((64, 64), (10.0, 10.0), "etd2rk", 0.1, 30, 1e-5),

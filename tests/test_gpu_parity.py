@@ -57,7 +57,9 @@ def context(dims, tau, scheme, prec, a, b, r):
 
 
 DTYPES = {"fp64": torch.float64, "fp32": torch.float32}
-STENCIL_DIMS = [(32, 32), (37, 29), (33, 33, 33), (45, 19, 23)]
+# the last two take the TMA-staged 3-D kernel (n1 >= 64, n2 >= 16) with ragged tiles in x1 and
+# x2 (tiles of 64 x 16) and a ragged last CTA in x3
+STENCIL_DIMS = [(32, 32), (37, 29), (33, 33, 33), (45, 19, 23), (132, 36, 20), (68, 16, 9)]
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
