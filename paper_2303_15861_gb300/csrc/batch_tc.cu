@@ -468,35 +468,39 @@ __global__ void __launch_bounds__(kThreads, 1) batch_tc_kernel(const __grid_cons
                 if (j0 + 8 < kN) load_ops(j0 + 8, sc_n, op_n);
                 __syncwarp();
                 tmem_ld8x4(tbase + j0, d);
-                if (rvalid && j0 < ncol) {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        if (j0 + j >= ncol) break;
-                        // D0 + 2^-8 D1 + 2^-16 D2 + 2^-24 D3 in double-float arithmetic
-                        float hi, lo;
-                        two_sum(d[0][j], d[1][j] * 0.00390625f, hi, lo);
-                        lo += fmaf(d[3][j], 5.9604644775390625e-08f, d[2][j] * 1.52587890625e-05f);
-                        quick_two_sum(hi, lo, hi, lo);
-                        hi *= sc_c[j];                 // a power of two: exact
-                        lo *= sc_c[j];
-                        const long long o = off0 + (long long)(j0 + j) * cstep;
-                        if (EPI == EPI_PHI) {
-                            df_mul(hi, lo, op_c[j].x, op_c[j].y, hi, lo);
-                        } else if (EPI == EPI_AXPY) {
-                            float th, tl2;
-                            df_mul(ah, al, hi, lo, th, tl2);
-                            df_add(op_c[j].x, op_c[j].y, th, tl2, hi, lo);
-                        }
-                        if (p.Ylo) {
-                            p.Y[o] = hi;
-                            p.Ylo[o] = lo;
-                        } else {
-                            hi = hi + lo;
-                            p.Y[o] = hi;
-                        }
-                        if (p.Yhs) p.Yhs[o] = hi;
-                        vmax = fmaxf(vmax, fabsf(hi));
+                auto combine = [&](int j) {
+                    // D0 + 2^-8 D1 + 2^-16 D2 + 2^-24 D3 in double-float arithmetic
+                    float hi, lo;
+                    two_sum(d[0][j], d[1][j] * 0.00390625f, hi, lo);
+                    lo += fmaf(d[3][j], 5.9604644775390625e-08f, d[2][j] * 1.52587890625e-05f);
+                    quick_two_sum(hi, lo, hi, lo);
+                    hi *= sc_c[j];                 // a power of two: exact
+                    lo *= sc_c[j];
+                    const long long o = off0 + (long long)(j0 + j) * cstep;
+                    if (EPI == EPI_PHI) {
+                        df_mul(hi, lo, op_c[j].x, op_c[j].y, hi, lo);
+                    } else if (EPI == EPI_AXPY) {
+                        float th, tl2;
+                        df_mul(ah, al, hi, lo, th, tl2);
+                        df_add(op_c[j].x, op_c[j].y, th, tl2, hi, lo);
                     }
+                    if (p.Ylo) {
+                        p.Y[o] = hi;
+                        p.Ylo[o] = lo;
+                    } else {
+                        hi = hi + lo;
+                        p.Y[o] = hi;
+                    }
+                    if (p.Yhs) p.Yhs[o] = hi;
+                    vmax = fmaxf(vmax, fabsf(hi));
+                };
+                if (rvalid && j0 + 8 <= ncol) {    // a whole group: no per-column branches
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) combine(j);
+                } else if (rvalid) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (j0 + j < ncol) combine(j);
                 }
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {

@@ -443,21 +443,25 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
                     scl8[0] = sback * s0.x; scl8[1] = sback * s0.y; scl8[2] = sback * s0.z; scl8[3] = sback * s0.w;
                     scl8[4] = sback * s1.x; scl8[5] = sback * s1.y; scl8[6] = sback * s1.z; scl8[7] = sback * s1.w;
                 }
-                if (rvalid && j0 < ncol) {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        if (j0 + j >= ncol) break;
-                        const float tail = fmaf(d[3][j], 5.9604644775390625e-08f, d[2][j] * 1.52587890625e-05f);
-                        if (EPI == EPI_STORE2) {     // double-float result: D0 + 2^-8 D1 exactly, then the tail
-                            float hi, lo;
-                            two_sum(d[0][j], d[1][j] * 0.00390625f, hi, lo);
-                            lo += tail;
-                            const float s = hi + lo;
-                            emit(j0 + j, s, lo - (s - hi), bcur[j], SA ? scl8[j] : rscale);
-                        } else {                     // one FP32 result: the smaller terms first, D0 last
-                            emit(j0 + j, d[0][j] + fmaf(d[1][j], 0.00390625f, tail), 0.f, bcur[j], SA ? scl8[j] : rscale);
-                        }
+                auto combine = [&](int j) {
+                    const float tail = fmaf(d[3][j], 5.9604644775390625e-08f, d[2][j] * 1.52587890625e-05f);
+                    if (EPI == EPI_STORE2) {     // double-float result: D0 + 2^-8 D1 exactly, then the tail
+                        float hi, lo;
+                        two_sum(d[0][j], d[1][j] * 0.00390625f, hi, lo);
+                        lo += tail;
+                        const float s = hi + lo;
+                        emit(j0 + j, s, lo - (s - hi), bcur[j], SA ? scl8[j] : rscale);
+                    } else {                     // one FP32 result: the smaller terms first, D0 last
+                        emit(j0 + j, d[0][j] + fmaf(d[1][j], 0.00390625f, tail), 0.f, bcur[j], SA ? scl8[j] : rscale);
                     }
+                };
+                if (rvalid && j0 + 8 <= ncol) {    // a whole group: no per-column branches
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) combine(j);
+                } else if (rvalid) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (j0 + j < ncol) combine(j);
                 }
 #pragma unroll
                 for (int j = 0; j < 8; ++j) bcur[j] = bnxt[j];
