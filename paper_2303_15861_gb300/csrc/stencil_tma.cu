@@ -75,9 +75,9 @@ __device__ __forceinline__ void f4a(float4 v, float (&o)[4]) {
     o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
 }
 
-template <bool HASLO, int NX, int NOUT>
+template <bool HASLO, bool NEEDF, int NX, int NOUT>
 __global__ void __launch_bounds__(kThreads, HASLO ? 2 : 3) stencil_tma_kernel(const __grid_constant__ StencilMaps m, StencilArgs<float> p,
-                                                               Coefs<float> c, bool needF, int zb) {
+                                                               Coefs<float> c, int zb) {
     using C = SCfg<HASLO, NX>;
     constexpr int kRing = C::RING, kAhead = C::AHEAD;
     extern __shared__ uint8_t smem_raw[];
@@ -150,16 +150,31 @@ __global__ void __launch_bounds__(kThreads, HASLO ? 2 : 3) stencil_tma_kernel(co
     for (int j = 0; j < NOUT; ++j) outabs[j] = 0.f;
     float uabs = 0.f;
 
+    // per-direction weights of the node arithmetic: w1 = (1/2)/h^2 on the face-sum form of the
+    // diffusion, w2 = (b - beta)/(2h) on the centred advection, and for F the constant part
+    // wa = abar/h^2, wb = beta/(2h)
+    float w1[3], w2[3], wa[3], wb[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        w1[d] = 0.5f * c.ih2[d];
+        w2[d] = c.bmb[d] * c.i2h[d];
+        wa[d] = c.abar * c.ih2[d];
+        wb[d] = c.beta[d] * c.i2h[d];
+    }
+    // slots of planes q and q + 1, and the barrier phase of plane q + 1, advanced step by step
+    int slot_q = 1 % kRing, slot_n = 2 % kRing;
+    uint32_t phase_n = uint32_t(2 / kRing) & 1u;
+
     for (int z = z0; ok && z < z1; ++z) {
         const int q = z - z0 + 1;
         // the slot of plane q + 1 + kAhead held plane q - 1, released by the barrier that ended
         // the previous step
         if (t == 0 && issued < nplanes && issued == q + 1 + kAhead) issue(issued++);
-        const bool w = wait_plane(q + 1);
+        const bool w = mbar_wait(bar0 + 8u * uint32_t(slot_n), phase_n, p.err, kErrStencilWait, &abort_s);
         ++waited;
         if (inside && w) {
-            const uint32_t sC = base + uint32_t(q % kRing) * C::SLOT;
-            const uint32_t sP = base + uint32_t((q + 1) % kRing) * C::SLOT;
+            const uint32_t sC = base + uint32_t(slot_q) * C::SLOT;
+            const uint32_t sP = base + uint32_t(slot_n) * C::SLOT;
             // next plane: centre values (staged) and the extra inputs (global, used next step)
             const float4 uP = lds4(sP + o), aP = lds4(sP + kPlaneSlot + o);
             const float4 lP = HASLO ? lds4(sP + C::LO + o) : zero4;
@@ -187,26 +202,46 @@ __global__ void __launch_bounds__(kThreads, HASLO ? 2 : 3) stencil_tma_kernel(co
             float res[NOUT][4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float uk = U[k], lk = L[k], ak = Aa[k];
-                const float dE = (UX[k + 2] - uk) + (LX[k + 2] - lk), dW = (uk - UX[k]) + (lk - LX[k]);
-                const float dN = (UN[k] - uk) + (LN[k] - lk), dS = (uk - US[k]) + (lk - LS[k]);
-                const float dP = (UP[k] - uk) + (LP[k] - lk), dM = (uk - UM[k]) + (lk - LM[k]);
-                const float uF = uk + lk;
+                const float uk = U[k], ak = Aa[k];
+                // one-sided differences (with the low part, the differences of the pairs)
+                float dE = UX[k + 2] - uk, dW = uk - UX[k], dN = UN[k] - uk, dS = uk - US[k], dP = UP[k] - uk,
+                      dM = uk - UM[k], uF = uk;
+                if (HASLO) {
+                    const float lk = L[k];
+                    dE += LX[k + 2] - lk; dW += lk - LX[k]; dN += LN[k] - lk; dS += lk - LS[k];
+                    dP += LP[k] - lk; dM += lk - LM[k]; uF += lk;
+                }
+                // face sums of (a - abar): 2 (a - abar)_C on every face in the a Lap u form
+                const float sE = p.adelta ? ak + ak : ak + AX[k + 2], sW = p.adelta ? ak + ak : ak + AX[k];
+                const float sN = p.adelta ? ak + ak : ak + AN[k], sS = p.adelta ? ak + ak : ak + AS[k];
+                const float sP = p.adelta ? ak + ak : ak + AP[k], sM = p.adelta ? ak + ak : ak + AM[k];
+                // g = sum_mu [w1 (s+ d+ - s- d-) + w2 (d+ + d-)] + r(u)
+                float g = fmaf(uF, fmaf(uF, fmaf(uF, c.r3, c.r2), c.r1), c.r0);
+                g = fmaf(w1[0], fmaf(-sW, dW, sE * dE), g);
+                g = fmaf(w2[0], dE + dW, g);
+                g = fmaf(w1[1], fmaf(-sS, dS, sN * dN), g);
+                g = fmaf(w2[1], dN + dS, g);
+                g = fmaf(w1[2], fmaf(-sM, dM, sP * dP), g);
+                g = fmaf(w2[2], dP + dM, g);
                 float F = 0.f;
-                const float g = p.adelta
-                    ? stencil_core<float, 3>(c, uF, dE, dW, dN, dS, dP, dM, ak + ak, ak + ak, ak + ak, ak + ak, ak + ak,
-                                             ak + ak, needF, F)
-                    : stencil_core<float, 3>(c, uF, dE, dW, dN, dS, dP, dM, ak + AX[k + 2], ak + AX[k], ak + AN[k],
-                                             ak + AS[k], ak + AP[k], ak + AM[k], needF, F);
+                if (NEEDF) {          // F = g + A u: abar times the second differences, beta the first
+                    F = fmaf(wa[0], dE - dW, g);
+                    F = fmaf(wb[0], dE + dW, F);
+                    F = fmaf(wa[1], dN - dS, F);
+                    F = fmaf(wb[1], dN + dS, F);
+                    F = fmaf(wa[2], dP - dM, F);
+                    F = fmaf(wb[2], dP + dM, F);
+                }
                 uabs = fmaxf(uabs, fabsf(uF));
 #pragma unroll
                 for (int j = 0; j < NOUT; ++j) {
-                    float v = c.cu[j] * uF + c.cg[j] * g + c.cF[j] * F;
+                    float v = fmaf(c.cg[j], g, c.cu[j] * uF);
+                    if (NEEDF) v = fmaf(c.cF[j], F, v);
 #pragma unroll
                     for (int e = 0; e < NX; ++e) {
                         float xe4[4];
                         f4a(xC[e], xe4);
-                        v += c.cx[j][e] * xe4[k];
+                        v = fmaf(c.cx[j][e], xe4[k], v);
                     }
                     res[j][k] = v;
                 }
@@ -219,6 +254,11 @@ __global__ void __launch_bounds__(kThreads, HASLO ? 2 : 3) stencil_tma_kernel(co
             uM = uC; uC = uP; lM = lC; lC = lP; aM = aC; aC = aP;
 #pragma unroll
             for (int e = 0; e < NX; ++e) xC[e] = xP[e];
+        }
+        slot_q = slot_n;
+        if (++slot_n == kRing) {
+            slot_n = 0;
+            phase_n ^= 1u;
         }
         // every thread is done with plane q: its slot may be refilled (and a timed-out wait ends
         // the walk for the whole CTA)
@@ -271,17 +311,17 @@ bool encode3(CUtensorMap* m, const float* x, long long d0, long long p0, long lo
 
 int g_sm_count = 0;
 
-template <bool HASLO, int NX, int NOUT>
-cudaError_t launch_variant(const StencilMaps& maps, const StencilArgs<float>& p, const Coefs<float>& c, bool needF,
+template <bool HASLO, bool NEEDF, int NX, int NOUT>
+cudaError_t launch_variant(const StencilMaps& maps, const StencilArgs<float>& p, const Coefs<float>& c,
                            cudaStream_t s) {
     using C = SCfg<HASLO, NX>;
     static int occ = -1;                       // resident CTAs per SM of this variant
     if (occ < 0) {
-        cudaError_t e = cudaFuncSetAttribute(stencil_tma_kernel<HASLO, NX, NOUT>,
+        cudaError_t e = cudaFuncSetAttribute(stencil_tma_kernel<HASLO, NEEDF, NX, NOUT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
         if (e != cudaSuccess) return e;
         int b = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stencil_tma_kernel<HASLO, NX, NOUT>, kThreads, C::SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stencil_tma_kernel<HASLO, NEEDF, NX, NOUT>, kThreads, C::SMEM);
         if (e != cudaSuccess) return e;
         occ = b > 0 ? b : 1;
     }
@@ -292,15 +332,16 @@ cudaError_t launch_variant(const StencilMaps& maps, const StencilArgs<float>& p,
     if (nz > p.n3) nz = p.n3;
     const int zb = (p.n3 + nz - 1) / nz;
     dim3 grid(unsigned(gx), unsigned(gy), unsigned((p.n3 + zb - 1) / zb));
-    stencil_tma_kernel<HASLO, NX, NOUT><<<grid, kThreads, C::SMEM, s>>>(maps, p, c, needF, zb);
+    stencil_tma_kernel<HASLO, NEEDF, NX, NOUT><<<grid, kThreads, C::SMEM, s>>>(maps, p, c, zb);
     return cudaGetLastError();
 }
 
 template <bool HASLO, int NX>
 cudaError_t launch_nout(const StencilMaps& maps, const StencilArgs<float>& p, const Coefs<float>& c, bool needF,
                         cudaStream_t s) {
-    return p.nout == 1 ? launch_variant<HASLO, NX, 1>(maps, p, c, needF, s)
-                       : launch_variant<HASLO, NX, 2>(maps, p, c, needF, s);
+    if (needF)
+        return p.nout == 1 ? launch_variant<HASLO, true, NX, 1>(maps, p, c, s) : launch_variant<HASLO, true, NX, 2>(maps, p, c, s);
+    return p.nout == 1 ? launch_variant<HASLO, false, NX, 1>(maps, p, c, s) : launch_variant<HASLO, false, NX, 2>(maps, p, c, s);
 }
 
 template <bool HASLO>
