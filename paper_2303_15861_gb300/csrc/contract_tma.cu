@@ -11,7 +11,8 @@
 //
 // Tiles. Modes >= 2 (state is A): a position tile is 128 consecutive q of one p (the state
 // seen as [P][n][Q]); mode 1 (state is B): 128 consecutive fibres. Output tiles are 128 rows
-// of the factor. Warps: 0-7 producers, 8-15 epilogue, 16 MMA issuer, 17 TMA and factor loader.
+// of the factor. Warps: 0-7 producers, then 8 (16 with the low part) epilogue warps, the MMA
+// issuer and the TMA and factor loader.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -29,11 +30,7 @@ constexpr int kM = 128;          // UMMA M, TMEM lanes
 constexpr int kN = 128;          // UMMA N
 constexpr int kKc = 32;          // K per stage: one 64-byte bf16 row (64-byte swizzle)
 constexpr int kProducerWarps = 8;
-constexpr int kEpiWarp0 = 8;      // warps 8-15: two per TMEM lane quarter, each half the columns
-constexpr int kEpiWarps = 8;
-constexpr int kMmaWarp = 16;
-constexpr int kLoadWarp = 17;
-constexpr int kThreads = 18 * 32;
+constexpr int kEpiWarp0 = 8;      // epilogue warps from 8: their TMEM lane quarter is warp % 4
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kN >> 3) << 17) | (uint32_t(kM >> 4) << 24);
 constexpr uint32_t kIdesc2 = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t((2 * kN) >> 3) << 17) |
@@ -69,6 +66,14 @@ struct Cfg {
     static constexpr int XSTAGE = PR ? 2 * XTILE : XTILE;   // hi (+ lo)
     static constexpr int NX = 2;
     static constexpr int SMEM = NSLICE * SBYTES + NF * FBYTES + NX * XSTAGE + 1024;
+    // warps: producers 0-7, then the epilogue (two per TMEM lane quarter, each half the columns;
+    // four per quarter in the double-float configuration, whose epilogue is the longer), the MMA
+    // issuer and the loader
+    static constexpr int EPIW = PR ? 16 : 8;
+    static constexpr int MMAW = kEpiWarp0 + EPIW;
+    static constexpr int LOADW = MMAW + 1;
+    static constexpr int THREADS = (LOADW + 1) * 32;
+    static constexpr int COLS = kN / (EPIW / 4);           // columns per epilogue warp
     static_assert(NACC * kN * NSETS <= 512, "TMEM");
     static_assert(SMEM <= 227 * 1024, "shared memory budget");
 };
@@ -184,7 +189,7 @@ __device__ __forceinline__ void mma_kstep(uint32_t d, const uint64_t (&S)[4], co
 }
 
 template <bool SA, bool PR, int EPI>
-__global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_constant__ TmaArgs p) {
+__global__ void __launch_bounds__(Cfg<PR>::THREADS, 1) tma_contract_kernel(const __grid_constant__ TmaArgs p) {
     using C = Cfg<PR>;
     extern __shared__ uint8_t smem_raw[];
     // barriers: xfull[NX] xempty[NX] sfull[NSLICE] sempty[NSLICE] ffull[NF] fempty[NF] accf[2] acce[2] drain
@@ -225,13 +230,13 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(accf(a), 1);
-            mbar_init(acce(a), kEpiWarps);                  // one arrival per epilogue warp
+            mbar_init(acce(a), C::EPIW);                    // one arrival per epilogue warp
         }
         mbar_init(drain_bar, 1);
         abort_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == kMmaWarp) {
+    if (warp == C::MMAW) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
                      "r"(kTmemCols)
                      : "memory");
@@ -255,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
     // tile -> (position tile, output tile); position tile -> (p, q0) or fibre f0
     auto tile_of = [&](long long it) { return blockIdx.x + (it / p.nK) * gridDim.x; };
 
-    if (warp == kLoadWarp) {
+    if (warp == C::LOADW) {
         // ------------------------------------------------------------ TMA loader
         // Lane 0 fills the factor ring (pre-sliced factor tiles, consumed directly by the MMA;
         // the slot of item i frees when the MMA of item i - NF retires, so each copy has NF - 1
@@ -356,10 +361,10 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
             __syncwarp();
             if (lane == 0) mbar_arrive(sfull(ss));
         }
-    } else if (warp < kEpiWarp0 + kEpiWarps) {
+    } else if (warp < kEpiWarp0 + C::EPIW) {
         // ------------------------------------------------------------ epilogue
         const int ew = (warp - kEpiWarp0) & 3;          // TMEM lane quarter (warp % 4)
-        const int half = (warp - kEpiWarp0) >> 2;       // column half
+        const int part = (warp - kEpiWarp0) >> 2;       // column part
         const int row = ew * 32 + lane;
         long long tl = 0;
         for (long long tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, ++tl) {
@@ -421,7 +426,7 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
                 for (int j = 0; j < 8; ++j)
                     b[j] = (EPI == EPI_AXPY && rvalid && j0 + j < ncol) ? __ldg(brow + (long long)(j0 + j) * cstep) : 0.f;
             };
-            const int jlo = half * (kN / 2), jhi = jlo + kN / 2;
+            const int jlo = part * C::COLS, jhi = jlo + C::COLS;
             float bcur[8], bnxt[8];
             load_base(jlo, bcur);
 #pragma unroll 1
@@ -469,8 +474,8 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
             for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
             if (lane == 0 && p.amax_out && vmax > 0.f) atomicMax(p.amax_out, __float_as_uint(vmax));
         }
-    } else if (warp == kMmaWarp && lane == 0) {
-        // ------------------------------------------------------------ MMA issuer (warp 12)
+    } else if (warp == C::MMAW && lane == 0) {
+        // ------------------------------------------------------------ MMA issuer
         long long g = 0, tl = 0;
         for (long long tile = blockIdx.x; tile < p.ntiles && !abort_s; tile += gridDim.x, ++tl) {
             const int a = int(tl % C::NSETS);
@@ -511,7 +516,7 @@ __global__ void __launch_bounds__(kThreads, 1) tma_contract_kernel(const __grid_
 
     tc_fence_before();
     __syncthreads();
-    if (warp == kMmaWarp) {
+    if (warp == C::MMAW) {
         __syncwarp();
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
@@ -529,7 +534,7 @@ cudaError_t launch_variant(const TmaArgs& a, unsigned grid, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    tma_contract_kernel<SA, PR, EPI><<<grid, kThreads, Cfg<PR>::SMEM, s>>>(a);
+    tma_contract_kernel<SA, PR, EPI><<<grid, Cfg<PR>::THREADS, Cfg<PR>::SMEM, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -2,7 +2,7 @@
 // staged in shared memory by TMA (cp.async.bulk.tensor) instead of loaded into registers.
 //
 // A CTA owns a tile of 64 x1 nodes x 16 x2 rows and walks zb planes of x3. One thread stages each
-// plane of u (with its low part) and of a into a ring of 5 or 6 slots, 3 or 4 planes beyond the one
+// plane of u (with its low part) and of a into a ring of 4 to 6 slots, 2 to 4 planes beyond the one
 // the current step needs, so the loads of several planes are in flight while a plane is computed:
 // memory latency is covered by the ring, not by registers or warps. The staged planes carry a halo
 // of one x2 row on each side and four x1 nodes (TMA copies start at x1 offsets that are multiples
@@ -42,11 +42,12 @@ struct StencilMaps {
     CUtensorMap u, lo, a;
 };
 
-// Ring depth per variant: as deep as the shared memory of the CTAs an SM holds allows (four CTAs
-// without extra inputs, three with, two with the low part; each step keeps planes z and z + 1).
+// Ring depth per variant: as deep as the shared memory of three CTAs per SM allows (each step keeps
+// planes z and z + 1). With the low part, a ring of 4 keeps three CTAs per SM (the register cap
+// of three CTAs spills a few values there, and is still faster than two CTAs with a deeper ring).
 template <bool HASLO, int NX>
 struct SCfg {
-    static constexpr int RING = HASLO ? 6 : (NX == 0 ? 5 : 6);
+    static constexpr int RING = HASLO ? 4 : (NX == 0 ? 5 : 6);
     static constexpr int AHEAD = RING - 2;                               // planes in flight beyond z + 1
     static constexpr uint32_t LO = 2 * kPlaneSlot;                       // offset of the low part
     static constexpr uint32_t SLOT = (HASLO ? 3 : 2) * kPlaneSlot;
@@ -76,7 +77,7 @@ __device__ __forceinline__ void f4a(float4 v, float (&o)[4]) {
 }
 
 template <bool HASLO, bool NEEDF, int NX, int NOUT>
-__global__ void __launch_bounds__(kThreads, HASLO ? 2 : 3) stencil_tma_kernel(const __grid_constant__ StencilMaps m, StencilArgs<float> p,
+__global__ void __launch_bounds__(kThreads, 3) stencil_tma_kernel(const __grid_constant__ StencilMaps m, StencilArgs<float> p,
                                                                Coefs<float> c, int zb) {
     using C = SCfg<HASLO, NX>;
     constexpr int kRing = C::RING, kAhead = C::AHEAD;
