@@ -2,16 +2,18 @@
 // staged in shared memory by TMA (cp.async.bulk.tensor) instead of loaded into registers.
 //
 // A CTA owns a tile of 64 x1 nodes x 16 x2 rows and walks zb planes of x3. One thread stages each
-// plane of u (with its low part) and of a into a ring of 4 to 6 slots, 2 to 4 planes beyond the one
-// the current step needs, so the loads of several planes are in flight while a plane is computed:
-// memory latency is covered by the ring, not by registers or warps. The staged planes carry a halo
-// of one x2 row on each side and four x1 nodes (TMA copies start at x1 offsets that are multiples
-// of 16 bytes); copies that reach past the grid read zeros, which are the Dirichlet ghosts of u,
-// while a carries its own boundary ring. Every thread computes 4 consecutive x1 nodes of one row:
-// the centre values of planes z - 1, z, z + 1 rotate in registers (each plane's centre is read
-// from shared memory once), the in-plane neighbours come from the staged plane z, and the extra
-// stage inputs (no halo) are read from global memory one plane ahead. The arithmetic is that of
-// the marching kernel, and the results are stored with 16-byte stores.
+// plane of u (with its low part), of a and of the extra stage inputs into a ring of 4 to 6 slots,
+// 2 to 4 planes beyond the one the current step needs, so the loads of several planes are in
+// flight while a plane is computed: memory latency is covered by the ring, not by registers or
+// warps. The staged planes of u and a carry a halo of one x2 row on each side and four x1 nodes
+// (TMA copies start at x1 offsets that are multiples of 16 bytes); copies that reach past the grid
+// read zeros, which are the Dirichlet ghosts of u, while a carries its own boundary ring. Every
+// thread computes 4 consecutive x1 nodes of one row: the centre values of planes z - 1, z, z + 1
+// rotate in registers (each plane's centre is read from shared memory once), the in-plane
+// neighbours and the extra inputs come from the staged plane z (with the low part, whose slots are
+// larger, the extra inputs are read from global memory one plane ahead instead). The node
+// arithmetic is that of stencil_core.cuh with the per-direction weights folded, and the results
+// are stored with 16-byte stores.
 //
 // Bounded waits: a plane that does not arrive within the wait limit records an error code in the
 // context's error word and ends the CTA (after waiting, again bounded, for its copies in flight).
@@ -35,22 +37,29 @@ constexpr int kHX = kTX + 8;                             // staged row: 4 halo n
 constexpr int kHY = kTY + 2;                             // staged rows: 1 halo row on each side
 constexpr uint32_t kPlaneBytes = kHX * kHY * 4;          // one staged plane of u, its low part or a
 constexpr uint32_t kPlaneSlot = (kPlaneBytes + 127u) / 128u * 128u;
+constexpr uint32_t kXBytes = kTX * kTY * 4;              // one staged plane of an extra input
+constexpr uint32_t kCtaSmem = 75u * 1024u;               // shared memory of one of three CTAs per SM
 constexpr int kMaxRing = 6;
 constexpr int kErrStencilWait = 0x40;
 
 struct StencilMaps {
-    CUtensorMap u, lo, a;
+    CUtensorMap u, lo, a, x[kMaxExtra];
 };
 
-// Ring depth per variant: as deep as the shared memory of three CTAs per SM allows (each step keeps
-// planes z and z + 1). With the low part, a ring of 4 keeps three CTAs per SM (the register cap
-// of three CTAs spills a few values there, and is still faster than two CTAs with a deeper ring).
+// Slot layout and ring depth per variant: the extra stage inputs are staged with the plane (XS)
+// except with the low part, whose slots are larger; the ring is as deep as the shared memory of
+// three CTAs per SM allows (each step keeps planes z and z + 1). With the low part the register
+// cap of three CTAs spills a few values, which is still faster than two CTAs with a deeper ring.
 template <bool HASLO, int NX>
 struct SCfg {
-    static constexpr int RING = HASLO ? 4 : (NX == 0 ? 5 : 6);
-    static constexpr int AHEAD = RING - 2;                               // planes in flight beyond z + 1
+    static constexpr bool XS = !HASLO && NX > 0;
     static constexpr uint32_t LO = 2 * kPlaneSlot;                       // offset of the low part
-    static constexpr uint32_t SLOT = (HASLO ? 3 : 2) * kPlaneSlot;
+    static constexpr uint32_t XO = (HASLO ? 3 : 2) * kPlaneSlot;         // offset of the extra inputs
+    static constexpr uint32_t SLOT = XO + (XS ? NX * kXBytes : 0u);
+    static constexpr int FIT = int((kCtaSmem - 256u) / SLOT);
+    static constexpr int RING = FIT < kMaxRing ? FIT : kMaxRing;
+    static constexpr int AHEAD = RING - 2;                               // planes in flight beyond z + 1
+    static_assert(RING >= 3, "ring");
     static constexpr uint32_t SMEM = RING * SLOT + 128;
     static_assert(RING <= kMaxRing, "barrier array");
 };
@@ -109,10 +118,15 @@ __global__ void __launch_bounds__(kThreads, 3) stencil_tma_kernel(const __grid_c
         const int pz = z0 - 1 + q;
         const uint32_t slot = base + uint32_t(q % kRing) * C::SLOT;
         const uint32_t bar = bar0 + 8u * uint32_t(q % kRing);
-        mbar_arrive_expect_tx(bar, (HASLO ? 3u : 2u) * kPlaneBytes);
+        const bool withx = C::XS && pz >= z0 && pz < z1;
+        mbar_arrive_expect_tx(bar, (HASLO ? 3u : 2u) * kPlaneBytes + (withx ? uint32_t(NX) * kXBytes : 0u));
         tma_load_3d(slot, &m.u, i1_0 - 4, i2_0 - 1, pz, bar);
         tma_load_3d(slot + kPlaneSlot, &m.a, i1_0, i2_0, pz + 1, bar);     // a: interior x1 at +4, x2 at +1
         if (HASLO) tma_load_3d(slot + C::LO, &m.lo, i1_0 - 4, i2_0 - 1, pz, bar);
+        if (withx) {
+#pragma unroll
+            for (int e = 0; e < NX; ++e) tma_load_3d(slot + C::XO + e * kXBytes, &m.x[e], i1_0, i2_0, pz, bar);
+        }
     };
     auto wait_plane = [&](int q) {
         return mbar_wait(bar0 + 8u * uint32_t(q % kRing), uint32_t(q / kRing) & 1u, p.err, kErrStencilWait, &abort_s);
@@ -124,6 +138,7 @@ __global__ void __launch_bounds__(kThreads, 3) stencil_tma_kernel(const __grid_c
     }
     // offset of the thread's 4 nodes in a staged plane (row ty + 1, column 4 + 4 tx)
     const uint32_t o = uint32_t(((ty + 1) * kHX + 4 + 4 * tx) * 4);
+    const uint32_t ox = uint32_t((ty * kTX + 4 * tx) * 4);        // the same nodes in a staged extra input
     constexpr uint32_t kRow = kHX * 4;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
 
@@ -139,8 +154,10 @@ __global__ void __launch_bounds__(kThreads, 3) stencil_tma_kernel(const __grid_c
         uM = lds4(s0 + o); aM = lds4(s0 + kPlaneSlot + o);
         uC = lds4(s1 + o); aC = lds4(s1 + kPlaneSlot + o);
         if (HASLO) { lM = lds4(s0 + C::LO + o); lC = lds4(s1 + C::LO + o); }
+        if (!C::XS) {
 #pragma unroll
-        for (int e = 0; e < NX; ++e) xC[e] = *reinterpret_cast<const float4*>(p.X[e] + z0 * plane_u + row_u);
+            for (int e = 0; e < NX; ++e) xC[e] = *reinterpret_cast<const float4*>(p.X[e] + z0 * plane_u + row_u);
+        }
     }
     // plane 0's slot is refilled in the first step: everyone has read it
     ok = !__syncthreads_or(!ok);
@@ -176,10 +193,14 @@ __global__ void __launch_bounds__(kThreads, 3) stencil_tma_kernel(const __grid_c
         if (inside && w) {
             const uint32_t sC = base + uint32_t(slot_q) * C::SLOT;
             const uint32_t sP = base + uint32_t(slot_n) * C::SLOT;
-            // next plane: centre values (staged) and the extra inputs (global, used next step)
+            // next plane: centre values (staged); the extra inputs of this plane (staged), or of the
+            // next one from global memory (used next step)
             const float4 uP = lds4(sP + o), aP = lds4(sP + kPlaneSlot + o);
             const float4 lP = HASLO ? lds4(sP + C::LO + o) : zero4;
-            if (z + 1 < z1) {
+            if (C::XS) {
+#pragma unroll
+                for (int e = 0; e < NX; ++e) xC[e] = lds4(sC + C::XO + e * kXBytes + ox);
+            } else if (z + 1 < z1) {
 #pragma unroll
                 for (int e = 0; e < NX; ++e) xP[e] = *reinterpret_cast<const float4*>(p.X[e] + (z + 1) * plane_u + row_u);
             }
@@ -253,8 +274,10 @@ __global__ void __launch_bounds__(kThreads, 3) stencil_tma_kernel(const __grid_c
                 outabs[j] = fmaxf(outabs[j], fmaxf(fmaxf(fabsf(res[j][0]), fabsf(res[j][1])), fmaxf(fabsf(res[j][2]), fabsf(res[j][3]))));
             }
             uM = uC; uC = uP; lM = lC; lC = lP; aM = aC; aC = aP;
+            if (!C::XS) {
 #pragma unroll
-            for (int e = 0; e < NX; ++e) xC[e] = xP[e];
+                for (int e = 0; e < NX; ++e) xC[e] = xP[e];
+            }
         }
         slot_q = slot_n;
         if (++slot_n == kRing) {
@@ -385,6 +408,9 @@ cudaError_t launch_stencil_tma(const StencilArgs<float>& p, const Coefs<float>& 
               encode3(&maps.a, p.a, p.apitch, p.apitch, n2 + 2, n3 + 2, kHX, kHY);
     maps.lo = maps.u;
     if (ok && p.u_lo) ok = encode3(&maps.lo, p.u_lo, n1, n1, n2, n3, kHX, kHY);
+    for (int e = 0; e < kMaxExtra; ++e) maps.x[e] = maps.u;
+    if (!p.u_lo)          // the extra inputs are staged only without the low part
+        for (int e = 0; ok && e < p.nx; ++e) ok = encode3(&maps.x[e], p.X[e], n1, n1, n2, n3, kTX, kTY);
     if (!ok) return cudaErrorInvalidValue;
     return p.u_lo ? launch_nx<true>(maps, p, c, needF, s) : launch_nx<false>(maps, p, c, needF, s);
 }
