@@ -10,8 +10,9 @@
 // read zeros, which are the Dirichlet ghosts of u, while a carries its own boundary ring. Every
 // thread computes 4 consecutive x1 nodes of one row: the centre values of planes z - 1, z, z + 1
 // rotate in registers (each plane's centre is read from shared memory once), the in-plane
-// neighbours and the extra inputs come from the staged plane z (with the low part, whose slots are
-// larger, the extra inputs are read from global memory one plane ahead instead). The node
+// neighbours and the extra inputs come from the staged plane z (where slots with all three extra
+// inputs and the low part would not fit, the extra inputs are read from global memory one plane
+// ahead instead). The node
 // arithmetic is that of stencil_core.cuh with the per-direction weights folded, and the results
 // are stored with 16-byte stores.
 //
@@ -47,12 +48,13 @@ struct StencilMaps {
 };
 
 // Slot layout and ring depth per variant: the extra stage inputs are staged with the plane (XS)
-// except with the low part, whose slots are larger; the ring is as deep as the shared memory of
-// three CTAs per SM allows (each step keeps planes z and z + 1). With the low part the register
-// cap of three CTAs spills a few values, which is still faster than two CTAs with a deeper ring.
+// wherever a ring of at least 3 slots of that size fits the shared memory of three CTAs per SM
+// (otherwise they are read from global memory one plane ahead); the ring is as deep as that
+// shared memory allows (each step keeps planes z and z + 1). With the low part the register cap
+// of three CTAs spills a few values, which is still faster than two CTAs with a deeper ring.
 template <bool HASLO, int NX>
 struct SCfg {
-    static constexpr bool XS = !HASLO && NX > 0;
+    static constexpr bool XS = NX > 0 && (kCtaSmem - 256u) / ((HASLO ? 3 : 2) * kPlaneSlot + NX * kXBytes) >= 3;
     static constexpr uint32_t LO = 2 * kPlaneSlot;                       // offset of the low part
     static constexpr uint32_t XO = (HASLO ? 3 : 2) * kPlaneSlot;         // offset of the extra inputs
     static constexpr uint32_t SLOT = XO + (XS ? NX * kXBytes : 0u);
@@ -85,7 +87,7 @@ __device__ __forceinline__ void f4a(float4 v, float (&o)[4]) {
     o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
 }
 
-template <bool HASLO, bool NEEDF, int NX, int NOUT>
+template <bool HASLO, bool NEEDF, bool ADELTA, int NX, int NOUT>
 __global__ void __launch_bounds__(kThreads, 3) stencil_tma_kernel(const __grid_constant__ StencilMaps m, StencilArgs<float> p,
                                                                Coefs<float> c, int zb) {
     using C = SCfg<HASLO, NX>;
@@ -234,9 +236,9 @@ __global__ void __launch_bounds__(kThreads, 3) stencil_tma_kernel(const __grid_c
                     dP += LP[k] - lk; dM += lk - LM[k]; uF += lk;
                 }
                 // face sums of (a - abar): 2 (a - abar)_C on every face in the a Lap u form
-                const float sE = p.adelta ? ak + ak : ak + AX[k + 2], sW = p.adelta ? ak + ak : ak + AX[k];
-                const float sN = p.adelta ? ak + ak : ak + AN[k], sS = p.adelta ? ak + ak : ak + AS[k];
-                const float sP = p.adelta ? ak + ak : ak + AP[k], sM = p.adelta ? ak + ak : ak + AM[k];
+                const float sE = ADELTA ? ak + ak : ak + AX[k + 2], sW = ADELTA ? ak + ak : ak + AX[k];
+                const float sN = ADELTA ? ak + ak : ak + AN[k], sS = ADELTA ? ak + ak : ak + AS[k];
+                const float sP = ADELTA ? ak + ak : ak + AP[k], sM = ADELTA ? ak + ak : ak + AM[k];
                 // g = sum_mu [w1 (s+ d+ - s- d-) + w2 (d+ + d-)] + r(u)
                 float g = fmaf(uF, fmaf(uF, fmaf(uF, c.r3, c.r2), c.r1), c.r0);
                 g = fmaf(w1[0], fmaf(-sW, dW, sE * dE), g);
@@ -335,17 +337,17 @@ bool encode3(CUtensorMap* m, const float* x, long long d0, long long p0, long lo
 
 int g_sm_count = 0;
 
-template <bool HASLO, bool NEEDF, int NX, int NOUT>
+template <bool HASLO, bool NEEDF, bool ADELTA, int NX, int NOUT>
 cudaError_t launch_variant(const StencilMaps& maps, const StencilArgs<float>& p, const Coefs<float>& c,
                            cudaStream_t s) {
     using C = SCfg<HASLO, NX>;
     static int occ = -1;                       // resident CTAs per SM of this variant
     if (occ < 0) {
-        cudaError_t e = cudaFuncSetAttribute(stencil_tma_kernel<HASLO, NEEDF, NX, NOUT>,
+        cudaError_t e = cudaFuncSetAttribute(stencil_tma_kernel<HASLO, NEEDF, ADELTA, NX, NOUT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
         if (e != cudaSuccess) return e;
         int b = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stencil_tma_kernel<HASLO, NEEDF, NX, NOUT>, kThreads, C::SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stencil_tma_kernel<HASLO, NEEDF, ADELTA, NX, NOUT>, kThreads, C::SMEM);
         if (e != cudaSuccess) return e;
         occ = b > 0 ? b : 1;
     }
@@ -356,16 +358,24 @@ cudaError_t launch_variant(const StencilMaps& maps, const StencilArgs<float>& p,
     if (nz > p.n3) nz = p.n3;
     const int zb = (p.n3 + nz - 1) / nz;
     dim3 grid(unsigned(gx), unsigned(gy), unsigned((p.n3 + zb - 1) / zb));
-    stencil_tma_kernel<HASLO, NEEDF, NX, NOUT><<<grid, kThreads, C::SMEM, s>>>(maps, p, c, zb);
+    stencil_tma_kernel<HASLO, NEEDF, ADELTA, NX, NOUT><<<grid, kThreads, C::SMEM, s>>>(maps, p, c, zb);
     return cudaGetLastError();
 }
 
 template <bool HASLO, int NX>
 cudaError_t launch_nout(const StencilMaps& maps, const StencilArgs<float>& p, const Coefs<float>& c, bool needF,
                         cudaStream_t s) {
-    if (needF)
-        return p.nout == 1 ? launch_variant<HASLO, true, NX, 1>(maps, p, c, s) : launch_variant<HASLO, true, NX, 2>(maps, p, c, s);
-    return p.nout == 1 ? launch_variant<HASLO, false, NX, 1>(maps, p, c, s) : launch_variant<HASLO, false, NX, 2>(maps, p, c, s);
+    // the a Lap u form and F as compile-time choices: no per-node selects
+    if (p.adelta) {
+        if (needF) return p.nout == 1 ? launch_variant<HASLO, true, true, NX, 1>(maps, p, c, s)
+                                      : launch_variant<HASLO, true, true, NX, 2>(maps, p, c, s);
+        return p.nout == 1 ? launch_variant<HASLO, false, true, NX, 1>(maps, p, c, s)
+                           : launch_variant<HASLO, false, true, NX, 2>(maps, p, c, s);
+    }
+    if (needF) return p.nout == 1 ? launch_variant<HASLO, true, false, NX, 1>(maps, p, c, s)
+                                  : launch_variant<HASLO, true, false, NX, 2>(maps, p, c, s);
+    return p.nout == 1 ? launch_variant<HASLO, false, false, NX, 1>(maps, p, c, s)
+                       : launch_variant<HASLO, false, false, NX, 2>(maps, p, c, s);
 }
 
 template <bool HASLO>
@@ -409,8 +419,7 @@ cudaError_t launch_stencil_tma(const StencilArgs<float>& p, const Coefs<float>& 
     maps.lo = maps.u;
     if (ok && p.u_lo) ok = encode3(&maps.lo, p.u_lo, n1, n1, n2, n3, kHX, kHY);
     for (int e = 0; e < kMaxExtra; ++e) maps.x[e] = maps.u;
-    if (!p.u_lo)          // the extra inputs are staged only without the low part
-        for (int e = 0; ok && e < p.nx; ++e) ok = encode3(&maps.x[e], p.X[e], n1, n1, n2, n3, kTX, kTY);
+    for (int e = 0; ok && e < p.nx; ++e) ok = encode3(&maps.x[e], p.X[e], n1, n1, n2, n3, kTX, kTY);
     if (!ok) return cudaErrorInvalidValue;
     return p.u_lo ? launch_nx<true>(maps, p, c, needF, s) : launch_nx<false>(maps, p, c, needF, s);
 }
