@@ -350,8 +350,8 @@ def test_mixed_adelta_stencil_F_and_g(dims, prec, tol):
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
-def test_adelta_form_with_dirichlet_faces(prec, tol):
-    dims = (24, 20, 18)
+@pytest.mark.parametrize("dims", [(24, 20, 18), (132, 36, 20)])     # the second: TMA-staged FP32 kernel
+def test_adelta_form_with_dirichlet_faces(prec, tol, dims):
     a, b, r, u0 = mixed_case(dims)
     ctx = adr.Context(dims, 1e-3, "lawson4", prec, form="adelta")
     ctx.set_coeffs(a, b, r)
