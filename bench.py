@@ -585,14 +585,14 @@ def ours_grid(args):
         # N-point transform (5 N log2 N flops each), the complex product (6 N) and the epilogue
         # (2 N). The state is L2-resident at this size, so the bound is arithmetic: the FP64 pipe
         # in FP64, otherwise latency (reported against the FP32 lanes).
-        # A stage kept in Fourier space (2-D Lawson2a, Lawson-Euler; five launches) takes seven
+        # A stage kept in Fourier space (2-D; four or five launches) takes seven
         # complex N-point transforms (u forward, two derivatives back, two fluxes and the
         # pointwise part forward, the result back), 35 N log2 N flops, and about 50 N pointwise.
         peak, src = alu_peak(prec)
         if 8 in kinds:
             c_ms = statistics.mean(kinds[8])
             flops = 35.0 * N * math.log2(N) + 50.0 * N
-            kname = "Fourier-space stage (five fourier_pass_kernel launches)"
+            kname = "Fourier-space stage (four or five fourier_pass_kernel launches)"
         else:
             c_ms = statistics.mean(kinds.get(7, [float("nan")]))
             flops = 10.0 * N * math.log2(N) + 8.0 * N

@@ -575,6 +575,7 @@ struct StageSpec {
     bool save = false;
     int ms = -1;                     // Ms
     double zu = 1, zF = 0, zg = 0;
+    bool hand_on = false, take_over = false;   // chained stages (see PeriodicStage)
 };
 
 template <typename T>
@@ -600,8 +601,10 @@ void push_periodic_stage(Sched& S, const T* x, T* y, const StageSpec& q) {
         st.zF = q.zF;
         st.zg = q.zg;
     }
+    st.hand_on = q.hand_on;
+    st.take_over = q.take_over;
     Op op{[P, st](cudaStream_t s) { return adr::launch_periodic_stage(P, st, s); }, OP_PERIODIC_STAGE};
-    op.launches = adr::periodic_stage_launches(c->dim);
+    op.launches = adr::periodic_stage_launches(c->dim, q.take_over);
     S.ops.push_back(op);
 }
 
@@ -859,6 +862,7 @@ bool push_fused_periodic_step(Sched& S, const adr_ctx* c, T* u) {
     default:
         return false;
     }
+    a.hand_on = b.take_over = true;            // stage b's input is stage a's result B0
     push_periodic_stage<T>(S, u, B0, a);
     push_periodic_stage<T>(S, B0, u, b);
     return true;

@@ -416,6 +416,9 @@ struct PeriodicStage {
     Cplx<T>* Zs = nullptr;
     double cu = 0, cgF = 0, cg = 0, cgz = 0, cz = 0;
     double zu = 1, zF = 0, zg = 0;
+    // chaining: the last pass also transforms y along x1 for the next stage (whose x is this y),
+    // and that stage then starts from the transform already in place (4 passes instead of 5)
+    bool hand_on = false, take_over = false;
 };
 
 // Sets the shared-memory limits of the Fourier kernels of one precision (once, before any
@@ -433,7 +436,7 @@ cudaError_t launch_periodic_rhs(const PeriodicArgs<float>& P, const StencilArgs<
 // y = base + alpha Re(IFFT(M FFT(x))) (y = Re(...) when base is null). Number of launches:
 int periodic_multiplier_launches(int dim);
 // Fused stages (2-D only; 5 launches). Number of launches (0: not available for dim):
-int periodic_stage_launches(int dim);
+int periodic_stage_launches(int dim, bool take_over);
 cudaError_t launch_periodic_stage(const PeriodicArgs<double>& P, const PeriodicStage<double>& s, cudaStream_t st);
 cudaError_t launch_periodic_stage(const PeriodicArgs<float>& P, const PeriodicStage<float>& s, cudaStream_t st);
 cudaError_t launch_periodic_multiplier(const PeriodicArgs<double>& P, const Cplx<double>* M, const double* x, double* y,

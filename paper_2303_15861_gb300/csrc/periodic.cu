@@ -29,6 +29,8 @@
 //   H = cgF F^ - cg s u^ and the whole stage Mu (cu u^) + Mg (H + cgz Z) + cz Z, saves
 //   Ms (zu u^ + zF F^ - zg s u^) for a later stage, and transforms back; the last x1 pass
 //   writes y.                                                                           2-D: 5 kernels
+//   When the next stage's input is this y, the last x1 pass also transforms y forward along x1
+//   into Cu, and the next stage starts at its pivot pass.                       2-D: 4 kernels more
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -55,6 +57,7 @@ enum PassMode {
     PM_PIVOT_STAGE = 8,  // F^ = sum_mu i k_mu F_d C[mu] + F_d CN, H = cgF F^ - cg s u^;
                          // C[0] = F_d^-1 (Mu (cu u^) + Mg (H + cgz Z) + cz Z);
                          // Zs = Ms (zu u^ + zF F^ - zg s u^)
+    PM_FINAL_FWD = 9,    // x1: y = Re F_1^-1 C[0]; Cu = F_1 y (the next stage's first pass)
 };
 
 constexpr int kPassThreads = 256;
@@ -234,6 +237,18 @@ __global__ void __launch_bounds__(kPassThreads) fourier_pass_kernel(const __grid
                 const T v = R[o].x * inv_n;
                 P.y[i] = P.base ? P.base[i] + P.alpha * v : v;
             });
+        } else if (MODE == PM_FINAL_FWD) {
+            for_elems(P, grp, [&](int o, long long i, int) { B0[o] = P.C[0][i]; });
+            __syncthreads();
+            Cplx<T>* R = fft_lines(P, tws, B0, B1, true);
+            for_elems(P, grp, [&](int o, long long i, int) {     // the same values FWD_REAL would read
+                const T v = R[o].x * inv_n;
+                P.y[i] = v;
+                R[o] = {v, T(0)};
+            });
+            __syncthreads();
+            Cplx<T>* R2 = fft_lines(P, tws, R, R == B0 ? B1 : B0, false);
+            for_elems(P, grp, [&](int o, long long i, int) { P.Cu[i] = R2[o]; });
         } else if (MODE == PM_PIVOT_DERIV) {
             for_elems(P, grp, [&](int o, long long i, int) { B0[o] = P.Cu[i]; });
             __syncthreads();
@@ -459,6 +474,7 @@ cudaError_t prepare_impl() {
     set(reinterpret_cast<const void*>(fourier_pass_kernel<T, PM_PIVOT_DIV>));
     set(reinterpret_cast<const void*>(fourier_pass_kernel<T, PM_FINAL_OUT>));
     set(reinterpret_cast<const void*>(fourier_pass_kernel<T, PM_PIVOT_STAGE>));
+    set(reinterpret_cast<const void*>(fourier_pass_kernel<T, PM_FINAL_FWD>));
     sms();
     return e;
 }
@@ -568,7 +584,7 @@ template <typename T>
 cudaError_t stage_impl(const PeriodicArgs<T>& A, const PeriodicStage<T>& s, cudaStream_t st) {
     if (A.dim != 2 || !s.x || !s.y || !A.CN || (s.Zs && !A.Cu)) return cudaErrorInvalidValue;
     cudaError_t e;
-    {
+    if (!s.take_over) {      // otherwise the previous stage's last pass left F_1 x in Cu
         Pass<T> P = make_pass(A, 0, PM_FWD_REAL);
         P.x = s.x;
         P.C[0] = A.Cu;
@@ -604,7 +620,11 @@ cudaError_t stage_impl(const PeriodicArgs<T>& A, const PeriodicStage<T>& s, cuda
         P.szg = T(s.zg);
         if ((e = launch_pass_on<T, PM_PIVOT_STAGE>(P, st)) != cudaSuccess) return e;
     }
-    {
+    if (s.hand_on) {
+        Pass<T> P = make_pass(A, 0, PM_FINAL_FWD);
+        P.y = s.y;
+        if ((e = launch_pass_on<T, PM_FINAL_FWD>(P, st)) != cudaSuccess) return e;
+    } else {
         Pass<T> P = make_pass(A, 0, PM_FINAL_AXPY);
         P.y = s.y;
         P.base = nullptr;
@@ -615,7 +635,7 @@ cudaError_t stage_impl(const PeriodicArgs<T>& A, const PeriodicStage<T>& s, cuda
 
 }  // namespace
 
-int periodic_stage_launches(int dim) { return dim == 2 ? 5 : 0; }
+int periodic_stage_launches(int dim, bool take_over) { return dim == 2 ? (take_over ? 4 : 5) : 0; }
 cudaError_t launch_periodic_stage(const PeriodicArgs<double>& P, const PeriodicStage<double>& s, cudaStream_t st) {
     return stage_impl(P, s, st);
 }

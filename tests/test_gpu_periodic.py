@@ -162,9 +162,10 @@ def test_context_facts_and_launch_count():
     assert info["abar"] == pytest.approx(max(x.max() for x in a))
     assert info["beta"][0] == pytest.approx(b[0].mean()) and info["beta"][1] == pytest.approx(b[1].mean())
     # 2-D: every stage is kept in Fourier space from the state's transform to the stage result,
-    # five passes (instead of a right-hand side of 5 passes and multipliers of 3); Lawson4 and
-    # stabilized Lawson2 keep the right-hand side and multiplier passes
-    assert ctx.kernels_per_step() == 2 * 5
+    # five passes (instead of a right-hand side of 5 passes and multipliers of 3), four for a
+    # stage that starts from the previous stage's result; Lawson4 and stabilized Lawson2 keep the
+    # right-hand side and multiplier passes
+    assert ctx.kernels_per_step() == 5 + 4
     ops = ctx.profile_step(dev(w.u0))
     assert [k for k, _ in ops] == [8, 8]
     w3, L3, a3, b3 = W.periodic_instance((8, 16, 8), scheme="lawson2a")
@@ -174,7 +175,7 @@ def test_context_facts_and_launch_count():
              "stabilized_lawson_euler": 1, "lawson2b": 2}
     for scheme, stages in fused.items():
         w2, L2, a2, b2 = W.periodic_instance((32, 16), scheme=scheme)
-        assert context(w2, L2, a2, b2).kernels_per_step() == 5 * stages, scheme
+        assert context(w2, L2, a2, b2).kernels_per_step() == 5 * stages - (stages - 1), scheme
     w4, L4, a4, b4 = W.periodic_instance((32, 16), scheme="lawson4")
     c4 = context(w4, L4, a4, b4)
     assert 8 not in [k for k, _ in c4.profile_step(dev(w4.u0))]
